@@ -1,0 +1,216 @@
+/*
+ * qmcgb.h -- C ABI of libqmcgb: batched all-electron walker evaluation with
+ * Slater matrices built from localized atomic Gaussians (arXiv:1209.6630,
+ * "Quantum Monte Carlo for large chemical systems: implementing efficient
+ * strategies for petascale platforms and beyond"), on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * What one walker evaluation computes (the paper's hot spot, Sec. II.C):
+ *   for a walker R = (r_1..r_N) and a single-determinant trial function
+ *   Psi = Det_up * Det_dn (no Jastrow; the benchmarks of Sec. III are
+ *   Hartree-Fock wave functions):
+ *     a1  screening: AO chi_mu is zero for electron e where its radial part
+ *         g < eps (Sec. III; radius test d2 < R2_shell, atomic early exit)
+ *     a2  AO values, gradients and Laplacians (Sec. II.C, AO form)
+ *     a3  the five products C_l = A B_l, l=1..5 (Sec. III, Eq. "abc")
+ *     a4  log|det|, sign and inverse of each spin's Slater matrix
+ *         (Sec. II.C; inversion step of Sec. IV.B)
+ *     a5  drift b = grad Psi / Psi (Eq. 2) and kinetic energy from D^-1 and
+ *         the Laplacian matrix (Sec. II.C vector products)
+ *     a6  local energy E_L = H Psi / Psi (Eq. 4) with the all-electron
+ *         Coulomb Hamiltonian: T + V_en + V_ee + V_nn
+ *     a7  adjoint d log|Psi| / dA for parameter optimisation
+ *
+ * Conventions (every entry point):
+ *   - Return value: QMC_OK (0) or a negative QMC_ERR_* code; the message of
+ *     the last failing call on this thread is in qmc_last_error().
+ *   - "device" pointers are CUDA device memory of the system's device, owned
+ *     by the caller; "host" pointers are ordinary host memory, only read
+ *     during the call.  Device work is queued on `stream` (NULL = legacy
+ *     default stream) and is asynchronous unless stated otherwise.
+ *   - A numerical failure of one walker (exactly singular Slater matrix,
+ *     non-finite input or result) is not a call error: it sets bits in that
+ *     walker's status word and the rest of the batch is valid.
+ *   - Layouts are row-major.  Electrons 0..n_up-1 are spin up, the rest
+ *     spin down (Sec. II.C: the first N_up electrons enter Det_up).
+ *   - There is no CPU fallback: without a usable GB300 every call fails.
+ */
+#ifndef QMCGB_H
+#define QMCGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qmc_stream_t;   /* the same handle as cudaStream_t */
+typedef struct qmc_system qmc_system;       /* opaque, device-resident system */
+
+enum {
+    QMC_OK = 0,
+    QMC_ERR_INVALID = -1,   /* bad argument, size or layout */
+    QMC_ERR_CUDA = -2,      /* a CUDA runtime/driver call failed */
+    QMC_ERR_TIMEOUT = -3,   /* a bounded device wait gave up */
+    QMC_ERR_CAPACITY = -4,  /* workspace too small / size above a kernel limit */
+    QMC_ERR_NOMEM = -5      /* the library could not allocate its own tables */
+};
+
+/* per-walker status bits */
+enum {
+    QMC_STATUS_SINGULAR_UP = 1u,   /* exact zero pivot in Det_up: log|Psi| = -inf, sign = 0 */
+    QMC_STATUS_SINGULAR_DN = 2u,
+    QMC_STATUS_NONFINITE = 4u      /* non-finite coordinate or result */
+};
+
+/* arithmetic of the products a3 (a4..a6 are always FP64) */
+enum {
+    QMC_PREC_F64 = 0,      /* plain FP64 path: AO values, products, LU, energies in FP64 */
+    QMC_PREC_MIXED = 1     /* products on the tcgen05 tensor cores from split-BF16
+                              operands with FP32 accumulation over short exact chunks
+                              summed in FP64; AO values in FP32; LU/inverse/energies FP64 */
+};
+
+enum { QMC_DTYPE_F64 = 0, QMC_DTYPE_F32 = 1 };
+
+/*
+ * System description, host memory.  Sec. II.C: MOs phi_k = sum_mu a_{k mu}
+ * chi_mu (Eq. "mo"); Cartesian Gaussian AOs chi_mu(r) = scale_mu
+ * (x-Qx)^nx (y-Qy)^ny (z-Qz)^nz g_s(r), g_s(r) = sum_p c_p exp(-gamma_p |r-Q|^2)
+ * (Eq. "Gaussian").  AOs must be stored shell by shell (each shell's
+ * Cartesian components contiguous) and shells atom by atom.
+ */
+typedef struct {
+    int n_atom;
+    const double *Z;             /* [n_atom] nuclear charges */
+    const double *Q;             /* [n_atom][3] positions (bohr) */
+    int n_shell;
+    const int32_t *shell_atom;   /* [n_shell] non-decreasing */
+    const int32_t *shell_L;      /* [n_shell] angular momentum 0..4 */
+    const int32_t *shell_nprim;  /* [n_shell] 1..16 primitives */
+    const int32_t *shell_pstart; /* [n_shell] offset into prim_* */
+    int n_prim;
+    const double *prim_gamma;    /* [n_prim] exponents > 0 */
+    const double *prim_coef;     /* [n_prim] contraction coefficients (> 0 for
+                                    the radius search to be meaningful) */
+    int n_ao;
+    const int32_t *ao_shell;     /* [n_ao] */
+    const int32_t *ao_pow;       /* [n_ao][3] (nx, ny, nz), nx+ny+nz = L */
+    const double *ao_scale;      /* [n_ao] per-component normalisation factor */
+    int n_up, n_dn;              /* electrons per spin = MOs per determinant */
+    int a_dtype;                 /* QMC_DTYPE_F64 or QMC_DTYPE_F32 */
+    const void *A_up;            /* [n_ao][n_up] MO coefficients, row = AO */
+    const void *A_dn;            /* [n_ao][n_dn] */
+    double eps;                  /* screening threshold on g (paper: 1e-8) */
+} qmc_system_desc;
+
+/*
+ * qmc_system_load -- copy a system to `device` and prepare it (Sec. III).
+ * Computes, on the host, each shell's screening radius R2_s = the smallest
+ * non-negative double x with g_s(x) < eps (g evaluated at squared distance x;
+ * bisection on the IEEE bit patterns of non-negative doubles), each atom's
+ * radius (max over its shells, the paper's early exit), V_nn, and the
+ * device tables (FP64 A and the split planes the mixed path reads).
+ * The library owns the returned system until qmc_system_free.  Blocking.
+ */
+int qmc_system_load(const qmc_system_desc *desc, int device, qmc_system **out);
+int qmc_system_free(qmc_system *sys);
+
+/* Copy the per-shell R2 used for screening to host memory [n_shell]. */
+int qmc_system_shell_r2(const qmc_system *sys, double *R2_host);
+
+/*
+ * qmc_workspace_size -- device scratch needed by qmc_walkers_eval for
+ * `n_walk` walkers at `precision` (bytes).  A smaller workspace is allowed:
+ * the walkers are then processed in consecutive chunks that fit, down to
+ * one walker; below that the call fails with QMC_ERR_CAPACITY.
+ */
+int qmc_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes);
+
+/* Outputs of one evaluation, device memory owned by the caller. */
+typedef struct {
+    double *logpsi;    /* [W]  log|Psi| = log|Det_up| + log|Det_dn|   (required) */
+    double *sign;      /* [W]  sign of Psi (0 if singular)            (required) */
+    double *logabs;    /* [W][2] log|Det_up|, log|Det_dn|             (optional) */
+    double *drift;     /* [W][N][3] grad Psi / Psi, Eq. (2)           (required) */
+    double *e_loc;     /* [W]  E_L, Eq. (4)                           (required) */
+    double *e_parts;   /* [W][4] T, V_en, V_ee, V_nn                  (optional) */
+    uint32_t *status;  /* [W]  QMC_STATUS_* bits                      (required) */
+    double *dinv;      /* [W][n_up*n_up + n_dn*n_dn] D^-1 per spin, rows = electrons,
+                          columns = MOs ((D^-1)_{ek}, D_{ke} = phi_k(r_e)) (optional;
+                          qmc_logpsi_backward reads it)                          */
+} qmc_eval_out;
+
+/*
+ * qmc_walkers_eval -- steps a1..a6 for W walkers.
+ *   R         device [W][N][3] FP64 electron positions
+ *   precision QMC_PREC_F64 or QMC_PREC_MIXED
+ *   ws        device scratch of ws_bytes (see qmc_workspace_size); contents
+ *             are overwritten; it must not be in use by another call
+ * Errors: QMC_ERR_INVALID (W < 0, NULL required output, unknown precision),
+ *         QMC_ERR_CAPACITY (workspace below one walker), QMC_ERR_CUDA.
+ */
+int qmc_walkers_eval(const qmc_system *sys, int n_walk, const double *R, int precision,
+                     const qmc_eval_out *out, void *ws, size_t ws_bytes, qmc_stream_t stream);
+
+/*
+ * qmc_logpsi_backward -- a7, the adjoint of log|Psi| with respect to the MO
+ * coefficients, weighted over walkers:
+ *   dA_s[mu][k] = sum_w g_w sum_{e in spin s} (D^-1)_{w,ek} chi_mu(r_{w,e})
+ * (from d log|det D| / dD_{ke} = (D^-1)_{ek} and D_{ke} = sum_mu a_{k mu} chi_mu(r_e)).
+ * chi is recomputed from R (screened exactly as in the forward pass), D^-1 is
+ * the forward pass's `dinv` output.  g = 1/W gives d<log|Psi|>/dA;
+ * g_w = 2 (E_L,w - <E_L>)/W gives the E_L-weighted gradient.
+ *   R     device [W][N][3] f64;  dinv  device [W][n_up^2 + n_dn^2] f64
+ *   g     device [W] f64;  walkers whose status is non-zero must have g_w = 0
+ *   dA_up device [n_ao][n_up], dA_dn [n_ao][n_dn], FP64 (overwritten)
+ */
+int qmc_logpsi_backward(const qmc_system *sys, int n_walk, const double *R, const double *dinv,
+                        const double *g, double *dA_up, double *dA_dn, qmc_stream_t stream);
+
+/*
+ * qmc_screen_ao -- steps a1+a2 alone, for inspection and parity tests.
+ * For each walker w and electron e: cnt[w][e] = number of non-zero AOs,
+ * idx[w][e][0..cnt) their indices in ascending order, B[w][e][l][k] the
+ * value (l=0), gradient (l=1..3) and Laplacian (l=4) of AO idx[w][e][k], FP64.
+ * Entries k >= min(cnt, cap) are left untouched; cnt may exceed cap.
+ *   R device [W][N][3];  cnt device [W][N] i32;  idx device [W][N][cap] i32;
+ *   B device [W][N][5][cap] f64 (may be NULL)
+ */
+int qmc_screen_ao(const qmc_system *sys, int n_walk, const double *R, int cap, int32_t *cnt,
+                  int32_t *idx, double *B, qmc_stream_t stream);
+
+/*
+ * qmc_slater_matrices -- steps a1..a3 alone: C_l[e][k] = d_l phi_k(r_e),
+ * l = 0 value, 1..3 gradient, 4 Laplacian; per walker the up block
+ * [5][n_up][n_up] followed by the down block [5][n_dn][n_dn], FP64, at the
+ * given precision (the mixed path's values are widened from its own result).
+ *   C device [W][5*(n_up^2 + n_dn^2)] f64;  ws/ws_bytes as for qmc_walkers_eval.
+ */
+int qmc_slater_matrices(const qmc_system *sys, int n_walk, const double *R, int precision,
+                        double *C, void *ws, size_t ws_bytes, qmc_stream_t stream);
+
+/*
+ * qmc_det_inverse -- step a4 alone on a batch of `batch` FP64 n x n matrices
+ * X (row-major, X[e][k] = phi_k(r_e), i.e. the transpose of the paper's
+ * D_{ke}): log|det X|, sign, and Dinv = X^-T (= D^-1, rows = electrons).
+ * Gauss-Jordan elimination with partial pivoting in panels of 16 columns;
+ * the pivots are those of LU with partial pivoting.  X is overwritten.
+ *   X, Dinv device [batch][n][n];  logabs, sign device [batch];  singular
+ *   device [batch] u32 (1 if an exact zero pivot occurred; Dinv is then NaN)
+ *   1 <= n <= 1024.
+ */
+int qmc_det_inverse(int batch, int n, double *X, double *Dinv, double *logabs, double *sign,
+                    uint32_t *singular, qmc_stream_t stream);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char *qmc_last_error(void);
+
+/* Library version string. */
+const char *qmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMCGB_H */

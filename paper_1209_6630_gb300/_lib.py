@@ -1,0 +1,85 @@
+"""ctypes declarations of the libqmcgb C ABI (include/qmcgb.h).
+
+Loading fails loudly when the library is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+QMC_OK, QMC_ERR_INVALID, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_CAPACITY, QMC_ERR_NOMEM = 0, -1, -2, -3, -4, -5
+STATUS_SINGULAR_UP, STATUS_SINGULAR_DN, STATUS_NONFINITE = 1, 2, 4
+PREC = {"f64": 0, "mixed": 1}
+DTYPE_F64, DTYPE_F32 = 0, 1
+
+_vp = C.c_void_p
+_i = C.c_int
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [
+        ("n_atom", _i), ("Z", _vp), ("Q", _vp),
+        ("n_shell", _i), ("shell_atom", _vp), ("shell_L", _vp), ("shell_nprim", _vp), ("shell_pstart", _vp),
+        ("n_prim", _i), ("prim_gamma", _vp), ("prim_coef", _vp),
+        ("n_ao", _i), ("ao_shell", _vp), ("ao_pow", _vp), ("ao_scale", _vp),
+        ("n_up", _i), ("n_dn", _i), ("a_dtype", _i), ("A_up", _vp), ("A_dn", _vp),
+        ("eps", C.c_double),
+    ]
+
+
+class EvalOut(C.Structure):
+    _fields_ = [("logpsi", _vp), ("sign", _vp), ("logabs", _vp), ("drift", _vp), ("e_loc", _vp),
+                ("e_parts", _vp), ("status", _vp), ("dinv", _vp)]
+
+
+class QmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libqmcgb error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libqmcgb (built on first use if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or os.environ.get("QMCGB_NO_AUTOBUILD") != "1":
+                path = _build.build()
+            L = C.CDLL(path)
+            L.qmc_last_error.restype = C.c_char_p
+            L.qmc_version.restype = C.c_char_p
+            L.qmc_system_load.argtypes = [C.POINTER(SystemDesc), _i, C.POINTER(_vp)]
+            L.qmc_system_free.argtypes = [_vp]
+            L.qmc_system_shell_r2.argtypes = [_vp, _vp]
+            L.qmc_workspace_size.argtypes = [_vp, _i, _i, C.POINTER(C.c_size_t)]
+            L.qmc_walkers_eval.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp]
+            L.qmc_logpsi_backward.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.qmc_screen_ao.argtypes = [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]
+            L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
+            L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
+            for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
+                         "qmc_walkers_eval", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+                         "qmc_det_inverse"):
+                getattr(L, name).restype = _i
+            _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != QMC_OK:
+        raise QmcError(rc, lib().qmc_last_error().decode())
+    return rc
+
+
+# every symbol include/qmcgb.h declares
+EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
+            "qmc_walkers_eval", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+            "qmc_det_inverse", "qmc_last_error", "qmc_version")

@@ -1,0 +1,209 @@
+"""PyTorch-facing binding of libqmcgb: argument marshalling only.
+
+Every step of the walker evaluation runs in the library's CUDA kernels;
+torch provides device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import PREC, DTYPE_F32, DTYPE_F64, EvalOut, QmcError, SystemDesc, check, lib
+
+__all__ = ["QmcSystem", "det_inverse", "LogPsi", "QmcError"]
+
+
+def _stream(device):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _req_cuda(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+class QmcSystem:
+    """A molecular system resident on one GPU (qmc_system_load)."""
+
+    def __init__(self, system, device: int = 0):
+        s = system
+        self.device = torch.device("cuda", device)
+        self.n_up, self.n_dn, self.n_ao = int(s.n_up), int(s.n_dn), int(s.n_ao)
+        self.N = self.n_up + self.n_dn
+        self.n_atom, self.n_shell = int(s.n_atom), int(s.n_shell)
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return C.c_void_p(a.ctypes.data)
+
+        d = SystemDesc()
+        d.n_atom = s.n_atom
+        d.Z, d.Q = arr(s.Z, np.float64), arr(s.Q, np.float64)
+        d.n_shell = s.n_shell
+        d.shell_atom, d.shell_L = arr(s.shell_atom, np.int32), arr(s.shell_L, np.int32)
+        d.shell_nprim, d.shell_pstart = arr(s.shell_nprim, np.int32), arr(s.shell_pstart, np.int32)
+        d.n_prim = int(np.asarray(s.prim_gamma).size)
+        d.prim_gamma, d.prim_coef = arr(s.prim_gamma, np.float64), arr(s.prim_coef, np.float64)
+        d.n_ao = s.n_ao
+        d.ao_shell, d.ao_pow, d.ao_scale = arr(s.ao_shell, np.int32), arr(s.ao_pow, np.int32), arr(s.ao_scale, np.float64)
+        d.n_up, d.n_dn = s.n_up, s.n_dn
+        f32 = np.asarray(s.A_up).dtype == np.float32
+        self.a_dtype = np.float32 if f32 else np.float64
+        d.a_dtype = DTYPE_F32 if f32 else DTYPE_F64
+        d.A_up, d.A_dn = arr(s.A_up, self.a_dtype), arr(s.A_dn, self.a_dtype)
+        d.eps = float(s.eps)
+        h = C.c_void_p()
+        check(lib().qmc_system_load(C.byref(d), device, C.byref(h)))
+        self._h = h
+        self._ws = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().qmc_system_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def shell_r2(self):
+        out = np.zeros(self.n_shell, np.float64)
+        check(lib().qmc_system_shell_r2(self._h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def workspace_size(self, n_walk: int, precision: str = "f64") -> int:
+        b = C.c_size_t()
+        check(lib().qmc_workspace_size(self._h, n_walk, PREC[precision], C.byref(b)))
+        return int(b.value)
+
+    def workspace(self, n_walk: int, precision: str = "f64"):
+        need = self.workspace_size(n_walk, precision)
+        ws = self._ws.get(precision)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self._ws[precision] = ws
+        return ws
+
+    def alloc_out(self, W: int, want_dinv: bool = False):
+        dev, f64 = self.device, torch.float64
+        o = dict(logpsi=torch.empty(W, dtype=f64, device=dev), sign=torch.empty(W, dtype=f64, device=dev),
+                 logabs=torch.empty(W, 2, dtype=f64, device=dev),
+                 drift=torch.empty(W, self.N, 3, dtype=f64, device=dev),
+                 e_loc=torch.empty(W, dtype=f64, device=dev), e_parts=torch.empty(W, 4, dtype=f64, device=dev),
+                 status=torch.empty(W, dtype=torch.int32, device=dev))
+        if want_dinv:
+            o["dinv"] = torch.empty(W, self.n_up ** 2 + self.n_dn ** 2, dtype=f64, device=dev)
+        return o
+
+    def eval(self, R, precision: str = "f64", want_dinv: bool = False, out=None, ws=None):
+        """Steps a1..a6 (qmc_walkers_eval).  R: cuda f64 [W, N, 3]."""
+        W = int(R.shape[0])
+        _req_cuda(R, torch.float64, "R", (W, self.N, 3))
+        o = out if out is not None else self.alloc_out(W, want_dinv)
+        if ws is None:
+            ws = self.workspace(W, precision)
+        eo = EvalOut(logpsi=_ptr(o["logpsi"]), sign=_ptr(o["sign"]), logabs=_ptr(o.get("logabs")),
+                     drift=_ptr(o["drift"]), e_loc=_ptr(o["e_loc"]), e_parts=_ptr(o.get("e_parts")),
+                     status=_ptr(o["status"]), dinv=_ptr(o.get("dinv")))
+        check(lib().qmc_walkers_eval(self._h, W, _ptr(R), PREC[precision], C.byref(eo), _ptr(ws), ws.numel(),
+                                     _stream(self.device)))
+        return o
+
+    def screen_ao(self, R, cap: int, want_B: bool = True):
+        """Steps a1+a2 (qmc_screen_ao): cnt [W,N], idx [W,N,cap], B [W,N,5,cap]."""
+        W = int(R.shape[0])
+        _req_cuda(R, torch.float64, "R", (W, self.N, 3))
+        cnt = torch.empty(W, self.N, dtype=torch.int32, device=self.device)
+        idx = torch.full((W, self.N, cap), -1, dtype=torch.int32, device=self.device)
+        B = torch.zeros(W, self.N, 5, cap, dtype=torch.float64, device=self.device) if want_B else None
+        check(lib().qmc_screen_ao(self._h, W, _ptr(R), cap, _ptr(cnt), _ptr(idx), _ptr(B), _stream(self.device)))
+        return cnt, idx, B
+
+    def slater(self, R, precision: str = "f64", ws=None):
+        """Steps a1..a3 (qmc_slater_matrices): per walker [5][n_up][n_up] then [5][n_dn][n_dn]."""
+        W = int(R.shape[0])
+        _req_cuda(R, torch.float64, "R", (W, self.N, 3))
+        msz = self.n_up ** 2 + self.n_dn ** 2
+        Cm = torch.empty(W, 5 * msz, dtype=torch.float64, device=self.device)
+        if ws is None:
+            ws = self.workspace(W, precision)
+        check(lib().qmc_slater_matrices(self._h, W, _ptr(R), PREC[precision], _ptr(Cm), _ptr(ws), ws.numel(),
+                                        _stream(self.device)))
+        nu2 = self.n_up ** 2
+        up = Cm[:, : 5 * nu2].reshape(W, 5, self.n_up, self.n_up)
+        dn = Cm[:, 5 * nu2:].reshape(W, 5, self.n_dn, self.n_dn)
+        return up, dn
+
+    def backward(self, R, dinv, g):
+        """Step a7 (qmc_logpsi_backward): dA_up [n_ao, n_up], dA_dn [n_ao, n_dn], FP64."""
+        W = int(R.shape[0])
+        _req_cuda(R, torch.float64, "R", (W, self.N, 3))
+        _req_cuda(dinv, torch.float64, "dinv", (W, self.n_up ** 2 + self.n_dn ** 2))
+        _req_cuda(g, torch.float64, "g", (W,))
+        dA_up = torch.empty(self.n_ao, self.n_up, dtype=torch.float64, device=self.device)
+        dA_dn = torch.empty(self.n_ao, self.n_dn, dtype=torch.float64, device=self.device)
+        check(lib().qmc_logpsi_backward(self._h, W, _ptr(R), _ptr(dinv), _ptr(g), _ptr(dA_up), _ptr(dA_dn),
+                                        _stream(self.device)))
+        return dA_up, dA_dn
+
+
+def det_inverse(X):
+    """Step a4 alone (qmc_det_inverse) on cuda f64 [batch, n, n]; X is consumed.
+    Returns (logabs, sign, Dinv = X^-T, singular)."""
+    _req_cuda(X, torch.float64, "X")
+    b, n, n2 = X.shape
+    assert n == n2
+    dev = X.device
+    Dinv = torch.empty_like(X)
+    la = torch.empty(b, dtype=torch.float64, device=dev)
+    sg = torch.empty(b, dtype=torch.float64, device=dev)
+    sing = torch.empty(b, dtype=torch.int32, device=dev)
+    check(lib().qmc_det_inverse(b, n, _ptr(X), _ptr(Dinv), _ptr(la), _ptr(sg), _ptr(sing), _stream(dev)))
+    return la, sg, Dinv, sing
+
+
+class LogPsi(torch.autograd.Function):
+    """log|Psi| per walker with a hand-written adjoint for the MO coefficients.
+
+    forward(A_up, A_dn, R, qsys, precision): qsys must hold the same A values
+    (the library keeps its own copy); returns (logpsi, e_loc).  backward
+    receives d L / d logpsi (E_L is treated as constant) and returns
+    d L / d A_up, d L / d A_dn through qmc_logpsi_backward.
+    """
+
+    @staticmethod
+    def forward(ctx, A_up, A_dn, R, qsys, precision="f64"):
+        o = qsys.eval(R, precision=precision, want_dinv=True)
+        ctx.qsys = qsys
+        ctx.save_for_backward(R, o["dinv"], o["status"])
+        ctx.a_dtypes = (A_up.dtype, A_dn.dtype)
+        ctx.mark_non_differentiable(o["e_loc"])
+        return o["logpsi"], o["e_loc"]
+
+    @staticmethod
+    def backward(ctx, g_logpsi, g_eloc):
+        R, dinv, status = ctx.saved_tensors
+        g = torch.where(status == 0, g_logpsi.to(torch.float64), torch.zeros_like(g_logpsi, dtype=torch.float64))
+        dA_up, dA_dn = ctx.qsys.backward(R, dinv, g.contiguous())
+        return dA_up.to(ctx.a_dtypes[0]), dA_dn.to(ctx.a_dtypes[1]), None, None, None

@@ -1,0 +1,125 @@
+// Steps a5-a6: drift, kinetic energy and local energy per walker, FP64.
+//
+//   drift_{e,l} = sum_k (D^-1)_{ek} d_l phi_k(r_e)     (Eq. 2 with the
+//   lap_e       = sum_k (D^-1)_{ek} lap phi_k(r_e)      Sec. II.C vector products;
+//   T           = -1/2 sum_e lap_e                       Psi is linear in column e)
+//   V_en = -sum_{e,a} Z_a / |r_e - Q_a|,  V_ee = sum_{i<j} 1 / |r_i - r_j|,
+//   V_nn = sum_{a<b} Z_a Z_b / |Q_a - Q_b| (load time),  E_L = T + V (Eq. 4)
+//
+// One CTA per walker; one warp per electron row for the dot products (rows
+// of D^-1 and of C2..C5 are contiguous); warp-shuffle reductions.
+#include <math.h>
+
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+constexpr int kEnThreads = 256;
+constexpr int kEnWarps = kEnThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const double *__restrict__ R,
+                                                             const double *__restrict__ Dinv,
+                                                             const TC *__restrict__ Cd,
+                                                             const double *__restrict__ logabs2,
+                                                             const double *__restrict__ sign2,
+                                                             const uint32_t *__restrict__ sing,
+                                                             qmc_eval_out o, int w_off)
+{
+    __shared__ double red[3][kEnWarps];
+    const int w = blockIdx.x;
+    const int wg = w + w_off;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int N = s.n_elec;
+    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+    const double *Rw = R + (size_t)w * N * 3;
+
+    double lap_acc = 0.0;
+    for (int e = wid; e < N; e += kEnWarps) {
+        const int spin = e >= s.n_up;
+        const int ei = spin ? e - s.n_up : e;
+        const int ns = spin ? s.n_dn : s.n_up;
+        const size_t soff = spin ? (size_t)s.n_up * s.n_up : 0;
+        const size_t nss = (size_t)ns * ns;
+        const double *drow = Dinv + (size_t)w * msz + soff + (size_t)ei * ns;
+        const TC *crow = Cd + (size_t)w * 4 * msz + 4 * soff + (size_t)ei * ns;
+        double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+        for (int k = lane; k < ns; k += 32) {
+            const double d = drow[k];
+            b0 = fma(d, (double)crow[k], b0);
+            b1 = fma(d, (double)crow[nss + k], b1);
+            b2 = fma(d, (double)crow[2 * nss + k], b2);
+            b3 = fma(d, (double)crow[3 * nss + k], b3);
+        }
+        b0 = warp_sum(b0); b1 = warp_sum(b1); b2 = warp_sum(b2); b3 = warp_sum(b3);
+        if (lane == 0) {
+            double *dr = o.drift + ((size_t)wg * N + e) * 3;
+            dr[0] = b0; dr[1] = b1; dr[2] = b2;
+            lap_acc += b3;
+        }
+    }
+
+    double ven = 0.0, vee = 0.0;
+    for (int e = wid; e < N; e += kEnWarps) {
+        const double rx = Rw[3 * e], ry = Rw[3 * e + 1], rz = Rw[3 * e + 2];
+        for (int a = lane; a < s.n_atom; a += 32) {
+            const double dx = rx - s.Q[3 * a], dy = ry - s.Q[3 * a + 1], dz = rz - s.Q[3 * a + 2];
+            ven -= s.Z[a] * rsqrt(dx * dx + dy * dy + dz * dz);
+        }
+        for (int j = e + 1 + lane; j < N; j += 32) {
+            const double dx = rx - Rw[3 * j], dy = ry - Rw[3 * j + 1], dz = rz - Rw[3 * j + 2];
+            vee += rsqrt(dx * dx + dy * dy + dz * dz);
+        }
+    }
+    ven = warp_sum(ven);
+    vee = warp_sum(vee);
+    if (lane == 0) { red[0][wid] = lap_acc; red[1][wid] = ven; red[2][wid] = vee; }
+    __syncthreads();
+    if (t == 0) {
+        double lap = 0.0, Ven = 0.0, Vee = 0.0;
+        for (int q = 0; q < kEnWarps; ++q) { lap += red[0][q]; Ven += red[1][q]; Vee += red[2][q]; }
+        const double T = -0.5 * lap;
+        const double el = T + Ven + Vee + s.vnn;
+        // a spin with no electrons contributes det = 1
+        const double la0 = s.n_up ? logabs2[2 * w] : 0.0, la1 = s.n_dn ? logabs2[2 * w + 1] : 0.0;
+        const double sg0 = s.n_up ? sign2[2 * w] : 1.0, sg1 = s.n_dn ? sign2[2 * w + 1] : 1.0;
+        uint32_t st = sing[w];
+        const bool singular = (st & (QMC_STATUS_SINGULAR_UP | QMC_STATUS_SINGULAR_DN)) != 0;
+        bool finite_in = true;
+        for (int q = 0; q < 3 * N; ++q) finite_in = finite_in && isfinite(Rw[q]);
+        if (!finite_in) st |= QMC_STATUS_NONFINITE;
+        if (!singular && !(isfinite(el) && isfinite(la0) && isfinite(la1))) st |= QMC_STATUS_NONFINITE;
+        o.logpsi[wg] = singular ? -INFINITY : la0 + la1;
+        o.sign[wg] = singular ? 0.0 : sg0 * sg1;
+        if (o.logabs) { o.logabs[2 * wg] = la0; o.logabs[2 * wg + 1] = la1; }
+        o.e_loc[wg] = el;
+        if (o.e_parts) {
+            o.e_parts[4 * wg] = T; o.e_parts[4 * wg + 1] = Ven;
+            o.e_parts[4 * wg + 2] = Vee; o.e_parts[4 * wg + 3] = s.vnn;
+        }
+        o.status[wg] = st;
+    }
+}
+
+cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv,
+                                const double *Cd, int cd_is_f32, const double *logabs2,
+                                const double *sign2, const uint32_t *sing, const qmc_eval_out &o,
+                                int w_off, cudaStream_t st)
+{
+    if (nw == 0) return cudaSuccess;
+    if (cd_is_f32)
+        k_drift_energy<float><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, reinterpret_cast<const float *>(Cd),
+                                                         logabs2, sign2, sing, o, w_off);
+    else
+        k_drift_energy<double><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, Cd, logabs2, sign2, sing, o, w_off);
+    return cudaGetLastError();
+}
+
+}  // namespace qmc

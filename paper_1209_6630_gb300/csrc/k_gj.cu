@@ -1,0 +1,250 @@
+// Step a4: log|det|, sign and inverse of each Slater matrix in FP64
+// (Sec. II.C: D^-1 for the drift/Laplacian vector products; Sec. IV.B: the
+// inversion step, double precision).
+//
+// One CTA per matrix.  Gauss-Jordan elimination with partial pivoting, done
+// in panels of NB = 16 columns:
+//   1. the n x NB panel is copied to shared memory and eliminated there,
+//      column by column (pivot = largest |entry| among rows not yet used;
+//      the pivots are exactly those of LU with partial pivoting);
+//   2. every other column j of the matrix receives the panel's row
+//      operations at once, as a rank-NB update
+//        X[i][j] <- [i not a pivot row] X[i][j] + sum_c P[i][c] X[piv_c][j]
+//      (P = the eliminated panel, which holds the composite row operations).
+// Pivoting is implicit: rows never move in memory; a row map records which
+// physical row was the pivot of each step.  After the last panel the array
+// holds Res with X^-1[a][b] = Res[pp[a]][ipp[b]] (pp = pivot rows, ipp its
+// inverse), and the kernel writes Dinv = X^-T with a tiled transpose:
+//   Dinv[pp[c]][k] = Res[pp[k]][c].
+// Flops: n^3 FMA = 2 n^3, the LU (2/3 n^3) plus inverse (4/3 n^3) count.
+#include <math.h>
+
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+constexpr int kGjThreads = 256;
+constexpr int kGjWarps = kGjThreads / 32;
+constexpr int NB = kGjPanel;
+
+struct GjJobs2 {
+    GjJob j[2];
+};
+
+// doubles reserved for the panel (also holds the 32 x 33 transpose tile)
+__host__ __device__ __forceinline__ size_t p_region(int n)
+{
+    const size_t a = (size_t)n * NB;
+    return a > 32 * 33 ? a : 32 * 33;
+}
+
+__device__ __forceinline__ void argmax_merge(double &v, int &i, double v2, int i2)
+{
+    if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+
+__global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
+{
+    const GjJob &J = jobs.j[blockIdx.y];
+    const int m = blockIdx.x;
+    if (m >= J.count) return;
+    const int n = J.n;
+    double *__restrict__ X = J.X + (size_t)m * J.x_stride;
+    double *__restrict__ Dout = J.Dinv + (size_t)m * J.d_stride;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *P = reinterpret_cast<double *>(smem_raw);   // [n][NB], later a [32][33] tile
+    double *U = P + p_region(n);                          // [NB][32]
+    int *used = reinterpret_cast<int *>(U + NB * 32);     // [n]
+    int *pp = used + n;                                   // [n] pivot row of step k
+    int *rowc = pp + n;                                   // [n] panel column of a pivot row, or -1
+    __shared__ double red_v[kGjWarps];
+    __shared__ int red_i[kGjWarps];
+    __shared__ int s_p, s_sing;
+
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int i = t; i < n; i += kGjThreads) { used[i] = 0; rowc[i] = -1; }
+    if (t == 0) s_sing = 0;
+    double logabs = 0.0;
+    int neg = 0;
+    __syncthreads();
+
+    for (int jb = 0; jb < n; jb += NB) {
+        const int w = min(NB, n - jb);
+        for (int q = t; q < n * NB; q += kGjThreads) {
+            const int i = q / NB, c = q - i * NB;
+            P[q] = (c < w) ? X[(size_t)i * n + jb + c] : 0.0;
+        }
+        __syncthreads();
+
+        for (int c = 0; c < w; ++c) {
+            // pivot: largest |P[i][c]| over unused rows, lowest row on ties
+            double bv = -1.0;
+            int bi = n;
+            for (int i = t; i < n; i += kGjThreads)
+                if (!used[i]) argmax_merge(bv, bi, fabs(P[i * NB + c]), i);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_down_sync(0xffffffffu, bv, o);
+                const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+                argmax_merge(bv, bi, v2, i2);
+            }
+            if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+            __syncthreads();
+            if (t == 0) {
+                for (int q = 1; q < kGjWarps; ++q) argmax_merge(bv, bi, red_v[q], red_i[q]);
+                s_p = bi;
+                if (!(bv > 0.0)) s_sing = 1;   // exact zero (or NaN) pivot
+            }
+            __syncthreads();
+            if (s_sing) break;
+            const int p = s_p;
+            const double piv = P[p * NB + c];
+            const double inv = 1.0 / piv;
+            if (t == 0) {
+                used[p] = 1;
+                pp[jb + c] = p;
+                rowc[p] = c;
+                logabs += log(fabs(piv));
+                neg ^= (piv < 0.0);
+            }
+            __syncthreads();   // every thread has read P[p][c] (piv)
+            if (t < NB) P[p * NB + t] = (t == c) ? inv : P[p * NB + t] * inv;
+            __syncthreads();
+            for (int i = t; i < n; i += kGjThreads) {
+                if (i == p) continue;
+                const double f = P[i * NB + c];
+#pragma unroll
+                for (int cc = 0; cc < NB; ++cc)
+                    if (cc != c) P[i * NB + cc] = fma(-f, P[p * NB + cc], P[i * NB + cc]);
+                P[i * NB + c] = -f * inv;
+            }
+            __syncthreads();
+        }
+        if (s_sing) break;
+
+        // store the eliminated panel
+        for (int q = t; q < n * w; q += kGjThreads) {
+            const int i = q / w, c = q - i * w;
+            X[(size_t)i * n + jb + c] = P[i * NB + c];
+        }
+
+        // rank-w update of every other column, 32 columns at a time
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            if (c0 >= jb && c0 + 32 <= jb + w) continue;   // chunk inside the panel
+            __syncthreads();
+            for (int q = t; q < NB * 32; q += kGjThreads) {
+                const int c = q >> 5, l = q & 31, col = c0 + l;
+                U[q] = (c < w && col < n) ? X[(size_t)pp[jb + c] * n + col] : 0.0;
+            }
+            __syncthreads();
+            const int col = c0 + lane;
+            const bool active = col < n && !(col >= jb && col < jb + w);
+            double u[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) u[c] = U[c * 32 + lane];
+            if (active) {
+                int i = wid;
+                for (; i + 3 * kGjWarps < n; i += 4 * kGjWarps) {
+                    double x[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int ii = i + r * kGjWarps;
+                        x[r] = (rowc[ii] >= 0) ? 0.0 : X[(size_t)ii * n + col];
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int ii = i + r * kGjWarps;
+                        const double2 *pr = reinterpret_cast<const double2 *>(P + ii * NB);
+#pragma unroll
+                        for (int c2 = 0; c2 < NB / 2; ++c2) {
+                            const double2 pv = pr[c2];
+                            x[r] = fma(pv.x, u[2 * c2], x[r]);
+                            x[r] = fma(pv.y, u[2 * c2 + 1], x[r]);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) X[(size_t)(i + r * kGjWarps) * n + col] = x[r];
+                }
+                for (; i < n; i += kGjWarps) {
+                    double x = (rowc[i] >= 0) ? 0.0 : X[(size_t)i * n + col];
+                    const double2 *pr = reinterpret_cast<const double2 *>(P + i * NB);
+#pragma unroll
+                    for (int c2 = 0; c2 < NB / 2; ++c2) {
+                        const double2 pv = pr[c2];
+                        x = fma(pv.x, u[2 * c2], x);
+                        x = fma(pv.y, u[2 * c2 + 1], x);
+                    }
+                    X[(size_t)i * n + col] = x;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = t; c < w; c += kGjThreads) rowc[pp[jb + c]] = -1;
+        __syncthreads();
+    }
+
+    if (s_sing) {
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        for (size_t q = t; q < (size_t)n * n; q += kGjThreads) Dout[q] = qnan;
+        if (t == 0) {
+            if (J.logabs) J.logabs[(size_t)m * J.la_stride] = -INFINITY;
+            if (J.sign) J.sign[(size_t)m * J.la_stride] = 0.0;
+            if (J.flag) atomicOr(J.flag + m, J.flag_bit);
+        }
+        return;
+    }
+    __syncthreads();   // all panel writes to X visible to the block
+
+    // Dinv[pp[c]][k] = Res[pp[k]][c], 32 x 32 tiles through shared memory
+    double *tile = P;   // [32][33]
+    for (int kb = 0; kb < n; kb += 32) {
+        for (int cb = 0; cb < n; cb += 32) {
+            for (int r = wid; r < 32; r += kGjWarps) {
+                const int k = kb + r, c = cb + lane;
+                tile[r * 33 + lane] = (k < n && c < n) ? X[(size_t)pp[k] * n + c] : 0.0;
+            }
+            __syncthreads();
+            for (int r = wid; r < 32; r += kGjWarps) {
+                const int c = cb + r, k = kb + lane;
+                if (c < n && k < n) Dout[(size_t)pp[c] * n + k] = tile[lane * 33 + r];
+            }
+            __syncthreads();
+        }
+    }
+
+    if (t == 0) {
+        // sign of the row permutation k -> pp[k]: parity from its cycles
+        int par = 0;
+        for (int i = 0; i < n; ++i) used[i] = 0;
+        for (int i = 0; i < n; ++i) {
+            if (used[i]) continue;
+            int len = 0, j = i;
+            while (!used[j]) { used[j] = 1; j = pp[j]; ++len; }
+            par ^= ((len & 1) == 0);
+        }
+        if (J.logabs) J.logabs[(size_t)m * J.la_stride] = logabs;
+        if (J.sign) J.sign[(size_t)m * J.la_stride] = (par ^ neg) ? -1.0 : 1.0;
+    }
+}
+
+cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st)
+{
+    GjJobs2 js;
+    int nmax = 0, cmax = 0;
+    for (int q = 0; q < 2; ++q) {
+        js.j[q] = jobs[q < n_jobs ? q : 0];
+        if (q >= n_jobs) js.j[q].count = 0;
+        nmax = max(nmax, js.j[q].n);
+        cmax = max(cmax, js.j[q].count);
+    }
+    if (cmax == 0) return cudaSuccess;
+    const size_t sm = sizeof(double) * (p_region(nmax) + NB * 32) + sizeof(int) * 3 * (size_t)nmax;
+    cudaError_t e = cudaFuncSetAttribute(k_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid(cmax, n_jobs);
+    k_gj<<<grid, kGjThreads, sm, st>>>(js);
+    return cudaGetLastError();
+}
+
+}  // namespace qmc
