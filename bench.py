@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of the batched walker evaluation on GB300 (walker-steps/s).
+
+One step = one qmc_walkers_eval (screening, AOs, products, log|det| +
+inverse, drift, local energy) over the whole batch of the 1056-electron
+synthetic peptide chain (528 + 528 electrons, 3040 AOs, 2048 walkers), with
+the positions already resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|f64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Multi-GPU (torchrun, one process per GPU): every rank evaluates its own
+2048-walker batch (walkers are independent; no collective on the data path),
+value = all walkers / max-over-ranks time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "1056e"
+METRIC = "walker-steps/s at 1056 e, mixed-prec vs FP64 GPU path, at <=1e-6 log|Psi| err"
+KERNEL_OF_STAGE = {"f64": ["k_contract_f64", "k_gj", "k_drift_energy"],
+                   "mixed": ["k_shell_mask+k_c15_ff+k_tc_contract", "k_gj", "k_drift_energy"],
+                   "mixed_bf16": ["k_shell_mask+k_c15_ff+k_tc_contract", "k_gj", "k_drift_energy"]}
+LAUNCHES_PER_STEP = {"f64": 3, "mixed": 5, "mixed_bf16": 5}
+DTYPE = {"f64": "f64", "mixed": "f64 (C1,C5 float-float; C2-C4 fp16x3 tensor cores)",
+         "mixed_bf16": "f64 (C1,C5 float-float; C2-C4 bf16x3 tensor cores)"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["f64", "mixed", "mixed_bf16"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--walkers", type=int, default=0, help="override the batch size")
+    p.add_argument("--cpu-sample", type=int, default=0, help="walkers in the oracle sample")
+    p.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison")
+    p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9 or f[0] != str(self.gpu_index):
+                    continue
+                rows.append(f)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def fp64_peak_tflops(pk):
+    # 152 SMs x 2 DFMA (4 flop) per clock per SM x maximum SM clock
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    return 152 * 4 * mhz * 1e6 / 1e12
+
+
+def kernel_traffic(kernel, workload):
+    """DRAM bytes per launch from profiles/ncu_traffic.txt, if the kernel's
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") != kernel or kv.get("workload") != workload:
+            continue
+        src = os.path.join(ROOT, "paper_1209_6630_gb300", "csrc", kv.get("source", ""))
+        if not os.path.exists(src):
+            return None
+        h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+        if h != kv.get("source_sha1"):
+            return None
+        return float(kv["bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(system, R, n_sample):
+    import oracle
+    o = oracle.Oracle(system)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = o.eval(R[:n_sample], nthreads=cores)
+    dt = time.perf_counter() - t0
+    return ref, dt, cores
+
+
+def reference_arm(a, ws, rank):
+    if rank != 0:
+        return
+    from synth import config_system, make_walkers
+    s = config_system(a.workload)
+    n = a.cpu_sample or {"158e": 100, "434e": 96, "1056e": 32, "1731e": 16}.get(a.workload, 16)
+    R = make_walkers(s, n)
+    import oracle
+    o = oracle.Oracle(s)
+    cores = os.cpu_count() or 1
+    for _ in range(a.warmup):
+        o.eval(R[: max(1, n // 4)], nthreads=cores)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        o.eval(R, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = n / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "walker-steps/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{a.workload} synthetic peptide chain", "walkers_per_step": n,
+                       "sample": f"{n} walkers of the {a.workload} workload per step"},
+            "cpu_baseline": {"value": v, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} walkers per step, OpenMP over walkers"},
+            "e2e": {"value": v, "unit": "walker-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    a = parse()
+    ws, rank, local = dist_env()
+    if a.impl == "reference":
+        reference_arm(a, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    if ws > 1:
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1209_6630_gb300 import QmcSystem
+    from synth import WALKERS, config_system, make_walkers
+
+    s = config_system(a.workload)
+    W = a.walkers or WALKERS[a.workload]
+    R_host = make_walkers(s, W, first=rank * W)
+    q = QmcSystem(s, local)
+    R = torch.from_numpy(R_host).to(dev)
+    prec = a.precision
+    wsbuf = q.workspace(W, prec)
+    out = q.alloc_out(W, want_dinv=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(max(a.warmup, 0)):
+        q.eval(R, precision=prec, out=out, ws=wsbuf)
+    barrier()
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except ValueError:
+            pass
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    stages = []
+    step_ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    for _ in range(a.steps):
+        flush.zero_()          # evict L2 between timed steps (not timed)
+        e0.record()
+        q.eval(R, precision=prec, out=out, ws=wsbuf, stage_ms=stages)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    clocks = clk.stop()
+    t_step = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = ws * W / (t_step / 1e3)
+    st = np.array(stages)            # [K, 4]
+    stage_mean = st.mean(axis=0)
+    launches_per_step = LAUNCHES_PER_STEP[prec]   # one walker chunk
+
+    # screening statistics of this batch (a1 on a sample, outside the timed region)
+    ns = 16
+    cnt, _, _ = q.screen_ao(R[:ns], cap=0, want_B=False)
+    kbar = float(cnt.float().mean().item())
+
+    n_up, n_dn = s.n_up, s.n_dn
+    flop_gj = 2.0 * (n_up ** 3 + n_dn ** 3) * W
+    flop_contract = 10.0 * (n_up + n_dn) * kbar * ((n_up * n_up + n_dn * n_dn) / (n_up + n_dn)) * W
+    pk = peaks()
+    dom = int(np.argmax(stage_mean[:3]))
+    kern = KERNEL_OF_STAGE[prec][dom]
+    if dom == 1:
+        achieved = flop_gj / (stage_mean[1] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": fp64_peak_tflops(pk),
+                "unit": "TFLOP/s", "peak_source": "FP64: 152 SMs x 4 flop/clk (measured DFMA rate) x sm_max_mhz"}
+    elif dom == 0 and prec == "f64":
+        achieved = flop_contract / (stage_mean[0] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": fp64_peak_tflops(pk),
+                "unit": "TFLOP/s", "peak_source": "FP64: 152 SMs x 4 flop/clk (measured DFMA rate) x sm_max_mhz"}
+    else:
+        achieved = flop_contract / (stage_mean[0] / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": pk.get("bf16_tflops_sustained"),
+                "unit": "TFLOP/s", "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json)"}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") else None
+    tr = kernel_traffic(kern, a.workload)
+    roof["traffic"] = tr
+    roof["stage_ms"] = {"a1_a3": stage_mean[0], "a4": stage_mean[1], "a5_a6": stage_mean[2]}
+
+    line = {"metric": METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+            "config": {"workload": f"{a.workload} synthetic peptide chain (528+528 e, 3040 AOs)"
+                       if a.workload == "1056e" else a.workload,
+                       "walkers_per_gpu": W, "precision": prec, "l2": "flushed between timed steps",
+                       "parallelism": f"walker replicas x{ws}", "kbar_active_aos": kbar},
+            "roofline": roof, "gpu_launches": launches_per_step * a.steps}
+    if clocks:
+        line["clocks"] = clocks
+
+    # end to end through the public API: pinned host positions in, results out
+    R_pin = torch.from_numpy(R_host).pin_memory()
+    host_out = {k: torch.empty(out[k].shape, dtype=out[k].dtype).pin_memory()
+                for k in ("logpsi", "sign", "e_loc", "drift", "status")}
+    R_dev = torch.empty_like(R)
+    q.eval(R, precision=prec, out=out, ws=wsbuf)
+    barrier()
+    e2e_ms = []
+    for _ in range(max(1, min(a.steps, 3))):
+        flush.zero_()
+        e0.record()
+        R_dev.copy_(R_pin, non_blocking=True)
+        q.eval(R_dev, precision=prec, out=out, ws=wsbuf)
+        for k, hb in host_out.items():
+            hb.copy_(out[k], non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    t_e2e = sum(e2e_ms) / len(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    line["e2e"] = {"value": ws * W / (t_e2e / 1e3), "unit": "walker-steps/s",
+                   "h2d_bytes_per_step": int(R_pin.numel() * 8),
+                   "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host_out.values()))}
+
+    # the plain FP64 GPU path on the same batch (the metric's comparison)
+    if prec != "f64" and not a.no_compare:
+        ws64 = q.workspace(W, "f64")
+        q.eval(R, precision="f64", out=out, ws=ws64)
+        t64 = []
+        for _ in range(2):
+            flush.zero_()
+            e0.record()
+            q.eval(R, precision="f64", out=out, ws=ws64)
+            e1.record()
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        m64 = sum(t64) / len(t64)
+        line["fp64_path"] = {"value": ws * W / (m64 / 1e3), "ms_per_step": m64}
+
+    # adjoint d log|Psi| / dA (E_L-weighted) on the same batch
+    if not a.no_adjoint:
+        o2 = q.eval(R, precision=prec, want_dinv=True, ws=wsbuf)
+        el = o2["e_loc"]
+        g = (2.0 * (el - el.mean()) / W).contiguous()
+        q.backward(R, o2["dinv"], g)
+        torch.cuda.synchronize()
+        e0.record()
+        q.backward(R, o2["dinv"], g)
+        e1.record()
+        e1.synchronize()
+        line["adjoint_ms"] = e0.elapsed_time(e1)
+
+    # parity on a sample and the CPU baseline (rank 0 only, N = 1 only)
+    if rank == 0 and ws == 1 and not a.no_cpu:
+        n_s = a.cpu_sample or 32
+        ref, dt, cores = cpu_oracle_sample(s, R_host, n_s)
+        got = q.eval(R[:n_s], precision=prec)
+        lp = got["logpsi"].cpu().numpy()
+        el = got["e_loc"].cpu().numpy()
+        ok = ref["status"] == 0
+        line["parity"] = {"walkers": n_s,
+                          "max_abs_logpsi_err": float(np.abs(lp[ok] - ref["logpsi"][ok]).max()),
+                          "max_rel_eloc_err": float((np.abs(el[ok] - ref["e_loc"][ok]) /
+                                                     np.abs(ref["e_loc"][ok])).max()),
+                          "status_mismatch": int((got["status"].cpu().numpy() != ref["status"]).sum())}
+        line["cpu_baseline"] = {"value": n_s / dt, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n_s} walkers of the same batch, FP64 oracle, OpenMP over walkers"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -61,15 +61,20 @@ enum {
 enum {
     QMC_STATUS_SINGULAR_UP = 1u,   /* exact zero pivot in Det_up: log|Psi| = -inf, sign = 0 */
     QMC_STATUS_SINGULAR_DN = 2u,
-    QMC_STATUS_NONFINITE = 4u      /* non-finite coordinate or result */
+    QMC_STATUS_NONFINITE = 4u,     /* non-finite coordinate or result */
+    QMC_STATUS_TIMEOUT = 8u        /* a bounded wait inside a tensor-core kernel gave up
+                                      for this walker's tile: its results are invalid */
 };
 
 /* arithmetic of the products a3 (a4..a6 are always FP64) */
 enum {
-    QMC_PREC_F64 = 0,      /* plain FP64 path: AO values, products, LU, energies in FP64 */
-    QMC_PREC_MIXED = 1     /* products on the tcgen05 tensor cores from split-BF16
-                              operands with FP32 accumulation over short exact chunks
-                              summed in FP64; AO values in FP32; LU/inverse/energies FP64 */
+    QMC_PREC_F64 = 0,        /* plain FP64 path: AO values, products, LU, energies in FP64 */
+    QMC_PREC_MIXED = 1,      /* C1 (the Slater matrix) from FP64 AO values with compensated
+                                float-float products (FP64-accurate); C2..C5 (gradient and
+                                Laplacian matrices) on the tcgen05 tensor cores from FP16
+                                hi/lo split operands (3 products, FP32 accumulation, exact
+                                power-of-two scaling); LU/inverse/energies FP64 */
+    QMC_PREC_MIXED_BF16 = 2  /* as QMC_PREC_MIXED with BF16 hi/lo splits for C2..C5 */
 };
 
 enum { QMC_DTYPE_F64 = 0, QMC_DTYPE_F32 = 1 };
@@ -153,6 +158,20 @@ typedef struct {
  */
 int qmc_walkers_eval(const qmc_system *sys, int n_walk, const double *R, int precision,
                      const qmc_eval_out *out, void *ws, size_t ws_bytes, qmc_stream_t stream);
+
+/*
+ * qmc_walkers_eval_timed -- qmc_walkers_eval that also measures its stages
+ * with CUDA events recorded on `stream` between the kernel launches:
+ *   stage_ms[0] a1-a3 (screening, AO evaluation, products)
+ *   stage_ms[1] a4 (log|det|, sign, inverse)
+ *   stage_ms[2] a5-a6 (drift, energies)
+ *   stage_ms[3] their sum
+ * (host float[4], summed over walker chunks).  Blocks until the work has
+ * finished.  Same arguments and errors as qmc_walkers_eval.
+ */
+int qmc_walkers_eval_timed(const qmc_system *sys, int n_walk, const double *R, int precision,
+                           const qmc_eval_out *out, void *ws, size_t ws_bytes, qmc_stream_t stream,
+                           float *stage_ms);
 
 /*
  * qmc_logpsi_backward -- a7, the adjoint of log|Psi| with respect to the MO

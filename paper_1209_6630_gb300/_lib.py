@@ -11,8 +11,8 @@ import threading
 from . import build as _build
 
 QMC_OK, QMC_ERR_INVALID, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_CAPACITY, QMC_ERR_NOMEM = 0, -1, -2, -3, -4, -5
-STATUS_SINGULAR_UP, STATUS_SINGULAR_DN, STATUS_NONFINITE = 1, 2, 4
-PREC = {"f64": 0, "mixed": 1}
+STATUS_SINGULAR_UP, STATUS_SINGULAR_DN, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4, 8
+PREC = {"f64": 0, "mixed": 1, "mixed_bf16": 2}
 DTYPE_F64, DTYPE_F32 = 0, 1
 
 _vp = C.c_void_p
@@ -61,12 +61,14 @@ def lib():
             L.qmc_system_shell_r2.argtypes = [_vp, _vp]
             L.qmc_workspace_size.argtypes = [_vp, _i, _i, C.POINTER(C.c_size_t)]
             L.qmc_walkers_eval.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp]
+            L.qmc_walkers_eval_timed.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp,
+                                                 C.POINTER(C.c_float)]
             L.qmc_logpsi_backward.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qmc_screen_ao.argtypes = [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
-                         "qmc_walkers_eval", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+                         "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
                          "qmc_det_inverse"):
                 getattr(L, name).restype = _i
             _lib = L
@@ -81,5 +83,5 @@ def check(rc):
 
 # every symbol include/qmcgb.h declares
 EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
-            "qmc_walkers_eval", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+            "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
             "qmc_det_inverse", "qmc_last_error", "qmc_version")

@@ -116,8 +116,10 @@ class QmcSystem:
             o["dinv"] = torch.empty(W, self.n_up ** 2 + self.n_dn ** 2, dtype=f64, device=dev)
         return o
 
-    def eval(self, R, precision: str = "f64", want_dinv: bool = False, out=None, ws=None):
-        """Steps a1..a6 (qmc_walkers_eval).  R: cuda f64 [W, N, 3]."""
+    def eval(self, R, precision: str = "f64", want_dinv: bool = False, out=None, ws=None, stage_ms=None):
+        """Steps a1..a6 (qmc_walkers_eval).  R: cuda f64 [W, N, 3].
+        With stage_ms (a list), qmc_walkers_eval_timed is called instead and
+        the per-stage device milliseconds are appended (blocking)."""
         W = int(R.shape[0])
         _req_cuda(R, torch.float64, "R", (W, self.N, 3))
         o = out if out is not None else self.alloc_out(W, want_dinv)
@@ -126,8 +128,14 @@ class QmcSystem:
         eo = EvalOut(logpsi=_ptr(o["logpsi"]), sign=_ptr(o["sign"]), logabs=_ptr(o.get("logabs")),
                      drift=_ptr(o["drift"]), e_loc=_ptr(o["e_loc"]), e_parts=_ptr(o.get("e_parts")),
                      status=_ptr(o["status"]), dinv=_ptr(o.get("dinv")))
-        check(lib().qmc_walkers_eval(self._h, W, _ptr(R), PREC[precision], C.byref(eo), _ptr(ws), ws.numel(),
-                                     _stream(self.device)))
+        if stage_ms is None:
+            check(lib().qmc_walkers_eval(self._h, W, _ptr(R), PREC[precision], C.byref(eo), _ptr(ws), ws.numel(),
+                                         _stream(self.device)))
+        else:
+            ms = (C.c_float * 4)()
+            check(lib().qmc_walkers_eval_timed(self._h, W, _ptr(R), PREC[precision], C.byref(eo), _ptr(ws),
+                                               ws.numel(), _stream(self.device), ms))
+            stage_ms.append([float(x) for x in ms])
         return o
 
     def screen_ao(self, R, cap: int, want_B: bool = True):

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(kAoThreads) k_contract_f64(SysDev s, const dou
             for (int l = 0; l < 5; ++l) B_s[l * kAoChunk + m] = v[l];
         }
         __syncthreads();
+        // MO slots j whose whole warp lies beyond ns are skipped (warp-uniform)
+        const int kwarp = t & ~31;
 #pragma unroll 2
         for (int m = 0; m < kc; ++m) {
             const double *__restrict__ arow = A + (size_t)idx_s[k0 + m] * ns;
@@ -85,11 +87,15 @@ __global__ void __launch_bounds__(kAoThreads) k_contract_f64(SysDev s, const dou
                 const int k = t + kAoThreads * j;
                 a[j] = (k < ns) ? __ldg(arow + k) : 0.0;
             }
+            double b[5];
 #pragma unroll
-            for (int l = 0; l < 5; ++l) {
-                const double b = B_s[l * kAoChunk + m];
+            for (int l = 0; l < 5; ++l) b[l] = B_s[l * kAoChunk + m];
 #pragma unroll
-                for (int j = 0; j < NJ; ++j) acc[l][j] = fma(a[j], b, acc[l][j]);
+            for (int j = 0; j < NJ; ++j) {
+                if (kwarp + kAoThreads * j < ns) {
+#pragma unroll
+                    for (int l = 0; l < 5; ++l) acc[l][j] = fma(a[j], b[l], acc[l][j]);
+                }
             }
         }
         __syncthreads();

@@ -20,20 +20,6 @@ namespace qmc {
 constexpr int kBwThreads = 128;
 constexpr int kBwBatch = 128;   // hits buffered before an accumulation pass
 
-__device__ __forceinline__ double ao_value_f64(const SysDev &s, int mu, double rx, double ry, double rz)
-{
-    const int sh = s.ao_shell[mu];
-    const int a = s.sh_atom[sh];
-    const double dx = rx - s.Q[3 * a], dy = ry - s.Q[3 * a + 1], dz = rz - s.Q[3 * a + 2];
-    const double d2 = dx * dx + dy * dy + dz * dz;
-    double g = 0.0;
-    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
-    for (int p = 0; p < np; ++p) g += s.pc[p0 + p] * exp(-s.pg[p0 + p] * d2);
-    const int pw = s.ao_pow[mu];
-    return s.ao_scale[mu] * ipow_small(dx, pw & 255) * ipow_small(dy, (pw >> 8) & 255) *
-           ipow_small(dz, (pw >> 16) & 255) * g;
-}
-
 template <int MAXAO>
 __global__ void __launch_bounds__(kBwThreads) k_backward_f64(SysDev s, int nw, const double *__restrict__ R,
                                                              const double *__restrict__ dinv,

@@ -24,10 +24,10 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <typename TC>
+template <typename TG>
 __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const double *__restrict__ R,
                                                              const double *__restrict__ Dinv,
-                                                             const TC *__restrict__ Cd,
+                                                             const TG *__restrict__ Cg, CView cv,
                                                              const double *__restrict__ logabs2,
                                                              const double *__restrict__ sign2,
                                                              const uint32_t *__restrict__ sing,
@@ -46,17 +46,20 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
         const int spin = e >= s.n_up;
         const int ei = spin ? e - s.n_up : e;
         const int ns = spin ? s.n_dn : s.n_up;
-        const size_t soff = spin ? (size_t)s.n_up * s.n_up : 0;
+        const size_t nu2 = (size_t)s.n_up * s.n_up;
+        const size_t soff = spin ? nu2 : 0;
         const size_t nss = (size_t)ns * ns;
         const double *drow = Dinv + (size_t)w * msz + soff + (size_t)ei * ns;
-        const TC *crow = Cd + (size_t)w * 4 * msz + 4 * soff + (size_t)ei * ns;
+        const TG *grow = Cg + (size_t)w * cv.g_wstride + (spin ? cv.g_ncomp * nu2 : 0) + (size_t)ei * ns;
+        const double *lrow = cv.l + (size_t)w * cv.l_wstride + (spin ? cv.l_ncomp * nu2 : 0) +
+                             (size_t)cv.l_comp * nss + (size_t)ei * ns;
         double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
         for (int k = lane; k < ns; k += 32) {
             const double d = drow[k];
-            b0 = fma(d, (double)crow[k], b0);
-            b1 = fma(d, (double)crow[nss + k], b1);
-            b2 = fma(d, (double)crow[2 * nss + k], b2);
-            b3 = fma(d, (double)crow[3 * nss + k], b3);
+            b0 = fma(d, (double)grow[k], b0);
+            b1 = fma(d, (double)grow[nss + k], b1);
+            b2 = fma(d, (double)grow[2 * nss + k], b2);
+            b3 = fma(d, lrow[k], b3);
         }
         b0 = warp_sum(b0); b1 = warp_sum(b1); b2 = warp_sum(b2); b3 = warp_sum(b3);
         if (lane == 0) {
@@ -108,17 +111,17 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
     }
 }
 
-cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv,
-                                const double *Cd, int cd_is_f32, const double *logabs2,
-                                const double *sign2, const uint32_t *sing, const qmc_eval_out &o,
-                                int w_off, cudaStream_t st)
+cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv, const CView &cv,
+                                const double *logabs2, const double *sign2, const uint32_t *sing,
+                                const qmc_eval_out &o, int w_off, cudaStream_t st)
 {
     if (nw == 0) return cudaSuccess;
-    if (cd_is_f32)
-        k_drift_energy<float><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, reinterpret_cast<const float *>(Cd),
+    if (cv.g_f32)
+        k_drift_energy<float><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, static_cast<const float *>(cv.g), cv,
                                                          logabs2, sign2, sing, o, w_off);
     else
-        k_drift_energy<double><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, Cd, logabs2, sign2, sing, o, w_off);
+        k_drift_energy<double><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, static_cast<const double *>(cv.g), cv,
+                                                          logabs2, sign2, sing, o, w_off);
     return cudaGetLastError();
 }
 

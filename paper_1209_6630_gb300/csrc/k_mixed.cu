@@ -1,0 +1,603 @@
+// Steps a1-a3 of the mixed-precision path.
+//
+// k_shell_mask   a1: per (walker, electron) bitmask of the active shells
+//                (the same correctly rounded d2 < R2 decisions as the FP64 path).
+// k_c15_ff       a2+a3 for C1 (the Slater matrix) and C5 (its Laplacian
+//                companion): AO values and Laplacians in FP64, products
+//                accumulated in compensated float-float arithmetic on the FP32
+//                pipes (~48-bit significand).  log|det| responds to C1 errors
+//                at the 1e-10 relative level for 1000+ electrons, and the
+//                kinetic energy (from C5) must hold 1e-5 of E_L even when T and
+//                V nearly cancel; FP32 accumulation alone stops near 1e-6.
+//                The FP32 pipe is 62x faster than the FP64 pipe on this part.
+// k_tc_contract  a2+a3 for C2..C4 (the gradient matrices, i.e. the drift) on the
+//                5th-generation tensor cores: tcgen05.mma kind::f16 with
+//                split 16-bit operands (hi*hi + hi*lo + lo*hi) and FP32
+//                accumulators in tensor memory.  FP16 splits (11 + 11
+//                significant bits) with exact power-of-two scaling of both
+//                operands keep each product to ~2^-22; BF16 splits (8 + 8)
+//                are available for comparison (~2^-17).
+//
+// Tensor-core tiling.  One CTA computes, for one electron index e of one
+// spin and 128 walkers (the M dimension: the same electron of different
+// walkers sits near the same nucleus, so their AO lists overlap), a chunk of
+// 128 MOs (N) of C2..C4.  K runs over the union of the 128 walkers' active
+// AOs, 64 per step:
+//   A operand (M x K, K-major, 128B swizzle): the walkers' AO derivative
+//     values, computed in FP32 by the 128 threads (one walker each) and split
+//     into BF16 hi/lo planes, zero where the walker's shell is screened out;
+//   B operand (N x K, MN-major, 128B swizzle): rows of the MO coefficient
+//     matrix A[mu][k0..k0+127] gathered by AO index from BF16 hi/lo planes
+//     prepared at system load (16-byte copies, no transpose);
+//   D: three 128 x 128 FP32 accumulators (384 of the 512 TMEM columns).
+// One thread issues the 36 MMAs of a K step and commits them to an mbarrier;
+// waits are bounded (%globaltimer, 2 s): a wait that gives up marks the
+// tile's walkers with QMC_STATUS_TIMEOUT instead of hanging.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "qmc_device.cuh"
+
+namespace qmc {
+
+// ---------------------------------------------------------------- masks ----
+constexpr int kMaskThreads = 128;
+
+__global__ void __launch_bounds__(kMaskThreads) k_shell_mask(SysDev s, const double *__restrict__ R, int mw,
+                                                             uint32_t *__restrict__ masks)
+{
+    extern __shared__ uint32_t mbits[];   // [mw]
+    const int e = blockIdx.x, w = blockIdx.y;
+    const double *r = R + ((size_t)w * s.n_elec + e) * 3;
+    const double rx = r[0], ry = r[1], rz = r[2];
+    for (int j = threadIdx.x; j < mw; j += kMaskThreads) mbits[j] = 0u;
+    __syncthreads();
+    for (int a = threadIdx.x; a < s.n_atom; a += kMaskThreads) {
+        const double d2 = sqdist_rn(rx, ry, rz, s.Q + 3 * a);
+        if (!(d2 < s.atom_R2[a])) continue;
+        for (int sh = s.atom_sh0[a]; sh < s.atom_sh0[a + 1]; ++sh)
+            if (d2 < s.sh_R2[sh]) atomicOr(&mbits[sh >> 5], 1u << (sh & 31));
+    }
+    __syncthreads();
+    uint32_t *dst = masks + ((size_t)w * s.n_elec + e) * mw;
+    for (int j = threadIdx.x; j < mw; j += kMaskThreads) dst[j] = mbits[j];
+}
+
+// Ordered list of the AOs of the shells set in `bits` (one word per thread
+// slot, NT threads).  Returns the count; idx_s receives the AO indices.
+template <int NT>
+__device__ int aos_from_mask(const SysDev &s, const uint32_t *bits, int mw, int *idx_s, int *sh_s, int *warp_s)
+{
+    int words_per = (mw + NT - 1) / NT;
+    const int w0 = min((int)threadIdx.x * words_per, mw), w1 = min(w0 + words_per, mw);
+    int nao = 0;
+    for (int j = w0; j < w1; ++j) {
+        uint32_t b = bits[j];
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            nao += ncart(s.sh_L[j * 32 + bit]);
+        }
+    }
+    int total;
+    int off = block_excl_scan<NT>(nao, warp_s, &total);
+    for (int j = w0; j < w1; ++j) {
+        uint32_t b = bits[j];
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            const int sh = j * 32 + bit;
+            const int a0 = s.sh_ao0[sh], nc = ncart(s.sh_L[sh]);
+            for (int c = 0; c < nc; ++c, ++off) {
+                idx_s[off] = a0 + c;
+                if (sh_s) sh_s[off] = sh;
+            }
+        }
+    }
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------ C1 and C5, FP64-accurate
+constexpr int kC1Threads = 128;
+constexpr int kC1Chunk = 1024;
+
+// Neumaier-compensated float-float accumulation of a*b, with a = ah + al and
+// b = bh + bl: sh + sc holds the sum of the leading products ah*bh, sl the
+// exact rounding errors of those products plus the cross terms.
+__device__ __forceinline__ void ff_acc(float ah, float al, float bh, float bl, float &sh, float &sc, float &sl)
+{
+    const float p = ah * bh;
+    const float pe = fmaf(ah, bh, -p);
+    sl += pe + fmaf(ah, bl, al * bh);
+    const float t = sh + p;
+    sc += (fabsf(sh) >= fabsf(p)) ? ((sh - t) + p) : ((p - t) + sh);
+    sh = t;
+}
+
+template <int NJ>
+__global__ void __launch_bounds__(kC1Threads) k_c15_ff(SysDev s, const double *__restrict__ R,
+                                                       const uint32_t *__restrict__ masks, int mw,
+                                                       const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
+                                                       const float *__restrict__ Ahi1, const float *__restrict__ Alo1,
+                                                       double *__restrict__ X, double *__restrict__ L5)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *b_s = reinterpret_cast<float *>(smem_raw);   // [4][kC1Chunk]: value hi, lo, Laplacian hi, lo
+    uint32_t *bits_s = reinterpret_cast<uint32_t *>(b_s + 4 * kC1Chunk);   // [mw]
+    int *idx_s = reinterpret_cast<int *>(bits_s + mw);   // [n_ao]
+    __shared__ int warp_s[kC1Threads / 32];
+
+    const int e = blockIdx.x, w = blockIdx.y, t = threadIdx.x;
+    const int spin = e >= s.n_up;
+    const int ei = spin ? e - s.n_up : e;
+    const int ns = spin ? s.n_dn : s.n_up;
+    const float *__restrict__ Ahi = spin ? Ahi1 : Ahi0;
+    const float *__restrict__ Alo = spin ? Alo1 : Alo0;
+    const double *r = R + ((size_t)w * s.n_elec + e) * 3;
+    const double rx = r[0], ry = r[1], rz = r[2];
+    const uint32_t *mrow = masks + ((size_t)w * s.n_elec + e) * mw;
+    for (int j = t; j < mw; j += kC1Threads) bits_s[j] = mrow[j];
+    __syncthreads();
+    const int K = aos_from_mask<kC1Threads>(s, bits_s, mw, idx_s, nullptr, warp_s);
+
+    float vh[NJ], vc[NJ], vl[NJ], lh[NJ], lc[NJ], ll[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) { vh[j] = vc[j] = vl[j] = 0.f; lh[j] = lc[j] = ll[j] = 0.f; }
+    const int kwarp = t & ~31;
+
+    for (int k0 = 0; k0 < K; k0 += kC1Chunk) {
+        const int kc = min(kC1Chunk, K - k0);
+        for (int m = t; m < kc; m += kC1Threads) {
+            double v[5];
+            ao_eval_f64(s, idx_s[k0 + m], rx, ry, rz, v);
+            const float h0 = (float)v[0], h4 = (float)v[4];
+            b_s[m] = h0;
+            b_s[kC1Chunk + m] = (float)(v[0] - (double)h0);
+            b_s[2 * kC1Chunk + m] = h4;
+            b_s[3 * kC1Chunk + m] = (float)(v[4] - (double)h4);
+        }
+        __syncthreads();
+        for (int m = 0; m < kc; ++m) {
+            const size_t row = (size_t)idx_s[k0 + m] * ns;
+            const float b0h = b_s[m], b0l = b_s[kC1Chunk + m];
+            const float b4h = b_s[2 * kC1Chunk + m], b4l = b_s[3 * kC1Chunk + m];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                if (kwarp + kC1Threads * j >= ns) continue;   // whole warp beyond ns
+                const int k = t + kC1Threads * j;
+                const float ah = (k < ns) ? __ldg(Ahi + row + k) : 0.f;
+                const float al = (k < ns) ? __ldg(Alo + row + k) : 0.f;
+                ff_acc(ah, al, b0h, b0l, vh[j], vc[j], vl[j]);
+                ff_acc(ah, al, b4h, b4l, lh[j], lc[j], ll[j]);
+            }
+        }
+        __syncthreads();
+    }
+    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+    const size_t off = (size_t)w * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = t + kC1Threads * j;
+        if (k < ns) {
+            X[off + k] = (double)vh[j] + ((double)vc[j] + (double)vl[j]);
+            L5[off + k] = (double)lh[j] + ((double)lc[j] + (double)ll[j]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ tcgen05 path
+constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kAPlaneBytes = TC_M * TC_K * 2;     // 16 KB, one output x one split
+constexpr uint32_t kBPlaneBytes = TC_K * TC_N * 2;     // 16 KB, one split
+constexpr uint32_t kBLbo = 1024;                        // MN-major: next 64-column atom
+constexpr uint32_t kBSbo = 2048;                        // MN-major: next group of 8 K rows
+constexpr int TC_OUT = 3;                               // C2, C3, C4
+constexpr uint32_t kTcSmemFixed = 2 * TC_OUT * kAPlaneBytes + 2 * kBPlaneBytes;   // 128 KB of operands
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// tcgen05 shared-memory matrix descriptor, 128-byte swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;    // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;    // SWIZZLE_128B
+    return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A and B both FP16 (format 0) or
+// both BF16 (format 1), A K-major, B MN-major, shape M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N, int bf16)
+{
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | (0u << 15) | (1u << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the mbarrier phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+// hi/lo split of two values into packed 16-bit pairs: hi = rn(x), lo = rn(x - hi)
+__device__ __forceinline__ void split2(float a, float b, int f16, uint32_t &hi, uint32_t &lo)
+{
+    if (f16) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+// K-major, 128B swizzle: byte offset of element (row m, k) in an [128][64] bf16 plane
+__device__ __forceinline__ uint32_t a_off(int m, int chunk16)
+{
+    return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((chunk16 ^ (m & 7)) << 4));
+}
+
+// MN-major, 128B swizzle: byte offset of the 16-byte chunk holding columns
+// n0..n0+7 (n0 multiple of 8) of K row r in a [64 K][128 N] bf16 plane
+__device__ __forceinline__ uint32_t b_off(int r, int n0)
+{
+    const int c = (n0 & 63) >> 3;
+    return (uint32_t)((r >> 3) * kBSbo + (n0 >> 6) * kBLbo + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+struct TcArgs {
+    SysDev s;
+    const double *R;
+    const uint32_t *masks;
+    int mw;
+    int nw;                  // walkers in this chunk
+    TcTables tt;             // 16-bit hi/lo planes of A [n_ao][ns_pad] and scales
+    float *Cg;               // [nw][3][msz] FP32 (C2..C4)
+    uint32_t *wstatus;       // [nw] per-walker status (QMC_STATUS_TIMEOUT on a timed-out wait)
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    // operands first (1024-aligned), then bookkeeping
+    unsigned char *base = tc_smem + ((1024 - (smem_u32(tc_smem) & 1023)) & 1023);
+    unsigned char *As = base;                                  // 6 planes [out l][split]
+    unsigned char *Bs = base + 2 * TC_OUT * kAPlaneBytes;      // 2 planes [split]
+    uint32_t *mask_s = reinterpret_cast<uint32_t *>(Bs + 2 * kBPlaneBytes);   // [128][mw]
+    int *ao_s = reinterpret_cast<int *>(mask_s + TC_M * p.mw);                // [n_ao + 64]
+    __shared__ uint32_t union_s[256];
+    __shared__ int warp_s[kTcThreads / 32];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+
+    const SysDev &s = p.s;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int e = blockIdx.y;
+    const int spin = e >= s.n_up;
+    const int ei = spin ? e - s.n_up : e;
+    const int ns = spin ? s.n_dn : s.n_up;
+    const int k0 = blockIdx.x * TC_N;
+    if (k0 >= ns) return;
+    const int nspad = p.tt.ns_pad[spin];
+    const int f16 = p.tt.f16;
+    const int ncols = min(TC_N, nspad - k0);   // multiple of 64
+    const int w = blockIdx.z * TC_M + t;       // this thread's walker (row)
+    const bool wvalid = w < p.nw;
+    const int mw = p.mw;
+
+    // masks of the tile's walkers and their union
+    for (int q = t; q < TC_M * mw; q += kTcThreads) {
+        const int m = q / mw, j = q - m * mw;
+        const int wm = blockIdx.z * TC_M + m;
+        mask_s[q] = (wm < p.nw) ? p.masks[((size_t)wm * s.n_elec + e) * mw + j] : 0u;
+    }
+    if (t == 0) s_abort = 0;
+    __syncthreads();
+    for (int j = t; j < mw; j += kTcThreads) {
+        uint32_t u = 0;
+        for (int m = 0; m < TC_M; ++m) u |= mask_s[m * mw + j];
+        union_s[j] = u;
+    }
+    __syncthreads();
+    const int KU = aos_from_mask<kTcThreads>(s, union_s, mw, ao_s, nullptr, warp_s);
+    const int nks = (KU + TC_K - 1) / TC_K;
+    for (int q = KU + t; q < nks * TC_K; q += kTcThreads) ao_s[q] = -1;
+
+    // TMEM: 4 accumulators x 128 columns
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
+                     :: "r"(smem_u32(&tmem_slot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t mbar_a = smem_u32(&mbar);
+    const uint32_t idesc = umma_idesc_f16(TC_M, ncols, f16 ? 0 : 1);
+    const uint64_t kWait = 2000000000ull;   // 2 s per wait
+
+    // this walker's position relative to the current atom
+    const double *rw = p.R + ((size_t)(wvalid ? w : 0) * s.n_elec + e) * 3;
+    const double rx = rw[0], ry = rw[1], rz = rw[2];
+    const uint32_t *my_mask = mask_s + t * mw;
+    const uint16_t *__restrict__ Bhi = p.tt.hi[spin];
+    const uint16_t *__restrict__ Blo = p.tt.lo[spin];
+    const float isc0 = p.tt.in_scale[0], isc1 = p.tt.in_scale[1], isc2 = p.tt.in_scale[2];
+
+    for (int ks = 0; ks < nks; ++ks) {
+        if (ks > 0) {
+            if (!mbar_wait(mbar_a, (ks - 1) & 1, kWait)) { s_abort = 1; }
+            __syncthreads();
+            if (s_abort) break;
+        }
+        // A operand: derivative values of 64 AOs for this walker (row t)
+        int last_atom = -1;
+        float dx = 0.f, dy = 0.f, dz = 0.f, d2 = 0.f;
+        for (int c8 = 0; c8 < TC_K / 8; ++c8) {
+            float v[TC_OUT][8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int pos = ks * TC_K + c8 * 8 + q;
+                const int mu = ao_s[pos];
+                float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+                if (mu >= 0 && wvalid) {
+                    const int sh = s.ao_shell[mu];
+                    if ((my_mask[sh >> 5] >> (sh & 31)) & 1u) {
+                        const int a = s.sh_atom[sh];
+                        if (a != last_atom) {
+                            last_atom = a;
+                            dx = (float)(rx - s.Q[3 * a]);
+                            dy = (float)(ry - s.Q[3 * a + 1]);
+                            dz = (float)(rz - s.Q[3 * a + 2]);
+                            d2 = dx * dx + dy * dy + dz * dz;
+                        }
+                        float g = 0.f, gd = 0.f;
+                        const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
+                        for (int pr = 0; pr < np; ++pr) {
+                            const float gam = (float)s.pg[p0 + pr];
+                            const float ce = (float)s.pc[p0 + pr] * expf(-gam * d2);
+                            g += ce;
+                            gd += gam * ce;
+                        }
+                        const int pw = s.ao_pow[mu];
+                        const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
+                        auto ip = [](float x, int n) {
+                            float y = 1.f;
+                            for (int i = 0; i < n; ++i) y *= x;
+                            return y;
+                        };
+                        const float px = ip(dx, nx), py = ip(dy, ny), pz = ip(dz, nz);
+                        const float P = px * py * pz;
+                        const float dpx = nx ? nx * ip(dx, nx - 1) : 0.f;
+                        const float dpy = ny ? ny * ip(dy, ny - 1) : 0.f;
+                        const float dpz = nz ? nz * ip(dz, nz - 1) : 0.f;
+                        const float c = (float)s.ao_scale[mu];
+                        const float m2gd = -2.f * gd;
+                        g1 = c * (dpx * py * pz * g + m2gd * dx * P);
+                        g2 = c * (px * dpy * pz * g + m2gd * dy * P);
+                        g3 = c * (px * py * dpz * g + m2gd * dz * P);
+                    }
+                }
+                v[0][q] = g1 * isc0; v[1][q] = g2 * isc1; v[2][q] = g3 * isc2;
+            }
+#pragma unroll
+            for (int l = 0; l < TC_OUT; ++l) {
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) split2(v[l][2 * q], v[l][2 * q + 1], f16, hi[q], lo[q]);
+                const uint32_t off = a_off(t, c8);
+                *reinterpret_cast<uint4 *>(As + (2 * l) * kAPlaneBytes + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4 *>(As + (2 * l + 1) * kAPlaneBytes + off) =
+                    make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+        // B operand: rows A[mu][k0 .. k0+127] of both planes, 16-byte chunks
+        for (int q = t; q < 2 * TC_K * (TC_N / 8); q += kTcThreads) {
+            const int plane = q / (TC_K * (TC_N / 8));
+            const int rem = q - plane * (TC_K * (TC_N / 8));
+            const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
+            const int mu = ao_s[ks * TC_K + r];
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (mu >= 0 && 8 * c < ncols) {
+                const uint16_t *src = (plane ? Blo : Bhi) + (size_t)mu * nspad + k0 + 8 * c;
+                val = __ldg(reinterpret_cast<const uint4 *>(src));
+            }
+            *reinterpret_cast<uint4 *>(Bs + plane * kBPlaneBytes + b_off(r, 8 * c)) = val;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 16; ++kk) {
+                const uint64_t bh = umma_desc(b0 + 2 * kk * kBSbo, kBLbo, kBSbo);
+                const uint64_t bl = umma_desc(b0 + kBPlaneBytes + 2 * kk * kBSbo, kBLbo, kBSbo);
+#pragma unroll
+                for (int l = 0; l < TC_OUT; ++l) {
+                    const uint64_t ah = umma_desc(a0 + (2 * l) * kAPlaneBytes + 32 * kk, 16, 1024);
+                    const uint64_t al = umma_desc(a0 + (2 * l + 1) * kAPlaneBytes + 32 * kk, 16, 1024);
+                    const uint32_t d = tmem + l * TC_N;
+                    umma_bf16(d, ah, bh, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16(d, ah, bl, idesc, 1u);
+                    umma_bf16(d, al, bh, idesc, 1u);
+                }
+            }
+            umma_commit(mbar_a);
+        }
+    }
+
+    bool ok = !s_abort;
+    if (ok && nks > 0) ok = mbar_wait(mbar_a, (nks - 1) & 1, kWait);
+    if (!ok) {
+        if (wvalid) atomicOr(p.wstatus + w, (uint32_t)QMC_STATUS_TIMEOUT);
+        // let any MMA still in flight drain (bounded) before freeing TMEM
+        if (nks > 0) mbar_wait(mbar_a, (nks - 1) & 1, kWait);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // epilogue: TMEM -> registers -> C2..C4 rows of this walker
+    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+    const size_t nss = (size_t)ns * ns;
+    float *crow = p.Cg + (size_t)(wvalid ? w : 0) * TC_OUT * msz + (spin ? TC_OUT * (size_t)s.n_up * s.n_up : 0) +
+                  (size_t)ei * ns;
+    for (int l = 0; l < TC_OUT; ++l) {
+        for (int cb = 0; cb < ncols; cb += 32) {
+            uint32_t v[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(l * TC_N + cb);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                           "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+                           "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+                           "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+                           "=r"(v[31])
+                         : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (wvalid && ok) {
+                float *dst = crow + (size_t)l * nss + k0 + cb;
+                const float osc = p.tt.out_scale[spin][l];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    if (k0 + cb + q < ns) dst[q] = (nks > 0) ? __uint_as_float(v[q]) * osc : 0.f;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
+}
+
+// --------------------------------------------------------------- launchers
+cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st)
+{
+    if (nw == 0) return cudaSuccess;
+    dim3 grid(s.n_elec, nw);
+    k_shell_mask<<<grid, kMaskThreads, sizeof(uint32_t) * mw, st>>>(s, R, mw, masks);
+    return cudaGetLastError();
+}
+
+template <int NJ>
+static cudaError_t launch_c15_nj(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+                                 const float *const *Ahi, const float *const *Alo, double *X, double *L5,
+                                 cudaStream_t st)
+{
+    const size_t sm = sizeof(float) * 4 * kC1Chunk + sizeof(uint32_t) * mw + sizeof(int) * (size_t)s.n_ao;
+    cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid(s.n_elec, nw);
+    k_c15_ff<NJ><<<grid, kC1Threads, sm, st>>>(s, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], X, L5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+                          const float *const *Ahi, const float *const *Alo, double *X, double *L5, cudaStream_t st)
+{
+    if (nw == 0) return cudaSuccess;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    switch ((nmax + kC1Threads - 1) / kC1Threads) {
+    case 1: return launch_c15_nj<1>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 2: return launch_c15_nj<2>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 3: return launch_c15_nj<3>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 4: return launch_c15_nj<4>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 5: return launch_c15_nj<5>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 6: return launch_c15_nj<6>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 7: return launch_c15_nj<7>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 8: return launch_c15_nj<8>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t tc_smem_bytes(const SysDev &s, int mw)
+{
+    return 1024 + kTcSmemFixed + sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
+}
+
+cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+                               const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st)
+{
+    if (nw == 0) return cudaSuccess;
+    TcArgs a;
+    a.s = s; a.R = R; a.masks = masks; a.mw = mw; a.nw = nw;
+    a.tt = tt;
+    a.Cg = Cg; a.wstatus = wstatus;
+    const size_t sm = tc_smem_bytes(s, mw);
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;   // system too large for one tile
+    cudaError_t e = cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    dim3 grid((nmax + TC_N - 1) / TC_N, s.n_elec, (nw + TC_M - 1) / TC_M);
+    k_tc_contract<<<grid, kTcThreads, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_widen(const float *__restrict__ src, size_t spitch, double *__restrict__ dst, size_t dpitch,
+                        size_t width)
+{
+    const float *srow = src + (size_t)blockIdx.y * spitch;
+    double *drow = dst + (size_t)blockIdx.y * dpitch;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < width; q += (size_t)gridDim.x * blockDim.x)
+        drow[q] = (double)srow[q];
+}
+
+// rows x width elements, pitches in elements
+cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
+                         cudaStream_t st)
+{
+    if (rows == 0 || width == 0) return cudaSuccess;
+    dim3 grid((unsigned)((width + 255) / 256 < 1024 ? (width + 255) / 256 : 1024), rows);
+    k_widen<<<grid, 256, 0, st>>>(src, spitch, dst, dpitch, width);
+    return cudaGetLastError();
+}
+
+}  // namespace qmc

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -62,6 +64,51 @@ static double shell_radius2(const qmc_system_desc *d, int sh)
     double r2;
     memcpy(&r2, &hi_bits, 8);
     return r2;
+}
+
+// float -> bfloat16 bits, round to nearest even
+static uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+static float bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// Upper bounds of |d chi / dx_l| (out[0]) and |lap chi| (out[1]) over the
+// screened sphere d2 < R2 of a shell, from |x|,|y|,|z| <= r on a radial grid
+// (with a 25% margin); used to pick exact power-of-two scales for FP16.
+static void shell_deriv_bound(const qmc_system_desc *d, int sh, int ao0, double R2, double out[2])
+{
+    const int L = d->shell_L[sh], p0 = d->shell_pstart[sh], np = d->shell_nprim[sh];
+    double sc = 0.0;
+    for (int c = 0; c < ncart_h(L); ++c) sc = std::max(sc, fabs(d->ao_scale[ao0 + c]));
+    const double rmax = sqrt(std::max(R2, 0.0));
+    double bg = 0.0, bl = 0.0;
+    const int npt = 4096;
+    for (int i = 0; i <= npt; ++i) {
+        const double r = rmax * i / npt, r2 = r * r;
+        double G = 0.0, GD = 0.0, GL = 0.0;
+        for (int q = 0; q < np; ++q) {
+            const double gam = d->prim_gamma[p0 + q], c = fabs(d->prim_coef[p0 + q]), ex = exp(-gam * r2);
+            G += c * ex;
+            GD += c * gam * ex;
+            GL += c * fabs(4.0 * gam * gam * r2 - 6.0 * gam) * ex;
+        }
+        const double rL = pow(r, L), rL1 = L >= 1 ? pow(r, L - 1) : 0.0, rL2 = L >= 2 ? pow(r, L - 2) : 0.0;
+        bg = std::max(bg, sc * (L * rL1 * G + 2.0 * r * rL * GD));
+        bl = std::max(bl, sc * (L * (L - 1) * rL2 * G + rL * (GL + 4.0 * L * GD)));
+    }
+    out[0] = 1.25 * bg;
+    out[1] = 1.25 * bl;
 }
 
 struct Blob {
@@ -184,6 +231,53 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     const size_t oSC = b.add(d->ao_scale, sizeof(double) * nao);
     const size_t oA0 = b.add(A64[0].data(), sizeof(double) * A64[0].size());
     const size_t oA1 = b.add(A64[1].data(), sizeof(double) * A64[1].size());
+    // mixed path: BF16 hi/lo planes [n_ao][ns_pad] (zero padded to 64 columns)
+    // and float-float planes [n_ao][ns] of the MO coefficients
+    // FP16 planes hold A * 2^a_exp, a_exp chosen so that max |A| * 2^a_exp <= 8192
+    size_t oBh[2], oBl[2], oHh[2], oHl[2], oFh[2], oFl[2];
+    int ns_pad[2], a_exp[2];
+    for (int spin = 0; spin < 2; ++spin) {
+        const int ns = spin ? nd : nu;
+        const int np = ((ns + 63) / 64) * 64;
+        ns_pad[spin] = np;
+        double amax = 0.0;
+        for (double a : A64[spin]) amax = std::max(amax, fabs(a));
+        a_exp[spin] = amax > 0.0 ? (int)floor(log2(8192.0 / amax)) : 0;
+        const double asc = ldexp(1.0, a_exp[spin]);
+        std::vector<uint16_t> bh((size_t)nao * np, 0), bl((size_t)nao * np, 0);
+        std::vector<uint16_t> hh((size_t)nao * np, 0), hl((size_t)nao * np, 0);
+        std::vector<float> fh((size_t)nao * ns), fl((size_t)nao * ns);
+        for (int mu = 0; mu < nao; ++mu)
+            for (int k = 0; k < ns; ++k) {
+                const double a = A64[spin][(size_t)mu * ns + k];
+                const uint16_t h = bf16_bits((float)a);
+                bh[(size_t)mu * np + k] = h;
+                bl[(size_t)mu * np + k] = bf16_bits((float)(a - (double)bf16_value(h)));
+                const double as = a * asc;
+                const __half h16 = __float2half_rn((float)as);
+                const __half l16 = __float2half_rn((float)(as - (double)__half2float(h16)));
+                memcpy(&hh[(size_t)mu * np + k], &h16, 2);
+                memcpy(&hl[(size_t)mu * np + k], &l16, 2);
+                const float f = (float)a;
+                fh[(size_t)mu * ns + k] = f;
+                fl[(size_t)mu * ns + k] = (float)(a - (double)f);
+            }
+        oBh[spin] = b.add(bh.data(), 2 * bh.size());
+        oBl[spin] = b.add(bl.data(), 2 * bl.size());
+        oHh[spin] = b.add(hh.data(), 2 * hh.size());
+        oHl[spin] = b.add(hl.data(), 2 * hl.size());
+        oFh[spin] = b.add(fh.data(), 4 * fh.size());
+        oFl[spin] = b.add(fl.data(), 4 * fl.size());
+    }
+    // AO derivative values enter the FP16 split scaled by 2^b_exp (bound * 2^b_exp <= 8192)
+    double dbound[2] = {0.0, 0.0};
+    for (int sh = 0; sh < nsh; ++sh) {
+        double bd[2];
+        shell_deriv_bound(d, sh, sh_ao0[sh], sys->R2_host[sh], bd);
+        dbound[0] = std::max(dbound[0], bd[0]);
+        dbound[1] = std::max(dbound[1], bd[1]);
+    }
+    const int b_exp = dbound[0] > 0.0 ? std::min(24, (int)floor(log2(8192.0 / dbound[0]))) : 0;
 
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) { delete sys; return cuda_fail(e, "qmc_system_load: cudaSetDevice"); }
@@ -214,7 +308,19 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     s.A64[0] = reinterpret_cast<const double *>(dev + oA0);
     s.A64[1] = reinterpret_cast<const double *>(dev + oA1);
     s.vnn = vnn;
-    memset(&sys->mixed, 0, sizeof(sys->mixed));
+    MixedTables &mt = sys->mixed;
+    for (int spin = 0; spin < 2; ++spin) {
+        mt.bhi[spin] = reinterpret_cast<const uint16_t *>(dev + oBh[spin]);
+        mt.blo[spin] = reinterpret_cast<const uint16_t *>(dev + oBl[spin]);
+        mt.hhi[spin] = reinterpret_cast<const uint16_t *>(dev + oHh[spin]);
+        mt.hlo[spin] = reinterpret_cast<const uint16_t *>(dev + oHl[spin]);
+        mt.a_exp[spin] = a_exp[spin];
+        mt.fhi[spin] = reinterpret_cast<const float *>(dev + oFh[spin]);
+        mt.flo[spin] = reinterpret_cast<const float *>(dev + oFl[spin]);
+        mt.ns_pad[spin] = ns_pad[spin];
+    }
+    mt.b_exp = b_exp;
+    mt.mask_words = (nsh + 31) / 32;
     *out = sys;
     return QMC_OK;
 }
@@ -247,7 +353,10 @@ namespace {
 struct Plan {
     size_t msz;        // n_up^2 + n_dn^2
     size_t per_walker; // bytes
-    size_t oX, oCd, oD, oLa, oSg, oSt;
+    bool mixed;
+    size_t cd_bytes;   // per walker: FP64 path C2..C5 in FP64; mixed C2..C4 FP32 + C5 FP64
+    size_t mask_bytes; // per walker (mixed path): N x mask_words x 4
+    bool dinv;
 };
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
@@ -256,20 +365,16 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
 {
     Plan p;
     p.msz = (size_t)sys->d.n_up * sys->d.n_up + (size_t)sys->d.n_dn * sys->d.n_dn;
-    const size_t cd_elem = precision == QMC_PREC_F64 ? 8 : 4;
-    size_t o = 0;
-    p.oX = o; o += p.msz * 8;
-    p.oCd = o; o += 4 * p.msz * cd_elem;
-    p.oD = o; o += need_dinv ? p.msz * 8 : 0;
-    p.oLa = o; o += 16;
-    p.oSg = o; o += 16;
-    p.oSt = o; o += 4;
-    p.per_walker = o;
+    p.mixed = precision != QMC_PREC_F64;
+    p.cd_bytes = p.mixed ? p.msz * (3 * 4 + 8) : p.msz * 4 * 8;
+    p.mask_bytes = p.mixed ? (size_t)sys->d.n_elec * sys->mixed.mask_words * 4 : 0;
+    p.dinv = need_dinv;
+    p.per_walker = p.msz * 8 + p.cd_bytes + (need_dinv ? p.msz * 8 : 0) + 36 + p.mask_bytes;
     return p;
 }
 
 struct Carve {
-    double *X; void *Cd; double *D; double *la; double *sg; uint32_t *st;
+    double *X; void *Cd; double *L5; double *D; double *la; double *sg; uint32_t *st; uint32_t *masks;
 };
 
 // Arrays for `nw` walkers laid out array by array inside ws.
@@ -279,18 +384,29 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
     size_t o = 0;
     auto take = [&](size_t bytes) { char *r = b + o; o = al(o + bytes); return r; };
     c.X = reinterpret_cast<double *>(take(p.msz * 8 * nw));
-    c.Cd = take((p.oD - p.oCd) * nw);
-    c.D = (p.oLa - p.oD) ? reinterpret_cast<double *>(take(p.msz * 8 * nw)) : nullptr;
+    if (p.mixed) {
+        c.Cd = take(p.msz * 3 * 4 * nw);
+        c.L5 = reinterpret_cast<double *>(take(p.msz * 8 * nw));
+    } else {
+        c.Cd = take(p.msz * 4 * 8 * nw);
+        c.L5 = nullptr;
+    }
+    c.D = p.dinv ? reinterpret_cast<double *>(take(p.msz * 8 * nw)) : nullptr;
     c.la = reinterpret_cast<double *>(take(16 * (size_t)nw));
     c.sg = reinterpret_cast<double *>(take(16 * (size_t)nw));
     c.st = reinterpret_cast<uint32_t *>(take(4 * (size_t)nw));
+    c.masks = p.mask_bytes ? reinterpret_cast<uint32_t *>(take(p.mask_bytes * nw)) : nullptr;
     return o <= ws_bytes;
 }
 
 size_t bytes_for(const Plan &p, int nw)
 {
-    return al(p.msz * 8 * nw) + al((p.oD - p.oCd) * nw) + ((p.oLa - p.oD) ? al(p.msz * 8 * nw) : 0) +
-           al(16 * (size_t)nw) * 2 + al(4 * (size_t)nw);
+    size_t o = al(p.msz * 8 * nw);
+    o += p.mixed ? al(p.msz * 3 * 4 * nw) + al(p.msz * 8 * nw) : al(p.msz * 4 * 8 * nw);
+    o += p.dinv ? al(p.msz * 8 * nw) : 0;
+    o += al(16 * (size_t)nw) * 2 + al(4 * (size_t)nw);
+    o += p.mask_bytes ? al(p.mask_bytes * nw) : 0;
+    return o;
 }
 
 int chunk_walkers(const Plan &p, int W, size_t ws_bytes)
@@ -303,46 +419,119 @@ int chunk_walkers(const Plan &p, int W, size_t ws_bytes)
     return lo;
 }
 
+CView cview(const Plan &p, const Carve &c)
+{
+    CView v;
+    v.g = c.Cd;
+    if (p.mixed) {
+        v.g_f32 = 1; v.g_wstride = 3 * p.msz; v.g_ncomp = 3;
+        v.l = c.L5; v.l_wstride = p.msz; v.l_ncomp = 1; v.l_comp = 0;
+    } else {
+        v.g_f32 = 0; v.g_wstride = 4 * p.msz; v.g_ncomp = 4;
+        v.l = static_cast<const double *>(c.Cd); v.l_wstride = 4 * p.msz; v.l_ncomp = 4; v.l_comp = 3;
+    }
+    return v;
+}
+
+// Steps a1-a3 for one chunk of walkers: C1 -> c.X (FP64), C2..C5 -> c.Cd
+// (FP64 in the FP64 path, FP32 in the mixed path).
+cudaError_t run_products(const qmc_system *sys, int precision, int nw, const double *Rc, const Carve &c,
+                         cudaStream_t st)
+{
+    const SysDev &s = sys->d;
+    if (precision == QMC_PREC_F64) return launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
+    const MixedTables &mt = sys->mixed;
+    cudaError_t e = launch_shell_mask(s, nw, Rc, mt.mask_words, c.masks, st);
+    if (e != cudaSuccess) return e;
+    e = launch_c15_ff(s, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, c.X, c.L5, st);
+    if (e != cudaSuccess) return e;
+    TcTables tt;
+    tt.f16 = precision == QMC_PREC_MIXED ? 1 : 0;
+    for (int spin = 0; spin < 2; ++spin) {
+        tt.hi[spin] = tt.f16 ? mt.hhi[spin] : mt.bhi[spin];
+        tt.lo[spin] = tt.f16 ? mt.hlo[spin] : mt.blo[spin];
+        tt.ns_pad[spin] = mt.ns_pad[spin];
+        for (int l = 0; l < 3; ++l)
+            tt.out_scale[spin][l] = tt.f16 ? (float)ldexp(1.0, -(mt.a_exp[spin] + mt.b_exp)) : 1.0f;
+    }
+    for (int l = 0; l < 3; ++l) tt.in_scale[l] = tt.f16 ? (float)ldexp(1.0, mt.b_exp) : 1.0f;
+    return launch_tc_contract(s, nw, Rc, c.masks, mt.mask_words, tt, static_cast<float *>(c.Cd), c.st, st);
+}
+
+
 }  // namespace
 
 extern "C" int qmc_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes)
 {
     if (!sys || !bytes || n_walk < 0) return invalid("qmc_workspace_size: bad argument");
-    if (precision != QMC_PREC_F64 && precision != QMC_PREC_MIXED) return invalid("qmc_workspace_size: precision");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_workspace_size: precision");
     const Plan p = make_plan(sys, precision, true);
     *bytes = bytes_for(p, std::min(n_walk, 65535));
     return QMC_OK;
 }
 
-extern "C" int qmc_walkers_eval(const qmc_system *sys, int n_walk, const double *R, int precision,
-                                const qmc_eval_out *out, void *ws, size_t ws_bytes, qmc_stream_t stream)
+namespace {
+
+// Events bracketing the three stages of one evaluation (contraction a1-a3,
+// inverse a4, energies a5-a6); created on first use per thread.
+struct StageEvents {
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int device = -1;
+    ~StageEvents()
+    {
+        for (auto &e : ev) if (e) cudaEventDestroy(e);
+    }
+    cudaError_t ensure(int dev)
+    {
+        if (device == dev && ev[0]) return cudaSuccess;
+        for (auto &e : ev) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+        }
+        device = dev;
+        return cudaSuccess;
+    }
+};
+thread_local StageEvents t_events;
+
+int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision, const qmc_eval_out *out, void *ws,
+              size_t ws_bytes, cudaStream_t st, float *stage_ms)
 {
     if (!sys || !out) return invalid("qmc_walkers_eval: null argument");
     if (n_walk < 0) return invalid("qmc_walkers_eval: n_walk < 0");
+    if (stage_ms) for (int q = 0; q < 4; ++q) stage_ms[q] = 0.0f;
     if (n_walk == 0) return QMC_OK;
     if (!R || !out->logpsi || !out->sign || !out->drift || !out->e_loc || !out->status)
         return invalid("qmc_walkers_eval: null required pointer");
-    if (precision != QMC_PREC_F64) return invalid("qmc_walkers_eval: precision not available in this build");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_walkers_eval: precision");
     const Plan p = make_plan(sys, precision, out->dinv == nullptr);
     const int chunk = chunk_walkers(p, n_walk, ws_bytes);
     if (chunk < 1) {
         set_error("qmc_walkers_eval: workspace smaller than one walker");
         return QMC_ERR_CAPACITY;
     }
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const SysDev &s = sys->d;
     cudaError_t e = cudaSetDevice(sys->device);
     if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: cudaSetDevice");
+    if (stage_ms) {
+        e = t_events.ensure(sys->device);
+        if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event create");
+    }
+    auto mark = [&](int q) -> cudaError_t { return stage_ms ? cudaEventRecord(t_events.ev[q], st) : cudaSuccess; };
     for (int w0 = 0; w0 < n_walk; w0 += chunk) {
         const int nw = std::min(chunk, n_walk - w0);
         Carve c;
         carve(p, nw, ws, ws_bytes, c);
         const double *Rc = R + (size_t)w0 * s.n_elec * 3;
         double *Dinv = out->dinv ? out->dinv + (size_t)w0 * p.msz : c.D;
+        if ((e = mark(0)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
-        e = launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
-        if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: contraction launch");
+        e = run_products(sys, precision, nw, Rc, c, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: products launch");
+        if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         GjJob jobs[2];
         int nj = 0;
         for (int spin = 0; spin < 2; ++spin) {
@@ -359,11 +548,39 @@ extern "C" int qmc_walkers_eval(const qmc_system *sys, int n_walk, const double 
         }
         e = launch_gj(jobs, nj, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: Gauss-Jordan launch");
-        e = launch_drift_energy(s, nw, Rc, Dinv, static_cast<double *>(c.Cd), precision != QMC_PREC_F64, c.la,
-                                c.sg, c.st, *out, w0, st);
+        if ((e = mark(2)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
+        e = launch_drift_energy(s, nw, Rc, Dinv, cview(p, c), c.la, c.sg, c.st, *out, w0, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: energy launch");
+        if (stage_ms) {
+            if ((e = mark(3)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
+            if ((e = cudaEventSynchronize(t_events.ev[3])) != cudaSuccess)
+                return cuda_fail(e, "qmc_walkers_eval: event sync");
+            for (int q = 0; q < 3; ++q) {
+                float ms = 0.0f;
+                if ((e = cudaEventElapsedTime(&ms, t_events.ev[q], t_events.ev[q + 1])) != cudaSuccess)
+                    return cuda_fail(e, "qmc_walkers_eval: elapsed");
+                stage_ms[q] += ms;
+                stage_ms[3] += ms;
+            }
+        }
     }
     return QMC_OK;
+}
+
+}  // namespace
+
+extern "C" int qmc_walkers_eval(const qmc_system *sys, int n_walk, const double *R, int precision,
+                                const qmc_eval_out *out, void *ws, size_t ws_bytes, qmc_stream_t stream)
+{
+    return eval_impl(sys, n_walk, R, precision, out, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" int qmc_walkers_eval_timed(const qmc_system *sys, int n_walk, const double *R, int precision,
+                                      const qmc_eval_out *out, void *ws, size_t ws_bytes, qmc_stream_t stream,
+                                      float *stage_ms)
+{
+    if (!stage_ms) return invalid("qmc_walkers_eval_timed: stage_ms is null");
+    return eval_impl(sys, n_walk, R, precision, out, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), stage_ms);
 }
 
 extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const double *R, int precision, double *C,
@@ -371,7 +588,7 @@ extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const doub
 {
     if (!sys || (n_walk > 0 && (!R || !C))) return invalid("qmc_slater_matrices: null argument");
     if (n_walk < 0) return invalid("qmc_slater_matrices: n_walk < 0");
-    if (precision != QMC_PREC_F64) return invalid("qmc_slater_matrices: precision not available in this build");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_slater_matrices: precision");
     if (n_walk == 0) return QMC_OK;
     const Plan p = make_plan(sys, precision, false);
     const int chunk = chunk_walkers(p, n_walk, ws_bytes);
@@ -390,20 +607,29 @@ extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const doub
         Carve c;
         carve(p, nw, ws, ws_bytes, c);
         const double *Rc = R + (size_t)w0 * s.n_elec * 3;
-        double *Cd = static_cast<double *>(c.Cd);
-        e = launch_contract_f64(s, nw, Rc, c.X, Cd, st);
-        if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: contraction launch");
+        e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: memset");
+        e = run_products(sys, precision, nw, Rc, c, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: products launch");
         char *o = reinterpret_cast<char *>(C + (size_t)w0 * 5 * p.msz);
         // per walker: [C1 up][C2..C5 up][C1 dn][C2..C5 dn]
-        struct { const double *src; size_t spitch, width, dst_off; } cp[4] = {
-            {c.X, p.msz * 8, nu2 * 8, 0},
-            {Cd, 4 * p.msz * 8, 4 * nu2 * 8, nu2 * 8},
-            {c.X + nu2, p.msz * 8, nd2 * 8, 5 * nu2 * 8},
-            {Cd + 4 * nu2, 4 * p.msz * 8, 4 * nd2 * 8, 6 * nu2 * 8},
-        };
-        for (auto &q : cp) {
-            if (q.width == 0) continue;
-            e = cudaMemcpy2DAsync(o + q.dst_off, opitch, q.src, q.spitch, q.width, nw, cudaMemcpyDeviceToDevice, st);
+        const size_t xs[2] = {0, nu2}, ws2[2] = {nu2, nd2}, os[2] = {0, 5 * nu2};
+        for (int spin = 0; spin < 2; ++spin) {
+            if (ws2[spin] == 0) continue;
+            e = cudaMemcpy2DAsync(o + os[spin] * 8, opitch, c.X + xs[spin], p.msz * 8, ws2[spin] * 8, nw,
+                                  cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: copy");
+            double *dst = reinterpret_cast<double *>(o) + os[spin] + ws2[spin];
+            if (!p.mixed) {
+                e = cudaMemcpy2DAsync(dst, opitch, static_cast<double *>(c.Cd) + 4 * xs[spin], 4 * p.msz * 8,
+                                      4 * ws2[spin] * 8, nw, cudaMemcpyDeviceToDevice, st);
+            } else {
+                e = launch_widen(static_cast<float *>(c.Cd) + 3 * xs[spin], 3 * p.msz, dst, 5 * p.msz, 3 * ws2[spin],
+                                 nw, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(dst + 3 * ws2[spin], opitch, c.L5 + xs[spin], p.msz * 8, ws2[spin] * 8,
+                                          nw, cudaMemcpyDeviceToDevice, st);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: copy");
         }
     }

@@ -145,4 +145,19 @@ __device__ __forceinline__ void ao_eval_f64(const SysDev &s, int mu, double rx, 
     out[4] = c * (lapP * g + P * (gl - 4.0 * L * gd));
 }
 
+// Value of AO mu at r, FP64.
+__device__ __forceinline__ double ao_value_f64(const SysDev &s, int mu, double rx, double ry, double rz)
+{
+    const int sh = s.ao_shell[mu];
+    const int a = s.sh_atom[sh];
+    const double dx = rx - s.Q[3 * a], dy = ry - s.Q[3 * a + 1], dz = rz - s.Q[3 * a + 2];
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    double g = 0.0;
+    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
+    for (int p = 0; p < np; ++p) g += s.pc[p0 + p] * exp(-s.pg[p0 + p] * d2);
+    const int pw = s.ao_pow[mu];
+    return s.ao_scale[mu] * ipow_small(dx, pw & 255) * ipow_small(dy, (pw >> 8) & 255) *
+           ipow_small(dz, (pw >> 16) & 255) * g;
+}
+
 }  // namespace qmc

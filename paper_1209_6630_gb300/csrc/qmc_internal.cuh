@@ -38,13 +38,23 @@ struct SysDev {
     double vnn;
 };
 
-// Split-precision tables of the mixed path (per spin).
+// Split-precision copies of the MO coefficients for the mixed path, per spin.
 struct MixedTables {
-    // A^T split planes, K-major bf16: [plane][n_s_pad][n_ao_pad]
-    uint16_t *At[2];
-    int n_s_pad[2];
-    int n_ao_pad;
-    int n_planes;
+    const uint16_t *bhi[2], *blo[2];   // BF16 hi/lo planes [n_ao][ns_pad], ns_pad = ns rounded up to 64
+    const uint16_t *hhi[2], *hlo[2];   // FP16 hi/lo planes of A * 2^a_exp[spin], same layout
+    const float *fhi[2], *flo[2];      // float-float planes [n_ao][ns]
+    int ns_pad[2];
+    int a_exp[2];                      // FP16 planes hold A * 2^a_exp
+    int b_exp;                         // FP16 path: AO gradients enter scaled by 2^b_exp
+    int mask_words;                    // 32-bit words of a per-electron shell bitmask
+};
+
+struct TcTables {                      // what the tensor-core kernel reads, one precision mode
+    const uint16_t *hi[2], *lo[2];
+    int ns_pad[2];
+    int f16;                           // 1: FP16 operands, 0: BF16
+    float out_scale[2][3];             // multiply accumulator (spin, gradient component) by this (power of 2)
+    float in_scale[3];                 // multiply AO gradient component l by this before the split
 };
 
 // Per-matrix parameters for the Gauss-Jordan kernel (one entry per spin).
@@ -71,10 +81,29 @@ cudaError_t launch_contract_f64(const SysDev &s, int nw, const double *R, double
 cudaError_t launch_screen_ao(const SysDev &s, int nw, const double *R, int cap, int32_t *cnt,
                              int32_t *idx, double *B, cudaStream_t st);
 cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st);
-cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv,
-                                const double *Cd, int cd_is_f32, const double *logabs2,
-                                const double *sign2, const uint32_t *sing, const qmc_eval_out &o,
-                                int w_off, cudaStream_t st);
+// Where the gradient (C2..C4) and Laplacian (C5) matrices of a walker chunk live:
+// component c of spin s, electron row ei: base + w*wstride + (s ? ncomp*n_up^2 : 0) + c*ns^2 + ei*ns
+struct CView {
+    const void *g;      // gradients, FP32 if g_f32 else FP64
+    int g_f32;
+    size_t g_wstride;
+    int g_ncomp;
+    const double *l;    // Laplacian, FP64, component l_comp of its block
+    size_t l_wstride;
+    int l_ncomp;
+    int l_comp;
+};
+
+cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv, const CView &cv,
+                                const double *logabs2, const double *sign2, const uint32_t *sing,
+                                const qmc_eval_out &o, int w_off, cudaStream_t st);
+cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st);
+cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+                          const float *const *Ahi, const float *const *Alo, double *X, double *L5, cudaStream_t st);
+cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+                               const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
+cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
+                         cudaStream_t st);
 cudaError_t launch_backward_f64(const SysDev &s, int nw, const double *R, const double *dinv,
                                 const double *g, double *dA_up, double *dA_dn, cudaStream_t st,
                                 int max_ao_per_atom);
