@@ -174,6 +174,30 @@ int qmc_walkers_eval_timed(const qmc_system *sys, int n_walk, const double *R, i
                            float *stage_ms);
 
 /*
+ * qmc_walkers_eval_static -- qmc_walkers_eval for callers that cannot
+ * allocate device memory (for example code running under a memory manager
+ * that owns the whole device, a latency-critical loop that must not hit
+ * cudaMalloc's implicit synchronisation, or a plug-in whose host forbids
+ * driver allocations).  The paper has no counterpart; it is a deployment
+ * convenience.  It allocates nothing: its scratch is one fixed device array
+ * of QMC_STATIC_SCRATCH_BYTES (64 MiB) inside the library, which every device
+ * that loads the library holds until the process exits.
+ *   - Walkers are processed in chunks that fit the array; a system whose
+ *     single walker needs more scratch than that (e.g. 1731 electrons in
+ *     QMC_PREC_F64) is rejected with QMC_ERR_CAPACITY and a message giving
+ *     the size.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents:
+ *     calls that overlap on the GPU (other streams, other threads) race and
+ *     corrupt each other's results; serialise them.
+ * Arguments, outputs and other errors as for qmc_walkers_eval.
+ */
+#define QMC_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const double *R, int precision,
+                            const qmc_eval_out *out, qmc_stream_t stream);
+
+/*
  * qmc_logpsi_backward -- a7, the adjoint of log|Psi| with respect to the MO
  * coefficients, weighted over walkers:
  *   dA_s[mu][k] = sum_w g_w sum_{e in spin s} (D^-1)_{w,ek} chi_mu(r_{w,e})

@@ -63,12 +63,14 @@ def lib():
             L.qmc_walkers_eval.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp]
             L.qmc_walkers_eval_timed.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp,
                                                  C.POINTER(C.c_float)]
+            L.qmc_walkers_eval_static.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp]
             L.qmc_logpsi_backward.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qmc_screen_ao.argtypes = [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
-                         "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+                         "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static",
+                         "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
                          "qmc_det_inverse"):
                 getattr(L, name).restype = _i
             _lib = L
@@ -83,5 +85,5 @@ def check(rc):
 
 # every symbol include/qmcgb.h declares
 EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
-            "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+            "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
             "qmc_det_inverse", "qmc_last_error", "qmc_version")

@@ -681,3 +681,53 @@ extern "C" int qmc_logpsi_backward(const qmc_system *sys, int n_walk, const doub
     if (e != cudaSuccess) return cuda_fail(e, "qmc_logpsi_backward: launch");
     return QMC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Walker evaluation without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs under a memory manager
+// owning all device memory (a framework's caching allocator that must not be
+// bypassed), code in a latency-critical loop where cudaMalloc's implicit
+// device synchronisation is not acceptable, or a plug-in inside a host
+// application that forbids driver allocations.  For them the scratch of
+// qmc_walkers_eval lives in the fixed array below, which every device that
+// loads this library holds until the process exits.
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)QMC_STATIC_SCRATCH_BYTES;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_static_ptr[kMaxDevices] = {nullptr};   // device address of the array, per device
+
+}  // namespace
+
+extern "C" int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const double *R, int precision,
+                                       const qmc_eval_out *out, qmc_stream_t stream)
+{
+    if (!sys) return invalid("qmc_walkers_eval_static: null system");
+    const int dev = sys->device;
+    if (dev < 0 || dev >= kMaxDevices) return invalid("qmc_walkers_eval_static: device index out of range");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16)
+        return invalid("qmc_walkers_eval_static: precision");
+    const Plan p = make_plan(sys, precision, out == nullptr || out->dinv == nullptr);
+    if (bytes_for(p, 1) > kStaticScratchBytes) {
+        set_error("qmc_walkers_eval_static: one walker of this system needs " + std::to_string(bytes_for(p, 1)) +
+                  " bytes of scratch, more than the library's fixed " + std::to_string(kStaticScratchBytes) +
+                  "-byte array; use qmc_walkers_eval with a caller workspace");
+        return QMC_ERR_CAPACITY;
+    }
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval_static: cudaSetDevice");
+    if (!g_static_ptr[dev]) {
+        // first call on this device: the host-side symbol is only a stand-in,
+        // the kernels need the array's device address
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval_static: cudaGetSymbolAddress");
+        g_static_ptr[dev] = ptr;
+    }
+    return eval_impl(sys, n_walk, R, precision, out, g_static_ptr[dev], kStaticScratchBytes,
+                     reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
