@@ -254,7 +254,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_step = float(t.item())
     value = ws * W / (t_step / 1e3)
-    st = np.array(stages)            # [K, 4]
+    st = np.array(stages)            # [K, 8]
     stage_mean = st.mean(axis=0)
     launches_per_step = LAUNCHES_PER_STEP[prec]   # one walker chunk
 
@@ -264,26 +264,42 @@ def main():
     kbar = float(cnt.float().mean().item())
 
     n_up, n_dn = s.n_up, s.n_dn
-    flop_gj = 2.0 * (n_up ** 3 + n_dn ** 3) * W
-    flop_contract = 10.0 * (n_up + n_dn) * kbar * ((n_up * n_up + n_dn * n_dn) / (n_up + n_dn)) * W
     pk = peaks()
-    dom = int(np.argmax(stage_mean[:3]))
-    kern = KERNEL_OF_STAGE[prec][dom]
-    if dom == 1:
-        achieved = flop_gj / (stage_mean[1] / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": fp64_peak_tflops(pk),
-                "unit": "TFLOP/s", "peak_source": "FP64: 152 SMs x 4 flop/clk (measured DFMA rate) x sm_max_mhz"}
-    elif dom == 0 and prec == "f64":
-        achieved = flop_contract / (stage_mean[0] / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": fp64_peak_tflops(pk),
-                "unit": "TFLOP/s", "peak_source": "FP64: 152 SMs x 4 flop/clk (measured DFMA rate) x sm_max_mhz"}
+    # algorithmic work per launch (whole batch); sum_s N_s * Kbar * N_s products per output
+    prod = kbar * (n_up * n_up + n_dn * n_dn) * W
+    flop_gj = 2.0 * (n_up ** 3 + n_dn ** 3) * W
+    fp64_peak = fp64_peak_tflops(pk)
+    fp32_inst_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12      # T instructions/s
+    if prec == "f64":
+        kern_ms = {"k_contract_f64": stage_mean[0], "k_gj": stage_mean[1], "k_drift_energy": stage_mean[2]}
     else:
-        achieved = flop_contract / (stage_mean[0] / 1e3) / 1e12
-        roof = {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": pk.get("bf16_tflops_sustained"),
-                "unit": "TFLOP/s", "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json)"}
-    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") else None
-    tr = kernel_traffic(kern, a.workload)
-    roof["traffic"] = tr
+        kern_ms = {"k_shell_mask": stage_mean[4], "k_c15_ff": stage_mean[5], "k_tc_contract": stage_mean[6],
+                   "k_gj": stage_mean[1], "k_drift_energy": stage_mean[2]}
+    kern = max(kern_ms, key=kern_ms.get)
+    t_k = kern_ms[kern] / 1e3
+    if kern == "k_gj":
+        roof = {"bound": "alu", "achieved": flop_gj / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_source": "FP64: 152 SMs x 4 flop/clk (measured DFMA rate, profiles/fp64_rate_gb300.md) "
+                               "x sm_max_mhz", "work": "2 (N_up^3 + N_dn^3) flop per walker"}
+    elif kern == "k_contract_f64":
+        roof = {"bound": "alu", "achieved": 10.0 * prod / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_source": "FP64: 152 SMs x 4 flop/clk x sm_max_mhz",
+                "work": "10 sum_s N_s Kbar N_s flop per walker"}
+    elif kern == "k_c15_ff":
+        # two outputs, 13 FP32 instructions per compensated float-float product
+        roof = {"bound": "alu", "achieved": 26.0 * prod / t_k / 1e12, "peak": fp32_inst_peak, "unit": "Tinst/s",
+                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x sm_max_mhz",
+                "work": "2 outputs x 13 FP32 instructions per product, sum_s N_s Kbar N_s products per walker"}
+    elif kern == "k_tc_contract":
+        roof = {"bound": "tensor", "achieved": 3 * 3 * 2.0 * prod / t_k / 1e12, "peak": pk.get("bf16_tflops_sustained"),
+                "unit": "TFLOP/s", "peak_source": "measured dense bf16 (= fp16) sustained, MEASURED_PEAKS.json",
+                "work": "3 outputs x 3 split products x 2 sum_s N_s Kbar N_s flop per walker"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s"}
+    roof["kernel"] = kern
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") and roof.get("achieved") else None
+    roof["traffic"] = kernel_traffic(kern, a.workload)
+    roof["kernel_ms"] = kern_ms
     roof["stage_ms"] = {"a1_a3": stage_mean[0], "a4": stage_mean[1], "a5_a6": stage_mean[2]}
 
     line = {"metric": METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": ws, "steps": a.steps,

@@ -122,6 +122,16 @@ typedef struct {
 int qmc_system_load(const qmc_system_desc *desc, int device, qmc_system **out);
 int qmc_system_free(qmc_system *sys);
 
+/*
+ * qmc_system_set_mo -- replace the MO coefficients a_{k mu} of a loaded
+ * system (Eq. "mo"), e.g. between the steps of a parameter optimisation
+ * driven by qmc_logpsi_backward.  A_up [n_ao][n_up], A_dn [n_ao][n_dn] host
+ * arrays of a_dtype.  Rebuilds the library's device copies (FP64 and the
+ * split planes of the mixed path) in place.  Blocking: it synchronises the
+ * device first, so no evaluation still reads the old coefficients.
+ */
+int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void *A_dn);
+
 /* Copy the per-shell R2 used for screening to host memory [n_shell]. */
 int qmc_system_shell_r2(const qmc_system *sys, double *R2_host);
 
@@ -166,7 +176,11 @@ int qmc_walkers_eval(const qmc_system *sys, int n_walk, const double *R, int pre
  *   stage_ms[1] a4 (log|det|, sign, inverse)
  *   stage_ms[2] a5-a6 (drift, energies)
  *   stage_ms[3] their sum
- * (host float[4], summed over walker chunks).  Blocks until the work has
+ *   stage_ms[4] mixed path: shell masks (a1)
+ *   stage_ms[5] mixed path: C1 and C5 products; FP64 path: all of a1-a3
+ *   stage_ms[6] mixed path: tensor-core C2..C4 products
+ *   stage_ms[7] 0 (reserved)
+ * (host float[8], summed over walker chunks).  Blocks until the work has
  * finished.  Same arguments and errors as qmc_walkers_eval.
  */
 int qmc_walkers_eval_timed(const qmc_system *sys, int n_walk, const double *R, int precision,

@@ -59,6 +59,7 @@ def lib():
             L.qmc_system_load.argtypes = [C.POINTER(SystemDesc), _i, C.POINTER(_vp)]
             L.qmc_system_free.argtypes = [_vp]
             L.qmc_system_shell_r2.argtypes = [_vp, _vp]
+            L.qmc_system_set_mo.argtypes = [_vp, _i, _vp, _vp]
             L.qmc_workspace_size.argtypes = [_vp, _i, _i, C.POINTER(C.c_size_t)]
             L.qmc_walkers_eval.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp]
             L.qmc_walkers_eval_timed.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp,
@@ -68,7 +69,8 @@ def lib():
             L.qmc_screen_ao.argtypes = [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
-            for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
+            for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo",
+                         "qmc_workspace_size",
                          "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static",
                          "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
                          "qmc_det_inverse"):
@@ -84,6 +86,6 @@ def check(rc):
 
 
 # every symbol include/qmcgb.h declares
-EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_workspace_size",
+EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo", "qmc_workspace_size",
             "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
             "qmc_det_inverse", "qmc_last_error", "qmc_version")

@@ -92,6 +92,16 @@ class QmcSystem:
         check(lib().qmc_system_shell_r2(self._h, C.c_void_p(out.ctypes.data)))
         return out
 
+    def set_mo(self, A_up, A_dn):
+        """Replace the MO coefficients (qmc_system_set_mo); host arrays [n_ao, n_s]."""
+        f32 = np.asarray(A_up).dtype == np.float32
+        dt = np.float32 if f32 else np.float64
+        au = np.ascontiguousarray(A_up, dtype=dt)
+        ad = np.ascontiguousarray(A_dn, dtype=dt)
+        assert au.shape == (self.n_ao, self.n_up) and ad.shape == (self.n_ao, self.n_dn)
+        check(lib().qmc_system_set_mo(self._h, DTYPE_F32 if f32 else DTYPE_F64, C.c_void_p(au.ctypes.data),
+                                      C.c_void_p(ad.ctypes.data)))
+
     def workspace_size(self, n_walk: int, precision: str = "f64") -> int:
         b = C.c_size_t()
         check(lib().qmc_workspace_size(self._h, n_walk, PREC[precision], C.byref(b)))
@@ -132,7 +142,7 @@ class QmcSystem:
             check(lib().qmc_walkers_eval(self._h, W, _ptr(R), PREC[precision], C.byref(eo), _ptr(ws), ws.numel(),
                                          _stream(self.device)))
         else:
-            ms = (C.c_float * 4)()
+            ms = (C.c_float * 8)()
             check(lib().qmc_walkers_eval_timed(self._h, W, _ptr(R), PREC[precision], C.byref(eo), _ptr(ws),
                                                ws.numel(), _stream(self.device), ms))
             stage_ms.append([float(x) for x in ms])

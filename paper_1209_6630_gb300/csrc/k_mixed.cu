@@ -23,9 +23,11 @@
 // walkers sits near the same nucleus, so their AO lists overlap), a chunk of
 // 128 MOs (N) of C2..C4.  K runs over the union of the 128 walkers' active
 // AOs, 64 per step:
-//   A operand (M x K, K-major, 128B swizzle): the walkers' AO derivative
-//     values, computed in FP32 by the 128 threads (one walker each) and split
-//     into BF16 hi/lo planes, zero where the walker's shell is screened out;
+//   A operand (M x K, K-major, 128B swizzle): the walkers' AO gradient
+//     values, computed in FP32 (two threads per walker, 32 AOs each; basis
+//     tables in FP32 and positions as float pairs, so no FP64 instruction
+//     runs here) and split into 16-bit hi/lo planes, zero where the walker's
+//     shell is screened out;
 //   B operand (N x K, MN-major, 128B swizzle): rows of the MO coefficient
 //     matrix A[mu][k0..k0+127] gathered by AO index from BF16 hi/lo planes
 //     prepared at system load (16-byte copies, no transpose);
@@ -99,8 +101,6 @@ __device__ int aos_from_mask(const SysDev &s, const uint32_t *bits, int mw, int 
 }
 
 // ------------------------------------------------ C1 and C5, FP64-accurate
-constexpr int kC1Threads = 128;
-constexpr int kC1Chunk = 1024;
 
 // Neumaier-compensated float-float accumulation of a*b, with a = ah + al and
 // b = bh + bl: sh + sc holds the sum of the leading products ah*bh, sl the
@@ -115,80 +115,165 @@ __device__ __forceinline__ void ff_acc(float ah, float al, float bh, float bl, f
     sh = t;
 }
 
+// Value and Laplacian of AO mu at r, FP64 (the two quantities C1 and C5 need).
+__device__ __forceinline__ void ao_val_lap_f64(const SysDev &s, int mu, double rx, double ry, double rz,
+                                               double &val, double &lap)
+{
+    const int sh = s.ao_shell[mu];
+    const int a = s.sh_atom[sh];
+    const double dx = rx - s.Q[3 * a], dy = ry - s.Q[3 * a + 1], dz = rz - s.Q[3 * a + 2];
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    double g = 0.0, gd = 0.0, gl = 0.0;
+    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
+    for (int p = 0; p < np; ++p) {
+        const double gam = s.pg[p0 + p];
+        const double ce = s.pc[p0 + p] * exp(-gam * d2);
+        g += ce;
+        gd += gam * ce;
+        gl += (4.0 * gam * d2 - 6.0) * gam * ce;
+    }
+    const int pw = s.ao_pow[mu];
+    const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
+    const int L = nx + ny + nz;
+    const double px = ipow_small(dx, nx), py = ipow_small(dy, ny), pz = ipow_small(dz, nz);
+    const double P = px * py * pz;
+    const double ddx = nx > 1 ? nx * (nx - 1) * ipow_small(dx, nx - 2) : 0.0;
+    const double ddy = ny > 1 ? ny * (ny - 1) * ipow_small(dy, ny - 2) : 0.0;
+    const double ddz = nz > 1 ? nz * (nz - 1) * ipow_small(dz, nz - 2) : 0.0;
+    const double c = s.ao_scale[mu];
+    val = c * P * g;
+    lap = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * g + P * (gl - 4.0 * L * gd));
+}
+
+// One CTA per (electron index e, group of kC15G walkers).  The float-float
+// MO coefficients of an AO are loaded once per thread and applied to every
+// walker of the group (the same electron of nearby-indexed walkers sees
+// largely the same AOs); AOs screened out for a walker are skipped.
+constexpr int kC15G = 4;
+constexpr int kC15Threads = 256;
+constexpr int kC15Chunk = 256;
+
 template <int NJ>
-__global__ void __launch_bounds__(kC1Threads) k_c15_ff(SysDev s, const double *__restrict__ R,
-                                                       const uint32_t *__restrict__ masks, int mw,
-                                                       const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
-                                                       const float *__restrict__ Ahi1, const float *__restrict__ Alo1,
-                                                       double *__restrict__ X, double *__restrict__ L5)
+__global__ void __launch_bounds__(kC15Threads, 1) k_c15_ff(SysDev s, int nw, const double *__restrict__ R,
+                                                        const uint32_t *__restrict__ masks, int mw,
+                                                        const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
+                                                        const float *__restrict__ Ahi1, const float *__restrict__ Alo1,
+                                                        double *__restrict__ X, double *__restrict__ L5)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *b_s = reinterpret_cast<float *>(smem_raw);   // [4][kC1Chunk]: value hi, lo, Laplacian hi, lo
-    uint32_t *bits_s = reinterpret_cast<uint32_t *>(b_s + 4 * kC1Chunk);   // [mw]
-    int *idx_s = reinterpret_cast<int *>(bits_s + mw);   // [n_ao]
-    __shared__ int warp_s[kC1Threads / 32];
+    float4 *b_s = reinterpret_cast<float4 *>(smem_raw);            // [kC15G][kC15Chunk]: (vh, vl, lh, ll)
+    uint32_t *mk_s = reinterpret_cast<uint32_t *>(b_s + kC15G * kC15Chunk);   // [kC15G][mw]
+    uint32_t *un_s = mk_s + kC15G * mw;                            // [mw]
+    int *idx_s = reinterpret_cast<int *>(un_s + mw);               // [n_ao]
+    __shared__ int warp_s[kC15Threads / 32];
 
-    const int e = blockIdx.x, w = blockIdx.y, t = threadIdx.x;
+    const int e = blockIdx.x, t = threadIdx.x;
+    const int w0 = blockIdx.y * kC15G;
+    const int ng = min(kC15G, nw - w0);
     const int spin = e >= s.n_up;
     const int ei = spin ? e - s.n_up : e;
     const int ns = spin ? s.n_dn : s.n_up;
     const float *__restrict__ Ahi = spin ? Ahi1 : Ahi0;
     const float *__restrict__ Alo = spin ? Alo1 : Alo0;
-    const double *r = R + ((size_t)w * s.n_elec + e) * 3;
-    const double rx = r[0], ry = r[1], rz = r[2];
-    const uint32_t *mrow = masks + ((size_t)w * s.n_elec + e) * mw;
-    for (int j = t; j < mw; j += kC1Threads) bits_s[j] = mrow[j];
-    __syncthreads();
-    const int K = aos_from_mask<kC1Threads>(s, bits_s, mw, idx_s, nullptr, warp_s);
 
-    float vh[NJ], vc[NJ], vl[NJ], lh[NJ], lc[NJ], ll[NJ];
+    for (int q = t; q < kC15G * mw; q += kC15Threads) {
+        const int g = q / mw, j = q - g * mw;
+        mk_s[q] = (g < ng) ? masks[((size_t)(w0 + g) * s.n_elec + e) * mw + j] : 0u;
+    }
+    __syncthreads();
+    for (int j = t; j < mw; j += kC15Threads) {
+        uint32_t u = 0;
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) { vh[j] = vc[j] = vl[j] = 0.f; lh[j] = lc[j] = ll[j] = 0.f; }
+        for (int g = 0; g < kC15G; ++g) u |= mk_s[g * mw + j];
+        un_s[j] = u;
+    }
+    __syncthreads();
+    const int K = aos_from_mask<kC15Threads>(s, un_s, mw, idx_s, nullptr, warp_s);
+
+    float vh[kC15G][NJ], vc[kC15G][NJ], vl[kC15G][NJ], lh[kC15G][NJ], lc[kC15G][NJ], ll[kC15G][NJ];
+#pragma unroll
+    for (int g = 0; g < kC15G; ++g)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            vh[g][j] = vc[g][j] = vl[g][j] = 0.f;
+            lh[g][j] = lc[g][j] = ll[g][j] = 0.f;
+        }
     const int kwarp = t & ~31;
 
-    for (int k0 = 0; k0 < K; k0 += kC1Chunk) {
-        const int kc = min(kC1Chunk, K - k0);
-        for (int m = t; m < kc; m += kC1Threads) {
-            double v[5];
-            ao_eval_f64(s, idx_s[k0 + m], rx, ry, rz, v);
-            const float h0 = (float)v[0], h4 = (float)v[4];
-            b_s[m] = h0;
-            b_s[kC1Chunk + m] = (float)(v[0] - (double)h0);
-            b_s[2 * kC1Chunk + m] = h4;
-            b_s[3 * kC1Chunk + m] = (float)(v[4] - (double)h4);
+    for (int k0 = 0; k0 < K; k0 += kC15Chunk) {
+        const int kc = min(kC15Chunk, K - k0);
+        for (int q = t; q < kC15G * kc; q += kC15Threads) {
+            const int g = q / kc, m = q - g * kc;
+            const int mu = idx_s[k0 + m];
+            const int sh = s.ao_shell[mu];
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < ng && ((mk_s[g * mw + (sh >> 5)] >> (sh & 31)) & 1u)) {
+                const double *r = R + ((size_t)(w0 + g) * s.n_elec + e) * 3;
+                double v, lp;
+                ao_val_lap_f64(s, mu, r[0], r[1], r[2], v, lp);
+                b.x = (float)v;
+                b.y = (float)(v - (double)b.x);
+                b.z = (float)lp;
+                b.w = (float)(lp - (double)b.z);
+            }
+            b_s[g * kC15Chunk + m] = b;
         }
         __syncthreads();
-        for (int m = 0; m < kc; ++m) {
-            const size_t row = (size_t)idx_s[k0 + m] * ns;
-            const float b0h = b_s[m], b0l = b_s[kC1Chunk + m];
-            const float b4h = b_s[2 * kC1Chunk + m], b4l = b_s[3 * kC1Chunk + m];
+        float ah[NJ], al[NJ];
+        {
+            const size_t row = (size_t)idx_s[k0] * ns;
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
-                if (kwarp + kC1Threads * j >= ns) continue;   // whole warp beyond ns
-                const int k = t + kC1Threads * j;
-                const float ah = (k < ns) ? __ldg(Ahi + row + k) : 0.f;
-                const float al = (k < ns) ? __ldg(Alo + row + k) : 0.f;
-                ff_acc(ah, al, b0h, b0l, vh[j], vc[j], vl[j]);
-                ff_acc(ah, al, b4h, b4l, lh[j], lc[j], ll[j]);
+                const int k = t + kC15Threads * j;
+                ah[j] = (k < ns) ? __ldg(Ahi + row + k) : 0.f;
+                al[j] = (k < ns) ? __ldg(Alo + row + k) : 0.f;
             }
+        }
+        for (int m = 0; m < kc; ++m) {
+            // next AO's coefficients in flight while this one is accumulated
+            float nh[NJ], nl[NJ];
+            const size_t nrow = (size_t)idx_s[k0 + min(m + 1, kc - 1)] * ns;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                const int k = t + kC15Threads * j;
+                nh[j] = (k < ns) ? __ldg(Ahi + nrow + k) : 0.f;
+                nl[j] = (k < ns) ? __ldg(Alo + nrow + k) : 0.f;
+            }
+#pragma unroll
+            for (int g = 0; g < kC15G; ++g) {
+                const float4 b = b_s[g * kC15Chunk + m];
+                if (b.x == 0.f && b.z == 0.f) continue;     // screened out (block-uniform)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    if (kwarp + kC15Threads * j >= ns) continue;
+                    ff_acc(ah[j], al[j], b.x, b.y, vh[g][j], vc[g][j], vl[g][j]);
+                    ff_acc(ah[j], al[j], b.z, b.w, lh[g][j], lc[g][j], ll[g][j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) { ah[j] = nh[j]; al[j] = nl[j]; }
         }
         __syncthreads();
     }
     const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
-    const size_t off = (size_t)w * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-        const int k = t + kC1Threads * j;
-        if (k < ns) {
-            X[off + k] = (double)vh[j] + ((double)vc[j] + (double)vl[j]);
-            L5[off + k] = (double)lh[j] + ((double)lc[j] + (double)ll[j]);
+    for (int g = 0; g < kC15G; ++g) {
+        if (g >= ng) break;
+        const size_t off = (size_t)(w0 + g) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int k = t + kC15Threads * j;
+            if (k < ns) {
+                X[off + k] = (double)vh[g][j] + ((double)vc[g][j] + (double)vl[g][j]);
+                L5[off + k] = (double)lh[g][j] + ((double)lc[g][j] + (double)ll[g][j]);
+            }
         }
     }
 }
 
 // ------------------------------------------------------------ tcgen05 path
 constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;   // two threads per walker row
 constexpr uint32_t kAPlaneBytes = TC_M * TC_K * 2;     // 16 KB, one output x one split
 constexpr uint32_t kBPlaneBytes = TC_K * TC_N * 2;     // 16 KB, one split
 constexpr uint32_t kBLbo = 1024;                        // MN-major: next 64-column atom
@@ -314,6 +399,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
 
     const SysDev &s = p.s;
     const int t = threadIdx.x, warp = t >> 5;
+    const int row = t & (TC_M - 1), khalf = t >> 7;   // walker row, half of the K step
     const int e = blockIdx.y;
     const int spin = e >= s.n_up;
     const int ei = spin ? e - s.n_up : e;
@@ -323,7 +409,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     const int nspad = p.tt.ns_pad[spin];
     const int f16 = p.tt.f16;
     const int ncols = min(TC_N, nspad - k0);   // multiple of 64
-    const int w = blockIdx.z * TC_M + t;       // this thread's walker (row)
+    const int w = blockIdx.z * TC_M + row;     // this thread's walker
     const bool wvalid = w < p.nw;
     const int mw = p.mw;
 
@@ -363,10 +449,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     const uint32_t idesc = umma_idesc_f16(TC_M, ncols, f16 ? 0 : 1);
     const uint64_t kWait = 2000000000ull;   // 2 s per wait
 
-    // this walker's position relative to the current atom
+    // this walker's position as float pairs (hi + lo)
     const double *rw = p.R + ((size_t)(wvalid ? w : 0) * s.n_elec + e) * 3;
-    const double rx = rw[0], ry = rw[1], rz = rw[2];
-    const uint32_t *my_mask = mask_s + t * mw;
+    const float rxh = (float)rw[0], ryh = (float)rw[1], rzh = (float)rw[2];
+    const float rxl = (float)(rw[0] - (double)rxh), ryl = (float)(rw[1] - (double)ryh),
+                rzl = (float)(rw[2] - (double)rzh);
+    const uint32_t *my_mask = mask_s + row * mw;
+    const float *__restrict__ pgf = p.tt.pgf;
+    const float *__restrict__ pcf = p.tt.pcf;
+    const float *__restrict__ scf = p.tt.scf;
+    const float *__restrict__ Qhi = p.tt.Qhi;
+    const float *__restrict__ Qlo = p.tt.Qlo;
     const uint16_t *__restrict__ Bhi = p.tt.hi[spin];
     const uint16_t *__restrict__ Blo = p.tt.lo[spin];
     const float isc0 = p.tt.in_scale[0], isc1 = p.tt.in_scale[1], isc2 = p.tt.in_scale[2];
@@ -377,10 +470,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
             __syncthreads();
             if (s_abort) break;
         }
-        // A operand: derivative values of 64 AOs for this walker (row t)
+        // A operand: gradient values of 32 AOs (this thread's half) for walker `row`
         int last_atom = -1;
         float dx = 0.f, dy = 0.f, dz = 0.f, d2 = 0.f;
-        for (int c8 = 0; c8 < TC_K / 8; ++c8) {
+        for (int c8 = khalf * (TC_K / 16); c8 < (khalf + 1) * (TC_K / 16); ++c8) {
             float v[TC_OUT][8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -393,16 +486,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
                         const int a = s.sh_atom[sh];
                         if (a != last_atom) {
                             last_atom = a;
-                            dx = (float)(rx - s.Q[3 * a]);
-                            dy = (float)(ry - s.Q[3 * a + 1]);
-                            dz = (float)(rz - s.Q[3 * a + 2]);
+                            dx = (rxh - Qhi[3 * a]) + (rxl - Qlo[3 * a]);
+                            dy = (ryh - Qhi[3 * a + 1]) + (ryl - Qlo[3 * a + 1]);
+                            dz = (rzh - Qhi[3 * a + 2]) + (rzl - Qlo[3 * a + 2]);
                             d2 = dx * dx + dy * dy + dz * dz;
                         }
                         float g = 0.f, gd = 0.f;
                         const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
                         for (int pr = 0; pr < np; ++pr) {
-                            const float gam = (float)s.pg[p0 + pr];
-                            const float ce = (float)s.pc[p0 + pr] * expf(-gam * d2);
+                            const float gam = pgf[p0 + pr];
+                            const float ce = pcf[p0 + pr] * expf(-gam * d2);
                             g += ce;
                             gd += gam * ce;
                         }
@@ -418,7 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
                         const float dpx = nx ? nx * ip(dx, nx - 1) : 0.f;
                         const float dpy = ny ? ny * ip(dy, ny - 1) : 0.f;
                         const float dpz = nz ? nz * ip(dz, nz - 1) : 0.f;
-                        const float c = (float)s.ao_scale[mu];
+                        const float c = scf[mu];
                         const float m2gd = -2.f * gd;
                         g1 = c * (dpx * py * pz * g + m2gd * dx * P);
                         g2 = c * (px * dpy * pz * g + m2gd * dy * P);
@@ -432,7 +525,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
                 uint32_t hi[4], lo[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) split2(v[l][2 * q], v[l][2 * q + 1], f16, hi[q], lo[q]);
-                const uint32_t off = a_off(t, c8);
+                const uint32_t off = a_off(row, c8);
                 *reinterpret_cast<uint4 *>(As + (2 * l) * kAPlaneBytes + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
                 *reinterpret_cast<uint4 *>(As + (2 * l + 1) * kAPlaneBytes + off) =
                     make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -489,9 +582,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     float *crow = p.Cg + (size_t)(wvalid ? w : 0) * TC_OUT * msz + (spin ? TC_OUT * (size_t)s.n_up * s.n_up : 0) +
                   (size_t)ei * ns;
     for (int l = 0; l < TC_OUT; ++l) {
-        for (int cb = 0; cb < ncols; cb += 32) {
+        for (int cb = (warp >> 2) * 32; cb < ncols; cb += 64) {   // warps w and w+4 share lanes, split columns
             uint32_t v[32];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(l * TC_N + cb);
+            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(l * TC_N + cb);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -532,11 +625,12 @@ static cudaError_t launch_c15_nj(const SysDev &s, int nw, const double *R, const
                                  const float *const *Ahi, const float *const *Alo, double *X, double *L5,
                                  cudaStream_t st)
 {
-    const size_t sm = sizeof(float) * 4 * kC1Chunk + sizeof(uint32_t) * mw + sizeof(int) * (size_t)s.n_ao;
+    const size_t sm = sizeof(float4) * kC15G * kC15Chunk + sizeof(uint32_t) * (kC15G + 1) * mw +
+                      sizeof(int) * (size_t)s.n_ao;
     cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    dim3 grid(s.n_elec, nw);
-    k_c15_ff<NJ><<<grid, kC1Threads, sm, st>>>(s, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], X, L5);
+    dim3 grid(s.n_elec, (nw + kC15G - 1) / kC15G);
+    k_c15_ff<NJ><<<grid, kC15Threads, sm, st>>>(s, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], X, L5);
     return cudaGetLastError();
 }
 
@@ -545,15 +639,11 @@ cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32
 {
     if (nw == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    switch ((nmax + kC1Threads - 1) / kC1Threads) {
+    switch ((nmax + kC15Threads - 1) / kC15Threads) {
     case 1: return launch_c15_nj<1>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
     case 2: return launch_c15_nj<2>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
     case 3: return launch_c15_nj<3>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
     case 4: return launch_c15_nj<4>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
-    case 5: return launch_c15_nj<5>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
-    case 6: return launch_c15_nj<6>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
-    case 7: return launch_c15_nj<7>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
-    case 8: return launch_c15_nj<8>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
     default: return cudaErrorInvalidValue;
     }
 }

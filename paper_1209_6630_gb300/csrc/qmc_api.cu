@@ -122,6 +122,74 @@ struct Blob {
     }
 };
 
+// Device copies of the MO coefficients: FP64 [n_ao][n_s]; BF16 hi/lo planes
+// and FP16 hi/lo planes of A * 2^a_exp, [n_ao][n_s padded to 64]; float-float
+// planes [n_ao][n_s].  a_exp is chosen so that max |A| * 2^a_exp <= 8192.
+struct MoLayout {
+    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oFh[2], oFl[2];
+    int ns_pad[2], a_exp[2];
+};
+
+static void build_mo(int nao, int nu, int nd, int a_dtype, const void *A_up, const void *A_dn, Blob &b,
+                     MoLayout &L)
+{
+    for (int spin = 0; spin < 2; ++spin) {
+        const int ns = spin ? nd : nu;
+        const void *src = spin ? A_dn : A_up;
+        std::vector<double> A64((size_t)nao * ns);
+        for (size_t q = 0; q < A64.size(); ++q)
+            A64[q] = a_dtype == QMC_DTYPE_F64 ? static_cast<const double *>(src)[q]
+                                              : (double) static_cast<const float *>(src)[q];
+        L.oA[spin] = b.add(A64.data(), sizeof(double) * A64.size());
+        const int np = ((ns + 63) / 64) * 64;
+        L.ns_pad[spin] = np;
+        double amax = 0.0;
+        for (double a : A64) amax = std::max(amax, fabs(a));
+        L.a_exp[spin] = amax > 0.0 ? (int)floor(log2(8192.0 / amax)) : 0;
+        const double asc = ldexp(1.0, L.a_exp[spin]);
+        std::vector<uint16_t> bh((size_t)nao * np, 0), bl((size_t)nao * np, 0);
+        std::vector<uint16_t> hh((size_t)nao * np, 0), hl((size_t)nao * np, 0);
+        std::vector<float> fh((size_t)nao * ns), fl((size_t)nao * ns);
+        for (int mu = 0; mu < nao; ++mu)
+            for (int k = 0; k < ns; ++k) {
+                const double a = A64[(size_t)mu * ns + k];
+                const uint16_t h = bf16_bits((float)a);
+                bh[(size_t)mu * np + k] = h;
+                bl[(size_t)mu * np + k] = bf16_bits((float)(a - (double)bf16_value(h)));
+                const double as = a * asc;
+                const __half h16 = __float2half_rn((float)as);
+                const __half l16 = __float2half_rn((float)(as - (double)__half2float(h16)));
+                memcpy(&hh[(size_t)mu * np + k], &h16, 2);
+                memcpy(&hl[(size_t)mu * np + k], &l16, 2);
+                const float f = (float)a;
+                fh[(size_t)mu * ns + k] = f;
+                fl[(size_t)mu * ns + k] = (float)(a - (double)f);
+            }
+        L.oBh[spin] = b.add(bh.data(), 2 * bh.size());
+        L.oBl[spin] = b.add(bl.data(), 2 * bl.size());
+        L.oHh[spin] = b.add(hh.data(), 2 * hh.size());
+        L.oHl[spin] = b.add(hl.data(), 2 * hl.size());
+        L.oFh[spin] = b.add(fh.data(), 4 * fh.size());
+        L.oFl[spin] = b.add(fl.data(), 4 * fl.size());
+    }
+}
+
+static void point_mo(qmc_system *sys, char *dev, const MoLayout &L)
+{
+    MixedTables &mt = sys->mixed;
+    for (int spin = 0; spin < 2; ++spin) {
+        sys->d.A64[spin] = reinterpret_cast<const double *>(dev + L.oA[spin]);
+        mt.bhi[spin] = reinterpret_cast<const uint16_t *>(dev + L.oBh[spin]);
+        mt.blo[spin] = reinterpret_cast<const uint16_t *>(dev + L.oBl[spin]);
+        mt.hhi[spin] = reinterpret_cast<const uint16_t *>(dev + L.oHh[spin]);
+        mt.hlo[spin] = reinterpret_cast<const uint16_t *>(dev + L.oHl[spin]);
+        mt.fhi[spin] = reinterpret_cast<const float *>(dev + L.oFh[spin]);
+        mt.flo[spin] = reinterpret_cast<const float *>(dev + L.oFl[spin]);
+        mt.ns_pad[spin] = L.ns_pad[spin];
+        mt.a_exp[spin] = L.a_exp[spin];
+    }
+}
+
 }  // namespace qmc
 
 using namespace qmc;
@@ -203,16 +271,6 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     std::vector<int> ao_pow(nao);
     for (int mu = 0; mu < nao; ++mu)
         ao_pow[mu] = d->ao_pow[3 * mu] | (d->ao_pow[3 * mu + 1] << 8) | (d->ao_pow[3 * mu + 2] << 16);
-    std::vector<double> A64[2];
-    for (int spin = 0; spin < 2; ++spin) {
-        const int ns = spin ? nd : nu;
-        const void *src = spin ? d->A_dn : d->A_up;
-        A64[spin].resize((size_t)nao * ns);
-        for (size_t q = 0; q < (size_t)nao * ns; ++q)
-            A64[spin][q] = d->a_dtype == QMC_DTYPE_F64 ? static_cast<const double *>(src)[q]
-                                                       : (double) static_cast<const float *>(src)[q];
-    }
-
     Blob b;
     const size_t oQ = b.add(d->Q, sizeof(double) * 3 * na);
     const size_t oZ = b.add(d->Z, sizeof(double) * na);
@@ -229,46 +287,14 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     const size_t oAP = b.add(ao_pow.data(), sizeof(int) * nao);
     const size_t oAO = b.add(d->ao_shell, sizeof(int) * nao);
     const size_t oSC = b.add(d->ao_scale, sizeof(double) * nao);
-    const size_t oA0 = b.add(A64[0].data(), sizeof(double) * A64[0].size());
-    const size_t oA1 = b.add(A64[1].data(), sizeof(double) * A64[1].size());
-    // mixed path: BF16 hi/lo planes [n_ao][ns_pad] (zero padded to 64 columns)
-    // and float-float planes [n_ao][ns] of the MO coefficients
-    // FP16 planes hold A * 2^a_exp, a_exp chosen so that max |A| * 2^a_exp <= 8192
-    size_t oBh[2], oBl[2], oHh[2], oHl[2], oFh[2], oFl[2];
-    int ns_pad[2], a_exp[2];
-    for (int spin = 0; spin < 2; ++spin) {
-        const int ns = spin ? nd : nu;
-        const int np = ((ns + 63) / 64) * 64;
-        ns_pad[spin] = np;
-        double amax = 0.0;
-        for (double a : A64[spin]) amax = std::max(amax, fabs(a));
-        a_exp[spin] = amax > 0.0 ? (int)floor(log2(8192.0 / amax)) : 0;
-        const double asc = ldexp(1.0, a_exp[spin]);
-        std::vector<uint16_t> bh((size_t)nao * np, 0), bl((size_t)nao * np, 0);
-        std::vector<uint16_t> hh((size_t)nao * np, 0), hl((size_t)nao * np, 0);
-        std::vector<float> fh((size_t)nao * ns), fl((size_t)nao * ns);
-        for (int mu = 0; mu < nao; ++mu)
-            for (int k = 0; k < ns; ++k) {
-                const double a = A64[spin][(size_t)mu * ns + k];
-                const uint16_t h = bf16_bits((float)a);
-                bh[(size_t)mu * np + k] = h;
-                bl[(size_t)mu * np + k] = bf16_bits((float)(a - (double)bf16_value(h)));
-                const double as = a * asc;
-                const __half h16 = __float2half_rn((float)as);
-                const __half l16 = __float2half_rn((float)(as - (double)__half2float(h16)));
-                memcpy(&hh[(size_t)mu * np + k], &h16, 2);
-                memcpy(&hl[(size_t)mu * np + k], &l16, 2);
-                const float f = (float)a;
-                fh[(size_t)mu * ns + k] = f;
-                fl[(size_t)mu * ns + k] = (float)(a - (double)f);
-            }
-        oBh[spin] = b.add(bh.data(), 2 * bh.size());
-        oBl[spin] = b.add(bl.data(), 2 * bl.size());
-        oHh[spin] = b.add(hh.data(), 2 * hh.size());
-        oHl[spin] = b.add(hl.data(), 2 * hl.size());
-        oFh[spin] = b.add(fh.data(), 4 * fh.size());
-        oFl[spin] = b.add(fl.data(), 4 * fl.size());
-    }
+    // FP32 copies of the basis tables and float-pair positions for the tensor-core producer
+    std::vector<float> pgf(d->n_prim), pcf(d->n_prim), scf(nao), qhi(3 * na), qlo(3 * na);
+    for (int q = 0; q < d->n_prim; ++q) { pgf[q] = (float)d->prim_gamma[q]; pcf[q] = (float)d->prim_coef[q]; }
+    for (int mu = 0; mu < nao; ++mu) scf[mu] = (float)d->ao_scale[mu];
+    for (int q = 0; q < 3 * na; ++q) { qhi[q] = (float)d->Q[q]; qlo[q] = (float)(d->Q[q] - (double)qhi[q]); }
+    const size_t oPgf = b.add(pgf.data(), 4 * pgf.size()), oPcf = b.add(pcf.data(), 4 * pcf.size());
+    const size_t oScf = b.add(scf.data(), 4 * scf.size());
+    const size_t oQh = b.add(qhi.data(), 4 * qhi.size()), oQl = b.add(qlo.data(), 4 * qlo.size());
     // AO derivative values enter the FP16 split scaled by 2^b_exp (bound * 2^b_exp <= 8192)
     double dbound[2] = {0.0, 0.0};
     for (int sh = 0; sh < nsh; ++sh) {
@@ -287,6 +313,19 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     sys->allocs.push_back(dev);
     e = cudaMemcpy(dev, b.host.data(), b.host.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { qmc_system_free(sys); return cuda_fail(e, "qmc_system_load: cudaMemcpy"); }
+    Blob bm;
+    MoLayout mo;
+    build_mo(nao, nu, nd, d->a_dtype, d->A_up, d->A_dn, bm, mo);
+    char *mdev = nullptr;
+    e = cudaMalloc(&mdev, bm.host.size());
+    if (e != cudaSuccess) { qmc_system_free(sys); return cuda_fail(e, "qmc_system_load: cudaMalloc"); }
+    sys->allocs.push_back(mdev);
+    e = cudaMemcpy(mdev, bm.host.data(), bm.host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { qmc_system_free(sys); return cuda_fail(e, "qmc_system_load: cudaMemcpy"); }
+    sys->mo_dev = mdev;
+    sys->mo_bytes = bm.host.size();
+    sys->a_dtype = d->a_dtype;
+    point_mo(sys, mdev, mo);
 
     SysDev &s = sys->d;
     s.n_atom = na; s.n_shell = nsh; s.n_ao = nao; s.n_up = nu; s.n_dn = nd; s.n_elec = nu + nd;
@@ -305,23 +344,34 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     s.ao_pow = reinterpret_cast<const int *>(dev + oAP);
     s.ao_shell = reinterpret_cast<const int *>(dev + oAO);
     s.ao_scale = reinterpret_cast<const double *>(dev + oSC);
-    s.A64[0] = reinterpret_cast<const double *>(dev + oA0);
-    s.A64[1] = reinterpret_cast<const double *>(dev + oA1);
     s.vnn = vnn;
     MixedTables &mt = sys->mixed;
-    for (int spin = 0; spin < 2; ++spin) {
-        mt.bhi[spin] = reinterpret_cast<const uint16_t *>(dev + oBh[spin]);
-        mt.blo[spin] = reinterpret_cast<const uint16_t *>(dev + oBl[spin]);
-        mt.hhi[spin] = reinterpret_cast<const uint16_t *>(dev + oHh[spin]);
-        mt.hlo[spin] = reinterpret_cast<const uint16_t *>(dev + oHl[spin]);
-        mt.a_exp[spin] = a_exp[spin];
-        mt.fhi[spin] = reinterpret_cast<const float *>(dev + oFh[spin]);
-        mt.flo[spin] = reinterpret_cast<const float *>(dev + oFl[spin]);
-        mt.ns_pad[spin] = ns_pad[spin];
-    }
     mt.b_exp = b_exp;
     mt.mask_words = (nsh + 31) / 32;
+    mt.pgf = reinterpret_cast<const float *>(dev + oPgf);
+    mt.pcf = reinterpret_cast<const float *>(dev + oPcf);
+    mt.scf = reinterpret_cast<const float *>(dev + oScf);
+    mt.Qhi = reinterpret_cast<const float *>(dev + oQh);
+    mt.Qlo = reinterpret_cast<const float *>(dev + oQl);
     *out = sys;
+    return QMC_OK;
+}
+
+extern "C" int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void *A_dn)
+{
+    if (!sys) return invalid("qmc_system_set_mo: null system");
+    if (a_dtype != QMC_DTYPE_F64 && a_dtype != QMC_DTYPE_F32) return invalid("qmc_system_set_mo: a_dtype");
+    if ((sys->d.n_up && !A_up) || (sys->d.n_dn && !A_dn)) return invalid("qmc_system_set_mo: null matrix");
+    Blob bm;
+    MoLayout mo;
+    build_mo(sys->d.n_ao, sys->d.n_up, sys->d.n_dn, a_dtype, A_up, A_dn, bm, mo);
+    if (bm.host.size() != sys->mo_bytes) return invalid("qmc_system_set_mo: layout mismatch");
+    cudaError_t e = cudaSetDevice(sys->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // no evaluation may still read the old tables
+    if (e == cudaSuccess) e = cudaMemcpy(sys->mo_dev, bm.host.data(), bm.host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_system_set_mo");
+    sys->a_dtype = a_dtype;
+    point_mo(sys, static_cast<char *>(sys->mo_dev), mo);
     return QMC_OK;
 }
 
@@ -435,16 +485,20 @@ CView cview(const Plan &p, const Carve &c)
 
 // Steps a1-a3 for one chunk of walkers: C1 -> c.X (FP64), C2..C5 -> c.Cd
 // (FP64 in the FP64 path, FP32 in the mixed path).
+// `mark(q)` (if set) records event q after product kernel q-4 (mask, C1/C5, tensor cores).
+template <typename Mark>
 cudaError_t run_products(const qmc_system *sys, int precision, int nw, const double *Rc, const Carve &c,
-                         cudaStream_t st)
+                         cudaStream_t st, Mark mark)
 {
     const SysDev &s = sys->d;
     if (precision == QMC_PREC_F64) return launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
     const MixedTables &mt = sys->mixed;
     cudaError_t e = launch_shell_mask(s, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
+    if ((e = mark(4)) != cudaSuccess) return e;
     e = launch_c15_ff(s, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, c.X, c.L5, st);
     if (e != cudaSuccess) return e;
+    if ((e = mark(5)) != cudaSuccess) return e;
     TcTables tt;
     tt.f16 = precision == QMC_PREC_MIXED ? 1 : 0;
     for (int spin = 0; spin < 2; ++spin) {
@@ -455,6 +509,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
             tt.out_scale[spin][l] = tt.f16 ? (float)ldexp(1.0, -(mt.a_exp[spin] + mt.b_exp)) : 1.0f;
     }
     for (int l = 0; l < 3; ++l) tt.in_scale[l] = tt.f16 ? (float)ldexp(1.0, mt.b_exp) : 1.0f;
+    tt.pgf = mt.pgf; tt.pcf = mt.pcf; tt.scf = mt.scf; tt.Qhi = mt.Qhi; tt.Qlo = mt.Qlo;
     return launch_tc_contract(s, nw, Rc, c.masks, mt.mask_words, tt, static_cast<float *>(c.Cd), c.st, st);
 }
 
@@ -475,7 +530,7 @@ namespace {
 // Events bracketing the three stages of one evaluation (contraction a1-a3,
 // inverse a4, energies a5-a6); created on first use per thread.
 struct StageEvents {
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int device = -1;
     ~StageEvents()
     {
@@ -501,7 +556,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
 {
     if (!sys || !out) return invalid("qmc_walkers_eval: null argument");
     if (n_walk < 0) return invalid("qmc_walkers_eval: n_walk < 0");
-    if (stage_ms) for (int q = 0; q < 4; ++q) stage_ms[q] = 0.0f;
+    if (stage_ms) for (int q = 0; q < 8; ++q) stage_ms[q] = 0.0f;
     if (n_walk == 0) return QMC_OK;
     if (!R || !out->logpsi || !out->sign || !out->drift || !out->e_loc || !out->status)
         return invalid("qmc_walkers_eval: null required pointer");
@@ -529,7 +584,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
         if ((e = mark(0)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
-        e = run_products(sys, precision, nw, Rc, c, st);
+        e = run_products(sys, precision, nw, Rc, c, st, mark);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: products launch");
         if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         GjJob jobs[2];
@@ -561,6 +616,16 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
                     return cuda_fail(e, "qmc_walkers_eval: elapsed");
                 stage_ms[q] += ms;
                 stage_ms[3] += ms;
+            }
+            if (precision != QMC_PREC_F64) {   // split of stage 0 into its three kernels
+                float m4 = 0.0f, m5 = 0.0f, m6 = 0.0f;
+                if ((e = cudaEventElapsedTime(&m4, t_events.ev[0], t_events.ev[4])) != cudaSuccess ||
+                    (e = cudaEventElapsedTime(&m5, t_events.ev[4], t_events.ev[5])) != cudaSuccess ||
+                    (e = cudaEventElapsedTime(&m6, t_events.ev[5], t_events.ev[1])) != cudaSuccess)
+                    return cuda_fail(e, "qmc_walkers_eval: elapsed");
+                stage_ms[4] += m4; stage_ms[5] += m5; stage_ms[6] += m6;
+            } else {
+                stage_ms[5] += stage_ms[0];
             }
         }
     }
@@ -609,7 +674,7 @@ extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const doub
         const double *Rc = R + (size_t)w0 * s.n_elec * 3;
         e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: memset");
-        e = run_products(sys, precision, nw, Rc, c, st);
+        e = run_products(sys, precision, nw, Rc, c, st, [](int) { return cudaSuccess; });
         if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: products launch");
         char *o = reinterpret_cast<char *>(C + (size_t)w0 * 5 * p.msz);
         // per walker: [C1 up][C2..C5 up][C1 dn][C2..C5 dn]

@@ -47,6 +47,9 @@ struct MixedTables {
     int a_exp[2];                      // FP16 planes hold A * 2^a_exp
     int b_exp;                         // FP16 path: AO gradients enter scaled by 2^b_exp
     int mask_words;                    // 32-bit words of a per-electron shell bitmask
+    const float *pgf, *pcf;            // FP32 copies of exponents and coefficients [n_prim]
+    const float *scf;                  // FP32 copy of ao_scale [n_ao]
+    const float *Qhi, *Qlo;            // nuclear positions as float pairs [n_atom][3]
 };
 
 struct TcTables {                      // what the tensor-core kernel reads, one precision mode
@@ -55,6 +58,7 @@ struct TcTables {                      // what the tensor-core kernel reads, one
     int f16;                           // 1: FP16 operands, 0: BF16
     float out_scale[2][3];             // multiply accumulator (spin, gradient component) by this (power of 2)
     float in_scale[3];                 // multiply AO gradient component l by this before the split
+    const float *pgf, *pcf, *scf, *Qhi, *Qlo;
 };
 
 // Per-matrix parameters for the Gauss-Jordan kernel (one entry per spin).
@@ -117,4 +121,7 @@ struct qmc_system {
     std::vector<double> R2_host;
     qmc::MixedTables mixed;
     int max_shell_per_atom;
+    void *mo_dev = nullptr;           // device tables derived from the MO coefficients
+    size_t mo_bytes = 0;
+    int a_dtype = 0;
 };
