@@ -102,17 +102,29 @@ __device__ int aos_from_mask(const SysDev &s, const uint32_t *bits, int mw, int 
 
 // ------------------------------------------------ C1 and C5, FP64-accurate
 
-// Neumaier-compensated float-float accumulation of a*b, with a = ah + al and
-// b = bh + bl: sh + sc holds the sum of the leading products ah*bh, sl the
-// exact rounding errors of those products plus the cross terms.
-__device__ __forceinline__ void ff_acc(float ah, float al, float bh, float bl, float &sh, float &sc, float &sl)
+// Exact float-float accumulation of a*b (a = ah + al, b = bh + bl) into a
+// biased pair (sh, sl): sh starts at a power of two BIG >= 2 max|partial|, so
+// |sh| >= |ah*bh| always holds and Fast2Sum is error-free; sl collects the
+// rounding errors of the sums and products and the cross terms.  The value
+// is (sh - BIG) + sl (the subtraction is exact).  9 FP32 instructions.
+__device__ __forceinline__ void ff_acc(float ah, float al, float bh, float bl, float &sh, float &sl)
 {
     const float p = ah * bh;
     const float pe = fmaf(ah, bh, -p);
-    sl += pe + fmaf(ah, bl, al * bh);
-    const float t = sh + p;
-    sc += (fabsf(sh) >= fabsf(p)) ? ((sh - t) + p) : ((p - t) + sh);
-    sh = t;
+    const float sn = sh + p;
+    const float e = p - (sn - sh);
+    sl = fmaf(ah, bl, sl);
+    sl = fmaf(al, bh, sl);
+    sl += pe + e;
+    sh = sn;
+}
+
+__device__ __forceinline__ float pow2_above(float x)   // smallest power of two >= x (x > 0), 1 if x == 0
+{
+    if (!(x > 0.f)) return 1.f;
+    int ex;
+    const float m = frexpf(x, &ex);                     // x = m 2^ex, m in [0.5, 1)
+    return ldexpf(1.f, m == 0.5f ? ex - 1 : ex);
 }
 
 // Value and Laplacian of AO mu at r, FP64 (the two quantities C1 and C5 need).
@@ -147,18 +159,21 @@ __device__ __forceinline__ void ao_val_lap_f64(const SysDev &s, int mu, double r
 
 // One CTA per (electron index e, group of kC15G walkers).  The float-float
 // MO coefficients of an AO are loaded once per thread and applied to every
-// walker of the group (the same electron of nearby-indexed walkers sees
-// largely the same AOs); AOs screened out for a walker are skipped.
+// walker of the group (the same electron of neighbouring walkers sees largely
+// the same AOs); AOs screened out for a walker are skipped.  The AO values
+// of up to kC15Chunk union AOs are staged at once; a larger union is handled
+// in several chunks whose partial sums are added in global memory.
 constexpr int kC15G = 4;
 constexpr int kC15Threads = 256;
-constexpr int kC15Chunk = 256;
+constexpr int kC15Chunk = 1024;
 
 template <int NJ>
-__global__ void __launch_bounds__(kC15Threads, 1) k_c15_ff(SysDev s, int nw, const double *__restrict__ R,
-                                                        const uint32_t *__restrict__ masks, int mw,
-                                                        const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
-                                                        const float *__restrict__ Ahi1, const float *__restrict__ Alo1,
-                                                        double *__restrict__ X, double *__restrict__ L5)
+__global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, const double *__restrict__ R,
+                                                           const uint32_t *__restrict__ masks, int mw,
+                                                           const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
+                                                           const float *__restrict__ Ahi1, const float *__restrict__ Alo1,
+                                                           const float *__restrict__ cmax0, const float *__restrict__ cmax1,
+                                                           double *__restrict__ X, double *__restrict__ L5)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *b_s = reinterpret_cast<float4 *>(smem_raw);            // [kC15G][kC15Chunk]: (vh, vl, lh, ll)
@@ -166,8 +181,9 @@ __global__ void __launch_bounds__(kC15Threads, 1) k_c15_ff(SysDev s, int nw, con
     uint32_t *un_s = mk_s + kC15G * mw;                            // [mw]
     int *idx_s = reinterpret_cast<int *>(un_s + mw);               // [n_ao]
     __shared__ int warp_s[kC15Threads / 32];
+    __shared__ float bsum_s[kC15G][2];                             // sum |b| per walker and output
 
-    const int e = blockIdx.x, t = threadIdx.x;
+    const int e = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int w0 = blockIdx.y * kC15G;
     const int ng = min(kC15G, nw - w0);
     const int spin = e >= s.n_up;
@@ -175,6 +191,7 @@ __global__ void __launch_bounds__(kC15Threads, 1) k_c15_ff(SysDev s, int nw, con
     const int ns = spin ? s.n_dn : s.n_up;
     const float *__restrict__ Ahi = spin ? Ahi1 : Ahi0;
     const float *__restrict__ Alo = spin ? Alo1 : Alo0;
+    const float *__restrict__ cmax = spin ? cmax1 : cmax0;
 
     for (int q = t; q < kC15G * mw; q += kC15Threads) {
         const int g = q / mw, j = q - g * mw;
@@ -190,15 +207,14 @@ __global__ void __launch_bounds__(kC15Threads, 1) k_c15_ff(SysDev s, int nw, con
     __syncthreads();
     const int K = aos_from_mask<kC15Threads>(s, un_s, mw, idx_s, nullptr, warp_s);
 
-    float vh[kC15G][NJ], vc[kC15G][NJ], vl[kC15G][NJ], lh[kC15G][NJ], lc[kC15G][NJ], ll[kC15G][NJ];
-#pragma unroll
-    for (int g = 0; g < kC15G; ++g)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            vh[g][j] = vc[g][j] = vl[g][j] = 0.f;
-            lh[g][j] = lc[g][j] = ll[g][j] = 0.f;
-        }
     const int kwarp = t & ~31;
+    float cm[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = t + kC15Threads * j;
+        cm[j] = (k < ns) ? cmax[k] : 0.f;
+    }
+    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
 
     for (int k0 = 0; k0 < K; k0 += kC15Chunk) {
         const int kc = min(kC15Chunk, K - k0);
@@ -219,25 +235,48 @@ __global__ void __launch_bounds__(kC15Threads, 1) k_c15_ff(SysDev s, int nw, con
             b_s[g * kC15Chunk + m] = b;
         }
         __syncthreads();
-        float ah[NJ], al[NJ];
-        {
-            const size_t row = (size_t)idx_s[k0] * ns;
+        // sum |b_hi| per (walker, output), one warp each, fixed order (deterministic bias)
+        if (wid < 2 * kC15G) {
+            const int g = wid >> 1, o = wid & 1;
+            float acc = 0.f;
+            for (int m = lane; m < kc; m += 32) {
+                const float4 b = b_s[g * kC15Chunk + m];
+                acc += fabsf(o ? b.z : b.x);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) bsum_s[g][o] = acc;
+        }
+        __syncthreads();
+        float vh[kC15G][NJ], vl[kC15G][NJ], lh[kC15G][NJ], ll[kC15G][NJ];
+#pragma unroll
+        for (int g = 0; g < kC15G; ++g)
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
-                const int k = t + kC15Threads * j;
-                ah[j] = (k < ns) ? __ldg(Ahi + row + k) : 0.f;
-                al[j] = (k < ns) ? __ldg(Alo + row + k) : 0.f;
+                vh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][0]);
+                lh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][1]);
+                vl[g][j] = 0.f;
+                ll[g][j] = 0.f;
             }
+        // two AOs of coefficients in flight ahead of the one being accumulated
+        float ah[NJ], al[NJ], nh[NJ], nl[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int k = t + kC15Threads * j;
+            const size_t r0 = (size_t)idx_s[k0] * ns, r1 = (size_t)idx_s[k0 + min(1, kc - 1)] * ns;
+            ah[j] = (k < ns) ? __ldg(Ahi + r0 + k) : 0.f;
+            al[j] = (k < ns) ? __ldg(Alo + r0 + k) : 0.f;
+            nh[j] = (k < ns) ? __ldg(Ahi + r1 + k) : 0.f;
+            nl[j] = (k < ns) ? __ldg(Alo + r1 + k) : 0.f;
         }
         for (int m = 0; m < kc; ++m) {
-            // next AO's coefficients in flight while this one is accumulated
-            float nh[NJ], nl[NJ];
-            const size_t nrow = (size_t)idx_s[k0 + min(m + 1, kc - 1)] * ns;
+            float fh[NJ], fl[NJ];
+            const size_t frow = (size_t)idx_s[k0 + min(m + 2, kc - 1)] * ns;
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
                 const int k = t + kC15Threads * j;
-                nh[j] = (k < ns) ? __ldg(Ahi + nrow + k) : 0.f;
-                nl[j] = (k < ns) ? __ldg(Alo + nrow + k) : 0.f;
+                fh[j] = (k < ns) ? __ldg(Ahi + frow + k) : 0.f;
+                fl[j] = (k < ns) ? __ldg(Alo + frow + k) : 0.f;
             }
 #pragma unroll
             for (int g = 0; g < kC15G; ++g) {
@@ -246,27 +285,37 @@ __global__ void __launch_bounds__(kC15Threads, 1) k_c15_ff(SysDev s, int nw, con
 #pragma unroll
                 for (int j = 0; j < NJ; ++j) {
                     if (kwarp + kC15Threads * j >= ns) continue;
-                    ff_acc(ah[j], al[j], b.x, b.y, vh[g][j], vc[g][j], vl[g][j]);
-                    ff_acc(ah[j], al[j], b.z, b.w, lh[g][j], lc[g][j], ll[g][j]);
+                    ff_acc(ah[j], al[j], b.x, b.y, vh[g][j], vl[g][j]);
+                    ff_acc(ah[j], al[j], b.z, b.w, lh[g][j], ll[g][j]);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) { ah[j] = nh[j]; al[j] = nl[j]; }
+            for (int j = 0; j < NJ; ++j) { ah[j] = nh[j]; al[j] = nl[j]; nh[j] = fh[j]; nl[j] = fl[j]; }
+        }
+        // (sh - BIG) is exact; add the chunk's sums to the outputs
+#pragma unroll
+        for (int g = 0; g < kC15G; ++g) {
+            if (g >= ng) break;
+            const size_t off = (size_t)(w0 + g) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                const int k = t + kC15Threads * j;
+                if (k < ns) {
+                    const float bv = pow2_above(2.f * cm[j] * bsum_s[g][0]);
+                    const float bl = pow2_above(2.f * cm[j] * bsum_s[g][1]);
+                    const double v = (double)(vh[g][j] - bv) + (double)vl[g][j];
+                    const double lp = (double)(lh[g][j] - bl) + (double)ll[g][j];
+                    if (k0 == 0) { X[off + k] = v; L5[off + k] = lp; }
+                    else { X[off + k] += v; L5[off + k] += lp; }
+                }
+            }
         }
         __syncthreads();
     }
-    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
-#pragma unroll
-    for (int g = 0; g < kC15G; ++g) {
-        if (g >= ng) break;
-        const size_t off = (size_t)(w0 + g) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int k = t + kC15Threads * j;
-            if (k < ns) {
-                X[off + k] = (double)vh[g][j] + ((double)vc[g][j] + (double)vl[g][j]);
-                L5[off + k] = (double)lh[g][j] + ((double)lc[g][j] + (double)ll[g][j]);
-            }
+    if (K == 0) {   // no active AO for any walker of the group: zero rows
+        for (int g = 0; g < ng; ++g) {
+            const size_t off = (size_t)(w0 + g) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+            for (int k = t; k < ns; k += kC15Threads) { X[off + k] = 0.0; L5[off + k] = 0.0; }
         }
     }
 }
@@ -622,28 +671,30 @@ cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, 
 
 template <int NJ>
 static cudaError_t launch_c15_nj(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
-                                 const float *const *Ahi, const float *const *Alo, double *X, double *L5,
-                                 cudaStream_t st)
+                                 const float *const *Ahi, const float *const *Alo, const float *const *cmax,
+                                 double *X, double *L5, cudaStream_t st)
 {
     const size_t sm = sizeof(float4) * kC15G * kC15Chunk + sizeof(uint32_t) * (kC15G + 1) * mw +
                       sizeof(int) * (size_t)s.n_ao;
     cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid(s.n_elec, (nw + kC15G - 1) / kC15G);
-    k_c15_ff<NJ><<<grid, kC15Threads, sm, st>>>(s, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], X, L5);
+    k_c15_ff<NJ><<<grid, kC15Threads, sm, st>>>(s, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], cmax[0],
+                                                cmax[1], X, L5);
     return cudaGetLastError();
 }
 
 cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
-                          const float *const *Ahi, const float *const *Alo, double *X, double *L5, cudaStream_t st)
+                          const float *const *Ahi, const float *const *Alo, const float *const *cmax, double *X,
+                          double *L5, cudaStream_t st)
 {
     if (nw == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     switch ((nmax + kC15Threads - 1) / kC15Threads) {
-    case 1: return launch_c15_nj<1>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
-    case 2: return launch_c15_nj<2>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
-    case 3: return launch_c15_nj<3>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
-    case 4: return launch_c15_nj<4>(s, nw, R, masks, mw, Ahi, Alo, X, L5, st);
+    case 1: return launch_c15_nj<1>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 2: return launch_c15_nj<2>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 3: return launch_c15_nj<3>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 4: return launch_c15_nj<4>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -126,7 +126,7 @@ struct Blob {
 // and FP16 hi/lo planes of A * 2^a_exp, [n_ao][n_s padded to 64]; float-float
 // planes [n_ao][n_s].  a_exp is chosen so that max |A| * 2^a_exp <= 8192.
 struct MoLayout {
-    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oFh[2], oFl[2];
+    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oFh[2], oFl[2], oCm[2];
     int ns_pad[2], a_exp[2];
 };
 
@@ -171,6 +171,10 @@ static void build_mo(int nao, int nu, int nd, int a_dtype, const void *A_up, con
         L.oHl[spin] = b.add(hl.data(), 2 * hl.size());
         L.oFh[spin] = b.add(fh.data(), 4 * fh.size());
         L.oFl[spin] = b.add(fl.data(), 4 * fl.size());
+        std::vector<float> cm(ns, 0.0f);
+        for (int mu = 0; mu < nao; ++mu)
+            for (int k = 0; k < ns; ++k) cm[k] = std::max(cm[k], (float)fabs(A64[(size_t)mu * ns + k]));
+        L.oCm[spin] = b.add(cm.data(), 4 * cm.size());
     }
 }
 
@@ -185,6 +189,7 @@ static void point_mo(qmc_system *sys, char *dev, const MoLayout &L)
         mt.hlo[spin] = reinterpret_cast<const uint16_t *>(dev + L.oHl[spin]);
         mt.fhi[spin] = reinterpret_cast<const float *>(dev + L.oFh[spin]);
         mt.flo[spin] = reinterpret_cast<const float *>(dev + L.oFl[spin]);
+        mt.colmax[spin] = reinterpret_cast<const float *>(dev + L.oCm[spin]);
         mt.ns_pad[spin] = L.ns_pad[spin];
         mt.a_exp[spin] = L.a_exp[spin];
     }
@@ -496,7 +501,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     cudaError_t e = launch_shell_mask(s, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    e = launch_c15_ff(s, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, c.X, c.L5, st);
+    e = launch_c15_ff(s, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, mt.colmax, c.X, c.L5, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     TcTables tt;
