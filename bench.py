@@ -51,7 +51,20 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="keep default tiles (no autotuner)")
     return p.parse_args()
+
+
+def aggregate(t_local_ms, walkers_local, world, dist=None, device=None):
+    """Whole-job throughput over `world` ranks: every rank evaluates its own
+    batch; the step time is the maximum over ranks."""
+    t = t_local_ms
+    if world > 1:
+        import torch
+        x = torch.tensor([t_local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, world * walkers_local / (t / 1e3)
 
 
 def dist_env():
@@ -188,11 +201,87 @@ def reference_arm(a, ws, rank):
 
 
 # ---------------------------------------------------------------------------
+def mixed_batch_arm(a, ws, rank, local):
+    """The mixed batch: 1024 walkers of each of the 158-, 434-, 1056- and
+    1731-electron systems (walker seeds interleaved: global walker 4j + s is
+    walker j of system s), tiles chosen by the autotuner per system, the
+    whole batch replayed as one CUDA graph per step."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1209_6630_gb300 import QmcBatch, QmcSystem
+    from paper_1209_6630_gb300.autotune import autotune
+    from synth import config_system, make_walkers
+    keys = ["158e", "434e", "1056e", "1731e"]
+    W = a.walkers or 1024
+    parts, systems, hosts, tiles = [], [], [], {}
+    for k in keys:
+        s = config_system(k)
+        q = QmcSystem(s, local)
+        Rh = make_walkers(s, W, first=rank * W)
+        R = torch.from_numpy(Rh).to(dev)
+        if not a.no_tune:
+            tiles[k] = autotune(q, R, precision=a.precision)["tiles"]
+        else:
+            tiles[k] = q.tiles()
+        parts.append((q, R))
+        systems.append(s)
+        hosts.append(Rh)
+    b = QmcBatch(parts, precision=a.precision, graph=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(a.warmup, 0)):
+        b.launch()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0.record()
+        b.launch()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = clk.stop()
+    t, value = aggregate(sum(times) / len(times), 4 * W, ws)
+    line = {"metric": "walker-steps/s, mixed batch of 158/434/1056/1731-electron systems in one CUDA graph",
+            "value": value, "unit": "walker-steps/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[a.precision], "data": "synthetic",
+            "config": {"workload": "mixed batch 4 x 1024 walkers (158, 434, 1056, 1731 e)", "walkers_per_system": W,
+                       "precision": a.precision, "l2": "flushed between timed steps", "tiles": tiles},
+            "gpu_launches": "one CUDA graph per step"}
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0 and not a.no_cpu:
+        import oracle
+        errs = {}
+        outs = b.eval()
+        torch.cuda.synchronize()
+        for k, s, Rh, o in zip(keys, systems, hosts, outs):
+            sample = [0, W - 1]
+            ref = oracle.Oracle(s).eval(Rh[sample], nthreads=os.cpu_count() or 1)
+            lp = o["logpsi"].cpu().numpy()[sample]
+            el = o["e_loc"].cpu().numpy()[sample]
+            errs[k] = {"max_abs_logpsi_err": float(np.abs(lp - ref["logpsi"]).max()),
+                       "max_rel_eloc_err": float((np.abs(el - ref["e_loc"]) / np.abs(ref["e_loc"])).max()),
+                       "walkers": len(sample)}
+        line["parity"] = errs
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     ws, rank, local = dist_env()
     if a.impl == "reference":
         reference_arm(a, ws, rank)
+        return
+    if a.workload == "mixed4":
+        mixed_batch_arm(a, ws, rank, local)
         return
 
     import numpy as np
@@ -213,6 +302,10 @@ def main():
     q = QmcSystem(s, local)
     R = torch.from_numpy(R_host).to(dev)
     prec = a.precision
+    tiles = q.tiles()
+    if not a.no_tune:
+        from paper_1209_6630_gb300.autotune import autotune
+        tiles = autotune(q, R[: min(W, 1024)], precision=prec)["tiles"]
     wsbuf = q.workspace(W, prec)
     out = q.alloc_out(W, want_dinv=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -248,12 +341,7 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
     barrier()
     clocks = clk.stop()
-    t_step = sum(step_ms) / len(step_ms)
-    if ws > 1:
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = ws * W / (t_step / 1e3)
+    t_step, value = aggregate(sum(step_ms) / len(step_ms), W, ws, dist, dev)
     st = np.array(stages)            # [K, 8]
     stage_mean = st.mean(axis=0)
     launches_per_step = LAUNCHES_PER_STEP[prec]   # one walker chunk
@@ -308,7 +396,7 @@ def main():
             "config": {"workload": f"{a.workload} synthetic peptide chain (528+528 e, 3040 AOs)"
                        if a.workload == "1056e" else a.workload,
                        "walkers_per_gpu": W, "precision": prec, "l2": "flushed between timed steps",
-                       "parallelism": f"walker replicas x{ws}", "kbar_active_aos": kbar},
+                       "parallelism": f"walker replicas x{ws}", "kbar_active_aos": kbar, "tiles": tiles},
             "roofline": roof, "gpu_launches": launches_per_step * a.steps}
     if clocks:
         line["clocks"] = clocks
@@ -331,12 +419,8 @@ def main():
         e1.record()
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    t_e2e = sum(e2e_ms) / len(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    line["e2e"] = {"value": ws * W / (t_e2e / 1e3), "unit": "walker-steps/s",
+    t_e2e, v_e2e = aggregate(sum(e2e_ms) / len(e2e_ms), W, ws, dist, dev)
+    line["e2e"] = {"value": v_e2e, "unit": "walker-steps/s",
                    "h2d_bytes_per_step": int(R_pin.numel() * 8),
                    "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host_out.values()))}
 

@@ -132,6 +132,24 @@ int qmc_system_free(qmc_system *sys);
  */
 int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void *A_dn);
 
+/*
+ * Tile choices of a system's kernels (set by the autotuner or by hand).
+ *   gj_panel           Gauss-Jordan panel width: 8, 16 or 32 columns (shared
+ *                      memory n*gj_panel doubles per matrix; wider = fewer
+ *                      sweeps over the matrix, fewer CTAs per SM)
+ *   c15_walkers        walkers per CTA in the mixed path's C1/C5 kernel: 2 or 4
+ *                      (more = fewer reads of the MO coefficients, more registers)
+ * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
+ * exceeds 640), c15_walkers = 4.  qmc_system_set_tiles returns
+ * QMC_ERR_INVALID for other values and keeps the previous choice.
+ */
+typedef struct {
+    int gj_panel;
+    int c15_walkers;
+} qmc_tiles;
+int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles);
+int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles);
+
 /* Copy the per-shell R2 used for screening to host memory [n_shell]. */
 int qmc_system_shell_r2(const qmc_system *sys, double *R2_host);
 
@@ -210,6 +228,36 @@ int qmc_walkers_eval_timed(const qmc_system *sys, int n_walk, const double *R, i
 #define QMC_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const double *R, int precision,
                             const qmc_eval_out *out, qmc_stream_t stream);
+
+/*
+ * Several systems in one step (mixed batch): each segment is one system's
+ * walkers with its own device positions and outputs.  Walkers of different
+ * systems are independent (Sec. II.B), so the segments run concurrently on
+ * internal streams forked from and joined back into `stream`.
+ */
+typedef struct {
+    const qmc_system *sys;
+    int n_walk;
+    const double *R;       /* device [n_walk][N][3] */
+    qmc_eval_out out;      /* device outputs, as for qmc_walkers_eval */
+} qmc_segment;
+
+/* Scratch for qmc_batch_eval: the sum of every segment's full workspace. */
+int qmc_batch_workspace_size(const qmc_segment *segs, int n_seg, int precision, size_t *bytes);
+
+/* a1..a6 for every segment (all systems on one device); ws of
+ * qmc_batch_workspace_size bytes (QMC_ERR_CAPACITY if smaller). */
+int qmc_batch_eval(const qmc_segment *segs, int n_seg, int precision, void *ws, size_t ws_bytes,
+                   qmc_stream_t stream);
+
+/* qmc_batch_eval captured once into a CUDA graph; each qmc_graph_launch
+ * replays the whole mixed batch (same pointers: refill the R buffers in
+ * place between launches).  Creation synchronises the device. */
+typedef struct qmc_graph qmc_graph;
+int qmc_batch_graph_create(const qmc_segment *segs, int n_seg, int precision, void *ws, size_t ws_bytes,
+                           qmc_graph **out);
+int qmc_graph_launch(qmc_graph *g, qmc_stream_t stream);
+int qmc_graph_free(qmc_graph *g);
 
 /*
  * qmc_logpsi_backward -- a7, the adjoint of log|Psi| with respect to the MO

@@ -35,6 +35,14 @@ class EvalOut(C.Structure):
                 ("e_parts", _vp), ("status", _vp), ("dinv", _vp)]
 
 
+class Tiles(C.Structure):
+    _fields_ = [("gj_panel", _i), ("c15_walkers", _i)]
+
+
+class Segment(C.Structure):
+    _fields_ = [("sys", _vp), ("n_walk", _i), ("R", _vp), ("out", EvalOut)]
+
+
 class QmcError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"libqmcgb error {code}: {msg}")
@@ -60,6 +68,13 @@ def lib():
             L.qmc_system_free.argtypes = [_vp]
             L.qmc_system_shell_r2.argtypes = [_vp, _vp]
             L.qmc_system_set_mo.argtypes = [_vp, _i, _vp, _vp]
+            L.qmc_system_set_tiles.argtypes = [_vp, C.POINTER(Tiles)]
+            L.qmc_system_get_tiles.argtypes = [_vp, C.POINTER(Tiles)]
+            L.qmc_batch_workspace_size.argtypes = [C.POINTER(Segment), _i, _i, C.POINTER(C.c_size_t)]
+            L.qmc_batch_eval.argtypes = [C.POINTER(Segment), _i, _i, _vp, C.c_size_t, _vp]
+            L.qmc_batch_graph_create.argtypes = [C.POINTER(Segment), _i, _i, _vp, C.c_size_t, C.POINTER(_vp)]
+            L.qmc_graph_launch.argtypes = [_vp, _vp]
+            L.qmc_graph_free.argtypes = [_vp]
             L.qmc_workspace_size.argtypes = [_vp, _i, _i, C.POINTER(C.c_size_t)]
             L.qmc_walkers_eval.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp]
             L.qmc_walkers_eval_timed.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp,
@@ -70,6 +85,8 @@ def lib():
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo",
+                         "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size",
+                         "qmc_batch_eval", "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
                          "qmc_workspace_size",
                          "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static",
                          "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
@@ -87,5 +104,7 @@ def check(rc):
 
 # every symbol include/qmcgb.h declares
 EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo", "qmc_workspace_size",
+            "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size", "qmc_batch_eval",
+            "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
             "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
             "qmc_det_inverse", "qmc_last_error", "qmc_version")

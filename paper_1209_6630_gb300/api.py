@@ -10,9 +10,9 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import PREC, DTYPE_F32, DTYPE_F64, EvalOut, QmcError, SystemDesc, check, lib
+from ._lib import PREC, DTYPE_F32, DTYPE_F64, EvalOut, QmcError, Segment, SystemDesc, Tiles, check, lib
 
-__all__ = ["QmcSystem", "det_inverse", "LogPsi", "QmcError"]
+__all__ = ["QmcSystem", "QmcBatch", "det_inverse", "LogPsi", "QmcError"]
 
 
 def _stream(device):
@@ -91,6 +91,16 @@ class QmcSystem:
         out = np.zeros(self.n_shell, np.float64)
         check(lib().qmc_system_shell_r2(self._h, C.c_void_p(out.ctypes.data)))
         return out
+
+    def tiles(self):
+        t = Tiles()
+        check(lib().qmc_system_get_tiles(self._h, C.byref(t)))
+        return {"gj_panel": t.gj_panel, "c15_walkers": t.c15_walkers}
+
+    def set_tiles(self, gj_panel=None, c15_walkers=None):
+        cur = self.tiles()
+        t = Tiles(gj_panel=gj_panel or cur["gj_panel"], c15_walkers=c15_walkers or cur["c15_walkers"])
+        check(lib().qmc_system_set_tiles(self._h, C.byref(t)))
 
     def set_mo(self, A_up, A_dn):
         """Replace the MO coefficients (qmc_system_set_mo); host arrays [n_ao, n_s]."""
@@ -184,6 +194,60 @@ class QmcSystem:
         check(lib().qmc_logpsi_backward(self._h, W, _ptr(R), _ptr(dinv), _ptr(g), _ptr(dA_up), _ptr(dA_dn),
                                         _stream(self.device)))
         return dA_up, dA_dn
+
+
+def _eval_out_struct(o):
+    return EvalOut(logpsi=_ptr(o["logpsi"]), sign=_ptr(o["sign"]), logabs=_ptr(o.get("logabs")),
+                   drift=_ptr(o["drift"]), e_loc=_ptr(o["e_loc"]), e_parts=_ptr(o.get("e_parts")),
+                   status=_ptr(o["status"]), dinv=_ptr(o.get("dinv")))
+
+
+class QmcBatch:
+    """Walkers of several systems evaluated together (qmc_batch_eval), and
+    the same batch captured once as a CUDA graph (qmc_batch_graph_create)."""
+
+    def __init__(self, parts, precision: str = "mixed", graph: bool = True):
+        """parts: list of (QmcSystem, R) with R cuda f64 [W, N, 3]."""
+        self.parts = parts
+        self.precision = precision
+        self.outs = [q.alloc_out(int(R.shape[0])) for q, R in parts]
+        segs = (Segment * len(parts))()
+        for i, ((q, R), o) in enumerate(zip(parts, self.outs)):
+            _req_cuda(R, torch.float64, "R", (int(R.shape[0]), q.N, 3))
+            segs[i].sys = q.handle
+            segs[i].n_walk = int(R.shape[0])
+            segs[i].R = _ptr(R)
+            segs[i].out = _eval_out_struct(o)
+        self._segs = segs
+        b = C.c_size_t()
+        check(lib().qmc_batch_workspace_size(segs, len(parts), PREC[precision], C.byref(b)))
+        self.device = parts[0][0].device
+        self.ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=self.device)
+        self._g = None
+        if graph:
+            h = C.c_void_p()
+            check(lib().qmc_batch_graph_create(segs, len(parts), PREC[precision], _ptr(self.ws), self.ws.numel(),
+                                               C.byref(h)))
+            self._g = h
+
+    def eval(self):
+        check(lib().qmc_batch_eval(self._segs, len(self.parts), PREC[self.precision], _ptr(self.ws), self.ws.numel(),
+                                   _stream(self.device)))
+        return self.outs
+
+    def launch(self):
+        """One CUDA-graph launch of the whole batch on the current stream."""
+        if self._g is None:
+            raise RuntimeError("QmcBatch created without a graph")
+        check(lib().qmc_graph_launch(self._g, _stream(self.device)))
+        return self.outs
+
+    def __del__(self):
+        try:
+            if self._g is not None and self._g.value:
+                lib().qmc_graph_free(self._g)
+        except Exception:
+            pass
 
 
 def det_inverse(X):

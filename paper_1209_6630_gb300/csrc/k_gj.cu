@@ -3,7 +3,7 @@
 // inversion step, double precision).
 //
 // One CTA per matrix.  Gauss-Jordan elimination with partial pivoting, done
-// in panels of NB = 16 columns:
+// in panels of NB = 8, 16 or 32 columns (a tile choice per system):
 //   1. the n x NB panel is copied to shared memory and eliminated there,
 //      column by column (pivot = largest |entry| among rows not yet used;
 //      the pivots are exactly those of LU with partial pivoting);
@@ -17,6 +17,8 @@
 // inverse), and the kernel writes Dinv = X^-T with a tiled transpose:
 //   Dinv[pp[c]][k] = Res[pp[k]][c].
 // Flops: n^3 FMA = 2 n^3, the LU (2/3 n^3) plus inverse (4/3 n^3) count.
+// Shared memory (n NB + 32 NB) doubles + 3n shorts: at NB = 16, ~75 KB for n = 528
+// (three CTAs per SM); NB = 8 halves it at the cost of twice the panel sweeps.
 #include <math.h>
 
 #include "qmc_internal.cuh"
@@ -25,16 +27,15 @@ namespace qmc {
 
 constexpr int kGjThreads = 256;
 constexpr int kGjWarps = kGjThreads / 32;
-constexpr int NB = kGjPanel;
 
 struct GjJobs2 {
     GjJob j[2];
 };
 
 // doubles reserved for the panel (also holds the 32 x 33 transpose tile)
-__host__ __device__ __forceinline__ size_t p_region(int n)
+__host__ __device__ __forceinline__ size_t p_region(int n, int nb)
 {
-    const size_t a = (size_t)n * NB;
+    const size_t a = (size_t)n * nb;
     return a > 32 * 33 ? a : 32 * 33;
 }
 
@@ -43,6 +44,18 @@ __device__ __forceinline__ void argmax_merge(double &v, int &i, double v2, int i
     if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
 }
 
+__device__ __forceinline__ void block_argmax(double &bv, int &bi, double *red_v, int *red_i, int lane, int wid)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_down_sync(0xffffffffu, bv, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+        argmax_merge(bv, bi, v2, i2);
+    }
+    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+}
+
+template <int NB>
 __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
 {
     const GjJob &J = jobs.j[blockIdx.y];
@@ -54,10 +67,10 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *P = reinterpret_cast<double *>(smem_raw);   // [n][NB], later a [32][33] tile
-    double *U = P + p_region(n);                          // [NB][32]
-    int *used = reinterpret_cast<int *>(U + NB * 32);     // [n]
-    int *pp = used + n;                                   // [n] pivot row of step k
-    int *rowc = pp + n;                                   // [n] panel column of a pivot row, or -1
+    double *U = P + p_region(n, NB);                      // [NB][32]
+    short *used = reinterpret_cast<short *>(U + NB * 32); // [n] 1 once a row has been a pivot
+    short *pp = used + n;                                 // [n] pivot row of step k
+    short *rowc = pp + n;                                 // [n] panel column of a pivot row, or -1
     __shared__ double red_v[kGjWarps];
     __shared__ int red_i[kGjWarps];
     __shared__ int s_p, s_sing;
@@ -76,25 +89,21 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
             P[q] = (c < w) ? X[(size_t)i * n + jb + c] : 0.0;
         }
         __syncthreads();
+        // pivot candidates of the panel's first column
+        double bv = -1.0;
+        int bi = n;
+        for (int i = t; i < n; i += kGjThreads)
+            if (!used[i]) argmax_merge(bv, bi, fabs(P[i * NB]), i);
+        block_argmax(bv, bi, red_v, red_i, lane, wid);
+        __syncthreads();
 
         for (int c = 0; c < w; ++c) {
-            // pivot: largest |P[i][c]| over unused rows, lowest row on ties
-            double bv = -1.0;
-            int bi = n;
-            for (int i = t; i < n; i += kGjThreads)
-                if (!used[i]) argmax_merge(bv, bi, fabs(P[i * NB + c]), i);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double v2 = __shfl_down_sync(0xffffffffu, bv, o);
-                const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
-                argmax_merge(bv, bi, v2, i2);
-            }
-            if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
-            __syncthreads();
             if (t == 0) {
-                for (int q = 1; q < kGjWarps; ++q) argmax_merge(bv, bi, red_v[q], red_i[q]);
-                s_p = bi;
-                if (!(bv > 0.0)) s_sing = 1;   // exact zero (or NaN) pivot
+                double v = red_v[0];
+                int b = red_i[0];
+                for (int q = 1; q < kGjWarps; ++q) argmax_merge(v, b, red_v[q], red_i[q]);
+                s_p = b;
+                if (!(v > 0.0)) s_sing = 1;   // exact zero (or NaN) pivot
             }
             __syncthreads();
             if (s_sing) break;
@@ -103,14 +112,19 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
             const double inv = 1.0 / piv;
             if (t == 0) {
                 used[p] = 1;
-                pp[jb + c] = p;
-                rowc[p] = c;
+                pp[jb + c] = (short)p;
+                rowc[p] = (short)c;
                 logabs += log(fabs(piv));
                 neg ^= (piv < 0.0);
             }
-            __syncthreads();   // every thread has read P[p][c] (piv)
+            __syncthreads();   // every thread has read P[p][c] (piv); used[p] is set
             if (t < NB) P[p * NB + t] = (t == c) ? inv : P[p * NB + t] * inv;
             __syncthreads();
+            // eliminate column c from the other rows and, on the way, find the
+            // pivot candidates of column c+1 among the rows not yet used
+            double nbv = -1.0;
+            int nbi = n;
+            const int cn = c + 1;
             for (int i = t; i < n; i += kGjThreads) {
                 if (i == p) continue;
                 const double f = P[i * NB + c];
@@ -118,7 +132,9 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
                 for (int cc = 0; cc < NB; ++cc)
                     if (cc != c) P[i * NB + cc] = fma(-f, P[p * NB + cc], P[i * NB + cc]);
                 P[i * NB + c] = -f * inv;
+                if (cn < w && !used[i]) argmax_merge(nbv, nbi, fabs(P[i * NB + cn]), i);
             }
+            block_argmax(nbv, nbi, red_v, red_i, lane, wid);
             __syncthreads();
         }
         if (s_sing) break;
@@ -129,15 +145,31 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
             X[(size_t)i * n + jb + c] = P[i * NB + c];
         }
 
-        // rank-w update of every other column, 32 columns at a time
-        for (int c0 = 0; c0 < n; c0 += 32) {
-            if (c0 >= jb && c0 + 32 <= jb + w) continue;   // chunk inside the panel
+        // rank-w update of every other column, 32 columns at a time; the pivot
+        // rows of the next chunk are read into registers while this one runs
+        int c0 = 0;
+        auto skip = [&](int cc0) { return cc0 >= jb && cc0 + 32 <= jb + w; };
+        while (c0 < n && skip(c0)) c0 += 32;
+        constexpr int UPT = NB * 32 / kGjThreads;   // U elements per thread
+        double upre[UPT];
+        __syncthreads();   // panel stores done before U reads of the same rows
+#pragma unroll
+        for (int r = 0; r < UPT; ++r) {
+            const int q = t + r * kGjThreads, c = q >> 5, col = c0 + (q & 31);
+            upre[r] = (c0 < n && c < w && col < n) ? X[(size_t)pp[jb + c] * n + col] : 0.0;
+        }
+        while (c0 < n) {
+            __syncthreads();   // previous chunk done with U
+#pragma unroll
+            for (int r = 0; r < UPT; ++r) U[t + r * kGjThreads] = upre[r];
             __syncthreads();
-            for (int q = t; q < NB * 32; q += kGjThreads) {
-                const int c = q >> 5, l = q & 31, col = c0 + l;
-                U[q] = (c < w && col < n) ? X[(size_t)pp[jb + c] * n + col] : 0.0;
+            int c1 = c0 + 32;
+            while (c1 < n && skip(c1)) c1 += 32;
+#pragma unroll
+            for (int r = 0; r < UPT; ++r) {
+                const int q = t + r * kGjThreads, c = q >> 5, col = c1 + (q & 31);
+                upre[r] = (c1 < n && c < w && col < n) ? X[(size_t)pp[jb + c] * n + col] : 0.0;
             }
-            __syncthreads();
             const int col = c0 + lane;
             const bool active = col < n && !(col >= jb && col < jb + w);
             double u[NB];
@@ -178,6 +210,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
                     X[(size_t)i * n + col] = x;
                 }
             }
+            c0 = c1;
         }
         __syncthreads();
         for (int c = t; c < w; c += kGjThreads) rowc[pp[jb + c]] = -1;
@@ -228,7 +261,20 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
     }
 }
 
-cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st)
+template <int NB>
+static cudaError_t launch_gj_nb(const GjJobs2 &js, int n_jobs, int nmax, int cmax, cudaStream_t st)
+{
+    const size_t sm = sizeof(double) * (p_region(nmax, NB) + NB * 32) + sizeof(short) * 3 * (size_t)nmax;
+    cudaError_t e = cudaFuncSetAttribute(k_gj<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gj<NB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    dim3 grid(cmax, n_jobs);
+    k_gj<NB><<<grid, kGjThreads, sm, st>>>(js);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb)
 {
     GjJobs2 js;
     int nmax = 0, cmax = 0;
@@ -239,12 +285,12 @@ cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st)
         cmax = max(cmax, js.j[q].count);
     }
     if (cmax == 0) return cudaSuccess;
-    const size_t sm = sizeof(double) * (p_region(nmax) + NB * 32) + sizeof(int) * 3 * (size_t)nmax;
-    cudaError_t e = cudaFuncSetAttribute(k_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid(cmax, n_jobs);
-    k_gj<<<grid, kGjThreads, sm, st>>>(js);
-    return cudaGetLastError();
+    switch (nb) {
+    case 8: return launch_gj_nb<8>(js, n_jobs, nmax, cmax, st);
+    case 16: return launch_gj_nb<16>(js, n_jobs, nmax, cmax, st);
+    case 32: return launch_gj_nb<32>(js, n_jobs, nmax, cmax, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace qmc

@@ -163,11 +163,10 @@ __device__ __forceinline__ void ao_val_lap_f64(const SysDev &s, int mu, double r
 // the same AOs); AOs screened out for a walker are skipped.  The AO values
 // of up to kC15Chunk union AOs are staged at once; a larger union is handled
 // in several chunks whose partial sums are added in global memory.
-constexpr int kC15G = 4;
 constexpr int kC15Threads = 256;
 constexpr int kC15Chunk = 1024;
 
-template <int NJ>
+template <int NJ, int kC15G>
 __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, const double *__restrict__ R,
                                                            const uint32_t *__restrict__ masks, int mw,
                                                            const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
@@ -176,7 +175,7 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, con
                                                            double *__restrict__ X, double *__restrict__ L5)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *b_s = reinterpret_cast<float4 *>(smem_raw);            // [kC15G][kC15Chunk]: (vh, vl, lh, ll)
+    float4 *b_s = reinterpret_cast<float4 *>(smem_raw);            // [G][kC15Chunk]: (vh, vl, lh, ll)
     uint32_t *mk_s = reinterpret_cast<uint32_t *>(b_s + kC15G * kC15Chunk);   // [kC15G][mw]
     uint32_t *un_s = mk_s + kC15G * mw;                            // [mw]
     int *idx_s = reinterpret_cast<int *>(un_s + mw);               // [n_ao]
@@ -236,6 +235,7 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, con
         }
         __syncthreads();
         // sum |b_hi| per (walker, output), one warp each, fixed order (deterministic bias)
+        static_assert(2 * kC15G <= kC15Threads / 32, "one warp per (walker, output)");
         if (wid < 2 * kC15G) {
             const int g = wid >> 1, o = wid & 1;
             float acc = 0.f;
@@ -669,32 +669,44 @@ cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, 
     return cudaGetLastError();
 }
 
-template <int NJ>
+template <int NJ, int G>
 static cudaError_t launch_c15_nj(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                                  const float *const *Ahi, const float *const *Alo, const float *const *cmax,
                                  double *X, double *L5, cudaStream_t st)
 {
-    const size_t sm = sizeof(float4) * kC15G * kC15Chunk + sizeof(uint32_t) * (kC15G + 1) * mw +
+    const size_t sm = sizeof(float4) * G * kC15Chunk + sizeof(uint32_t) * (G + 1) * mw +
                       sizeof(int) * (size_t)s.n_ao;
-    cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    dim3 grid(s.n_elec, (nw + kC15G - 1) / kC15G);
-    k_c15_ff<NJ><<<grid, kC15Threads, sm, st>>>(s, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], cmax[0],
-                                                cmax[1], X, L5);
+    dim3 grid(s.n_elec, (nw + G - 1) / G);
+    k_c15_ff<NJ, G><<<grid, kC15Threads, sm, st>>>(s, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], cmax[0],
+                                                  cmax[1], X, L5);
     return cudaGetLastError();
+}
+
+template <int G>
+static cudaError_t launch_c15_g(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+                                const float *const *Ahi, const float *const *Alo, const float *const *cmax, double *X,
+                                double *L5, cudaStream_t st)
+{
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    switch ((nmax + kC15Threads - 1) / kC15Threads) {
+    case 1: return launch_c15_nj<1, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 2: return launch_c15_nj<2, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 3: return launch_c15_nj<3, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 4: return launch_c15_nj<4, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                           const float *const *Ahi, const float *const *Alo, const float *const *cmax, double *X,
-                          double *L5, cudaStream_t st)
+                          double *L5, cudaStream_t st, int walkers_per_cta)
 {
     if (nw == 0) return cudaSuccess;
-    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    switch ((nmax + kC15Threads - 1) / kC15Threads) {
-    case 1: return launch_c15_nj<1>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 2: return launch_c15_nj<2>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 3: return launch_c15_nj<3>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 4: return launch_c15_nj<4>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    switch (walkers_per_cta) {
+    case 2: return launch_c15_g<2>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 4: return launch_c15_g<4>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
     default: return cudaErrorInvalidValue;
     }
 }

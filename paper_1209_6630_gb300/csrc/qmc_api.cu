@@ -258,6 +258,8 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
 
     qmc_system *sys = new qmc_system();
     sys->device = device;
+    sys->tiles.gj_panel = (d->n_up > 640 || d->n_dn > 640) ? 8 : 16;
+    sys->tiles.c15_walkers = 4;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
     std::vector<double> atom_R2(na, 0.0);
@@ -377,6 +379,24 @@ extern "C" int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up,
     if (e != cudaSuccess) return cuda_fail(e, "qmc_system_set_mo");
     sys->a_dtype = a_dtype;
     point_mo(sys, static_cast<char *>(sys->mo_dev), mo);
+    return QMC_OK;
+}
+
+extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
+{
+    if (!sys || !tiles) return invalid("qmc_system_set_tiles: null argument");
+    if (tiles->gj_panel != 8 && tiles->gj_panel != 16 && tiles->gj_panel != 32)
+        return invalid("qmc_system_set_tiles: gj_panel must be 8, 16 or 32");
+    if (tiles->c15_walkers != 2 && tiles->c15_walkers != 4)
+        return invalid("qmc_system_set_tiles: c15_walkers must be 2 or 4");
+    sys->tiles = *tiles;
+    return QMC_OK;
+}
+
+extern "C" int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles)
+{
+    if (!sys || !tiles) return invalid("qmc_system_get_tiles: null argument");
+    *tiles = sys->tiles;
     return QMC_OK;
 }
 
@@ -501,7 +521,8 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     cudaError_t e = launch_shell_mask(s, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    e = launch_c15_ff(s, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, mt.colmax, c.X, c.L5, st);
+    e = launch_c15_ff(s, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, mt.colmax, c.X, c.L5, st,
+                      sys->tiles.c15_walkers);
     if (e != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     TcTables tt;
@@ -606,7 +627,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             j.flag = c.st; j.flag_bit = spin ? QMC_STATUS_SINGULAR_DN : QMC_STATUS_SINGULAR_UP;
             j.n = ns; j.count = nw;
         }
-        e = launch_gj(jobs, nj, st);
+        e = launch_gj(jobs, nj, st, sys->tiles.gj_panel);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: Gauss-Jordan launch");
         if ((e = mark(2)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         e = launch_drift_energy(s, nw, Rc, Dinv, cview(p, c), c.la, c.sg, c.st, *out, w0, st);
@@ -724,7 +745,7 @@ extern "C" int qmc_det_inverse(int batch, int n, double *X, double *Dinv, double
         cudaError_t e = cudaMemsetAsync(singular, 0, sizeof(uint32_t) * batch, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_det_inverse: memset");
     }
-    cudaError_t e = launch_gj(&j, 1, st);
+    cudaError_t e = launch_gj(&j, 1, st, n > 640 ? 8 : 16);
     if (e != cudaSuccess) return cuda_fail(e, "qmc_det_inverse: launch");
     return QMC_OK;
 }
@@ -800,4 +821,163 @@ extern "C" int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const 
     }
     return eval_impl(sys, n_walk, R, precision, out, g_static_ptr[dev], kStaticScratchBytes,
                      reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed batch: segments of several systems, concurrent on forked streams.
+namespace {
+
+constexpr int kPoolStreams = 8;
+
+struct StreamPool {
+    int device = -1;
+    cudaStream_t st[kPoolStreams] = {};
+    cudaEvent_t fork = nullptr, done[kPoolStreams] = {};
+};
+StreamPool g_pool[kMaxDevices];
+
+int pool_for(int dev, StreamPool **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return invalid("batch: device index out of range");
+    StreamPool &p = g_pool[dev];
+    if (p.device != dev) {
+        cudaError_t e = cudaSetDevice(dev);
+        for (int q = 0; q < kPoolStreams && e == cudaSuccess; ++q)
+            e = cudaStreamCreateWithFlags(&p.st[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming);
+        for (int q = 0; q < kPoolStreams && e == cudaSuccess; ++q)
+            e = cudaEventCreateWithFlags(&p.done[q], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "batch: stream pool");
+        p.device = dev;
+    }
+    *out = &p;
+    return QMC_OK;
+}
+
+int check_segments(const qmc_segment *segs, int n_seg, int precision)
+{
+    if (!segs || n_seg < 1) return invalid("batch: need at least one segment");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("batch: precision");
+    for (int i = 0; i < n_seg; ++i) {
+        if (!segs[i].sys || segs[i].n_walk < 0) return invalid("batch: bad segment");
+        if (segs[i].sys->device != segs[0].sys->device) return invalid("batch: segments on different devices");
+    }
+    return QMC_OK;
+}
+
+size_t seg_bytes(const qmc_segment &g, int precision)
+{
+    const Plan p = make_plan(g.sys, precision, g.out.dinv == nullptr);
+    return al(bytes_for(p, std::max(g.n_walk, 1)));
+}
+
+}  // namespace
+
+extern "C" int qmc_batch_workspace_size(const qmc_segment *segs, int n_seg, int precision, size_t *bytes)
+{
+    int rc = check_segments(segs, n_seg, precision);
+    if (rc) return rc;
+    if (!bytes) return invalid("qmc_batch_workspace_size: null bytes");
+    size_t tot = 0;
+    for (int i = 0; i < n_seg; ++i) tot += seg_bytes(segs[i], precision);
+    *bytes = tot;
+    return QMC_OK;
+}
+
+extern "C" int qmc_batch_eval(const qmc_segment *segs, int n_seg, int precision, void *ws, size_t ws_bytes,
+                              qmc_stream_t stream)
+{
+    int rc = check_segments(segs, n_seg, precision);
+    if (rc) return rc;
+    size_t need = 0;
+    for (int i = 0; i < n_seg; ++i) need += seg_bytes(segs[i], precision);
+    if (need > ws_bytes) {
+        set_error("qmc_batch_eval: workspace smaller than qmc_batch_workspace_size");
+        return QMC_ERR_CAPACITY;
+    }
+    StreamPool *pool = nullptr;
+    if ((rc = pool_for(segs[0].sys->device, &pool))) return rc;
+    cudaStream_t main = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaEventRecord(pool->fork, main);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_batch_eval: fork");
+    const int nst = std::min(n_seg, kPoolStreams);
+    for (int q = 0; q < nst; ++q)
+        if ((e = cudaStreamWaitEvent(pool->st[q], pool->fork, 0)) != cudaSuccess)
+            return cuda_fail(e, "qmc_batch_eval: fork wait");
+    char *base = static_cast<char *>(ws);
+    for (int i = 0; i < n_seg; ++i) {
+        const size_t b = seg_bytes(segs[i], precision);
+        rc = eval_impl(segs[i].sys, segs[i].n_walk, segs[i].R, precision, &segs[i].out, base, b,
+                       pool->st[i % kPoolStreams], nullptr);
+        if (rc) return rc;
+        base += b;
+    }
+    for (int q = 0; q < nst; ++q) {
+        if ((e = cudaEventRecord(pool->done[q], pool->st[q])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(main, pool->done[q], 0)) != cudaSuccess)
+            return cuda_fail(e, "qmc_batch_eval: join");
+    }
+    return QMC_OK;
+}
+
+struct qmc_graph {
+    int device;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" int qmc_batch_graph_create(const qmc_segment *segs, int n_seg, int precision, void *ws, size_t ws_bytes,
+                                      qmc_graph **out)
+{
+    int rc = check_segments(segs, n_seg, precision);
+    if (rc) return rc;
+    if (!out) return invalid("qmc_batch_graph_create: null out");
+    *out = nullptr;
+    const int dev = segs[0].sys->device;
+    StreamPool *pool = nullptr;
+    if ((rc = pool_for(dev, &pool))) return rc;
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaSetDevice(dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_batch_graph_create: stream");
+    // first run outside capture: kernel attributes are set, tables touched
+    rc = qmc_batch_eval(segs, n_seg, precision, ws, ws_bytes, reinterpret_cast<qmc_stream_t>(cap));
+    if (rc == QMC_OK && (e = cudaStreamSynchronize(cap)) != cudaSuccess) rc = cuda_fail(e, "qmc_batch_graph_create");
+    if (rc) { cudaStreamDestroy(cap); return rc; }
+    qmc_graph *g = new qmc_graph();
+    g->device = dev;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { delete g; cudaStreamDestroy(cap); return cuda_fail(e, "qmc_batch_graph_create: capture"); }
+    rc = qmc_batch_eval(segs, n_seg, precision, ws, ws_bytes, reinterpret_cast<qmc_stream_t>(cap));
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        delete g;
+        return rc ? rc : cuda_fail(e, "qmc_batch_graph_create: end capture");
+    }
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); delete g; return cuda_fail(e, "qmc_batch_graph_create: instantiate"); }
+    g->graph = graph;
+    *out = g;
+    return QMC_OK;
+}
+
+extern "C" int qmc_graph_launch(qmc_graph *g, qmc_stream_t stream)
+{
+    if (!g) return invalid("qmc_graph_launch: null graph");
+    cudaError_t e = cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_graph_launch");
+    return QMC_OK;
+}
+
+extern "C" int qmc_graph_free(qmc_graph *g)
+{
+    if (!g) return QMC_OK;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return QMC_OK;
 }

@@ -85,7 +85,7 @@ cudaError_t launch_contract_f64(const SysDev &s, int nw, const double *R, double
                                 cudaStream_t st);
 cudaError_t launch_screen_ao(const SysDev &s, int nw, const double *R, int cap, int32_t *cnt,
                              int32_t *idx, double *B, cudaStream_t st);
-cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st);
+cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb);
 // Where the gradient (C2..C4) and Laplacian (C5) matrices of a walker chunk live:
 // component c of spin s, electron row ei: base + w*wstride + (s ? ncomp*n_up^2 : 0) + c*ns^2 + ei*ns
 struct CView {
@@ -105,7 +105,7 @@ cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const 
 cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st);
 cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                           const float *const *Ahi, const float *const *Alo, const float *const *colmax, double *X,
-                          double *L5, cudaStream_t st);
+                          double *L5, cudaStream_t st, int walkers_per_cta);
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                                const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
 cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
@@ -118,6 +118,7 @@ cudaError_t launch_backward_f64(const SysDev &s, int nw, const double *R, const 
 
 struct qmc_system {
     int device;
+    qmc_tiles tiles;                  // tile choices (autotuned or default)
     qmc::SysDev d;
     std::vector<void *> allocs;     // device allocations owned by the system
     std::vector<double> R2_host;
