@@ -69,11 +69,13 @@ enum {
 /* arithmetic of the products a3 (a4..a6 are always FP64) */
 enum {
     QMC_PREC_F64 = 0,        /* plain FP64 path: AO values, products, LU, energies in FP64 */
-    QMC_PREC_MIXED = 1,      /* C1 (the Slater matrix) from FP64 AO values with compensated
-                                float-float products (FP64-accurate); C2..C5 (gradient and
-                                Laplacian matrices) on the tcgen05 tensor cores from FP16
-                                hi/lo split operands (3 products, FP32 accumulation, exact
-                                power-of-two scaling); LU/inverse/energies FP64 */
+    QMC_PREC_MIXED = 1,      /* C1 (the Slater matrix) and C5 (its Laplacian) from FP64 AO
+                                values with exact float-float products; C2..C4 (gradient
+                                matrices) on the tcgen05 tensor cores from FP16 hi/lo split
+                                operands (3 products, FP32 accumulation, exact power-of-two
+                                scaling); a4 per qmc_tiles.a4_mode (float-float Gauss-Jordan
+                                with FP64 recomputation near nodal surfaces, or FP64);
+                                energies FP64 */
     QMC_PREC_MIXED_BF16 = 2  /* as QMC_PREC_MIXED with BF16 hi/lo splits for C2..C5 */
 };
 
@@ -133,19 +135,32 @@ int qmc_system_free(qmc_system *sys);
 int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void *A_dn);
 
 /*
- * Tile choices of a system's kernels (set by the autotuner or by hand).
+ * Tile and arithmetic choices of a system's kernels (set by the autotuner or
+ * by hand).
  *   gj_panel           Gauss-Jordan panel width: 8, 16 or 32 columns (shared
  *                      memory n*gj_panel doubles per matrix; wider = fewer
  *                      sweeps over the matrix, fewer CTAs per SM)
  *   c15_walkers        walkers per CTA in the mixed path's C1/C5 kernel: 2 or 4
  *                      (more = fewer reads of the MO coefficients, more registers)
+ *   a4_mode            a4 arithmetic of the mixed paths (the FP64 path always
+ *                      uses FP64): QMC_A4_FP64, or QMC_A4_FLOAT_FLOAT = the same
+ *                      Gauss-Jordan elimination on float pairs (~48-bit
+ *                      significand, FP32 pipes) whose matrices with
+ *                      kappa_inf = ||X||_inf ||X^-1||_inf above a4_kappa_max (near a
+ *                      nodal surface), with a zero pivot or a non-finite result
+ *                      are recomputed in FP64
+ *   a4_kappa_max       that threshold (> 0)
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
- * exceeds 640), c15_walkers = 4.  qmc_system_set_tiles returns
- * QMC_ERR_INVALID for other values and keeps the previous choice.
+ * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT,
+ * a4_kappa_max = 1e9.  qmc_system_set_tiles returns QMC_ERR_INVALID for other
+ * values and keeps the previous choice.
  */
+enum { QMC_A4_FP64 = 0, QMC_A4_FLOAT_FLOAT = 1 };
 typedef struct {
     int gj_panel;
     int c15_walkers;
+    int a4_mode;
+    double a4_kappa_max;
 } qmc_tiles;
 int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles);
 int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles);

@@ -36,7 +36,10 @@ class EvalOut(C.Structure):
 
 
 class Tiles(C.Structure):
-    _fields_ = [("gj_panel", _i), ("c15_walkers", _i)]
+    _fields_ = [("gj_panel", _i), ("c15_walkers", _i), ("a4_mode", _i), ("a4_kappa_max", C.c_double)]
+
+
+A4_MODE = {"fp64": 0, "float_float": 1}
 
 
 class Segment(C.Structure):

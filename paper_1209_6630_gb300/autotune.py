@@ -47,7 +47,7 @@ def autotune(q, R, precision="mixed", cache=DEFAULT_CACHE, force=False, verbose=
     if key in table and not force:
         q.set_tiles(**table[key]["tiles"])
         return table[key]
-    start = q.tiles()
+    start = {k: v for k, v in q.tiles().items() if k in ("gj_panel", "c15_walkers")}
     timings = {}
     best_gj, best_gj_ms = start["gj_panel"], float("inf")
     for nb in (8, 16, 32):

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
     const GjJob &J = jobs.j[blockIdx.y];
     const int m = blockIdx.x;
     if (m >= J.count) return;
+    if (J.only_redo && !J.redo[m * J.redo_stride]) return;   // recompute pass: flagged matrices only
     const int n = J.n;
     double *__restrict__ X = J.X + (size_t)m * J.x_stride;
     double *__restrict__ Dout = J.Dinv + (size_t)m * J.d_stride;
@@ -289,6 +290,354 @@ cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb)
     case 8: return launch_gj_nb<8>(js, n_jobs, nmax, cmax, st);
     case 16: return launch_gj_nb<16>(js, n_jobs, nmax, cmax, st);
     case 32: return launch_gj_nb<32>(js, n_jobs, nmax, cmax, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Float-float Gauss-Jordan (mixed path, a4 arithmetic QMC_A4_FLOAT_FLOAT).  Same elimination as k_gj, but every
+// value is a pair of floats (hi + lo, ~48-bit significand) and the arithmetic
+// runs on the FP32 pipes (62x the FP64 rate on this GPU).  The FP64 input X is
+// left intact; the elimination works on a float-pair copy.  At the end the
+// kernel measures kappa_inf = ||X||_inf ||X^-1||_inf of the result; a matrix
+// above `kappa_max` (near a nodal surface of Psi, where the Slater matrix
+// becomes singular) or with a non-finite result is flagged, and the caller
+// recomputes the flagged matrices with the FP64 k_gj, which skips the others.
+namespace ff {
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)   // |a| >= |b|
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+// x * y as a normalised pair
+__device__ __forceinline__ float2 mul(float2 x, float2 y)
+{
+    const float p = x.x * y.x;
+    float pe = fmaf(x.x, y.x, -p);
+    pe = fmaf(x.x, y.y, pe);
+    pe = fmaf(x.y, y.x, pe);
+    float s, e;
+    fast_two_sum(p, pe, s, e);
+    return make_float2(s, e);
+}
+
+// acc + x * y as a normalised pair
+__device__ __forceinline__ float2 fma2(float2 acc, float2 x, float2 y)
+{
+    const float p = x.x * y.x;
+    float pe = fmaf(x.x, y.x, -p);
+    pe = fmaf(x.x, y.y, pe);
+    pe = fmaf(x.y, y.x, pe);
+    float s, se;
+    two_sum(acc.x, p, s, se);
+    se += acc.y + pe;
+    float h, l;
+    fast_two_sum(s, se, h, l);
+    return make_float2(h, l);
+}
+
+// 1 / x: FP32 reciprocal refined once (Newton step in float-float)
+__device__ __forceinline__ float2 inv(float2 x)
+{
+    const float q = 1.0f / x.x;
+    const float2 px = mul(x, make_float2(q, 0.f));
+    float rh, rl;
+    two_sum(1.0f, -px.x, rh, rl);
+    rl -= px.y;
+    const float r = rh + rl;
+    float s, e;
+    fast_two_sum(q, q * r, s, e);
+    return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ double val(float2 x) { return (double)x.x + (double)x.y; }
+
+}  // namespace ff
+
+template <int NB>
+__global__ void __launch_bounds__(kGjThreads) k_gj_ff(GjJobs2 jobs, double kappa_max)
+{
+    const GjJob &J = jobs.j[blockIdx.y];
+    const int m = blockIdx.x;
+    if (m >= J.count) return;
+    const int n = J.n;
+    const double *__restrict__ X = J.X + (size_t)m * J.x_stride;
+    float2 *__restrict__ Wk = J.work + (size_t)m * J.x_stride;
+    double *__restrict__ Dout = J.Dinv + (size_t)m * J.d_stride;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *P = reinterpret_cast<float2 *>(smem_raw);   // [n][NB], later a [32][33] tile
+    float2 *U = P + p_region(n, NB);                      // [NB][32]
+    short *used = reinterpret_cast<short *>(U + NB * 32);
+    short *pp = used + n;
+    short *rowc = pp + n;
+    __shared__ double red_v[kGjWarps];
+    __shared__ int red_i[kGjWarps];
+    __shared__ float red_f[kGjWarps];
+    __shared__ int s_p, s_sing;
+    __shared__ float s_xnorm;
+
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    // float-pair copy of X and ||X||_inf (max row sum of |x|, one warp per row)
+    float rmax = 0.f;
+    for (int i = wid; i < n; i += kGjWarps) {
+        float rs = 0.f;
+        for (int c = lane; c < n; c += 32) {
+            const double x = X[(size_t)i * n + c];
+            const float h = (float)x;
+            Wk[(size_t)i * n + c] = make_float2(h, (float)(x - (double)h));
+            rs += fabsf(h);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        rmax = fmaxf(rmax, rs);
+    }
+    if (lane == 0) red_f[wid] = rmax;
+    for (int i = t; i < n; i += kGjThreads) { used[i] = 0; rowc[i] = -1; }
+    if (t == 0) s_sing = 0;
+    __syncthreads();
+    if (t == 0) {
+        float xm = 0.f;
+        for (int q = 0; q < kGjWarps; ++q) xm = fmaxf(xm, red_f[q]);
+        s_xnorm = xm;
+    }
+    double logabs = 0.0;
+    int neg = 0;
+    __syncthreads();
+
+    for (int jb = 0; jb < n; jb += NB) {
+        const int w = min(NB, n - jb);
+        for (int q = t; q < n * NB; q += kGjThreads) {
+            const int i = q / NB, c = q - i * NB;
+            P[q] = (c < w) ? Wk[(size_t)i * n + jb + c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        double bv = -1.0;
+        int bi = n;
+        for (int i = t; i < n; i += kGjThreads)
+            if (!used[i]) argmax_merge(bv, bi, (double)fabsf(P[i * NB].x), i);
+        block_argmax(bv, bi, red_v, red_i, lane, wid);
+        __syncthreads();
+
+        for (int c = 0; c < w; ++c) {
+            if (t == 0) {
+                double v = red_v[0];
+                int b = red_i[0];
+                for (int q = 1; q < kGjWarps; ++q) argmax_merge(v, b, red_v[q], red_i[q]);
+                s_p = b;
+                if (!(v > 0.0)) s_sing = 1;
+            }
+            __syncthreads();
+            if (s_sing) break;
+            const int p = s_p;
+            const float2 piv = P[p * NB + c];
+            const float2 pinv = ff::inv(piv);
+            if (t == 0) {
+                used[p] = 1;
+                pp[jb + c] = (short)p;
+                rowc[p] = (short)c;
+                const double pv = ff::val(piv);
+                logabs += log(fabs(pv));
+                neg ^= (pv < 0.0);
+            }
+            __syncthreads();
+            if (t < NB) P[p * NB + t] = (t == c) ? pinv : ff::mul(P[p * NB + t], pinv);
+            __syncthreads();
+            double nbv = -1.0;
+            int nbi = n;
+            const int cn = c + 1;
+            for (int i = t; i < n; i += kGjThreads) {
+                if (i == p) continue;
+                const float2 f = P[i * NB + c];
+                const float2 mf = ff::neg(f);
+#pragma unroll
+                for (int cc = 0; cc < NB; ++cc)
+                    if (cc != c) P[i * NB + cc] = ff::fma2(P[i * NB + cc], mf, P[p * NB + cc]);
+                P[i * NB + c] = ff::mul(mf, pinv);
+                if (cn < w && !used[i]) argmax_merge(nbv, nbi, (double)fabsf(P[i * NB + cn].x), i);
+            }
+            block_argmax(nbv, nbi, red_v, red_i, lane, wid);
+            __syncthreads();
+        }
+        if (s_sing) break;
+
+        for (int q = t; q < n * w; q += kGjThreads) {
+            const int i = q / w, c = q - i * w;
+            Wk[(size_t)i * n + jb + c] = P[i * NB + c];
+        }
+
+        int c0 = 0;
+        auto skip = [&](int cc0) { return cc0 >= jb && cc0 + 32 <= jb + w; };
+        while (c0 < n && skip(c0)) c0 += 32;
+        constexpr int UPT = NB * 32 / kGjThreads;
+        float2 upre[UPT];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < UPT; ++r) {
+            const int q = t + r * kGjThreads, c = q >> 5, col = c0 + (q & 31);
+            upre[r] = (c0 < n && c < w && col < n) ? Wk[(size_t)pp[jb + c] * n + col] : make_float2(0.f, 0.f);
+        }
+        while (c0 < n) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < UPT; ++r) U[t + r * kGjThreads] = upre[r];
+            __syncthreads();
+            int c1 = c0 + 32;
+            while (c1 < n && skip(c1)) c1 += 32;
+#pragma unroll
+            for (int r = 0; r < UPT; ++r) {
+                const int q = t + r * kGjThreads, c = q >> 5, col = c1 + (q & 31);
+                upre[r] = (c1 < n && c < w && col < n) ? Wk[(size_t)pp[jb + c] * n + col] : make_float2(0.f, 0.f);
+            }
+            const int col = c0 + lane;
+            const bool active = col < n && !(col >= jb && col < jb + w);
+            float2 u[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) u[c] = U[c * 32 + lane];
+            if (active) {
+                for (int i = wid; i < n; i += 2 * kGjWarps) {
+                    // two rows at a time; products of a row summed with TwoSum
+                    // into the hi part and plain FP32 into the lo part, one
+                    // renormalisation per row at the end
+                    const int i2 = i + kGjWarps;
+                    const bool has2 = i2 < n;
+                    float2 x0 = (rowc[i] >= 0) ? make_float2(0.f, 0.f) : Wk[(size_t)i * n + col];
+                    float2 x1 = make_float2(0.f, 0.f);
+                    if (has2 && rowc[i2] < 0) x1 = Wk[(size_t)i2 * n + col];
+                    const float4 *pr0 = reinterpret_cast<const float4 *>(P + i * NB);
+                    const float4 *pr1 = reinterpret_cast<const float4 *>(P + (has2 ? i2 : i) * NB);
+#pragma unroll
+                    for (int c2 = 0; c2 < NB / 2; ++c2) {
+                        const float4 a0 = pr0[c2], a1 = pr1[c2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 uv = u[2 * c2 + h];
+                            const float ph0 = h ? a0.z : a0.x, pl0 = h ? a0.w : a0.y;
+                            const float ph1 = h ? a1.z : a1.x, pl1 = h ? a1.w : a1.y;
+                            float p = ph0 * uv.x, pe = fmaf(ph0, uv.x, -p);
+                            pe = fmaf(ph0, uv.y, pe);
+                            pe = fmaf(pl0, uv.x, pe);
+                            float s, e;
+                            ff::two_sum(x0.x, p, s, e);
+                            x0.x = s;
+                            x0.y += pe + e;
+                            p = ph1 * uv.x;
+                            pe = fmaf(ph1, uv.x, -p);
+                            pe = fmaf(ph1, uv.y, pe);
+                            pe = fmaf(pl1, uv.x, pe);
+                            ff::two_sum(x1.x, p, s, e);
+                            x1.x = s;
+                            x1.y += pe + e;
+                        }
+                    }
+                    float h0, l0;
+                    ff::fast_two_sum(x0.x, x0.y, h0, l0);
+                    Wk[(size_t)i * n + col] = make_float2(h0, l0);
+                    if (has2) {
+                        ff::fast_two_sum(x1.x, x1.y, h0, l0);
+                        Wk[(size_t)i2 * n + col] = make_float2(h0, l0);
+                    }
+                }
+            }
+            c0 = c1;
+        }
+        __syncthreads();
+        for (int c = t; c < w; c += kGjThreads) rowc[pp[jb + c]] = -1;
+        __syncthreads();
+    }
+
+    if (s_sing) {
+        // a zero pivot in the float pairs: the FP64 kernel decides whether X is singular
+        if (t == 0 && J.redo) J.redo[m * J.redo_stride] = 1;
+        return;
+    }
+    __syncthreads();
+
+    // ||X^-1||_inf: the rows of X^-1 are the rows of the result (columns permuted)
+    float imax = 0.f;
+    for (int i = wid; i < n; i += kGjWarps) {
+        float rs = 0.f;
+        for (int c = lane; c < n; c += 32) rs += fabsf(Wk[(size_t)i * n + c].x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        imax = fmaxf(imax, rs);
+    }
+    if (lane == 0) red_f[wid] = imax;
+
+    float2 *tile = P;   // [32][33]
+    for (int kb = 0; kb < n; kb += 32) {
+        for (int cb = 0; cb < n; cb += 32) {
+            for (int r = wid; r < 32; r += kGjWarps) {
+                const int k = kb + r, c = cb + lane;
+                tile[r * 33 + lane] = (k < n && c < n) ? Wk[(size_t)pp[k] * n + c] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int r = wid; r < 32; r += kGjWarps) {
+                const int c = cb + r, k = kb + lane;
+                if (c < n && k < n) Dout[(size_t)pp[c] * n + k] = ff::val(tile[lane * 33 + r]);
+            }
+            __syncthreads();
+        }
+    }
+
+    if (t == 0) {
+        float im = 0.f;
+        for (int q = 0; q < kGjWarps; ++q) im = fmaxf(im, red_f[q]);
+        const double kappa = (double)s_xnorm * (double)im;
+        int par = 0;
+        for (int i = 0; i < n; ++i) used[i] = 0;
+        for (int i = 0; i < n; ++i) {
+            if (used[i]) continue;
+            int len = 0, j = i;
+            while (!used[j]) { used[j] = 1; j = pp[j]; ++len; }
+            par ^= ((len & 1) == 0);
+        }
+        if (J.logabs) J.logabs[(size_t)m * J.la_stride] = logabs;
+        if (J.sign) J.sign[(size_t)m * J.la_stride] = (par ^ neg) ? -1.0 : 1.0;
+        if (J.redo && !(kappa <= kappa_max && isfinite(logabs))) J.redo[m * J.redo_stride] = 1;
+    }
+}
+
+template <int NB>
+static cudaError_t launch_gj_ff_nb(const GjJobs2 &js, int n_jobs, int nmax, int cmax, double kappa_max,
+                                   cudaStream_t st)
+{
+    const size_t sm = sizeof(float2) * (p_region(nmax, NB) + NB * 32) + sizeof(short) * 3 * (size_t)nmax;
+    cudaError_t e = cudaFuncSetAttribute(k_gj_ff<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gj_ff<NB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    dim3 grid(cmax, n_jobs);
+    k_gj_ff<NB><<<grid, kGjThreads, sm, st>>>(js, kappa_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gj_ff(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb, double kappa_max)
+{
+    GjJobs2 js;
+    int nmax = 0, cmax = 0;
+    for (int q = 0; q < 2; ++q) {
+        js.j[q] = jobs[q < n_jobs ? q : 0];
+        if (q >= n_jobs) js.j[q].count = 0;
+        nmax = max(nmax, js.j[q].n);
+        cmax = max(cmax, js.j[q].count);
+    }
+    if (cmax == 0) return cudaSuccess;
+    switch (nb) {
+    case 8: return launch_gj_ff_nb<8>(js, n_jobs, nmax, cmax, kappa_max, st);
+    case 16: return launch_gj_ff_nb<16>(js, n_jobs, nmax, cmax, kappa_max, st);
+    case 32: return launch_gj_ff_nb<32>(js, n_jobs, nmax, cmax, kappa_max, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -24,7 +24,7 @@
 // 128 MOs (N) of C2..C4.  K runs over the union of the 128 walkers' active
 // AOs, 64 per step:
 //   A operand (M x K, K-major, 128B swizzle): the walkers' AO gradient
-//     values, computed in FP32 (two threads per walker, 32 AOs each; basis
+//     values, computed in FP32 (four threads per walker, 16 AOs each; basis
 //     tables in FP32 and positions as float pairs, so no FP64 instruction
 //     runs here) and split into 16-bit hi/lo planes, zero where the walker's
 //     shell is screened out;
@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, con
 
     for (int k0 = 0; k0 < K; k0 += kC15Chunk) {
         const int kc = min(kC15Chunk, K - k0);
+        // FP64 values and Laplacians, one (walker, AO) per thread and step
         for (int q = t; q < kC15G * kc; q += kC15Threads) {
             const int g = q / kc, m = q - g * kc;
             const int mu = idx_s[k0 + m];
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, con
 
 // ------------------------------------------------------------ tcgen05 path
 constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
-constexpr int kTcThreads = 256;   // two threads per walker row
+constexpr int kTcThreads = 512;   // four threads per walker row
 constexpr uint32_t kAPlaneBytes = TC_M * TC_K * 2;     // 16 KB, one output x one split
 constexpr uint32_t kBPlaneBytes = TC_K * TC_N * 2;     // 16 KB, one split
 constexpr uint32_t kBLbo = 1024;                        // MN-major: next 64-column atom
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
 
     const SysDev &s = p.s;
     const int t = threadIdx.x, warp = t >> 5;
-    const int row = t & (TC_M - 1), khalf = t >> 7;   // walker row, half of the K step
+    const int row = t & (TC_M - 1), kq = t >> 7;      // walker row, quarter of the K step
     const int e = blockIdx.y;
     const int spin = e >= s.n_up;
     const int ei = spin ? e - s.n_up : e;
@@ -519,10 +520,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
             __syncthreads();
             if (s_abort) break;
         }
-        // A operand: gradient values of 32 AOs (this thread's half) for walker `row`
+        // A operand: gradient values of 16 AOs (this thread's quarter) for walker `row`
         int last_atom = -1;
         float dx = 0.f, dy = 0.f, dz = 0.f, d2 = 0.f;
-        for (int c8 = khalf * (TC_K / 16); c8 < (khalf + 1) * (TC_K / 16); ++c8) {
+        for (int c8 = kq * (TC_K / 32); c8 < (kq + 1) * (TC_K / 32); ++c8) {
             float v[TC_OUT][8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -631,7 +632,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     float *crow = p.Cg + (size_t)(wvalid ? w : 0) * TC_OUT * msz + (spin ? TC_OUT * (size_t)s.n_up * s.n_up : 0) +
                   (size_t)ei * ns;
     for (int l = 0; l < TC_OUT; ++l) {
-        for (int cb = (warp >> 2) * 32; cb < ncols; cb += 64) {   // warps w and w+4 share lanes, split columns
+        for (int cb = (warp >> 2) * 32; cb < ncols; cb += 32 * (kTcThreads / 128)) {   // warps w, w+4, ... share lanes
             uint32_t v[32];
             const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(l * TC_N + cb);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "

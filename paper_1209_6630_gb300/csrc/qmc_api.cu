@@ -260,6 +260,8 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     sys->device = device;
     sys->tiles.gj_panel = (d->n_up > 640 || d->n_dn > 640) ? 8 : 16;
     sys->tiles.c15_walkers = 4;
+    sys->tiles.a4_mode = QMC_A4_FLOAT_FLOAT;
+    sys->tiles.a4_kappa_max = 1e9;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
     std::vector<double> atom_R2(na, 0.0);
@@ -389,6 +391,9 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
         return invalid("qmc_system_set_tiles: gj_panel must be 8, 16 or 32");
     if (tiles->c15_walkers != 2 && tiles->c15_walkers != 4)
         return invalid("qmc_system_set_tiles: c15_walkers must be 2 or 4");
+    if (tiles->a4_mode != QMC_A4_FP64 && tiles->a4_mode != QMC_A4_FLOAT_FLOAT)
+        return invalid("qmc_system_set_tiles: a4_mode");
+    if (!(tiles->a4_kappa_max > 0.0)) return invalid("qmc_system_set_tiles: a4_kappa_max must be > 0");
     sys->tiles = *tiles;
     return QMC_OK;
 }
@@ -429,6 +434,7 @@ struct Plan {
     size_t msz;        // n_up^2 + n_dn^2
     size_t per_walker; // bytes
     bool mixed;
+    bool ffgj;         // a4 on float pairs (+ FP64 recompute flags)
     size_t cd_bytes;   // per walker: FP64 path C2..C5 in FP64; mixed C2..C4 FP32 + C5 FP64
     size_t mask_bytes; // per walker (mixed path): N x mask_words x 4
     bool dinv;
@@ -444,12 +450,15 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
     p.cd_bytes = p.mixed ? p.msz * (3 * 4 + 8) : p.msz * 4 * 8;
     p.mask_bytes = p.mixed ? (size_t)sys->d.n_elec * sys->mixed.mask_words * 4 : 0;
     p.dinv = need_dinv;
-    p.per_walker = p.msz * 8 + p.cd_bytes + (need_dinv ? p.msz * 8 : 0) + 36 + p.mask_bytes;
+    p.ffgj = p.mixed && sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT;
+    p.per_walker = p.msz * 8 + p.cd_bytes + (need_dinv ? p.msz * 8 : 0) + 36 + p.mask_bytes +
+                   (p.ffgj ? p.msz * 8 + 2 : 0);
     return p;
 }
 
 struct Carve {
     double *X; void *Cd; double *L5; double *D; double *la; double *sg; uint32_t *st; uint32_t *masks;
+    float2 *work; uint8_t *redo;
 };
 
 // Arrays for `nw` walkers laid out array by array inside ws.
@@ -471,6 +480,8 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
     c.sg = reinterpret_cast<double *>(take(16 * (size_t)nw));
     c.st = reinterpret_cast<uint32_t *>(take(4 * (size_t)nw));
     c.masks = p.mask_bytes ? reinterpret_cast<uint32_t *>(take(p.mask_bytes * nw)) : nullptr;
+    c.work = p.ffgj ? reinterpret_cast<float2 *>(take(p.msz * 8 * nw)) : nullptr;
+    c.redo = p.ffgj ? reinterpret_cast<uint8_t *>(take(2 * (size_t)nw)) : nullptr;
     return o <= ws_bytes;
 }
 
@@ -481,6 +492,7 @@ size_t bytes_for(const Plan &p, int nw)
     o += p.dinv ? al(p.msz * 8 * nw) : 0;
     o += al(16 * (size_t)nw) * 2 + al(4 * (size_t)nw);
     o += p.mask_bytes ? al(p.mask_bytes * nw) : 0;
+    o += p.ffgj ? al(p.msz * 8 * nw) + al(2 * (size_t)nw) : 0;
     return o;
 }
 
@@ -613,7 +625,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
         e = run_products(sys, precision, nw, Rc, c, st, mark);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: products launch");
         if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
-        GjJob jobs[2];
+        GjJob jobs[2] = {GjJob(), GjJob()};
         int nj = 0;
         for (int spin = 0; spin < 2; ++spin) {
             const int ns = spin ? s.n_dn : s.n_up;
@@ -626,6 +638,17 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             j.sign = c.sg + spin;
             j.flag = c.st; j.flag_bit = spin ? QMC_STATUS_SINGULAR_DN : QMC_STATUS_SINGULAR_UP;
             j.n = ns; j.count = nw;
+            if (p.ffgj) { j.work = c.work + off; j.redo = c.redo + spin; j.redo_stride = 2; }
+        }
+        if (p.ffgj) {
+            // float-pair elimination for every matrix, FP64 for those it flags
+            e = cudaMemsetAsync(c.redo, 0, 2 * (size_t)nw, st);
+            if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
+            GjJob ffj[2] = {jobs[0], jobs[1]};
+            for (int q = 0; q < nj; ++q) ffj[q].flag = nullptr;
+            e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, sys->tiles.a4_kappa_max);
+            if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: float-float Gauss-Jordan launch");
+            for (int q = 0; q < nj; ++q) jobs[q].only_redo = 1;
         }
         e = launch_gj(jobs, nj, st, sys->tiles.gj_panel);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: Gauss-Jordan launch");
@@ -734,7 +757,7 @@ extern "C" int qmc_det_inverse(int batch, int n, double *X, double *Dinv, double
     if (batch == 0) return QMC_OK;
     if (!X || !Dinv) return invalid("qmc_det_inverse: null matrix pointer");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    GjJob j;
+    GjJob j = GjJob();
     j.X = X; j.x_stride = (long long)n * n;
     j.Dinv = Dinv; j.d_stride = (long long)n * n;
     j.logabs = logabs; j.la_stride = 1;

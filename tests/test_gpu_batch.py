@@ -49,7 +49,7 @@ def test_every_tile_choice_agrees_with_oracle(systems):
     R = make_walkers(s, 12, first=777)
     Rd = torch.from_numpy(R).to(dev)
     ref = Oracle(s).eval(R)
-    start = q.tiles()
+    start = {k: v for k, v in q.tiles().items() if k in ("gj_panel", "c15_walkers")}
     try:
         for nb in (8, 16, 32):
             for g in (2, 4):
@@ -73,7 +73,7 @@ def test_autotune_chooses_valid_tiles_and_caches(systems, tmp_path):
     cache = str(tmp_path / "tiles.json")
     e1 = autotune(q, R, precision="mixed", cache=cache)
     assert e1["tiles"]["gj_panel"] in (8, 16, 32) and e1["tiles"]["c15_walkers"] in (2, 4)
-    assert q.tiles() == e1["tiles"]
+    assert {k: q.tiles()[k] for k in e1["tiles"]} == e1["tiles"]
     table = json.load(open(cache))
     assert len(table) == 1
     e2 = autotune(q, R, precision="mixed", cache=cache)      # served from the cache
