@@ -21,6 +21,7 @@
 // (three CTAs per SM); NB = 8 halves it at the cost of twice the panel sweeps.
 #include <math.h>
 
+#include "ff_math.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -304,66 +305,7 @@ cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb)
 // above `kappa_max` (near a nodal surface of Psi, where the Slater matrix
 // becomes singular) or with a non-finite result is flagged, and the caller
 // recomputes the flagged matrices with the FP64 k_gj, which skips the others.
-namespace ff {
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)   // |a| >= |b|
-{
-    s = a + b;
-    e = b - (s - a);
-}
-
-// x * y as a normalised pair
-__device__ __forceinline__ float2 mul(float2 x, float2 y)
-{
-    const float p = x.x * y.x;
-    float pe = fmaf(x.x, y.x, -p);
-    pe = fmaf(x.x, y.y, pe);
-    pe = fmaf(x.y, y.x, pe);
-    float s, e;
-    fast_two_sum(p, pe, s, e);
-    return make_float2(s, e);
-}
-
-// acc + x * y as a normalised pair
-__device__ __forceinline__ float2 fma2(float2 acc, float2 x, float2 y)
-{
-    const float p = x.x * y.x;
-    float pe = fmaf(x.x, y.x, -p);
-    pe = fmaf(x.x, y.y, pe);
-    pe = fmaf(x.y, y.x, pe);
-    float s, se;
-    two_sum(acc.x, p, s, se);
-    se += acc.y + pe;
-    float h, l;
-    fast_two_sum(s, se, h, l);
-    return make_float2(h, l);
-}
-
-// 1 / x: FP32 reciprocal refined once (Newton step in float-float)
-__device__ __forceinline__ float2 inv(float2 x)
-{
-    const float q = 1.0f / x.x;
-    const float2 px = mul(x, make_float2(q, 0.f));
-    float rh, rl;
-    two_sum(1.0f, -px.x, rh, rl);
-    rl -= px.y;
-    const float r = rh + rl;
-    float s, e;
-    fast_two_sum(q, q * r, s, e);
-    return make_float2(s, e);
-}
-
-__device__ __forceinline__ float2 neg(float2 x) { return make_float2(-x.x, -x.y); }
-__device__ __forceinline__ double val(float2 x) { return (double)x.x + (double)x.y; }
-
-}  // namespace ff
+// (float-float helpers: ff_math.cuh)
 
 template <int NB>
 __global__ void __launch_bounds__(kGjThreads) k_gj_ff(GjJobs2 jobs, double kappa_max)
@@ -525,20 +467,20 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_ff(GjJobs2 jobs, double kappa
                             const float2 uv = u[2 * c2 + h];
                             const float ph0 = h ? a0.z : a0.x, pl0 = h ? a0.w : a0.y;
                             const float ph1 = h ? a1.z : a1.x, pl1 = h ? a1.w : a1.y;
-                            float p = ph0 * uv.x, pe = fmaf(ph0, uv.x, -p);
+                            float p = __fmul_rn(ph0, uv.x), pe = fmaf(ph0, uv.x, -p);
                             pe = fmaf(ph0, uv.y, pe);
                             pe = fmaf(pl0, uv.x, pe);
                             float s, e;
                             ff::two_sum(x0.x, p, s, e);
                             x0.x = s;
-                            x0.y += pe + e;
-                            p = ph1 * uv.x;
+                            x0.y = __fadd_rn(x0.y, __fadd_rn(pe, e));
+                            p = __fmul_rn(ph1, uv.x);
                             pe = fmaf(ph1, uv.x, -p);
                             pe = fmaf(ph1, uv.y, pe);
                             pe = fmaf(pl1, uv.x, pe);
                             ff::two_sum(x1.x, p, s, e);
                             x1.x = s;
-                            x1.y += pe + e;
+                            x1.y = __fadd_rn(x1.y, __fadd_rn(pe, e));
                         }
                     }
                     float h0, l0;

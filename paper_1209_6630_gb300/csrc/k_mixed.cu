@@ -3,9 +3,9 @@
 // k_shell_mask   a1: per (walker, electron) bitmask of the active shells
 //                (the same correctly rounded d2 < R2 decisions as the FP64 path).
 // k_c15_ff       a2+a3 for C1 (the Slater matrix) and C5 (its Laplacian
-//                companion): AO values and Laplacians in FP64, products
-//                accumulated in compensated float-float arithmetic on the FP32
-//                pipes (~48-bit significand).  log|det| responds to C1 errors
+//                companion): AO values and Laplacians, and the products,
+//                in float-float arithmetic on the FP32 pipes (~48-bit
+//                significand; the products accumulated exactly).  log|det| responds to C1 errors
 //                at the 1e-10 relative level for 1000+ electrons, and the
 //                kinetic energy (from C5) must hold 1e-5 of E_L even when T and
 //                V nearly cancel; FP32 accumulation alone stops near 1e-6.
@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "ff_math.cuh"
 #include "qmc_device.cuh"
 
 namespace qmc {
@@ -109,10 +110,10 @@ __device__ int aos_from_mask(const SysDev &s, const uint32_t *bits, int mw, int 
 // is (sh - BIG) + sl (the subtraction is exact).  9 FP32 instructions.
 __device__ __forceinline__ void ff_acc(float ah, float al, float bh, float bl, float &sh, float &sl)
 {
-    const float p = ah * bh;
+    const float p = __fmul_rn(ah, bh);               // _rn: never contracted into the sum below
     const float pe = fmaf(ah, bh, -p);
-    const float sn = sh + p;
-    const float e = p - (sn - sh);
+    const float sn = __fadd_rn(sh, p);
+    const float e = __fsub_rn(p, __fsub_rn(sn, sh));
     sl = fmaf(ah, bl, sl);
     sl = fmaf(al, bh, sl);
     sl += pe + e;
@@ -127,34 +128,63 @@ __device__ __forceinline__ float pow2_above(float x)   // smallest power of two 
     return ldexpf(1.f, m == 0.5f ? ex - 1 : ex);
 }
 
-// Value and Laplacian of AO mu at r, FP64 (the two quantities C1 and C5 need).
-__device__ __forceinline__ void ao_val_lap_f64(const SysDev &s, int mu, double rx, double ry, double rz,
-                                               double &val, double &lap)
+__device__ __forceinline__ float2 ff_ipow(float2 x, int n)   // x^n, n <= 4
+{
+    switch (n) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return x;
+    case 2: return ff::mul(x, x);
+    case 3: return ff::mul(ff::mul(x, x), x);
+    case 4: { const float2 y = ff::mul(x, x); return ff::mul(y, y); }
+    default: return make_float2(0.f, 0.f);
+    }
+}
+
+// Value and Laplacian of AO mu (the two quantities C1 and C5 need) at the
+// position r (three float pairs), in float-float arithmetic:
+//   chi = c P(d) g(d2),  g = sum_p c_p e^{-gamma_p d2},  P = dx^nx dy^ny dz^nz
+//   lap chi = c (lap P g + P (gl - 4 L gd)),  gd = sum_p c_p gamma_p e_p,
+//                                            gl = sum_p c_p (4 gamma_p d2 - 6) gamma_p e_p
+// (the FP64 formulas of the other paths, each operation on float pairs).
+__device__ __forceinline__ void ao_val_lap_ff(const SysDev &s, const FfBasis &fb, int mu, const float2 *r,
+                                              float2 &val, float2 &lap)
 {
     const int sh = s.ao_shell[mu];
     const int a = s.sh_atom[sh];
-    const double dx = rx - s.Q[3 * a], dy = ry - s.Q[3 * a + 1], dz = rz - s.Q[3 * a + 2];
-    const double d2 = dx * dx + dy * dy + dz * dz;
-    double g = 0.0, gd = 0.0, gl = 0.0;
+    const float2 dx = ff::sub(r[0], fb.Q[3 * a]), dy = ff::sub(r[1], fb.Q[3 * a + 1]),
+                 dz = ff::sub(r[2], fb.Q[3 * a + 2]);
+    const float2 d2 = ff::add(ff::add(ff::mul(dx, dx), ff::mul(dy, dy)), ff::mul(dz, dz));
+    float2 g = make_float2(0.f, 0.f), gd = g, gl = g;
     const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
     for (int p = 0; p < np; ++p) {
-        const double gam = s.pg[p0 + p];
-        const double ce = s.pc[p0 + p] * exp(-gam * d2);
-        g += ce;
-        gd += gam * ce;
-        gl += (4.0 * gam * d2 - 6.0) * gam * ce;
+        const float2 gam = fb.pg[p0 + p];
+        const float2 x = ff::mul(gam, d2);
+        const float2 ce = ff::mul(fb.pc[p0 + p], ff::exp_neg(x, fb.expj));
+        g = ff::add(g, ce);
+        const float2 gce = ff::mul(gam, ce);
+        gd = ff::add(gd, gce);
+        const float2 t = ff::add(make_float2(4.f * x.x, 4.f * x.y), make_float2(-6.f, 0.f));
+        gl = ff::fma2(gl, t, gce);
     }
     const int pw = s.ao_pow[mu];
     const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
     const int L = nx + ny + nz;
-    const double px = ipow_small(dx, nx), py = ipow_small(dy, ny), pz = ipow_small(dz, nz);
-    const double P = px * py * pz;
-    const double ddx = nx > 1 ? nx * (nx - 1) * ipow_small(dx, nx - 2) : 0.0;
-    const double ddy = ny > 1 ? ny * (ny - 1) * ipow_small(dy, ny - 2) : 0.0;
-    const double ddz = nz > 1 ? nz * (nz - 1) * ipow_small(dz, nz - 2) : 0.0;
-    const double c = s.ao_scale[mu];
-    val = c * P * g;
-    lap = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * g + P * (gl - 4.0 * L * gd));
+    const float2 c = fb.sc[mu];
+    if (L == 0) {
+        val = ff::mul(c, g);
+        lap = ff::mul(c, gl);
+        return;
+    }
+    const float2 px = ff_ipow(dx, nx), py = ff_ipow(dy, ny), pz = ff_ipow(dz, nz);
+    const float2 pyz = ff::mul(py, pz);
+    const float2 P = ff::mul(px, pyz);
+    float2 lapP = make_float2(0.f, 0.f);
+    if (nx > 1) lapP = ff::mulf(ff::mul(ff_ipow(dx, nx - 2), pyz), (float)(nx * (nx - 1)));
+    if (ny > 1) lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, ff_ipow(dy, ny - 2)), pz), (float)(ny * (ny - 1))));
+    if (nz > 1) lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, py), ff_ipow(dz, nz - 2)), (float)(nz * (nz - 1))));
+    val = ff::mul(c, ff::mul(P, g));
+    const float2 inner = ff::fma2(ff::mul(lapP, g), P, ff::sub(gl, ff::mulf(gd, (float)(4 * L))));
+    lap = ff::mul(c, inner);
 }
 
 // One CTA per (electron index e, group of kC15G walkers).  The float-float
@@ -167,7 +197,7 @@ constexpr int kC15Threads = 256;
 constexpr int kC15Chunk = 1024;
 
 template <int NJ, int kC15G>
-__global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, const double *__restrict__ R,
+__global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, FfBasis fb, int nw, const double *__restrict__ R,
                                                            const uint32_t *__restrict__ masks, int mw,
                                                            const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
                                                            const float *__restrict__ Ahi1, const float *__restrict__ Alo1,
@@ -181,6 +211,7 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, con
     int *idx_s = reinterpret_cast<int *>(un_s + mw);               // [n_ao]
     __shared__ int warp_s[kC15Threads / 32];
     __shared__ float bsum_s[kC15G][2];                             // sum |b| per walker and output
+    __shared__ float2 r_s[kC15G][3];                               // walker positions as float pairs
 
     const int e = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int w0 = blockIdx.y * kC15G;
@@ -195,6 +226,10 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, con
     for (int q = t; q < kC15G * mw; q += kC15Threads) {
         const int g = q / mw, j = q - g * mw;
         mk_s[q] = (g < ng) ? masks[((size_t)(w0 + g) * s.n_elec + e) * mw + j] : 0u;
+    }
+    if (t < 3 * kC15G) {
+        const int g = t / 3, c = t - 3 * g;
+        r_s[g][c] = (g < ng) ? ff::from_double(R[((size_t)(w0 + g) * s.n_elec + e) * 3 + c]) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     for (int j = t; j < mw; j += kC15Threads) {
@@ -217,20 +252,16 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, int nw, con
 
     for (int k0 = 0; k0 < K; k0 += kC15Chunk) {
         const int kc = min(kC15Chunk, K - k0);
-        // FP64 values and Laplacians, one (walker, AO) per thread and step
+        // float-float values and Laplacians, one (walker, AO) per thread and step
         for (int q = t; q < kC15G * kc; q += kC15Threads) {
             const int g = q / kc, m = q - g * kc;
             const int mu = idx_s[k0 + m];
             const int sh = s.ao_shell[mu];
             float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
             if (g < ng && ((mk_s[g * mw + (sh >> 5)] >> (sh & 31)) & 1u)) {
-                const double *r = R + ((size_t)(w0 + g) * s.n_elec + e) * 3;
-                double v, lp;
-                ao_val_lap_f64(s, mu, r[0], r[1], r[2], v, lp);
-                b.x = (float)v;
-                b.y = (float)(v - (double)b.x);
-                b.z = (float)lp;
-                b.w = (float)(lp - (double)b.z);
+                float2 v, lp;
+                ao_val_lap_ff(s, fb, mu, r_s[g], v, lp);
+                b = make_float4(v.x, v.y, lp.x, lp.y);
             }
             b_s[g * kC15Chunk + m] = b;
         }
@@ -671,7 +702,7 @@ cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, 
 }
 
 template <int NJ, int G>
-static cudaError_t launch_c15_nj(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+static cudaError_t launch_c15_nj(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks, int mw,
                                  const float *const *Ahi, const float *const *Alo, const float *const *cmax,
                                  double *X, double *L5, cudaStream_t st)
 {
@@ -680,34 +711,34 @@ static cudaError_t launch_c15_nj(const SysDev &s, int nw, const double *R, const
     cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid(s.n_elec, (nw + G - 1) / G);
-    k_c15_ff<NJ, G><<<grid, kC15Threads, sm, st>>>(s, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], cmax[0],
+    k_c15_ff<NJ, G><<<grid, kC15Threads, sm, st>>>(s, fb, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], cmax[0],
                                                   cmax[1], X, L5);
     return cudaGetLastError();
 }
 
 template <int G>
-static cudaError_t launch_c15_g(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
+static cudaError_t launch_c15_g(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks, int mw,
                                 const float *const *Ahi, const float *const *Alo, const float *const *cmax, double *X,
                                 double *L5, cudaStream_t st)
 {
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     switch ((nmax + kC15Threads - 1) / kC15Threads) {
-    case 1: return launch_c15_nj<1, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 2: return launch_c15_nj<2, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 3: return launch_c15_nj<3, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 4: return launch_c15_nj<4, G>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 1: return launch_c15_nj<1, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 2: return launch_c15_nj<2, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 3: return launch_c15_nj<3, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 4: return launch_c15_nj<4, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
-                          const float *const *Ahi, const float *const *Alo, const float *const *cmax, double *X,
-                          double *L5, cudaStream_t st, int walkers_per_cta)
+cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks,
+                          int mw, const float *const *Ahi, const float *const *Alo, const float *const *cmax,
+                          double *X, double *L5, cudaStream_t st, int walkers_per_cta)
 {
     if (nw == 0) return cudaSuccess;
     switch (walkers_per_cta) {
-    case 2: return launch_c15_g<2>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 4: return launch_c15_g<4>(s, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 2: return launch_c15_g<2>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 4: return launch_c15_g<4>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -304,6 +304,16 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     const size_t oPgf = b.add(pgf.data(), 4 * pgf.size()), oPcf = b.add(pcf.data(), 4 * pcf.size());
     const size_t oScf = b.add(scf.data(), 4 * scf.size());
     const size_t oQh = b.add(qhi.data(), 4 * qhi.size()), oQl = b.add(qlo.data(), 4 * qlo.size());
+    // float-pair tables for the float-float AO evaluation of C1/C5
+    auto pair = [](double v) { const float h = (float)v; return float2{h, (float)(v - (double)h)}; };
+    std::vector<float2> pg2(d->n_prim), pc2(d->n_prim), sc2(nao), q2(3 * na), ej(25);
+    for (int q = 0; q < d->n_prim; ++q) { pg2[q] = pair(d->prim_gamma[q]); pc2[q] = pair(d->prim_coef[q]); }
+    for (int mu = 0; mu < nao; ++mu) sc2[mu] = pair(d->ao_scale[mu]);
+    for (int q = 0; q < 3 * na; ++q) q2[q] = pair(d->Q[q]);
+    for (int j = -12; j <= 12; ++j) ej[j + 12] = pair(exp(-j / 32.0));
+    const size_t oPg2 = b.add(pg2.data(), 8 * pg2.size()), oPc2 = b.add(pc2.data(), 8 * pc2.size());
+    const size_t oSc2 = b.add(sc2.data(), 8 * sc2.size()), oQ2 = b.add(q2.data(), 8 * q2.size());
+    const size_t oEj = b.add(ej.data(), 8 * ej.size());
     // AO derivative values enter the FP16 split scaled by 2^b_exp (bound * 2^b_exp <= 8192)
     double dbound[2] = {0.0, 0.0};
     for (int sh = 0; sh < nsh; ++sh) {
@@ -362,6 +372,11 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     mt.scf = reinterpret_cast<const float *>(dev + oScf);
     mt.Qhi = reinterpret_cast<const float *>(dev + oQh);
     mt.Qlo = reinterpret_cast<const float *>(dev + oQl);
+    mt.ffb.pg = reinterpret_cast<const float2 *>(dev + oPg2);
+    mt.ffb.pc = reinterpret_cast<const float2 *>(dev + oPc2);
+    mt.ffb.sc = reinterpret_cast<const float2 *>(dev + oSc2);
+    mt.ffb.Q = reinterpret_cast<const float2 *>(dev + oQ2);
+    mt.ffb.expj = reinterpret_cast<const float2 *>(dev + oEj);
     *out = sys;
     return QMC_OK;
 }
@@ -533,7 +548,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     cudaError_t e = launch_shell_mask(s, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    e = launch_c15_ff(s, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, mt.colmax, c.X, c.L5, st,
+    e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, mt.colmax, c.X, c.L5, st,
                       sys->tiles.c15_walkers);
     if (e != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;

@@ -38,6 +38,14 @@ struct SysDev {
     double vnn;
 };
 
+// Float-pair (hi + lo) copies of the basis for the float-float AO evaluation.
+struct FfBasis {
+    const float2 *pg, *pc;             // exponents and coefficients [n_prim]
+    const float2 *sc;                  // ao_scale [n_ao]
+    const float2 *Q;                   // nuclear positions [n_atom][3]
+    const float2 *expj;                // exp(-j/32) for j = -12..12 (index j + 12)
+};
+
 // Split-precision copies of the MO coefficients for the mixed path, per spin.
 struct MixedTables {
     const uint16_t *bhi[2], *blo[2];   // BF16 hi/lo planes [n_ao][ns_pad], ns_pad = ns rounded up to 64
@@ -51,6 +59,7 @@ struct MixedTables {
     const float *pgf, *pcf;            // FP32 copies of exponents and coefficients [n_prim]
     const float *scf;                  // FP32 copy of ao_scale [n_ao]
     const float *Qhi, *Qlo;            // nuclear positions as float pairs [n_atom][3]
+    FfBasis ffb;
 };
 
 struct TcTables {                      // what the tensor-core kernel reads, one precision mode
@@ -108,9 +117,9 @@ cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const 
                                 const double *logabs2, const double *sign2, const uint32_t *sing,
                                 const qmc_eval_out &o, int w_off, cudaStream_t st);
 cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st);
-cudaError_t launch_c15_ff(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
-                          const float *const *Ahi, const float *const *Alo, const float *const *colmax, double *X,
-                          double *L5, cudaStream_t st, int walkers_per_cta);
+cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks,
+                          int mw, const float *const *Ahi, const float *const *Alo, const float *const *colmax,
+                          double *X, double *L5, cudaStream_t st, int walkers_per_cta);
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                                const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
 cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
