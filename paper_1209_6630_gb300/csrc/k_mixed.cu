@@ -187,89 +187,303 @@ __device__ __forceinline__ void ao_val_lap_ff(const SysDev &s, const FfBasis &fb
     lap = ff::mul(c, inner);
 }
 
-// One CTA per (electron index e, group of kC15G walkers).  The float-float
-// MO coefficients of an AO are loaded once per thread and applied to every
-// walker of the group (the same electron of neighbouring walkers sees largely
-// the same AOs); AOs screened out for a walker are skipped.  The AO values
-// of up to kC15Chunk union AOs are staged at once; a larger union is handled
-// in several chunks whose partial sums are added in global memory.
-constexpr int kC15Threads = 256;
+// Ordered list of the AOs of the shells set in `bits` for a block of any
+// size (a multiple of 32 threads).  Returns the count; idx_s receives the AO indices.
+__device__ int aos_from_mask_n(const SysDev &s, const uint32_t *bits, int mw, int *idx_s, int *warp_s)
+{
+    const int nthr = blockDim.x, nwarps = nthr >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int words_per = (mw + nthr - 1) / nthr;
+    const int w0 = min((int)threadIdx.x * words_per, mw), w1 = min(w0 + words_per, mw);
+    int nao = 0;
+    for (int j = w0; j < w1; ++j)
+        for (uint32_t b = bits[j]; b; b &= b - 1) nao += ncart(s.sh_L[j * 32 + __ffs(b) - 1]);
+    // exclusive block scan of nao
+    int x = nao;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_s[wid] = x;
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int q = 0; q < nwarps; ++q) {
+        const int v = warp_s[q];
+        if (q < wid) base += v;
+        total += v;
+    }
+    __syncthreads();
+    int off = base + x - nao;
+    for (int j = w0; j < w1; ++j)
+        for (uint32_t b = bits[j]; b; b &= b - 1) {
+            const int sh = j * 32 + __ffs(b) - 1;
+            const int a0 = s.sh_ao0[sh], nc = ncart(s.sh_L[sh]);
+            for (int c = 0; c < nc; ++c, ++off) idx_s[off] = a0 + c;
+        }
+    __syncthreads();
+    return total;
+}
+
+// One CTA per (electron index e, group of G walkers).  The float-float MO
+// coefficients of an AO are loaded once per thread and applied to every
+// walker of the group that has the AO active (the same electron of
+// neighbouring walkers sees largely the same AOs).
+//
+// Columns: the N_s MO columns are split into units of 32 (one warp-wide
+// coalesced load of a coefficient row); warp w of the CTA owns units
+// w, w + nwarps, w + 2 nwarps, ...  A warp runs a loop compiled for its own
+// unit count, so no unit is computed under a false predicate.
+//
+// Union list: the CTA's AO list is the union of the G walkers' active AOs.
+// It is sorted (stably, by a counting sort) by the pattern of walkers for
+// which the AO is active, so each run of equal patterns is processed by a
+// loop compiled for that pattern: screened-out (walker, AO) pairs cost no
+// instruction.  The AO values of up to kC15Chunk union AOs are staged at
+// once; a larger union is handled in several chunks whose partial sums are
+// added in global memory.
+constexpr int kC15MaxThreads = 256;
 constexpr int kC15Chunk = 1024;
 
-template <int NJ, int kC15G>
-__global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, FfBasis fb, int nw, const double *__restrict__ R,
-                                                           const uint32_t *__restrict__ masks, int mw,
-                                                           const float *__restrict__ Ahi0, const float *__restrict__ Alo0,
-                                                           const float *__restrict__ Ahi1, const float *__restrict__ Alo1,
-                                                           const float *__restrict__ cmax0, const float *__restrict__ cmax1,
-                                                           double *__restrict__ X, double *__restrict__ L5)
+struct C15Args {
+    SysDev s;
+    FfBasis fb;
+    int nw, mw;
+    const double *R;
+    const uint32_t *masks;
+    const float *Ahi[2], *Alo[2], *cmax[2];
+    double *X, *L5;
+};
+
+// Accumulators of one warp's units for the G walkers, and the coefficient
+// pipeline (the AO being accumulated and the next one).
+template <int NU, int G>
+struct C15Acc {
+    float vh[G][NU], vl[G][NU], lh[G][NU], ll[G][NU];
+    float ah[NU], al[NU], nh[NU], nl[NU];
+};
+
+template <int NU, int G, int P>
+__device__ __forceinline__ void c15_run(C15Acc<NU, G> &acc, int m, int m_end, int k0, const int *__restrict__ idx_s,
+                                        const float4 *__restrict__ b_s, const float *__restrict__ Ahi,
+                                        const float *__restrict__ Alo, int ns, const int (&col)[NU])
+{
+    for (; m < m_end; ++m) {
+        const size_t frow = (size_t)idx_s[m + 2] * ns;    // two AOs ahead (the list is padded)
+        float fh[NU], fl[NU];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+            fh[j] = __ldg(Ahi + frow + col[j]);
+            fl[j] = __ldg(Alo + frow + col[j]);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (((P >> g) & 1) != 0) {              // constant after unrolling
+                const float4 b = b_s[g * kC15Chunk + (m - k0)];
+#pragma unroll
+                for (int j = 0; j < NU; ++j) {
+                    ff_acc(acc.ah[j], acc.al[j], b.x, b.y, acc.vh[g][j], acc.vl[g][j]);
+                    ff_acc(acc.ah[j], acc.al[j], b.z, b.w, acc.lh[g][j], acc.ll[g][j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+            acc.ah[j] = acc.nh[j]; acc.al[j] = acc.nl[j];
+            acc.nh[j] = fh[j]; acc.nl[j] = fl[j];
+        }
+    }
+}
+
+template <int NU, int G, int P>
+__device__ __forceinline__ void c15_dispatch(int p, C15Acc<NU, G> &acc, int m, int m_end, int k0,
+                                             const int *idx_s, const float4 *b_s, const float *Ahi,
+                                             const float *Alo, int ns, const int (&col)[NU])
+{
+    if constexpr (P < (1 << G)) {
+        if (p == P) c15_run<NU, G, P>(acc, m, m_end, k0, idx_s, b_s, Ahi, Alo, ns, col);
+        else c15_dispatch<NU, G, P + 1>(p, acc, m, m_end, k0, idx_s, b_s, Ahi, Alo, ns, col);
+    }
+}
+
+// Products of one chunk [k0, k0 + kc) of the sorted union list for one warp
+// owning NU column units (units whose columns lie beyond N_s read a clamped
+// column and are not stored).
+template <int NU, int G>
+__device__ __forceinline__ void c15_chunk(const C15Args &a, int unit0, int ustep, int ns, int spin, int ei, int e0w,
+                                          int ng, int k0, int kc, const int *__restrict__ idx_s,
+                                          const int *__restrict__ seg_s, const float4 *__restrict__ b_s,
+                                          const float (*bsum_s)[2])
+{
+    const int lane = threadIdx.x & 31;
+    const float *__restrict__ Ahi = spin ? a.Ahi[1] : a.Ahi[0];
+    const float *__restrict__ Alo = spin ? a.Alo[1] : a.Alo[0];
+    const float *__restrict__ cmax = spin ? a.cmax[1] : a.cmax[0];
+    int col[NU];
+    bool ok[NU];
+    float cm[NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+        const int k = (unit0 + ustep * j) * 32 + lane;
+        ok[j] = k < ns;
+        col[j] = ok[j] ? k : ns - 1;
+        cm[j] = ok[j] ? cmax[k] : 0.f;
+    }
+    C15Acc<NU, G> acc;
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+            acc.vh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][0]);
+            acc.lh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][1]);
+            acc.vl[g][j] = 0.f;
+            acc.ll[g][j] = 0.f;
+        }
+    {
+        const size_t r0 = (size_t)idx_s[k0] * ns, r1 = (size_t)idx_s[k0 + 1] * ns;
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+            acc.ah[j] = __ldg(Ahi + r0 + col[j]);
+            acc.al[j] = __ldg(Alo + r0 + col[j]);
+            acc.nh[j] = __ldg(Ahi + r1 + col[j]);
+            acc.nl[j] = __ldg(Alo + r1 + col[j]);
+        }
+    }
+    for (int p = 1; p < (1 << G); ++p) {
+        const int m = max(seg_s[p], k0), m_end = min(seg_s[p + 1], k0 + kc);
+        if (m < m_end) c15_dispatch<NU, G, 1>(p, acc, m, m_end, k0, idx_s, b_s, Ahi, Alo, ns, col);
+    }
+    // (sh - BIG) is exact; add the chunk's sums to the outputs
+    const size_t msz = (size_t)a.s.n_up * a.s.n_up + (size_t)a.s.n_dn * a.s.n_dn;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g >= ng) break;
+        const size_t off = (size_t)(e0w + g) * msz + (spin ? (size_t)a.s.n_up * a.s.n_up : 0) + (size_t)ei * ns;
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+            if (!ok[j]) continue;
+            const int k = col[j];
+            const float bv = pow2_above(2.f * cm[j] * bsum_s[g][0]);
+            const float bl = pow2_above(2.f * cm[j] * bsum_s[g][1]);
+            const double v = (double)(acc.vh[g][j] - bv) + (double)acc.vl[g][j];
+            const double lp = (double)(acc.lh[g][j] - bl) + (double)acc.ll[g][j];
+            if (k0 == 0) { a.X[off + k] = v; a.L5[off + k] = lp; }
+            else { a.X[off + k] += v; a.L5[off + k] += lp; }
+        }
+    }
+}
+
+template <int NJ, int G>
+__global__ void __launch_bounds__(kC15MaxThreads, 2) k_c15_ff(C15Args a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *b_s = reinterpret_cast<float4 *>(smem_raw);            // [G][kC15Chunk]: (vh, vl, lh, ll)
-    uint32_t *mk_s = reinterpret_cast<uint32_t *>(b_s + kC15G * kC15Chunk);   // [kC15G][mw]
-    uint32_t *un_s = mk_s + kC15G * mw;                            // [mw]
-    int *idx_s = reinterpret_cast<int *>(un_s + mw);               // [n_ao]
-    __shared__ int warp_s[kC15Threads / 32];
-    __shared__ float bsum_s[kC15G][2];                             // sum |b| per walker and output
-    __shared__ float2 r_s[kC15G][3];                               // walker positions as float pairs
+    uint32_t *mk_s = reinterpret_cast<uint32_t *>(b_s + G * kC15Chunk);   // [G][mw]
+    uint32_t *un_s = mk_s + G * a.mw;                               // [mw]
+    int *idx_s = reinterpret_cast<int *>(un_s + a.mw);              // [n_ao + 2], sorted union list
+    int *tmp_s = reinterpret_cast<int *>(b_s);                      // unsorted list (b_s is free then)
+    __shared__ int warp_s[kC15MaxThreads / 32];
+    __shared__ float bsum_s[G][2];                                  // sum |b| per walker and output
+    __shared__ float2 r_s[G][3];                                    // walker positions as float pairs
+    __shared__ int seg_s[(1 << G) + 1];                             // start of each pattern's run
 
+    const SysDev &s = a.s;
+    const int mw = a.mw;
     const int e = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int w0 = blockIdx.y * kC15G;
-    const int ng = min(kC15G, nw - w0);
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
+    const int w0 = blockIdx.y * G;
+    const int ng = min(G, a.nw - w0);
     const int spin = e >= s.n_up;
     const int ei = spin ? e - s.n_up : e;
     const int ns = spin ? s.n_dn : s.n_up;
-    const float *__restrict__ Ahi = spin ? Ahi1 : Ahi0;
-    const float *__restrict__ Alo = spin ? Alo1 : Alo0;
-    const float *__restrict__ cmax = spin ? cmax1 : cmax0;
 
-    for (int q = t; q < kC15G * mw; q += kC15Threads) {
+    for (int q = t; q < G * mw; q += nthr) {
         const int g = q / mw, j = q - g * mw;
-        mk_s[q] = (g < ng) ? masks[((size_t)(w0 + g) * s.n_elec + e) * mw + j] : 0u;
+        mk_s[q] = (g < ng) ? a.masks[((size_t)(w0 + g) * s.n_elec + e) * mw + j] : 0u;
     }
-    if (t < 3 * kC15G) {
+    if (t < 3 * G) {
         const int g = t / 3, c = t - 3 * g;
-        r_s[g][c] = (g < ng) ? ff::from_double(R[((size_t)(w0 + g) * s.n_elec + e) * 3 + c]) : make_float2(0.f, 0.f);
+        r_s[g][c] = (g < ng) ? ff::from_double(a.R[((size_t)(w0 + g) * s.n_elec + e) * 3 + c]) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int j = t; j < mw; j += kC15Threads) {
+    for (int j = t; j < mw; j += nthr) {
         uint32_t u = 0;
 #pragma unroll
-        for (int g = 0; g < kC15G; ++g) u |= mk_s[g * mw + j];
+        for (int g = 0; g < G; ++g) u |= mk_s[g * mw + j];
         un_s[j] = u;
     }
     __syncthreads();
-    const int K = aos_from_mask<kC15Threads>(s, un_s, mw, idx_s, nullptr, warp_s);
+    const int K = aos_from_mask_n(s, un_s, mw, tmp_s, warp_s);
 
-    const int kwarp = t & ~31;
-    float cm[NJ];
+    // activity pattern of every union AO, packed above the AO index
+    for (int m = t; m < K; m += nthr) {
+        const int mu = tmp_s[m], sh = s.ao_shell[mu];
+        int p = 0;
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-        const int k = t + kC15Threads * j;
-        cm[j] = (k < ns) ? cmax[k] : 0.f;
+        for (int g = 0; g < G; ++g) p |= (int)((mk_s[g * mw + (sh >> 5)] >> (sh & 31)) & 1u) << g;
+        tmp_s[m] = mu | (p << 24);
     }
+    if (t <= (1 << G)) seg_s[t] = 0;
+    __syncthreads();
+    // stable counting sort by pattern (one warp; deterministic order)
+    if (wid == 0) {
+        for (int m0 = 0; m0 < K; m0 += 32) {
+            const int m = m0 + lane;
+            const int p = m < K ? (tmp_s[m] >> 24) : (1 << G);
+            const unsigned same = __match_any_sync(0xffffffffu, p);
+            if (m < K && lane == __ffs(same) - 1) seg_s[p + 1] += __popc(same);
+            __syncwarp();
+        }
+        if (lane == 0)
+            for (int p = 1; p <= (1 << G); ++p) seg_s[p] += seg_s[p - 1];
+        __syncwarp();
+        // seg_s[p] now holds the start of pattern p's run; place entries
+        for (int m0 = 0; m0 < K; m0 += 32) {
+            const int m = m0 + lane;
+            const int v = m < K ? tmp_s[m] : 0;
+            const int p = m < K ? (v >> 24) : (1 << G);
+            const unsigned same = __match_any_sync(0xffffffffu, p);
+            int pos = 0;
+            if (m < K) pos = seg_s[p] + __popc(same & ((1u << lane) - 1u));
+            __syncwarp();
+            if (m < K) {
+                idx_s[pos] = v & 0xffffff;
+                if (lane == __ffs(same) - 1) seg_s[p] += __popc(same);
+            }
+            __syncwarp();
+        }
+        // seg_s[p] is now the end of run p = the start of run p + 1; shift back
+        if (lane == 0) {
+            for (int p = (1 << G); p >= 1; --p) seg_s[p] = seg_s[p - 1];
+            seg_s[0] = 0;
+            idx_s[K] = K > 0 ? idx_s[K - 1] : 0;     // padding read by the two-ahead prefetch
+            idx_s[K + 1] = idx_s[K];
+        }
+    }
+    __syncthreads();
+
+    const int U = (ns + 31) >> 5;                    // column units of this spin
+    const int nu = wid < U ? (U - 1 - wid) / nwarps + 1 : 0;   // units owned by this warp
     const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
 
     for (int k0 = 0; k0 < K; k0 += kC15Chunk) {
         const int kc = min(kC15Chunk, K - k0);
         // float-float values and Laplacians, one (walker, AO) per thread and step
-        for (int q = t; q < kC15G * kc; q += kC15Threads) {
+        for (int q = t; q < G * kc; q += nthr) {
             const int g = q / kc, m = q - g * kc;
             const int mu = idx_s[k0 + m];
             const int sh = s.ao_shell[mu];
             float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
             if (g < ng && ((mk_s[g * mw + (sh >> 5)] >> (sh & 31)) & 1u)) {
                 float2 v, lp;
-                ao_val_lap_ff(s, fb, mu, r_s[g], v, lp);
+                ao_val_lap_ff(s, a.fb, mu, r_s[g], v, lp);
                 b = make_float4(v.x, v.y, lp.x, lp.y);
             }
             b_s[g * kC15Chunk + m] = b;
         }
         __syncthreads();
         // sum |b_hi| per (walker, output), one warp each, fixed order (deterministic bias)
-        static_assert(2 * kC15G <= kC15Threads / 32, "one warp per (walker, output)");
-        if (wid < 2 * kC15G) {
-            const int g = wid >> 1, o = wid & 1;
+        for (int go = wid; go < 2 * G; go += nwarps) {
+            const int g = go >> 1, o = go & 1;
             float acc = 0.f;
             for (int m = lane; m < kc; m += 32) {
                 const float4 b = b_s[g * kC15Chunk + m];
@@ -280,74 +494,16 @@ __global__ void __launch_bounds__(kC15Threads, 2) k_c15_ff(SysDev s, FfBasis fb,
             if (lane == 0) bsum_s[g][o] = acc;
         }
         __syncthreads();
-        float vh[kC15G][NJ], vl[kC15G][NJ], lh[kC15G][NJ], ll[kC15G][NJ];
-#pragma unroll
-        for (int g = 0; g < kC15G; ++g)
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                vh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][0]);
-                lh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][1]);
-                vl[g][j] = 0.f;
-                ll[g][j] = 0.f;
-            }
-        // two AOs of coefficients in flight ahead of the one being accumulated
-        float ah[NJ], al[NJ], nh[NJ], nl[NJ];
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int k = t + kC15Threads * j;
-            const size_t r0 = (size_t)idx_s[k0] * ns, r1 = (size_t)idx_s[k0 + min(1, kc - 1)] * ns;
-            ah[j] = (k < ns) ? __ldg(Ahi + r0 + k) : 0.f;
-            al[j] = (k < ns) ? __ldg(Alo + r0 + k) : 0.f;
-            nh[j] = (k < ns) ? __ldg(Ahi + r1 + k) : 0.f;
-            nl[j] = (k < ns) ? __ldg(Alo + r1 + k) : 0.f;
-        }
-        for (int m = 0; m < kc; ++m) {
-            float fh[NJ], fl[NJ];
-            const size_t frow = (size_t)idx_s[k0 + min(m + 2, kc - 1)] * ns;
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const int k = t + kC15Threads * j;
-                fh[j] = (k < ns) ? __ldg(Ahi + frow + k) : 0.f;
-                fl[j] = (k < ns) ? __ldg(Alo + frow + k) : 0.f;
-            }
-#pragma unroll
-            for (int g = 0; g < kC15G; ++g) {
-                const float4 b = b_s[g * kC15Chunk + m];
-                if (b.x == 0.f && b.z == 0.f) continue;     // screened out (block-uniform)
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) {
-                    if (kwarp + kC15Threads * j >= ns) continue;
-                    ff_acc(ah[j], al[j], b.x, b.y, vh[g][j], vl[g][j]);
-                    ff_acc(ah[j], al[j], b.z, b.w, lh[g][j], ll[g][j]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) { ah[j] = nh[j]; al[j] = nl[j]; nh[j] = fh[j]; nl[j] = fl[j]; }
-        }
-        // (sh - BIG) is exact; add the chunk's sums to the outputs
-#pragma unroll
-        for (int g = 0; g < kC15G; ++g) {
-            if (g >= ng) break;
-            const size_t off = (size_t)(w0 + g) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const int k = t + kC15Threads * j;
-                if (k < ns) {
-                    const float bv = pow2_above(2.f * cm[j] * bsum_s[g][0]);
-                    const float bl = pow2_above(2.f * cm[j] * bsum_s[g][1]);
-                    const double v = (double)(vh[g][j] - bv) + (double)vl[g][j];
-                    const double lp = (double)(lh[g][j] - bl) + (double)ll[g][j];
-                    if (k0 == 0) { X[off + k] = v; L5[off + k] = lp; }
-                    else { X[off + k] += v; L5[off + k] += lp; }
-                }
-            }
+        if (nu >= NJ) c15_chunk<NJ, G>(a, wid, nwarps, ns, spin, ei, w0, ng, k0, kc, idx_s, seg_s, b_s, bsum_s);
+        else if constexpr (NJ > 1) {
+            if (nu > 0) c15_chunk<NJ - 1, G>(a, wid, nwarps, ns, spin, ei, w0, ng, k0, kc, idx_s, seg_s, b_s, bsum_s);
         }
         __syncthreads();
     }
     if (K == 0) {   // no active AO for any walker of the group: zero rows
         for (int g = 0; g < ng; ++g) {
             const size_t off = (size_t)(w0 + g) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
-            for (int k = t; k < ns; k += kC15Threads) { X[off + k] = 0.0; L5[off + k] = 0.0; }
+            for (int k = t; k < ns; k += nthr) { a.X[off + k] = 0.0; a.L5[off + k] = 0.0; }
         }
     }
 }
@@ -702,31 +858,33 @@ cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, 
 }
 
 template <int NJ, int G>
-static cudaError_t launch_c15_nj(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks, int mw,
-                                 const float *const *Ahi, const float *const *Alo, const float *const *cmax,
-                                 double *X, double *L5, cudaStream_t st)
+static cudaError_t launch_c15_nj(const C15Args &a, int nwarps, cudaStream_t st)
 {
-    const size_t sm = sizeof(float4) * G * kC15Chunk + sizeof(uint32_t) * (G + 1) * mw +
-                      sizeof(int) * (size_t)s.n_ao;
+    const size_t sm = sizeof(float4) * G * kC15Chunk + sizeof(uint32_t) * (G + 1) * a.mw +
+                      sizeof(int) * ((size_t)a.s.n_ao + 2);
     cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    dim3 grid(s.n_elec, (nw + G - 1) / G);
-    k_c15_ff<NJ, G><<<grid, kC15Threads, sm, st>>>(s, fb, nw, R, masks, mw, Ahi[0], Alo[0], Ahi[1], Alo[1], cmax[0],
-                                                  cmax[1], X, L5);
+    dim3 grid(a.s.n_elec, (a.nw + G - 1) / G);
+    k_c15_ff<NJ, G><<<grid, 32 * nwarps, sm, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int G>
-static cudaError_t launch_c15_g(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks, int mw,
-                                const float *const *Ahi, const float *const *Alo, const float *const *cmax, double *X,
-                                double *L5, cudaStream_t st)
+static cudaError_t launch_c15_g(const C15Args &a, cudaStream_t st)
 {
-    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    switch ((nmax + kC15Threads - 1) / kC15Threads) {
-    case 1: return launch_c15_nj<1, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 2: return launch_c15_nj<2, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 3: return launch_c15_nj<3, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 4: return launch_c15_nj<4, G>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    // the unsorted union list is staged in the AO-value buffer
+    if ((size_t)a.s.n_ao > (size_t)G * kC15Chunk * 4) return cudaErrorInvalidValue;
+    const int nmax = a.s.n_up > a.s.n_dn ? a.s.n_up : a.s.n_dn;
+    const int U = (nmax + 31) / 32;                       // 32-column units
+    const int nwarps = U < kC15MaxThreads / 32 ? (U > 0 ? U : 1) : kC15MaxThreads / 32;
+    switch ((U + nwarps - 1) / nwarps) {
+    case 0:
+    case 1: return launch_c15_nj<1, G>(a, nwarps, st);
+    case 2: return launch_c15_nj<2, G>(a, nwarps, st);
+    case 3: return launch_c15_nj<3, G>(a, nwarps, st);
+    case 4:
+        if constexpr (G <= 2) return launch_c15_nj<4, G>(a, nwarps, st);
+        else return launch_c15_g<2>(a, st);           // 4 units x 4 walkers would not fit the registers
     default: return cudaErrorInvalidValue;
     }
 }
@@ -736,9 +894,13 @@ cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const doub
                           double *X, double *L5, cudaStream_t st, int walkers_per_cta)
 {
     if (nw == 0) return cudaSuccess;
+    C15Args a;
+    a.s = s; a.fb = fb; a.nw = nw; a.mw = mw; a.R = R; a.masks = masks;
+    for (int spin = 0; spin < 2; ++spin) { a.Ahi[spin] = Ahi[spin]; a.Alo[spin] = Alo[spin]; a.cmax[spin] = cmax[spin]; }
+    a.X = X; a.L5 = L5;
     switch (walkers_per_cta) {
-    case 2: return launch_c15_g<2>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
-    case 4: return launch_c15_g<4>(s, fb, nw, R, masks, mw, Ahi, Alo, cmax, X, L5, st);
+    case 2: return launch_c15_g<2>(a, st);
+    case 4: return launch_c15_g<4>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }
