@@ -302,7 +302,8 @@ def main():
     tiles = q.tiles()
     if not a.no_tune:
         from paper_1209_6630_gb300.autotune import autotune
-        tiles = autotune(q, R[: min(W, 1024)], precision=prec)["tiles"]
+        tuned = autotune(q, R[: min(W, 1024)], precision=prec)
+        tiles = dict(tuned["tiles"], stage_ms=tuned.get("stage_ms"))
     wsbuf = q.workspace(W, prec)
     out = q.alloc_out(W, want_dinv=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)

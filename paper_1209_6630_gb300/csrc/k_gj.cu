@@ -308,7 +308,7 @@ cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb)
 // (float-float helpers: ff_math.cuh)
 
 template <int NB>
-__global__ void __launch_bounds__(kGjThreads) k_gj_ff(GjJobs2 jobs, double kappa_max)
+__global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) k_gj_ff(GjJobs2 jobs, double kappa_max)
 {
     const GjJob &J = jobs.j[blockIdx.y];
     const int m = blockIdx.x;
@@ -399,15 +399,20 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_ff(GjJobs2 jobs, double kappa
             double nbv = -1.0;
             int nbi = n;
             const int cn = c + 1;
-            for (int i = t; i < n; i += kGjThreads) {
-                if (i == p) continue;
-                const float2 f = P[i * NB + c];
-                const float2 mf = ff::neg(f);
-#pragma unroll
-                for (int cc = 0; cc < NB; ++cc)
-                    if (cc != c) P[i * NB + cc] = ff::fma2(P[i * NB + cc], mf, P[p * NB + cc]);
-                P[i * NB + c] = ff::mul(mf, pinv);
-                if (cn < w && !used[i]) argmax_merge(nbv, nbi, (double)fabsf(P[i * NB + cn].x), i);
+            // NB consecutive lanes share a row, one panel column each: the
+            // accesses of a warp are contiguous (no bank conflicts)
+            const int cc = t & (NB - 1);
+            const float2 prow = P[p * NB + cc];
+            for (int base = (t & ~31) / NB; base < n; base += kGjThreads / NB) {
+                const int i = base + lane / NB;
+                const bool live = i < n && i != p;
+                const float2 mf = live ? ff::neg(P[i * NB + c]) : make_float2(0.f, 0.f);
+                __syncwarp();                              // every lane has read P[i][c]
+                if (live) {
+                    const float2 v = (cc != c) ? ff::fma2(P[i * NB + cc], mf, prow) : ff::mul(mf, pinv);
+                    P[i * NB + cc] = v;
+                    if (cc == cn && cn < w && !used[i]) argmax_merge(nbv, nbi, (double)fabsf(v.x), i);
+                }
             }
             block_argmax(nbv, nbi, red_v, red_i, lane, wid);
             __syncthreads();
@@ -448,15 +453,23 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_ff(GjJobs2 jobs, double kappa
 #pragma unroll
             for (int c = 0; c < NB; ++c) u[c] = U[c * 32 + lane];
             if (active) {
+                // rows (i, i + 8) of the next iteration are loaded while the
+                // current pair is updated
+                auto load_pair = [&](int i, float2 &a, float2 &b) {
+                    const int i2 = i + kGjWarps;
+                    a = (i < n && rowc[i] < 0) ? Wk[(size_t)i * n + col] : make_float2(0.f, 0.f);
+                    b = (i2 < n && rowc[i2] < 0) ? Wk[(size_t)i2 * n + col] : make_float2(0.f, 0.f);
+                };
+                float2 nx0, nx1;
+                load_pair(wid, nx0, nx1);
                 for (int i = wid; i < n; i += 2 * kGjWarps) {
                     // two rows at a time; products of a row summed with TwoSum
                     // into the hi part and plain FP32 into the lo part, one
                     // renormalisation per row at the end
                     const int i2 = i + kGjWarps;
                     const bool has2 = i2 < n;
-                    float2 x0 = (rowc[i] >= 0) ? make_float2(0.f, 0.f) : Wk[(size_t)i * n + col];
-                    float2 x1 = make_float2(0.f, 0.f);
-                    if (has2 && rowc[i2] < 0) x1 = Wk[(size_t)i2 * n + col];
+                    float2 x0 = nx0, x1 = nx1;
+                    load_pair(i + 2 * kGjWarps, nx0, nx1);
                     const float4 *pr0 = reinterpret_cast<const float4 *>(P + i * NB);
                     const float4 *pr1 = reinterpret_cast<const float4 *>(P + (has2 ? i2 : i) * NB);
 #pragma unroll
