@@ -229,10 +229,13 @@ __device__ int aos_from_mask_n(const SysDev &s, const uint32_t *bits, int mw, in
 // walker of the group that has the AO active (the same electron of
 // neighbouring walkers sees largely the same AOs).
 //
-// Columns: the N_s MO columns are split into units of 32 (one warp-wide
-// coalesced load of a coefficient row); warp w of the CTA owns units
-// w, w + nwarps, w + 2 nwarps, ...  A warp runs a loop compiled for its own
-// unit count, so no unit is computed under a false predicate.
+// Columns: the MO columns are split into units of 32 (one coalesced 256-byte
+// load of (hi, lo) pairs per coefficient row).  With U units and W warps,
+// warp w owns the q = U / W main units w, w + W, ..., and runs a loop
+// compiled for q units.  The r = U - q W remaining units are shared by all
+// warps along the AO list: each warp accumulates them over its 1/W slice of
+// the list and the W partial sums are added in a fixed order, so every warp
+// carries the same load.
 //
 // Union list: the CTA's AO list is the union of the G walkers' active AOs.
 // It is sorted (stably, by a counting sort) by the pattern of walkers for
@@ -241,7 +244,8 @@ __device__ int aos_from_mask_n(const SysDev &s, const uint32_t *bits, int mw, in
 // instruction.  The AO values of up to kC15Chunk union AOs are staged at
 // once; a larger union is handled in several chunks whose partial sums are
 // added in global memory.
-constexpr int kC15MaxThreads = 256;
+constexpr int kC15Warps = 8;                       // warps when there are >= 8 units
+constexpr int kC15MaxThreads = 32 * kC15Warps;
 constexpr int kC15Chunk = 1024;
 
 struct C15Args {
@@ -250,138 +254,181 @@ struct C15Args {
     int nw, mw;
     const double *R;
     const uint32_t *masks;
-    const float *Ahi[2], *Alo[2], *cmax[2];
+    const float2 *A[2];                            // (hi, lo) coefficient planes [n_ao][ns32]
+    int ns32[2];
+    const float *cmax[2];
     double *X, *L5;
 };
 
-// Accumulators of one warp's units for the G walkers, and the coefficient
+// Accumulators of NU column units for the G walkers, and the coefficient
 // pipeline (the AO being accumulated and the next one).
 template <int NU, int G>
 struct C15Acc {
     float vh[G][NU], vl[G][NU], lh[G][NU], ll[G][NU];
-    float ah[NU], al[NU], nh[NU], nl[NU];
+    float2 a[NU], n[NU];
 };
 
+// Units of a warp are kC15Warps units apart (a compile-time stride).
 template <int NU, int G, int P>
 __device__ __forceinline__ void c15_run(C15Acc<NU, G> &acc, int m, int m_end, int k0, const int *__restrict__ idx_s,
-                                        const float4 *__restrict__ b_s, const float *__restrict__ Ahi,
-                                        const float *__restrict__ Alo, int ns, const int (&col)[NU])
+                                        const float4 *__restrict__ b_s, const float2 *__restrict__ A, int ns32,
+                                        int col0)
 {
+    // unrolled so that the running sums and the prefetch ring rotate through
+    // registers instead of being copied at the end of every iteration
+#pragma unroll 4
     for (; m < m_end; ++m) {
-        const size_t frow = (size_t)idx_s[m + 2] * ns;    // two AOs ahead (the list is padded)
-        float fh[NU], fl[NU];
+        const float2 *row = A + (size_t)idx_s[m + 2] * ns32 + col0;    // two AOs ahead (the list is padded)
+        float2 f[NU];
 #pragma unroll
-        for (int j = 0; j < NU; ++j) {
-            fh[j] = __ldg(Ahi + frow + col[j]);
-            fl[j] = __ldg(Alo + frow + col[j]);
-        }
+        for (int j = 0; j < NU; ++j) f[j] = __ldg(row + 32 * kC15Warps * j);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             if (((P >> g) & 1) != 0) {              // constant after unrolling
                 const float4 b = b_s[g * kC15Chunk + (m - k0)];
 #pragma unroll
                 for (int j = 0; j < NU; ++j) {
-                    ff_acc(acc.ah[j], acc.al[j], b.x, b.y, acc.vh[g][j], acc.vl[g][j]);
-                    ff_acc(acc.ah[j], acc.al[j], b.z, b.w, acc.lh[g][j], acc.ll[g][j]);
+                    ff_acc(acc.a[j].x, acc.a[j].y, b.x, b.y, acc.vh[g][j], acc.vl[g][j]);
+                    ff_acc(acc.a[j].x, acc.a[j].y, b.z, b.w, acc.lh[g][j], acc.ll[g][j]);
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < NU; ++j) {
-            acc.ah[j] = acc.nh[j]; acc.al[j] = acc.nl[j];
-            acc.nh[j] = fh[j]; acc.nl[j] = fl[j];
-        }
+        for (int j = 0; j < NU; ++j) { acc.a[j] = acc.n[j]; acc.n[j] = f[j]; }
     }
 }
 
 template <int NU, int G, int P>
 __device__ __forceinline__ void c15_dispatch(int p, C15Acc<NU, G> &acc, int m, int m_end, int k0,
-                                             const int *idx_s, const float4 *b_s, const float *Ahi,
-                                             const float *Alo, int ns, const int (&col)[NU])
+                                             const int *idx_s, const float4 *b_s, const float2 *A, int ns32,
+                                             int col0)
 {
     if constexpr (P < (1 << G)) {
-        if (p == P) c15_run<NU, G, P>(acc, m, m_end, k0, idx_s, b_s, Ahi, Alo, ns, col);
-        else c15_dispatch<NU, G, P + 1>(p, acc, m, m_end, k0, idx_s, b_s, Ahi, Alo, ns, col);
+        if (p == P) c15_run<NU, G, P>(acc, m, m_end, k0, idx_s, b_s, A, ns32, col0);
+        else c15_dispatch<NU, G, P + 1>(p, acc, m, m_end, k0, idx_s, b_s, A, ns32, col0);
     }
 }
 
-// Products of one chunk [k0, k0 + kc) of the sorted union list for one warp
-// owning NU column units (units whose columns lie beyond N_s read a clamped
-// column and are not stored).
+// Biased sums over the AOs [ma, mb) of the chunk starting at k0, for the
+// units of columns col0 + 32 kC15Warps j (j < NU) of the lane.
 template <int NU, int G>
-__device__ __forceinline__ void c15_chunk(const C15Args &a, int unit0, int ustep, int ns, int spin, int ei, int e0w,
-                                          int ng, int k0, int kc, const int *__restrict__ idx_s,
-                                          const int *__restrict__ seg_s, const float4 *__restrict__ b_s,
-                                          const float (*bsum_s)[2])
+__device__ __forceinline__ void c15_accumulate(C15Acc<NU, G> &acc, const float (&bias_v)[G][NU],
+                                               const float (&bias_l)[G][NU], int ma, int mb, int k0,
+                                               const int *__restrict__ idx_s, const int *__restrict__ seg_s,
+                                               const float4 *__restrict__ b_s, const float2 *__restrict__ A,
+                                               int ns32, int col0)
 {
-    const int lane = threadIdx.x & 31;
-    const float *__restrict__ Ahi = spin ? a.Ahi[1] : a.Ahi[0];
-    const float *__restrict__ Alo = spin ? a.Alo[1] : a.Alo[0];
-    const float *__restrict__ cmax = spin ? a.cmax[1] : a.cmax[0];
-    int col[NU];
-    bool ok[NU];
-    float cm[NU];
-#pragma unroll
-    for (int j = 0; j < NU; ++j) {
-        const int k = (unit0 + ustep * j) * 32 + lane;
-        ok[j] = k < ns;
-        col[j] = ok[j] ? k : ns - 1;
-        cm[j] = ok[j] ? cmax[k] : 0.f;
-    }
-    C15Acc<NU, G> acc;
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
-            acc.vh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][0]);
-            acc.lh[g][j] = pow2_above(2.f * cm[j] * bsum_s[g][1]);
+            acc.vh[g][j] = bias_v[g][j];
+            acc.lh[g][j] = bias_l[g][j];
             acc.vl[g][j] = 0.f;
             acc.ll[g][j] = 0.f;
         }
+    if (ma >= mb) return;
     {
-        const size_t r0 = (size_t)idx_s[k0] * ns, r1 = (size_t)idx_s[k0 + 1] * ns;
+        const float2 *r0 = A + (size_t)idx_s[ma] * ns32 + col0, *r1 = A + (size_t)idx_s[ma + 1] * ns32 + col0;
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
-            acc.ah[j] = __ldg(Ahi + r0 + col[j]);
-            acc.al[j] = __ldg(Alo + r0 + col[j]);
-            acc.nh[j] = __ldg(Ahi + r1 + col[j]);
-            acc.nl[j] = __ldg(Alo + r1 + col[j]);
+            acc.a[j] = __ldg(r0 + 32 * kC15Warps * j);
+            acc.n[j] = __ldg(r1 + 32 * kC15Warps * j);
         }
     }
     for (int p = 1; p < (1 << G); ++p) {
-        const int m = max(seg_s[p], k0), m_end = min(seg_s[p + 1], k0 + kc);
-        if (m < m_end) c15_dispatch<NU, G, 1>(p, acc, m, m_end, k0, idx_s, b_s, Ahi, Alo, ns, col);
+        const int m = max(seg_s[p], ma), m_end = min(seg_s[p + 1], mb);
+        if (m < m_end) c15_dispatch<NU, G, 1>(p, acc, m, m_end, k0, idx_s, b_s, A, ns32, col0);
     }
+}
+
+__device__ __forceinline__ size_t c15_row_offset(const SysDev &s, int w, int spin, int ei, int ns)
+{
+    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+    return (size_t)w * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+}
+
+// The NU main units of a warp (unit w + kC15Warps j): accumulate over the
+// whole chunk and add to the outputs.
+template <int NU, int G>
+__device__ __forceinline__ void c15_main(const C15Args &a, int spin, int ei, int ns, int w0, int ng, int k0, int kc,
+                                         const int *idx_s, const int *seg_s, const float4 *b_s,
+                                         const float (*bsum_s)[2])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float2 *__restrict__ A = spin ? a.A[1] : a.A[0];
+    const float *__restrict__ cmax = spin ? a.cmax[1] : a.cmax[0];
+    const int ns32 = spin ? a.ns32[1] : a.ns32[0];
+    const int col0 = wid * 32 + lane;
+    float bias_v[G][NU], bias_l[G][NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+        const float cm = cmax[col0 + 32 * kC15Warps * j];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            bias_v[g][j] = pow2_above(2.f * cm * bsum_s[g][0]);
+            bias_l[g][j] = pow2_above(2.f * cm * bsum_s[g][1]);
+        }
+    }
+    C15Acc<NU, G> acc;
+    c15_accumulate<NU, G>(acc, bias_v, bias_l, k0, k0 + kc, k0, idx_s, seg_s, b_s, A, ns32, col0);
     // (sh - BIG) is exact; add the chunk's sums to the outputs
-    const size_t msz = (size_t)a.s.n_up * a.s.n_up + (size_t)a.s.n_dn * a.s.n_dn;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         if (g >= ng) break;
-        const size_t off = (size_t)(e0w + g) * msz + (spin ? (size_t)a.s.n_up * a.s.n_up : 0) + (size_t)ei * ns;
+        const size_t off = c15_row_offset(a.s, w0 + g, spin, ei, ns);
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
-            if (!ok[j]) continue;
-            const int k = col[j];
-            const float bv = pow2_above(2.f * cm[j] * bsum_s[g][0]);
-            const float bl = pow2_above(2.f * cm[j] * bsum_s[g][1]);
-            const double v = (double)(acc.vh[g][j] - bv) + (double)acc.vl[g][j];
-            const double lp = (double)(acc.lh[g][j] - bl) + (double)acc.ll[g][j];
+            const int k = col0 + 32 * kC15Warps * j;
+            if (k >= ns) continue;
+            const double v = (double)(acc.vh[g][j] - bias_v[g][j]) + (double)acc.vl[g][j];
+            const double lp = (double)(acc.lh[g][j] - bias_l[g][j]) + (double)acc.ll[g][j];
             if (k0 == 0) { a.X[off + k] = v; a.L5[off + k] = lp; }
             else { a.X[off + k] += v; a.L5[off + k] += lp; }
         }
     }
 }
 
-template <int NJ, int G>
+// One remainder unit: this warp's partial sums over its slice of the chunk,
+// written to part_s[wid][g][o][lane].
+template <int G>
+__device__ __forceinline__ void c15_slice(const C15Args &a, int spin, int unit, int nwarps, int k0, int kc,
+                                          const int *idx_s, const int *seg_s, const float4 *b_s,
+                                          const float (*bsum_s)[2], double *part_s)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float2 *__restrict__ A = spin ? a.A[1] : a.A[0];
+    const float *__restrict__ cmax = spin ? a.cmax[1] : a.cmax[0];
+    const int ns32 = spin ? a.ns32[1] : a.ns32[0];
+    const int col0 = unit * 32 + lane;
+    const int ma = k0 + (int)((long long)kc * wid / nwarps), mb = k0 + (int)((long long)kc * (wid + 1) / nwarps);
+    float bias_v[G][1], bias_l[G][1];
+    const float cm = cmax[col0];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        bias_v[g][0] = pow2_above(2.f * cm * bsum_s[g][0]);
+        bias_l[g][0] = pow2_above(2.f * cm * bsum_s[g][1]);
+    }
+    C15Acc<1, G> acc;
+    c15_accumulate<1, G>(acc, bias_v, bias_l, ma, mb, k0, idx_s, seg_s, b_s, A, ns32, col0);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        part_s[((wid * G + g) * 2 + 0) * 32 + lane] = (double)(acc.vh[g][0] - bias_v[g][0]) + (double)acc.vl[g][0];
+        part_s[((wid * G + g) * 2 + 1) * 32 + lane] = (double)(acc.lh[g][0] - bias_l[g][0]) + (double)acc.ll[g][0];
+    }
+}
+
+template <int NQ, int G>
 __global__ void __launch_bounds__(kC15MaxThreads, 2) k_c15_ff(C15Args a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *b_s = reinterpret_cast<float4 *>(smem_raw);            // [G][kC15Chunk]: (vh, vl, lh, ll)
-    uint32_t *mk_s = reinterpret_cast<uint32_t *>(b_s + G * kC15Chunk);   // [G][mw]
+    double *part_s = reinterpret_cast<double *>(b_s + G * kC15Chunk);   // [warps][G][2][32] remainder partials
+    uint32_t *mk_s = reinterpret_cast<uint32_t *>(part_s + kC15Warps * G * 64);   // [G][mw]
     uint32_t *un_s = mk_s + G * a.mw;                               // [mw]
     int *idx_s = reinterpret_cast<int *>(un_s + a.mw);              // [n_ao + 2], sorted union list
     int *tmp_s = reinterpret_cast<int *>(b_s);                      // unsorted list (b_s is free then)
-    __shared__ int warp_s[kC15MaxThreads / 32];
+    __shared__ int warp_s[kC15Warps];
     __shared__ float bsum_s[G][2];                                  // sum |b| per walker and output
     __shared__ float2 r_s[G][3];                                    // walker positions as float pairs
     __shared__ int seg_s[(1 << G) + 1];                             // start of each pattern's run
@@ -436,7 +483,7 @@ __global__ void __launch_bounds__(kC15MaxThreads, 2) k_c15_ff(C15Args a)
         if (lane == 0)
             for (int p = 1; p <= (1 << G); ++p) seg_s[p] += seg_s[p - 1];
         __syncwarp();
-        // seg_s[p] now holds the start of pattern p's run; place entries
+        // seg_s[p] holds the start of pattern p's run; place the entries
         for (int m0 = 0; m0 < K; m0 += 32) {
             const int m = m0 + lane;
             const int v = m < K ? tmp_s[m] : 0;
@@ -451,7 +498,7 @@ __global__ void __launch_bounds__(kC15MaxThreads, 2) k_c15_ff(C15Args a)
             }
             __syncwarp();
         }
-        // seg_s[p] is now the end of run p = the start of run p + 1; shift back
+        // seg_s[p] is now the end of run p, i.e. the start of run p + 1
         if (lane == 0) {
             for (int p = (1 << G); p >= 1; --p) seg_s[p] = seg_s[p - 1];
             seg_s[0] = 0;
@@ -461,15 +508,18 @@ __global__ void __launch_bounds__(kC15MaxThreads, 2) k_c15_ff(C15Args a)
     }
     __syncthreads();
 
-    const int U = (ns + 31) >> 5;                    // column units of this spin
-    const int nu = wid < U ? (U - 1 - wid) / nwarps + 1 : 0;   // units owned by this warp
-    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+    // column units of this spin: q main units per warp (when a loop is
+    // compiled for that count, else none) and r units shared along the list
+    const int U = (ns + 31) >> 5;
+    int q = U / nwarps;
+    if (q != NQ && (NQ == 1 || q != NQ - 1)) q = 0;
+    const int r = U - q * nwarps;
 
     for (int k0 = 0; k0 < K; k0 += kC15Chunk) {
         const int kc = min(kC15Chunk, K - k0);
         // float-float values and Laplacians, one (walker, AO) per thread and step
-        for (int q = t; q < G * kc; q += nthr) {
-            const int g = q / kc, m = q - g * kc;
+        for (int qq = t; qq < G * kc; qq += nthr) {
+            const int g = qq / kc, m = qq - g * kc;
             const int mu = idx_s[k0 + m];
             const int sh = s.ao_shell[mu];
             float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -494,15 +544,33 @@ __global__ void __launch_bounds__(kC15MaxThreads, 2) k_c15_ff(C15Args a)
             if (lane == 0) bsum_s[g][o] = acc;
         }
         __syncthreads();
-        if (nu >= NJ) c15_chunk<NJ, G>(a, wid, nwarps, ns, spin, ei, w0, ng, k0, kc, idx_s, seg_s, b_s, bsum_s);
-        else if constexpr (NJ > 1) {
-            if (nu > 0) c15_chunk<NJ - 1, G>(a, wid, nwarps, ns, spin, ei, w0, ng, k0, kc, idx_s, seg_s, b_s, bsum_s);
+        // main units (q is the same for every warp)
+        if (q == NQ) c15_main<NQ, G>(a, spin, ei, ns, w0, ng, k0, kc, idx_s, seg_s, b_s, bsum_s);
+        else if constexpr (NQ > 1) {
+            if (q == NQ - 1) c15_main<NQ - 1, G>(a, spin, ei, ns, w0, ng, k0, kc, idx_s, seg_s, b_s, bsum_s);
+        }
+        // remainder units, split along the AO list
+        for (int i = 0; i < r; ++i) {
+            const int unit = q * nwarps + i;
+            c15_slice<G>(a, spin, unit, nwarps, k0, kc, idx_s, seg_s, b_s, bsum_s, part_s);
+            __syncthreads();
+            for (int qq = t; qq < G * 64; qq += nthr) {
+                const int g = qq >> 6, o = (qq >> 5) & 1, l = qq & 31;
+                const int k = unit * 32 + l;
+                if (g >= ng || k >= ns) continue;
+                double v = 0.0;
+                for (int w = 0; w < nwarps; ++w) v += part_s[((w * G + g) * 2 + o) * 32 + l];
+                double *dst = (o ? a.L5 : a.X) + c15_row_offset(s, w0 + g, spin, ei, ns) + k;
+                if (k0 == 0) *dst = v;
+                else *dst += v;
+            }
+            __syncthreads();
         }
         __syncthreads();
     }
     if (K == 0) {   // no active AO for any walker of the group: zero rows
         for (int g = 0; g < ng; ++g) {
-            const size_t off = (size_t)(w0 + g) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+            const size_t off = c15_row_offset(s, w0 + g, spin, ei, ns);
             for (int k = t; k < ns; k += nthr) { a.X[off + k] = 0.0; a.L5[off + k] = 0.0; }
         }
     }
@@ -857,15 +925,15 @@ cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, 
     return cudaGetLastError();
 }
 
-template <int NJ, int G>
-static cudaError_t launch_c15_nj(const C15Args &a, int nwarps, cudaStream_t st)
+template <int NQ, int G>
+static cudaError_t launch_c15_nq(const C15Args &a, int nwarps, cudaStream_t st)
 {
-    const size_t sm = sizeof(float4) * G * kC15Chunk + sizeof(uint32_t) * (G + 1) * a.mw +
-                      sizeof(int) * ((size_t)a.s.n_ao + 2);
-    cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NJ, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = sizeof(float4) * G * kC15Chunk + sizeof(double) * kC15Warps * G * 64 +
+                      sizeof(uint32_t) * (G + 1) * a.mw + sizeof(int) * ((size_t)a.s.n_ao + 2);
+    cudaError_t e = cudaFuncSetAttribute(k_c15_ff<NQ, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid(a.s.n_elec, (a.nw + G - 1) / G);
-    k_c15_ff<NJ, G><<<grid, 32 * nwarps, sm, st>>>(a);
+    k_c15_ff<NQ, G><<<grid, 32 * nwarps, sm, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -874,29 +942,30 @@ static cudaError_t launch_c15_g(const C15Args &a, cudaStream_t st)
 {
     // the unsorted union list is staged in the AO-value buffer
     if ((size_t)a.s.n_ao > (size_t)G * kC15Chunk * 4) return cudaErrorInvalidValue;
-    const int nmax = a.s.n_up > a.s.n_dn ? a.s.n_up : a.s.n_dn;
-    const int U = (nmax + 31) / 32;                       // 32-column units
-    const int nwarps = U < kC15MaxThreads / 32 ? (U > 0 ? U : 1) : kC15MaxThreads / 32;
-    switch ((U + nwarps - 1) / nwarps) {
+    const int u_up = (a.s.n_up + 31) / 32, u_dn = (a.s.n_dn + 31) / 32;
+    const int umax = u_up > u_dn ? u_up : u_dn;
+    if (umax > 32) return cudaErrorInvalidValue;          // more than 1024 orbitals per spin
+    const int nwarps = umax < kC15Warps ? (umax > 0 ? umax : 1) : kC15Warps;
+    switch (umax / nwarps) {
     case 0:
-    case 1: return launch_c15_nj<1, G>(a, nwarps, st);
-    case 2: return launch_c15_nj<2, G>(a, nwarps, st);
-    case 3: return launch_c15_nj<3, G>(a, nwarps, st);
+    case 1: return launch_c15_nq<1, G>(a, nwarps, st);
+    case 2: return launch_c15_nq<2, G>(a, nwarps, st);
+    case 3: return launch_c15_nq<3, G>(a, nwarps, st);
     case 4:
-        if constexpr (G <= 2) return launch_c15_nj<4, G>(a, nwarps, st);
+        if constexpr (G <= 2) return launch_c15_nq<4, G>(a, nwarps, st);
         else return launch_c15_g<2>(a, st);           // 4 units x 4 walkers would not fit the registers
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks,
-                          int mw, const float *const *Ahi, const float *const *Alo, const float *const *cmax,
+                          int mw, const float2 *const *A, const int *ns32, const float *const *cmax,
                           double *X, double *L5, cudaStream_t st, int walkers_per_cta)
 {
     if (nw == 0) return cudaSuccess;
     C15Args a;
     a.s = s; a.fb = fb; a.nw = nw; a.mw = mw; a.R = R; a.masks = masks;
-    for (int spin = 0; spin < 2; ++spin) { a.Ahi[spin] = Ahi[spin]; a.Alo[spin] = Alo[spin]; a.cmax[spin] = cmax[spin]; }
+    for (int spin = 0; spin < 2; ++spin) { a.A[spin] = A[spin]; a.ns32[spin] = ns32[spin]; a.cmax[spin] = cmax[spin]; }
     a.X = X; a.L5 = L5;
     switch (walkers_per_cta) {
     case 2: return launch_c15_g<2>(a, st);

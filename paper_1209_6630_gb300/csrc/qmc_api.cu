@@ -126,8 +126,8 @@ struct Blob {
 // and FP16 hi/lo planes of A * 2^a_exp, [n_ao][n_s padded to 64]; float-float
 // planes [n_ao][n_s].  a_exp is chosen so that max |A| * 2^a_exp <= 8192.
 struct MoLayout {
-    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oFh[2], oFl[2], oCm[2];
-    int ns_pad[2], a_exp[2];
+    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oF[2], oCm[2];
+    int ns_pad[2], ns32[2], a_exp[2];
 };
 
 static void build_mo(int nao, int nu, int nd, int a_dtype, const void *A_up, const void *A_dn, Blob &b,
@@ -149,7 +149,9 @@ static void build_mo(int nao, int nu, int nd, int a_dtype, const void *A_up, con
         const double asc = ldexp(1.0, L.a_exp[spin]);
         std::vector<uint16_t> bh((size_t)nao * np, 0), bl((size_t)nao * np, 0);
         std::vector<uint16_t> hh((size_t)nao * np, 0), hl((size_t)nao * np, 0);
-        std::vector<float> fh((size_t)nao * ns), fl((size_t)nao * ns);
+        const int n32 = ((ns + 31) / 32) * 32;
+        L.ns32[spin] = n32;
+        std::vector<float2> ff((size_t)nao * n32, float2{0.f, 0.f});
         for (int mu = 0; mu < nao; ++mu)
             for (int k = 0; k < ns; ++k) {
                 const double a = A64[(size_t)mu * ns + k];
@@ -162,16 +164,14 @@ static void build_mo(int nao, int nu, int nd, int a_dtype, const void *A_up, con
                 memcpy(&hh[(size_t)mu * np + k], &h16, 2);
                 memcpy(&hl[(size_t)mu * np + k], &l16, 2);
                 const float f = (float)a;
-                fh[(size_t)mu * ns + k] = f;
-                fl[(size_t)mu * ns + k] = (float)(a - (double)f);
+                ff[(size_t)mu * n32 + k] = float2{f, (float)(a - (double)f)};
             }
         L.oBh[spin] = b.add(bh.data(), 2 * bh.size());
         L.oBl[spin] = b.add(bl.data(), 2 * bl.size());
         L.oHh[spin] = b.add(hh.data(), 2 * hh.size());
         L.oHl[spin] = b.add(hl.data(), 2 * hl.size());
-        L.oFh[spin] = b.add(fh.data(), 4 * fh.size());
-        L.oFl[spin] = b.add(fl.data(), 4 * fl.size());
-        std::vector<float> cm(ns, 0.0f);
+        L.oF[spin] = b.add(ff.data(), sizeof(float2) * ff.size());
+        std::vector<float> cm(n32, 0.0f);
         for (int mu = 0; mu < nao; ++mu)
             for (int k = 0; k < ns; ++k) cm[k] = std::max(cm[k], (float)fabs(A64[(size_t)mu * ns + k]));
         L.oCm[spin] = b.add(cm.data(), 4 * cm.size());
@@ -187,8 +187,8 @@ static void point_mo(qmc_system *sys, char *dev, const MoLayout &L)
         mt.blo[spin] = reinterpret_cast<const uint16_t *>(dev + L.oBl[spin]);
         mt.hhi[spin] = reinterpret_cast<const uint16_t *>(dev + L.oHh[spin]);
         mt.hlo[spin] = reinterpret_cast<const uint16_t *>(dev + L.oHl[spin]);
-        mt.fhi[spin] = reinterpret_cast<const float *>(dev + L.oFh[spin]);
-        mt.flo[spin] = reinterpret_cast<const float *>(dev + L.oFl[spin]);
+        mt.ff[spin] = reinterpret_cast<const float2 *>(dev + L.oF[spin]);
+        mt.ns32[spin] = L.ns32[spin];
         mt.colmax[spin] = reinterpret_cast<const float *>(dev + L.oCm[spin]);
         mt.ns_pad[spin] = L.ns_pad[spin];
         mt.a_exp[spin] = L.a_exp[spin];
@@ -548,7 +548,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     cudaError_t e = launch_shell_mask(s, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.fhi, mt.flo, mt.colmax, c.X, c.L5, st,
+    e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.ff, mt.ns32, mt.colmax, c.X, c.L5, st,
                       sys->tiles.c15_walkers);
     if (e != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;

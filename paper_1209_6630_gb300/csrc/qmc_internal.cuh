@@ -50,8 +50,9 @@ struct FfBasis {
 struct MixedTables {
     const uint16_t *bhi[2], *blo[2];   // BF16 hi/lo planes [n_ao][ns_pad], ns_pad = ns rounded up to 64
     const uint16_t *hhi[2], *hlo[2];   // FP16 hi/lo planes of A * 2^a_exp[spin], same layout
-    const float *fhi[2], *flo[2];      // float-float planes [n_ao][ns]
-    const float *colmax[2];            // max over AOs of |A[mu][k]| per MO column k [ns]
+    const float2 *ff[2];               // float-float (hi, lo) plane [n_ao][ns32], zero beyond ns
+    int ns32[2];                       // ns rounded up to 32
+    const float *colmax[2];            // max over AOs of |A[mu][k]| per MO column k [ns32], zero beyond ns
     int ns_pad[2];
     int a_exp[2];                      // FP16 planes hold A * 2^a_exp
     int b_exp;                         // FP16 path: AO gradients enter scaled by 2^b_exp
@@ -118,7 +119,7 @@ cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const 
                                 const qmc_eval_out &o, int w_off, cudaStream_t st);
 cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st);
 cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks,
-                          int mw, const float *const *Ahi, const float *const *Alo, const float *const *colmax,
+                          int mw, const float2 *const *A, const int *ns32, const float *const *colmax,
                           double *X, double *L5, cudaStream_t st, int walkers_per_cta);
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                                const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
