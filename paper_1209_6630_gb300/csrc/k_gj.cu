@@ -56,6 +56,22 @@ __device__ __forceinline__ void block_argmax(double &bv, int &bi, double *red_v,
     if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
 }
 
+__device__ __forceinline__ void argmax_merge_f(float &v, int &i, float v2, int i2)
+{
+    if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+
+__device__ __forceinline__ void block_argmax_f(float &bv, int &bi, float *red_v, int *red_i, int lane, int wid)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_down_sync(0xffffffffu, bv, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+        argmax_merge_f(bv, bi, v2, i2);
+    }
+    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+}
+
 template <int NB>
 __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
 {
@@ -324,10 +340,8 @@ __global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) 
     short *used = reinterpret_cast<short *>(U + NB * 32);
     short *pp = used + n;
     short *rowc = pp + n;
-    __shared__ double red_v[kGjWarps];
     __shared__ int red_i[kGjWarps];
     __shared__ float red_f[kGjWarps];
-    __shared__ int s_p, s_sing;
     __shared__ float s_xnorm;
 
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -347,15 +361,17 @@ __global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) 
     }
     if (lane == 0) red_f[wid] = rmax;
     for (int i = t; i < n; i += kGjThreads) { used[i] = 0; rowc[i] = -1; }
-    if (t == 0) s_sing = 0;
     __syncthreads();
     if (t == 0) {
         float xm = 0.f;
         for (int q = 0; q < kGjWarps; ++q) xm = fmaxf(xm, red_f[q]);
         s_xnorm = xm;
     }
-    double logabs = 0.0;
-    int neg = 0;
+    // |det| = (mag_h + mag_l) 2^mag_e, kept by every thread (the pivots are
+    // the same in all threads); the sign from the parity of negative pivots
+    float mag_h = 1.f, mag_l = 0.f;
+    int mag_e = 0, neg = 0;
+    bool sing = false;
     __syncthreads();
 
     for (int jb = 0; jb < n; jb += NB) {
@@ -365,59 +381,60 @@ __global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) 
             P[q] = (c < w) ? Wk[(size_t)i * n + jb + c] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        double bv = -1.0;
+        float bv = -1.f;
         int bi = n;
         for (int i = t; i < n; i += kGjThreads)
-            if (!used[i]) argmax_merge(bv, bi, (double)fabsf(P[i * NB].x), i);
-        block_argmax(bv, bi, red_v, red_i, lane, wid);
+            if (!used[i]) argmax_merge_f(bv, bi, fabsf(P[i * NB].x), i);
+        block_argmax_f(bv, bi, red_f, red_i, lane, wid);
         __syncthreads();
 
+        // NB consecutive lanes share a row, one panel column each: the
+        // accesses of a warp are contiguous (no bank conflicts)
+        const int cc = t & (NB - 1);
         for (int c = 0; c < w; ++c) {
-            if (t == 0) {
-                double v = red_v[0];
-                int b = red_i[0];
-                for (int q = 1; q < kGjWarps; ++q) argmax_merge(v, b, red_v[q], red_i[q]);
-                s_p = b;
-                if (!(v > 0.0)) s_sing = 1;
-            }
-            __syncthreads();
-            if (s_sing) break;
-            const int p = s_p;
+            // every thread merges the warps' candidates in the same order
+            float v = red_f[0];
+            int p = red_i[0];
+            for (int q = 1; q < kGjWarps; ++q) argmax_merge_f(v, p, red_f[q], red_i[q]);
+            if (!(v > 0.f)) { sing = true; break; }
             const float2 piv = P[p * NB + c];
             const float2 pinv = ff::inv(piv);
+            const float2 prow = (cc == c) ? pinv : ff::mul(P[p * NB + cc], pinv);
+            {
+                const float2 a = piv.x < 0.f ? ff::neg(piv) : piv;
+                const float2 mg = ff::mul(make_float2(mag_h, mag_l), a);
+                int ex;
+                frexpf(mg.x, &ex);
+                mag_h = ldexpf(mg.x, -ex);
+                mag_l = ldexpf(mg.y, -ex);
+                mag_e += ex;
+                neg ^= piv.x < 0.f;
+            }
             if (t == 0) {
                 used[p] = 1;
                 pp[jb + c] = (short)p;
                 rowc[p] = (short)c;
-                const double pv = ff::val(piv);
-                logabs += log(fabs(pv));
-                neg ^= (pv < 0.0);
             }
-            __syncthreads();
-            if (t < NB) P[p * NB + t] = (t == c) ? pinv : ff::mul(P[p * NB + t], pinv);
-            __syncthreads();
-            double nbv = -1.0;
+            __syncthreads();                               // the candidates and row p have been read
+            if (t < NB) P[p * NB + t] = prow;              // t < NB: column cc == t
+            float nbv = -1.f;
             int nbi = n;
             const int cn = c + 1;
-            // NB consecutive lanes share a row, one panel column each: the
-            // accesses of a warp are contiguous (no bank conflicts)
-            const int cc = t & (NB - 1);
-            const float2 prow = P[p * NB + cc];
             for (int base = (t & ~31) / NB; base < n; base += kGjThreads / NB) {
                 const int i = base + lane / NB;
                 const bool live = i < n && i != p;
                 const float2 mf = live ? ff::neg(P[i * NB + c]) : make_float2(0.f, 0.f);
                 __syncwarp();                              // every lane has read P[i][c]
                 if (live) {
-                    const float2 v = (cc != c) ? ff::fma2(P[i * NB + cc], mf, prow) : ff::mul(mf, pinv);
-                    P[i * NB + cc] = v;
-                    if (cc == cn && cn < w && !used[i]) argmax_merge(nbv, nbi, (double)fabsf(v.x), i);
+                    const float2 x = (cc != c) ? ff::fma2(P[i * NB + cc], mf, prow) : ff::mul(mf, pinv);
+                    P[i * NB + cc] = x;
+                    if (cc == cn && cn < w && !used[i]) argmax_merge_f(nbv, nbi, fabsf(x.x), i);
                 }
             }
-            block_argmax(nbv, nbi, red_v, red_i, lane, wid);
+            block_argmax_f(nbv, nbi, red_f, red_i, lane, wid);
             __syncthreads();
         }
-        if (s_sing) break;
+        if (sing) break;
 
         for (int q = t; q < n * w; q += kGjThreads) {
             const int i = q / w, c = q - i * w;
@@ -512,7 +529,7 @@ __global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) 
         __syncthreads();
     }
 
-    if (s_sing) {
+    if (sing) {
         // a zero pivot in the float pairs: the FP64 kernel decides whether X is singular
         if (t == 0 && J.redo) J.redo[m * J.redo_stride] = 1;
         return;
@@ -558,6 +575,7 @@ __global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) 
             while (!used[j]) { used[j] = 1; j = pp[j]; ++len; }
             par ^= ((len & 1) == 0);
         }
+        const double logabs = log((double)mag_h + (double)mag_l) + mag_e * 0.69314718055994530942;
         if (J.logabs) J.logabs[(size_t)m * J.la_stride] = logabs;
         if (J.sign) J.sign[(size_t)m * J.la_stride] = (par ^ neg) ? -1.0 : 1.0;
         if (J.redo && !(kappa <= kappa_max && isfinite(logabs))) J.redo[m * J.redo_stride] = 1;
