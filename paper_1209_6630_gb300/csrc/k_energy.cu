@@ -8,8 +8,18 @@
 //
 // One CTA per walker; one warp per electron row for the dot products (rows
 // of D^-1 and of C2..C5 are contiguous); warp-shuffle reductions.
+//
+// FP64 path: everything in FP64.  Mixed path (C2..C4 in FP32): the drift
+// dots in FP32 (D^-1 truncated to float by integer operations), the
+// Laplacian dot in FP64, and the Coulomb sums in float-float on the FP32
+// pipes: differences of float-pair positions, r^2 as a float pair, 1/r from
+// the FP32 reciprocal square root refined by one Newton step (relative error
+// ~2^-43), sums kept as float pairs.
 #include <math.h>
 
+#include <type_traits>
+
+#include "ff_math.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -24,6 +34,50 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// x rounded toward zero to a float by integer operations (|x| in the normal
+// float range or 0; used where a 2^-23 relative error is acceptable)
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (ex <= 0) return 0.f;
+    const unsigned int f = (unsigned int)(b >> 32 & 0x80000000u) | ((unsigned int)min(ex, 254) << 23) |
+                           (unsigned int)((b >> 29) & 0x7fffffu);
+    return __uint_as_float(f);
+}
+
+// 1/r for the float-pair difference (dx, dy, dz)
+__device__ __forceinline__ float2 ff_inv_r(float2 dx, float2 dy, float2 dz)
+{
+    const float2 r2 = ff::add(ff::add(ff::mul(dx, dx), ff::mul(dy, dy)), ff::mul(dz, dz));
+    const float y0 = rsqrtf(r2.x);
+    const float y0s = __fmul_rn(y0, y0);
+    const float2 t = make_float2(y0s, fmaf(y0, y0, -y0s));      // y0^2 exactly
+    const float2 e = ff::sub(make_float2(1.f, 0.f), ff::mul(r2, t));   // 1 - r2 y0^2, small
+    return ff::renorm(y0, 0.5f * y0 * e.x);                      // Newton step y0 (1 + e/2)
+}
+
+// Coulomb sums of one walker in float-float (mixed path); rs: 3N positions,
+// qs: 3 n_atom nuclear positions, zs: charges, all staged in shared memory.
+__device__ __forceinline__ void coulomb_ff(const SysDev &s, const float2 *rs, const float2 *qs, const float *zs,
+                                           double &ven, double &vee)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int N = s.n_elec;
+    float2 en = make_float2(0.f, 0.f), ee = make_float2(0.f, 0.f);
+    for (int e = wid; e < N; e += kEnWarps) {
+        const float2 rx = rs[3 * e], ry = rs[3 * e + 1], rz = rs[3 * e + 2];
+        for (int a = lane; a < s.n_atom; a += 32) {
+            const float2 y = ff_inv_r(ff::sub(rx, qs[3 * a]), ff::sub(ry, qs[3 * a + 1]), ff::sub(rz, qs[3 * a + 2]));
+            en = ff::add(en, ff::mulf(y, zs[a]));
+        }
+        for (int j = e + 1 + lane; j < N; j += 32)
+            ee = ff::add(ee, ff_inv_r(ff::sub(rx, rs[3 * j]), ff::sub(ry, rs[3 * j + 1]), ff::sub(rz, rs[3 * j + 2])));
+    }
+    ven = -ff::val(en);
+    vee = ff::val(ee);
+}
+
 template <typename TG>
 __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const double *__restrict__ R,
                                                              const double *__restrict__ Dinv,
@@ -31,9 +85,12 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
                                                              const double *__restrict__ logabs2,
                                                              const double *__restrict__ sign2,
                                                              const uint32_t *__restrict__ sing,
-                                                             qmc_eval_out o, int w_off)
+                                                             qmc_eval_out o, int w_off, const float2 *__restrict__ Q2)
 {
+    constexpr bool kMixed = std::is_same<TG, float>::value;
+    extern __shared__ __align__(16) unsigned char en_smem[];   // mixed: positions, nuclei, charges
     __shared__ double red[3][kEnWarps];
+    __shared__ int s_nonfinite;
     const int w = blockIdx.x;
     const int wg = w + w_off;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -54,14 +111,34 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
         const double *lrow = cv.l + (size_t)w * cv.l_wstride + (spin ? cv.l_ncomp * nu2 : 0) +
                              (size_t)cv.l_comp * nss + (size_t)ei * ns;
         double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-        for (int k = lane; k < ns; k += 32) {
-            const double d = drow[k];
-            b0 = fma(d, (double)grow[k], b0);
-            b1 = fma(d, (double)grow[nss + k], b1);
-            b2 = fma(d, (double)grow[2 * nss + k], b2);
-            b3 = fma(d, lrow[k], b3);
+        if constexpr (kMixed) {
+            float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+            for (int k = lane; k < ns; k += 32) {
+                const double d = drow[k];
+                const float df = f32_trunc(d);
+                f0 = fmaf(df, grow[k], f0);
+                f1 = fmaf(df, grow[nss + k], f1);
+                f2 = fmaf(df, grow[2 * nss + k], f2);
+                b3 = fma(d, lrow[k], b3);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                f0 += __shfl_xor_sync(0xffffffffu, f0, off);
+                f1 += __shfl_xor_sync(0xffffffffu, f1, off);
+                f2 += __shfl_xor_sync(0xffffffffu, f2, off);
+            }
+            b0 = f0; b1 = f1; b2 = f2;
+        } else {
+            for (int k = lane; k < ns; k += 32) {
+                const double d = drow[k];
+                b0 = fma(d, (double)grow[k], b0);
+                b1 = fma(d, (double)grow[nss + k], b1);
+                b2 = fma(d, (double)grow[2 * nss + k], b2);
+                b3 = fma(d, lrow[k], b3);
+            }
+            b0 = warp_sum(b0); b1 = warp_sum(b1); b2 = warp_sum(b2);
         }
-        b0 = warp_sum(b0); b1 = warp_sum(b1); b2 = warp_sum(b2); b3 = warp_sum(b3);
+        b3 = warp_sum(b3);
         if (lane == 0) {
             double *dr = o.drift + ((size_t)wg * N + e) * 3;
             dr[0] = b0; dr[1] = b1; dr[2] = b2;
@@ -70,15 +147,34 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
     }
 
     double ven = 0.0, vee = 0.0;
-    for (int e = wid; e < N; e += kEnWarps) {
-        const double rx = Rw[3 * e], ry = Rw[3 * e + 1], rz = Rw[3 * e + 2];
-        for (int a = lane; a < s.n_atom; a += 32) {
-            const double dx = rx - s.Q[3 * a], dy = ry - s.Q[3 * a + 1], dz = rz - s.Q[3 * a + 2];
-            ven -= s.Z[a] * rsqrt(dx * dx + dy * dy + dz * dz);
+    if constexpr (kMixed) {
+        float2 *rs = reinterpret_cast<float2 *>(en_smem);
+        float2 *qs = rs + 3 * N;
+        float *zs = reinterpret_cast<float *>(qs + 3 * s.n_atom);
+        if (t == 0) s_nonfinite = 0;
+        __syncthreads();
+        int bad = 0;
+        for (int q = t; q < 3 * N; q += kEnThreads) {
+            const double x = Rw[q];
+            bad |= !isfinite(x);
+            rs[q] = ff::from_double(x);
         }
-        for (int j = e + 1 + lane; j < N; j += 32) {
-            const double dx = rx - Rw[3 * j], dy = ry - Rw[3 * j + 1], dz = rz - Rw[3 * j + 2];
-            vee += rsqrt(dx * dx + dy * dy + dz * dz);
+        for (int q = t; q < 3 * s.n_atom; q += kEnThreads) qs[q] = Q2[q];
+        for (int a = t; a < s.n_atom; a += kEnThreads) zs[a] = (float)s.Z[a];
+        if (bad) s_nonfinite = 1;
+        __syncthreads();
+        coulomb_ff(s, rs, qs, zs, ven, vee);
+    } else {
+        for (int e = wid; e < N; e += kEnWarps) {
+            const double rx = Rw[3 * e], ry = Rw[3 * e + 1], rz = Rw[3 * e + 2];
+            for (int a = lane; a < s.n_atom; a += 32) {
+                const double dx = rx - s.Q[3 * a], dy = ry - s.Q[3 * a + 1], dz = rz - s.Q[3 * a + 2];
+                ven -= s.Z[a] * rsqrt(dx * dx + dy * dy + dz * dz);
+            }
+            for (int j = e + 1 + lane; j < N; j += 32) {
+                const double dx = rx - Rw[3 * j], dy = ry - Rw[3 * j + 1], dz = rz - Rw[3 * j + 2];
+                vee += rsqrt(dx * dx + dy * dy + dz * dz);
+            }
         }
     }
     ven = warp_sum(ven);
@@ -96,7 +192,9 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
         uint32_t st = sing[w];
         const bool singular = (st & (QMC_STATUS_SINGULAR_UP | QMC_STATUS_SINGULAR_DN)) != 0;
         bool finite_in = true;
-        for (int q = 0; q < 3 * N; ++q) finite_in = finite_in && isfinite(Rw[q]);
+        if constexpr (kMixed) finite_in = !s_nonfinite;
+        else
+            for (int q = 0; q < 3 * N; ++q) finite_in = finite_in && isfinite(Rw[q]);
         if (!finite_in) st |= QMC_STATUS_NONFINITE;
         if (!singular && !(isfinite(el) && isfinite(la0) && isfinite(la1))) st |= QMC_STATUS_NONFINITE;
         o.logpsi[wg] = singular ? -INFINITY : la0 + la1;
@@ -113,15 +211,20 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
 
 cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv, const CView &cv,
                                 const double *logabs2, const double *sign2, const uint32_t *sing,
-                                const qmc_eval_out &o, int w_off, cudaStream_t st)
+                                const qmc_eval_out &o, int w_off, cudaStream_t st, const float2 *Q2)
 {
     if (nw == 0) return cudaSuccess;
-    if (cv.g_f32)
-        k_drift_energy<float><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, static_cast<const float *>(cv.g), cv,
-                                                         logabs2, sign2, sing, o, w_off);
-    else
+    if (cv.g_f32) {
+        const size_t sm = sizeof(float2) * 3 * ((size_t)s.n_elec + s.n_atom) + sizeof(float) * (size_t)s.n_atom;
+        cudaError_t e = cudaFuncSetAttribute(k_drift_energy<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+        k_drift_energy<float><<<nw, kEnThreads, sm, st>>>(s, R, Dinv, static_cast<const float *>(cv.g), cv,
+                                                          logabs2, sign2, sing, o, w_off, Q2);
+    } else {
         k_drift_energy<double><<<nw, kEnThreads, 0, st>>>(s, R, Dinv, static_cast<const double *>(cv.g), cv,
-                                                          logabs2, sign2, sing, o, w_off);
+                                                           logabs2, sign2, sing, o, w_off, nullptr);
+    }
     return cudaGetLastError();
 }
 

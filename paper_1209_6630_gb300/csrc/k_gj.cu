@@ -470,15 +470,17 @@ __global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) 
 #pragma unroll
             for (int c = 0; c < NB; ++c) u[c] = U[c * 32 + lane];
             if (active) {
-                // rows (i, i + 8) of the next iteration are loaded while the
+                // rows (i, i + 8) two iterations ahead are loaded while the
                 // current pair is updated
                 auto load_pair = [&](int i, float2 &a, float2 &b) {
                     const int i2 = i + kGjWarps;
                     a = (i < n && rowc[i] < 0) ? Wk[(size_t)i * n + col] : make_float2(0.f, 0.f);
                     b = (i2 < n && rowc[i2] < 0) ? Wk[(size_t)i2 * n + col] : make_float2(0.f, 0.f);
                 };
-                float2 nx0, nx1;
+                float2 nx0, nx1, mx0, mx1;                 // two row pairs ahead
                 load_pair(wid, nx0, nx1);
+                load_pair(wid + 2 * kGjWarps, mx0, mx1);
+#pragma unroll 2
                 for (int i = wid; i < n; i += 2 * kGjWarps) {
                     // two rows at a time; products of a row summed with TwoSum
                     // into the hi part and plain FP32 into the lo part, one
@@ -486,7 +488,9 @@ __global__ void __launch_bounds__(kGjThreads, NB == 8 ? 4 : (NB == 16 ? 3 : 1)) 
                     const int i2 = i + kGjWarps;
                     const bool has2 = i2 < n;
                     float2 x0 = nx0, x1 = nx1;
-                    load_pair(i + 2 * kGjWarps, nx0, nx1);
+                    nx0 = mx0;
+                    nx1 = mx1;
+                    load_pair(i + 4 * kGjWarps, mx0, mx1);
                     const float4 *pr0 = reinterpret_cast<const float4 *>(P + i * NB);
                     const float4 *pr1 = reinterpret_cast<const float4 *>(P + (has2 ? i2 : i) * NB);
 #pragma unroll

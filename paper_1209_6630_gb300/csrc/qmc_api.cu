@@ -668,7 +668,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
         e = launch_gj(jobs, nj, st, sys->tiles.gj_panel);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: Gauss-Jordan launch");
         if ((e = mark(2)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
-        e = launch_drift_energy(s, nw, Rc, Dinv, cview(p, c), c.la, c.sg, c.st, *out, w0, st);
+        e = launch_drift_energy(s, nw, Rc, Dinv, cview(p, c), c.la, c.sg, c.st, *out, w0, st, sys->mixed.ffb.Q);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: energy launch");
         if (stage_ms) {
             if ((e = mark(3)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");

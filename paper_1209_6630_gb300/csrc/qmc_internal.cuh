@@ -116,7 +116,7 @@ struct CView {
 
 cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv, const CView &cv,
                                 const double *logabs2, const double *sign2, const uint32_t *sing,
-                                const qmc_eval_out &o, int w_off, cudaStream_t st);
+                                const qmc_eval_out &o, int w_off, cudaStream_t st, const float2 *Q2);
 cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st);
 cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks,
                           int mw, const float2 *const *A, const int *ns32, const float *const *colmax,
