@@ -302,6 +302,18 @@ int qmc_screen_ao(const qmc_system *sys, int n_walk, const double *R, int cap, i
                   int32_t *idx, double *B, qmc_stream_t stream);
 
 /*
+ * qmc_shell_masks -- step a1 of the mixed path alone: bit (sh & 31) of word
+ * (sh >> 5) of masks[w][e] is set iff shell sh is active for electron e of
+ * walker w (Sec. III: d^2 < R^2_shell and d^2 < R^2_atom, the same
+ * correctly rounded FP64 decisions as qmc_screen_ao).  *mask_words receives
+ * the number of 32-bit words per electron, ceil(n_shell / 32); with
+ * masks == NULL only that number is returned.
+ *   R device [W][N][3] f64;  masks device [W][N][mask_words] u32
+ */
+int qmc_shell_masks(const qmc_system *sys, int n_walk, const double *R, uint32_t *masks, int *mask_words,
+                    qmc_stream_t stream);
+
+/*
  * qmc_slater_matrices -- steps a1..a3 alone: C_l[e][k] = d_l phi_k(r_e),
  * l = 0 value, 1..3 gradient, 4 Laplacian; per walker the up block
  * [5][n_up][n_up] followed by the down block [5][n_dn][n_dn], FP64, at the

@@ -85,6 +85,7 @@ def lib():
             L.qmc_walkers_eval_static.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp]
             L.qmc_logpsi_backward.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qmc_screen_ao.argtypes = [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]
+            L.qmc_shell_masks.argtypes = [_vp, _i, _vp, _vp, C.POINTER(_i), _vp]
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo",
@@ -92,7 +93,7 @@ def lib():
                          "qmc_batch_eval", "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
                          "qmc_workspace_size",
                          "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static",
-                         "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+                         "qmc_logpsi_backward", "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices",
                          "qmc_det_inverse"):
                 getattr(L, name).restype = _i
             _lib = L
@@ -109,5 +110,5 @@ def check(rc):
 EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo", "qmc_workspace_size",
             "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size", "qmc_batch_eval",
             "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
-            "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_slater_matrices",
+            "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices",
             "qmc_det_inverse", "qmc_last_error", "qmc_version")

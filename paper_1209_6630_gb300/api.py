@@ -172,6 +172,16 @@ class QmcSystem:
         check(lib().qmc_screen_ao(self._h, W, _ptr(R), cap, _ptr(cnt), _ptr(idx), _ptr(B), _stream(self.device)))
         return cnt, idx, B
 
+    def shell_masks(self, R):
+        """Step a1 of the mixed path (qmc_shell_masks): active-shell bitmasks [W, N, words] (int32 view)."""
+        W = int(R.shape[0])
+        _req_cuda(R, torch.float64, "R", (W, self.N, 3))
+        words = C.c_int(0)
+        check(lib().qmc_shell_masks(self._h, 0, None, None, C.byref(words), _stream(self.device)))
+        masks = torch.zeros(W, self.N, words.value, dtype=torch.int32, device=self.device)
+        check(lib().qmc_shell_masks(self._h, W, _ptr(R), _ptr(masks), C.byref(words), _stream(self.device)))
+        return masks
+
     def slater(self, R, precision: str = "f64", ws=None):
         """Steps a1..a3 (qmc_slater_matrices): per walker [5][n_up][n_up] then [5][n_dn][n_dn]."""
         W = int(R.shape[0])

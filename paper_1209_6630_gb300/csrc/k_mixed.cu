@@ -44,22 +44,45 @@
 namespace qmc {
 
 // ---------------------------------------------------------------- masks ----
+// The decision d2 < R2 must equal the FP64 one (d2 rounded as in sqdist_rn).
+// It is taken in FP32 when the FP32 value of d2 lies outside a band around R2
+// that bounds its error: with S = sum_c (|r_c| + |Q_c|),
+//   |d2_f32 - d2| <= 2^-20 (d2_f32 + S^2)  (input rounding 2^-24 per coordinate,
+//   three roundings of the sum of squares), |R2_f32 - R2| <= 2^-24 R2;
+// the band used is 2^-18 (d2_f32 + S^2 + R2_f32).  Inside the band (a few
+// pairs in a thousand) the exact FP64 test decides.
 constexpr int kMaskThreads = 128;
 
-__global__ void __launch_bounds__(kMaskThreads) k_shell_mask(SysDev s, const double *__restrict__ R, int mw,
+__global__ void __launch_bounds__(kMaskThreads) k_shell_mask(SysDev s, const float *__restrict__ Qf,
+                                                             const float *__restrict__ aR2f,
+                                                             const float *__restrict__ sR2f,
+                                                             const double *__restrict__ R, int mw,
                                                              uint32_t *__restrict__ masks)
 {
     extern __shared__ uint32_t mbits[];   // [mw]
     const int e = blockIdx.x, w = blockIdx.y;
     const double *r = R + ((size_t)w * s.n_elec + e) * 3;
     const double rx = r[0], ry = r[1], rz = r[2];
+    const float fx = (float)rx, fy = (float)ry, fz = (float)rz;
     for (int j = threadIdx.x; j < mw; j += kMaskThreads) mbits[j] = 0u;
     __syncthreads();
     for (int a = threadIdx.x; a < s.n_atom; a += kMaskThreads) {
-        const double d2 = sqdist_rn(rx, ry, rz, s.Q + 3 * a);
-        if (!(d2 < s.atom_R2[a])) continue;
+        const float qx = Qf[3 * a], qy = Qf[3 * a + 1], qz = Qf[3 * a + 2];
+        const float dx = fx - qx, dy = fy - qy, dz = fz - qz;
+        const float d2f = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        const float S = fabsf(fx) + fabsf(qx) + fabsf(fy) + fabsf(qy) + fabsf(fz) + fabsf(qz);
+        const float band0 = 0x1p-18f * (d2f + S * S);
+        double d2 = -1.0;                                   // exact value, computed on demand
+        auto inside = [&](float r2f, double r2) {
+            const float band = band0 + 0x1p-18f * r2f;
+            if (d2f < r2f - band) return true;
+            if (d2f > r2f + band) return false;
+            if (d2 < 0.0) d2 = sqdist_rn(rx, ry, rz, s.Q + 3 * a);
+            return d2 < r2;                                 // also false for NaN
+        };
+        if (!inside(aR2f[a], s.atom_R2[a])) continue;
         for (int sh = s.atom_sh0[a]; sh < s.atom_sh0[a + 1]; ++sh)
-            if (d2 < s.sh_R2[sh]) atomicOr(&mbits[sh >> 5], 1u << (sh & 31));
+            if (inside(sR2f[sh], s.sh_R2[sh])) atomicOr(&mbits[sh >> 5], 1u << (sh & 31));
     }
     __syncthreads();
     uint32_t *dst = masks + ((size_t)w * s.n_elec + e) * mw;
@@ -698,6 +721,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     int *ao_s = reinterpret_cast<int *>(mask_s + TC_M * p.mw);                // [n_ao + 64]
     __shared__ uint32_t union_s[256];
     __shared__ int warp_s[kTcThreads / 32];
+    __shared__ int4 meta_s[2][TC_K];                           // {mu, shell, atom, first primitive}
+    __shared__ int4 meta2_s[2][TC_K];                          // {primitives, powers, scale bits, -}
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
@@ -769,26 +794,64 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     const uint16_t *__restrict__ Blo = p.tt.lo[spin];
     const float isc0 = p.tt.in_scale[0], isc1 = p.tt.in_scale[1], isc2 = p.tt.in_scale[2];
 
-    for (int ks = 0; ks < nks; ++ks) {
-        if (ks > 0) {
-            if (!mbar_wait(mbar_a, (ks - 1) & 1, kWait)) { s_abort = 1; }
-            __syncthreads();
-            if (s_abort) break;
+    // Per K step, the 64 AOs' metadata is staged in shared memory one step
+    // ahead (threads 0..63 walk AO -> shell -> atom / primitives while the
+    // step before is being produced); the B rows of a step are loaded into
+    // registers first, and the first 8 AO gradients of a thread are computed
+    // before waiting for the previous step's MMAs, which therefore overlap
+    // the production.  The radial part is computed once per shell.
+    auto load_meta = [&](int ks_, int4 &m0, int4 &m1) {
+        const int mu = ao_s[ks_ * TC_K + t];
+        if (mu >= 0) {
+            const int sh = s.ao_shell[mu];
+            m0 = make_int4(mu, sh, s.sh_atom[sh], s.sh_pstart[sh]);
+            m1 = make_int4(s.sh_nprim[sh], s.ao_pow[mu], __float_as_int(scf[mu]), 0);
+        } else {
+            m0 = make_int4(-1, 0, 0, 0);
+            m1 = make_int4(0, 0, 0, 0);
         }
-        // A operand: gradient values of 16 AOs (this thread's quarter) for walker `row`
-        int last_atom = -1;
-        float dx = 0.f, dy = 0.f, dz = 0.f, d2 = 0.f;
-        for (int c8 = kq * (TC_K / 32); c8 < (kq + 1) * (TC_K / 32); ++c8) {
-            float v[TC_OUT][8];
+    };
+    if (t < TC_K && nks > 0) {
+        int4 m0, m1;
+        load_meta(0, m0, m1);
+        meta_s[0][t] = m0;
+        meta2_s[0][t] = m1;
+    }
+    __syncthreads();
+
+    constexpr int kBChunks = 2 * TC_K * (TC_N / 8) / kTcThreads;   // 16-byte B chunks per thread
+    for (int ks = 0; ks < nks; ++ks) {
+        const int buf = ks & 1;
+        const bool has_next = ks + 1 < nks;
+        int4 nm0 = make_int4(-1, 0, 0, 0), nm1 = make_int4(0, 0, 0, 0);
+        if (t < TC_K && has_next) load_meta(ks + 1, nm0, nm1);
+        // B operand rows A[mu][k0 .. k0+127] of both planes, into registers
+        uint4 bv[kBChunks];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int pos = ks * TC_K + c8 * 8 + q;
-                const int mu = ao_s[pos];
-                float g1 = 0.f, g2 = 0.f, g3 = 0.f;
-                if (mu >= 0 && wvalid) {
-                    const int sh = s.ao_shell[mu];
-                    if ((my_mask[sh >> 5] >> (sh & 31)) & 1u) {
-                        const int a = s.sh_atom[sh];
+        for (int j = 0; j < kBChunks; ++j) {
+            const int q = t + j * kTcThreads;
+            const int plane = q / (TC_K * (TC_N / 8));
+            const int rem = q - plane * (TC_K * (TC_N / 8));
+            const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
+            const int mu = meta_s[buf][r].x;
+            bv[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (mu >= 0 && 8 * c < ncols)
+                bv[j] = __ldg(reinterpret_cast<const uint4 *>((plane ? Blo : Bhi) + (size_t)mu * nspad + k0 + 8 * c));
+        }
+        // A operand: gradient values of 16 AOs (this thread's quarter) for walker `row`, 8 at a time
+        {
+            int last_atom = -1, last_sh = -1;
+            float dx = 0.f, dy = 0.f, dz = 0.f, d2 = 0.f, g = 0.f, gd = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                float v[TC_OUT][8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int4 m0 = meta_s[buf][kq * 16 + 8 * h + q];
+                    const int sh = m0.y;
+                    float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+                    if (m0.x >= 0 && wvalid && ((my_mask[sh >> 5] >> (sh & 31)) & 1u)) {
+                        const int4 m1 = meta2_s[buf][kq * 16 + 8 * h + q];
+                        const int a = m0.z;
                         if (a != last_atom) {
                             last_atom = a;
                             dx = (rxh - Qhi[3 * a]) + (rxl - Qlo[3 * a]);
@@ -796,15 +859,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
                             dz = (rzh - Qhi[3 * a + 2]) + (rzl - Qlo[3 * a + 2]);
                             d2 = dx * dx + dy * dy + dz * dz;
                         }
-                        float g = 0.f, gd = 0.f;
-                        const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
-                        for (int pr = 0; pr < np; ++pr) {
-                            const float gam = pgf[p0 + pr];
-                            const float ce = pcf[p0 + pr] * expf(-gam * d2);
-                            g += ce;
-                            gd += gam * ce;
+                        if (sh != last_sh) {
+                            last_sh = sh;
+                            g = 0.f;
+                            gd = 0.f;
+                            for (int pr = 0; pr < m1.x; ++pr) {
+                                const float gam = pgf[m0.w + pr];
+                                const float ce = pcf[m0.w + pr] * expf(-gam * d2);
+                                g += ce;
+                                gd += gam * ce;
+                            }
                         }
-                        const int pw = s.ao_pow[mu];
+                        const int pw = m1.y;
                         const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
                         auto ip = [](float x, int n) {
                             float y = 1.f;
@@ -816,38 +882,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
                         const float dpx = nx ? nx * ip(dx, nx - 1) : 0.f;
                         const float dpy = ny ? ny * ip(dy, ny - 1) : 0.f;
                         const float dpz = nz ? nz * ip(dz, nz - 1) : 0.f;
-                        const float c = scf[mu];
+                        const float c = __int_as_float(m1.z);
                         const float m2gd = -2.f * gd;
                         g1 = c * (dpx * py * pz * g + m2gd * dx * P);
                         g2 = c * (px * dpy * pz * g + m2gd * dy * P);
                         g3 = c * (px * py * dpz * g + m2gd * dz * P);
                     }
+                    v[0][q] = g1 * isc0; v[1][q] = g2 * isc1; v[2][q] = g3 * isc2;
                 }
-                v[0][q] = g1 * isc0; v[1][q] = g2 * isc1; v[2][q] = g3 * isc2;
-            }
+                if (h == 0) {
+                    // the previous step's MMAs read the operand buffers: wait before overwriting them
+                    if (ks > 0 && !mbar_wait(mbar_a, (ks - 1) & 1, kWait)) s_abort = 1;
+                    __syncthreads();
+                    if (s_abort) break;
+                }
+                const int c8 = kq * 2 + h;
 #pragma unroll
-            for (int l = 0; l < TC_OUT; ++l) {
-                uint32_t hi[4], lo[4];
+                for (int l = 0; l < TC_OUT; ++l) {
+                    uint32_t hi[4], lo[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) split2(v[l][2 * q], v[l][2 * q + 1], f16, hi[q], lo[q]);
-                const uint32_t off = a_off(row, c8);
-                *reinterpret_cast<uint4 *>(As + (2 * l) * kAPlaneBytes + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<uint4 *>(As + (2 * l + 1) * kAPlaneBytes + off) =
-                    make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    for (int q = 0; q < 4; ++q) split2(v[l][2 * q], v[l][2 * q + 1], f16, hi[q], lo[q]);
+                    const uint32_t off = a_off(row, c8);
+                    *reinterpret_cast<uint4 *>(As + (2 * l) * kAPlaneBytes + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(As + (2 * l + 1) * kAPlaneBytes + off) =
+                        make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
             }
         }
-        // B operand: rows A[mu][k0 .. k0+127] of both planes, 16-byte chunks
-        for (int q = t; q < 2 * TC_K * (TC_N / 8); q += kTcThreads) {
+        if (s_abort) break;
+#pragma unroll
+        for (int j = 0; j < kBChunks; ++j) {
+            const int q = t + j * kTcThreads;
             const int plane = q / (TC_K * (TC_N / 8));
             const int rem = q - plane * (TC_K * (TC_N / 8));
             const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
-            const int mu = ao_s[ks * TC_K + r];
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (mu >= 0 && 8 * c < ncols) {
-                const uint16_t *src = (plane ? Blo : Bhi) + (size_t)mu * nspad + k0 + 8 * c;
-                val = __ldg(reinterpret_cast<const uint4 *>(src));
-            }
-            *reinterpret_cast<uint4 *>(Bs + plane * kBPlaneBytes + b_off(r, 8 * c)) = val;
+            *reinterpret_cast<uint4 *>(Bs + plane * kBPlaneBytes + b_off(r, 8 * c)) = bv[j];
+        }
+        if (t < TC_K && has_next) {
+            meta_s[buf ^ 1][t] = nm0;
+            meta2_s[buf ^ 1][t] = nm1;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -917,11 +990,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
 }
 
 // --------------------------------------------------------------- launchers
-cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st)
+cudaError_t launch_shell_mask(const SysDev &s, const MixedTables &mt, int nw, const double *R, int mw,
+                              uint32_t *masks, cudaStream_t st)
 {
     if (nw == 0) return cudaSuccess;
     dim3 grid(s.n_elec, nw);
-    k_shell_mask<<<grid, kMaskThreads, sizeof(uint32_t) * mw, st>>>(s, R, mw, masks);
+    k_shell_mask<<<grid, kMaskThreads, sizeof(uint32_t) * mw, st>>>(s, mt.Qhi, mt.atom_R2f, mt.sh_R2f, R, mw, masks);
     return cudaGetLastError();
 }
 

@@ -314,6 +314,10 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     const size_t oPg2 = b.add(pg2.data(), 8 * pg2.size()), oPc2 = b.add(pc2.data(), 8 * pc2.size());
     const size_t oSc2 = b.add(sc2.data(), 8 * sc2.size()), oQ2 = b.add(q2.data(), 8 * q2.size());
     const size_t oEj = b.add(ej.data(), 8 * ej.size());
+    std::vector<float> ar2f(na), sr2f(nsh);
+    for (int a = 0; a < na; ++a) ar2f[a] = (float)atom_R2[a];
+    for (int sh = 0; sh < nsh; ++sh) sr2f[sh] = (float)sys->R2_host[sh];
+    const size_t oAR2f = b.add(ar2f.data(), 4 * ar2f.size()), oSR2f = b.add(sr2f.data(), 4 * sr2f.size());
     // AO derivative values enter the FP16 split scaled by 2^b_exp (bound * 2^b_exp <= 8192)
     double dbound[2] = {0.0, 0.0};
     for (int sh = 0; sh < nsh; ++sh) {
@@ -372,6 +376,8 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     mt.scf = reinterpret_cast<const float *>(dev + oScf);
     mt.Qhi = reinterpret_cast<const float *>(dev + oQh);
     mt.Qlo = reinterpret_cast<const float *>(dev + oQl);
+    mt.atom_R2f = reinterpret_cast<const float *>(dev + oAR2f);
+    mt.sh_R2f = reinterpret_cast<const float *>(dev + oSR2f);
     mt.ffb.pg = reinterpret_cast<const float2 *>(dev + oPg2);
     mt.ffb.pc = reinterpret_cast<const float2 *>(dev + oPc2);
     mt.ffb.sc = reinterpret_cast<const float2 *>(dev + oSc2);
@@ -545,7 +551,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     const SysDev &s = sys->d;
     if (precision == QMC_PREC_F64) return launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
     const MixedTables &mt = sys->mixed;
-    cudaError_t e = launch_shell_mask(s, nw, Rc, mt.mask_words, c.masks, st);
+    cudaError_t e = launch_shell_mask(s, mt, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.ff, mt.ns32, mt.colmax, c.X, c.L5, st,
@@ -797,6 +803,20 @@ extern "C" int qmc_screen_ao(const qmc_system *sys, int n_walk, const double *R,
     if (n_walk > 65535) return invalid("qmc_screen_ao: at most 65535 walkers per call");
     cudaError_t e = launch_screen_ao(sys->d, n_walk, R, cap, cnt, idx, B, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "qmc_screen_ao: launch");
+    return QMC_OK;
+}
+
+extern "C" int qmc_shell_masks(const qmc_system *sys, int n_walk, const double *R, uint32_t *masks,
+                               int *mask_words, qmc_stream_t stream)
+{
+    if (!sys || n_walk < 0 || !mask_words) return invalid("qmc_shell_masks: bad argument");
+    *mask_words = sys->mixed.mask_words;
+    if (!masks || n_walk == 0) return QMC_OK;
+    if (!R) return invalid("qmc_shell_masks: null pointer");
+    if (n_walk > 65535) return invalid("qmc_shell_masks: at most 65535 walkers per call");
+    cudaError_t e = launch_shell_mask(sys->d, sys->mixed, n_walk, R, sys->mixed.mask_words, masks,
+                                      reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_shell_masks: launch");
     return QMC_OK;
 }
 

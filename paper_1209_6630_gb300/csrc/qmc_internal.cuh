@@ -60,6 +60,7 @@ struct MixedTables {
     const float *pgf, *pcf;            // FP32 copies of exponents and coefficients [n_prim]
     const float *scf;                  // FP32 copy of ao_scale [n_ao]
     const float *Qhi, *Qlo;            // nuclear positions as float pairs [n_atom][3]
+    const float *atom_R2f, *sh_R2f;    // screening radii rounded to float [n_atom], [n_shell]
     FfBasis ffb;
 };
 
@@ -117,7 +118,8 @@ struct CView {
 cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv, const CView &cv,
                                 const double *logabs2, const double *sign2, const uint32_t *sing,
                                 const qmc_eval_out &o, int w_off, cudaStream_t st, const float2 *Q2);
-cudaError_t launch_shell_mask(const SysDev &s, int nw, const double *R, int mw, uint32_t *masks, cudaStream_t st);
+cudaError_t launch_shell_mask(const SysDev &s, const MixedTables &mt, int nw, const double *R, int mw,
+                              uint32_t *masks, cudaStream_t st);
 cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks,
                           int mw, const float2 *const *A, const int *ns32, const float *const *colmax,
                           double *X, double *L5, cudaStream_t st, int walkers_per_cta);
