@@ -30,7 +30,20 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "1056e"
 METRIC = "walker-steps/s at 1056 e, mixed-prec vs FP64 GPU path, at <=1e-6 log|Psi| err"
-LAUNCHES_PER_STEP = {"f64": 3, "mixed": 5, "mixed_bf16": 5}
+
+
+def launches_per_step(q, prec):
+    """Library kernels launched by one qmc_walkers_eval of a single walker chunk."""
+    if prec == "f64":
+        return 3                      # contraction, Gauss-Jordan, energy
+    t = q.tiles()
+    n = 4                             # masks, C1/C5, tensor cores, energy
+    if t["a4_mode"] == "float_float":
+        panels = -(-max(q.n_up, q.n_dn) // t["gj_panel"])
+        n += 1 + 1 + 2 * panels + 1 + 1   # float-float GJ, list, panel+update per panel, final, FP64 pass
+    else:
+        n += 1
+    return n
 DTYPE = {"f64": "f64", "mixed": "f64 (C1,C5 float-float; C2-C4 fp16x3 tensor cores)",
          "mixed_bf16": "f64 (C1,C5 float-float; C2-C4 bf16x3 tensor cores)"}
 
@@ -342,7 +355,7 @@ def main():
     t_step, value = aggregate(sum(step_ms) / len(step_ms), W, ws, dist, dev)
     st = np.array(stages)            # [K, 8]
     stage_mean = st.mean(axis=0)
-    launches_per_step = LAUNCHES_PER_STEP[prec]   # one walker chunk
+    n_launch = launches_per_step(q, prec)   # one walker chunk
 
     # screening statistics of this batch (a1 on a sample, outside the timed region)
     ns = 16
@@ -402,7 +415,7 @@ def main():
                        if a.workload == "1056e" else a.workload,
                        "walkers_per_gpu": W, "precision": prec, "l2": "flushed between timed steps",
                        "parallelism": f"walker replicas x{ws}", "kbar_active_aos": kbar, "tiles": tiles},
-            "roofline": roof, "gpu_launches": launches_per_step * a.steps}
+            "roofline": roof, "gpu_launches": n_launch * a.steps}
     if clocks:
         line["clocks"] = clocks
 

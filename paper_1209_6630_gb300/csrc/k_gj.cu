@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj(GjJobs2 jobs)
     const GjJob &J = jobs.j[blockIdx.y];
     const int m = blockIdx.x;
     if (m >= J.count) return;
-    if (J.only_redo && !J.redo[m * J.redo_stride]) return;   // recompute pass: flagged matrices only
+    if (J.only_redo && J.redo[m * J.redo_stride] != 1) return;   // recompute pass: flagged, not yet handled
     const int n = J.n;
     double *__restrict__ X = J.X + (size_t)m * J.x_stride;
     double *__restrict__ Dout = J.Dinv + (size_t)m * J.d_stride;

@@ -291,6 +291,8 @@ struct C15Acc {
     float2 a[NU], n[NU];
 };
 
+constexpr int popc_const(int x) { return x ? (x & 1) + popc_const(x >> 1) : 0; }
+
 // Units of a warp are kC15Warps units apart (a compile-time stride).
 template <int NU, int G, int P>
 __device__ __forceinline__ void c15_run(C15Acc<NU, G> &acc, int m, int m_end, int k0, const int *__restrict__ idx_s,
@@ -298,8 +300,12 @@ __device__ __forceinline__ void c15_run(C15Acc<NU, G> &acc, int m, int m_end, in
                                         int col0)
 {
     // unrolled so that the running sums and the prefetch ring rotate through
-    // registers instead of being copied at the end of every iteration
-#pragma unroll 4
+    // registers instead of being copied at the end of every iteration; only
+    // the common patterns (all walkers, all but one) are unrolled, to keep
+    // the code within the instruction cache
+    constexpr int kPop = popc_const(P);
+    constexpr int kUnroll = kPop == G ? 4 : (kPop == G - 1 ? 2 : 1);
+#pragma unroll kUnroll
     for (; m < m_end; ++m) {
         const float2 *row = A + (size_t)idx_s[m + 2] * ns32 + col0;    // two AOs ahead (the list is padded)
         float2 f[NU];

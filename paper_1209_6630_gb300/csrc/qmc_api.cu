@@ -458,6 +458,7 @@ struct Plan {
     bool ffgj;         // a4 on float pairs (+ FP64 recompute flags)
     size_t cd_bytes;   // per walker: FP64 path C2..C5 in FP64; mixed C2..C4 FP32 + C5 FP64
     size_t mask_bytes; // per walker (mixed path): N x mask_words x 4
+    size_t redo_bytes; // per chunk (float-float a4): list and state of the FP64 recomputation
     bool dinv;
 };
 
@@ -472,6 +473,7 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
     p.mask_bytes = p.mixed ? (size_t)sys->d.n_elec * sys->mixed.mask_words * 4 : 0;
     p.dinv = need_dinv;
     p.ffgj = p.mixed && sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT;
+    p.redo_bytes = p.ffgj ? redo_scratch_bytes(std::max(sys->d.n_up, sys->d.n_dn)) : 0;
     p.per_walker = p.msz * 8 + p.cd_bytes + (need_dinv ? p.msz * 8 : 0) + 36 + p.mask_bytes +
                    (p.ffgj ? p.msz * 8 + 2 : 0);
     return p;
@@ -479,7 +481,7 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
 
 struct Carve {
     double *X; void *Cd; double *L5; double *D; double *la; double *sg; uint32_t *st; uint32_t *masks;
-    float2 *work; uint8_t *redo;
+    float2 *work; uint8_t *redo; void *redo_scratch;
 };
 
 // Arrays for `nw` walkers laid out array by array inside ws.
@@ -503,6 +505,7 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
     c.masks = p.mask_bytes ? reinterpret_cast<uint32_t *>(take(p.mask_bytes * nw)) : nullptr;
     c.work = p.ffgj ? reinterpret_cast<float2 *>(take(p.msz * 8 * nw)) : nullptr;
     c.redo = p.ffgj ? reinterpret_cast<uint8_t *>(take(2 * (size_t)nw)) : nullptr;
+    c.redo_scratch = p.ffgj ? take(p.redo_bytes) : nullptr;
     return o <= ws_bytes;
 }
 
@@ -513,7 +516,7 @@ size_t bytes_for(const Plan &p, int nw)
     o += p.dinv ? al(p.msz * 8 * nw) : 0;
     o += al(16 * (size_t)nw) * 2 + al(4 * (size_t)nw);
     o += p.mask_bytes ? al(p.mask_bytes * nw) : 0;
-    o += p.ffgj ? al(p.msz * 8 * nw) + al(2 * (size_t)nw) : 0;
+    o += p.ffgj ? al(p.msz * 8 * nw) + al(2 * (size_t)nw) + al(p.redo_bytes) : 0;
     return o;
 }
 
@@ -669,6 +672,8 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             for (int q = 0; q < nj; ++q) ffj[q].flag = nullptr;
             e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, sys->tiles.a4_kappa_max);
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: float-float Gauss-Jordan launch");
+            e = launch_gj_redo(jobs, nj, c.redo_scratch, st, sys->tiles.gj_panel);
+            if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: FP64 recomputation launch");
             for (int q = 0; q < nj; ++q) jobs[q].only_redo = 1;
         }
         e = launch_gj(jobs, nj, st, sys->tiles.gj_panel);
