@@ -37,15 +37,29 @@ def launches_per_step(q, prec):
     if prec == "f64":
         return 3                      # contraction, Gauss-Jordan, energy
     t = q.tiles()
-    n = 4                             # masks, C1/C5, tensor cores, energy
+    n = 3                             # masks, tensor cores (C2..C4), energy
+    if t["c15_mode"] == "tensor":
+        n += 2 * -(-q.N // 32)         # slice producer + MMA kernel per batch of 32 electrons
+    else:
+        n += 1
     if t["a4_mode"] == "float_float":
         panels = -(-max(q.n_up, q.n_dn) // t["gj_panel"])
         n += 1 + 1 + 2 * panels + 1 + 1   # float-float GJ, list, panel+update per panel, final, FP64 pass
     else:
         n += 1
     return n
-DTYPE = {"f64": "f64", "mixed": "f64 (C1,C5 float-float; C2-C4 fp16x3 tensor cores)",
-         "mixed_bf16": "f64 (C1,C5 float-float; C2-C4 bf16x3 tensor cores)"}
+DTYPE = {"f64": "f64", "mixed": "f64 (C1,C5 bf16 exact slices on tcgen05; C2-C4 fp16x3 tcgen05; a4 float-float)",
+         "mixed_bf16": "f64 (C1,C5 bf16 exact slices on tcgen05; C2-C4 bf16x3 tcgen05; a4 float-float)"}
+
+
+def dtype_of(q, prec):
+    if prec == "f64":
+        return "f64"
+    t = q.tiles()
+    c15 = "bf16 exact slices on tcgen05" if t["c15_mode"] == "tensor" else "float-float FP32 pipes"
+    c24 = "fp16x3" if prec == "mixed" else "bf16x3"
+    a4 = "float-float + FP64 near nodes" if t["a4_mode"] == "float_float" else "FP64"
+    return f"f64 (C1,C5 {c15}; C2-C4 {c24} tcgen05; a4 {a4})"
 
 
 def parse():
@@ -373,7 +387,8 @@ def main():
         kern_ms = {"k_contract_f64": stage_mean[0], "k_gj": stage_mean[1], "k_drift_energy": stage_mean[2]}
     else:
         a4_kern = "k_gj_ff+k_gj" if q.tiles()["a4_mode"] == "float_float" else "k_gj"
-        kern_ms = {"k_shell_mask": stage_mean[4], "k_c15_ff": stage_mean[5], "k_tc_contract": stage_mean[6],
+        c15_kern = "k_c15_prep+k_c15_mma" if q.tiles()["c15_mode"] == "tensor" else "k_c15_ff"
+        kern_ms = {"k_shell_mask": stage_mean[4], c15_kern: stage_mean[5], "k_tc_contract": stage_mean[6],
                    a4_kern: stage_mean[1], "k_drift_energy": stage_mean[2]}
     kern = max(kern_ms, key=kern_ms.get)
     t_k = kern_ms[kern] / 1e3
@@ -396,6 +411,11 @@ def main():
         roof = {"bound": "alu", "achieved": 18.0 * prod / t_k / 1e12, "peak": fp32_inst_peak, "unit": "Tinst/s",
                 "peak_source": "FP32 pipe: 152 SMs x 128 lanes x sm_max_mhz",
                 "work": "2 outputs x 9 FP32 instructions per product, sum_s N_s Kbar N_s products per walker"}
+    elif kern == "k_c15_prep+k_c15_mma":
+        roof = {"bound": "tensor", "achieved": 21 * 2 * 2.0 * prod / t_k / 1e12,
+                "peak": pk.get("bf16_tflops_sustained"), "unit": "TFLOP/s",
+                "peak_source": "measured dense bf16 sustained, MEASURED_PEAKS.json",
+                "work": "2 outputs x 21 BF16 slice-pair products x 2 sum_s N_s Kbar N_s flop per walker"}
     elif kern == "k_tc_contract":
         roof = {"bound": "tensor", "achieved": 3 * 3 * 2.0 * prod / t_k / 1e12, "peak": pk.get("bf16_tflops_sustained"),
                 "unit": "TFLOP/s", "peak_source": "measured dense bf16 (= fp16) sustained, MEASURED_PEAKS.json",
@@ -410,7 +430,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype_of(q, prec), "data": "synthetic",
             "config": {"workload": f"{a.workload} synthetic peptide chain (528+528 e, 3040 AOs)"
                        if a.workload == "1056e" else a.workload,
                        "walkers_per_gpu": W, "precision": prec, "l2": "flushed between timed steps",

@@ -150,17 +150,28 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      nodal surface), with a zero pivot or a non-finite result
  *                      are recomputed in FP64
  *   a4_kappa_max       that threshold (> 0)
+ *   c15_mode           arithmetic of C1/C5 on the mixed paths:
+ *                      QMC_C15_FLOAT_FLOAT = float-float products on the FP32
+ *                      pipes; QMC_C15_TENSOR = tcgen05 BF16 MMAs on exact 7-bit
+ *                      slices of both operands (six each, per-row / per-column
+ *                      power-of-two scaling, four FP32 accumulators per output,
+ *                      ~2^-40 normwise), with a staging buffer in the workspace
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT,
- * a4_kappa_max = 1e9.  qmc_system_set_tiles returns QMC_ERR_INVALID for other
- * values and keeps the previous choice.
+ * a4_kappa_max = 1e9, c15_mode = QMC_C15_TENSOR where the system fits that
+ * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
+ * QMC_C15_FLOAT_FLOAT.  qmc_system_set_tiles returns QMC_ERR_INVALID for
+ * other values (or a tensor mode that does not fit) and keeps the previous
+ * choice.
  */
 enum { QMC_A4_FP64 = 0, QMC_A4_FLOAT_FLOAT = 1 };
+enum { QMC_C15_FLOAT_FLOAT = 0, QMC_C15_TENSOR = 1 };
 typedef struct {
     int gj_panel;
     int c15_walkers;
     int a4_mode;
     double a4_kappa_max;
+    int c15_mode;
 } qmc_tiles;
 int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles);
 int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles);

@@ -36,10 +36,12 @@ class EvalOut(C.Structure):
 
 
 class Tiles(C.Structure):
-    _fields_ = [("gj_panel", _i), ("c15_walkers", _i), ("a4_mode", _i), ("a4_kappa_max", C.c_double)]
+    _fields_ = [("gj_panel", _i), ("c15_walkers", _i), ("a4_mode", _i), ("a4_kappa_max", C.c_double),
+                ("c15_mode", _i)]
 
 
 A4_MODE = {"fp64": 0, "float_float": 1}
+C15_MODE = {"float_float": 0, "tensor": 1}
 
 
 class Segment(C.Structure):

@@ -96,14 +96,16 @@ class QmcSystem:
         t = Tiles()
         check(lib().qmc_system_get_tiles(self._h, C.byref(t)))
         return {"gj_panel": t.gj_panel, "c15_walkers": t.c15_walkers,
-                "a4_mode": "float_float" if t.a4_mode == 1 else "fp64", "a4_kappa_max": t.a4_kappa_max}
+                "a4_mode": "float_float" if t.a4_mode == 1 else "fp64", "a4_kappa_max": t.a4_kappa_max,
+                "c15_mode": "tensor" if t.c15_mode == 1 else "float_float"}
 
-    def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None):
-        from ._lib import A4_MODE
+    def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None, c15_mode=None):
+        from ._lib import A4_MODE, C15_MODE
         cur = self.tiles()
         t = Tiles(gj_panel=gj_panel or cur["gj_panel"], c15_walkers=c15_walkers or cur["c15_walkers"],
                   a4_mode=A4_MODE[a4_mode or cur["a4_mode"]],
-                  a4_kappa_max=a4_kappa_max if a4_kappa_max is not None else cur["a4_kappa_max"])
+                  a4_kappa_max=a4_kappa_max if a4_kappa_max is not None else cur["a4_kappa_max"],
+                  c15_mode=C15_MODE[c15_mode or cur["c15_mode"]])
         check(lib().qmc_system_set_tiles(self._h, C.byref(t)))
 
     def set_mo(self, A_up, A_dn):

@@ -1,0 +1,469 @@
+// Steps a2+a3 of the mixed path for C1 (the Slater matrix) and C5 (its
+// Laplacian companion) on the tcgen05 tensor cores, at the accuracy the
+// float-float kernel gives (~2^-40 normwise), from exact BF16 slices.
+//
+// Splitting (error-free, in the manner of Ozaki's scheme): with E_w the
+// exponent bound of walker row w (|b| < 2^E_w over its AOs) and F_k that of MO
+// column k (|A| < 2^F_k),
+//   b = 2^E_w sum_i s_i,   A = 2^F_k sum_j t_j,   s_i, t_j = integer 2^(-7 (i+1))
+// with |integer| <= 128 (i = 0) or about 64 (i >= 1), six slices each (42
+// bits).  Every slice is exact in BF16, every product s_i t_j exact in FP32,
+// and a sum over K <= 1024 AOs of the products with the same i + j = d stays
+// an integer multiple of 2^(-7 (d+2)) below 2^24 of that unit: the FP32
+// tensor-core accumulator holds it exactly.  Four accumulators per output:
+// d = 0, 1, 2 exactly and d = 3..5 together (its rounding is 2^-45 of the
+// result); pairs with d > 5 are dropped (< 2^-42).  The epilogue adds the
+// four in FP64 and scales by 2^(E_w + F_k).
+//
+// k_c15_prep (one CTA per electron and tile of 128 walkers): the union AO
+// list of the tile (as in k_tc_contract), a first pass in FP32 for the row
+// bounds E_w of the values and of the Laplacians, then float-float AO values
+// and Laplacians (as in k_c15_ff), sliced and written as 12 operand planes
+// per K step of 64 AOs ([output][slice], K-major 128-byte swizzle, the
+// layout the MMA reads) to a staging buffer in HBM.
+//
+// k_c15_mma (one CTA per MO tile of 128, walker tile, electron and output):
+// per K step, the 6 slice planes of its output (copied with cp.async) and the
+// 6 slice planes of the MO coefficient rows gathered by AO index (MN-major);
+// one thread issues the 21 slice-pair MMAs of each K16 sub-step into the four
+// TMEM accumulators and commits to an mbarrier; waits are bounded by
+// %globaltimer (QMC_STATUS_TIMEOUT on expiry).  Unions longer than 1024 AOs
+// are accumulated in chunks of 1024, each added to the output in FP64.
+#include "ao_ff.cuh"
+#include "qmc_internal.cuh"
+#include "umma.cuh"
+
+namespace qmc {
+
+constexpr int kPrepThreads = 256;                              // two threads per walker row
+constexpr int kMmaThreads = 512;
+constexpr int kPlanesPerStep = 2 * kC15Slices;                 // [output][slice]
+constexpr size_t kStepBytes = (size_t)kPlanesPerStep * kAPlaneBytes;
+constexpr int kChunkSteps = 16;                                // 1024 AOs per exact accumulation
+constexpr int kAcc = 4;                                        // accumulators per output
+
+struct C15TcArgs {
+    SysDev s;
+    FfBasis fb;
+    const float *pgf, *pcf, *scf, *Qhi, *Qlo;
+    const double *R;
+    const uint32_t *masks;
+    int mw, nw;
+    int e0;                        // first electron of the batch
+    int n_tiles;                   // walker tiles of 128
+    int kmax_steps;                // staging capacity per (electron, tile), in K steps
+    unsigned char *planes;         // [batch e][tile][kmax_steps][12][16 KB]
+    int *ao_list;                  // [batch e][tile][kmax_steps * 64]
+    int *nks;                      // [batch e][tile]
+    int *rexp;                     // [batch e][tile][128][2]
+    const uint16_t *slice[2];
+    const int *fexp[2];
+    int ns_pad[2];
+    double *X, *L5;
+    uint32_t *wstatus;
+};
+
+__device__ __forceinline__ int exp_bound(float x)   // 2^E > 1.001 x (x >= 0)
+{
+    const float y = x * 1.001f;
+    return ((__float_as_int(y) >> 23) & 0xff) - 126;
+}
+
+// Value and Laplacian of AO mu in FP32 (for the row bounds only).
+__device__ __forceinline__ void ao_val_lap_f32(const SysDev &s, const C15TcArgs &a, int mu, int sh, float rxh,
+                                               float rxl, float ryh, float ryl, float rzh, float rzl, float &v,
+                                               float &lp)
+{
+    const int at = s.sh_atom[sh];
+    const float dx = (rxh - a.Qhi[3 * at]) + (rxl - a.Qlo[3 * at]);
+    const float dy = (ryh - a.Qhi[3 * at + 1]) + (ryl - a.Qlo[3 * at + 1]);
+    const float dz = (rzh - a.Qhi[3 * at + 2]) + (rzl - a.Qlo[3 * at + 2]);
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    float g = 0.f, gd = 0.f, gl = 0.f;
+    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
+    for (int p = 0; p < np; ++p) {
+        const float gam = a.pgf[p0 + p];
+        const float ce = a.pcf[p0 + p] * expf(-gam * d2);
+        g += ce;
+        gd += gam * ce;
+        gl += (4.f * gam * d2 - 6.f) * gam * ce;
+    }
+    const int pw = s.ao_pow[mu];
+    const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
+    auto ip = [](float x, int n) {
+        float y = 1.f;
+        for (int i = 0; i < n; ++i) y *= x;
+        return y;
+    };
+    const float px = ip(dx, nx), py = ip(dy, ny), pz = ip(dz, nz);
+    const float P = px * py * pz;
+    const float ddx = nx > 1 ? nx * (nx - 1) * ip(dx, nx - 2) : 0.f;
+    const float ddy = ny > 1 ? ny * (ny - 1) * ip(dy, ny - 2) : 0.f;
+    const float ddz = nz > 1 ? nz * (nz - 1) * ip(dz, nz - 2) : 0.f;
+    const float c = a.scf[mu];
+    v = c * P * g;
+    lp = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * g + P * (gl - 4.f * (nx + ny + nz) * gd));
+}
+
+// Slices of the float pair x with |x| < 2^E: s_j = rint(r 2^(7(j+1))) 2^(-7(j+1)),
+// r the remainder, computed exactly in float pairs.
+__device__ __forceinline__ void slice6(float2 x, int E, float (&s)[kC15Slices])
+{
+    E = min(max(E, -125), 126);
+    const float sc = __int_as_float((127 - E) << 23);
+    float2 r = make_float2(x.x * sc, x.y * sc);
+#pragma unroll
+    for (int j = 0; j < kC15Slices; ++j) {
+        const int sh = kC15SliceBits * (j + 1);
+        const float q = rintf(r.x * __int_as_float((127 + sh) << 23));
+        const float sj = q * __int_as_float((127 - sh) << 23);
+        s[j] = sj;
+        r = ff::sub(r, make_float2(sj, 0.f));
+    }
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi)   // exact: both have <= 8 significant bits
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *mask_s = reinterpret_cast<uint32_t *>(smem_raw);           // [128][mw]
+    int *ao_s = reinterpret_cast<int *>(mask_s + TC_M * a.mw);           // [n_ao + 64]
+    __shared__ uint32_t union_s[256];
+    __shared__ int warp_s[kPrepThreads / 32];
+
+    const SysDev &s = a.s;
+    const int tile = blockIdx.x, el = blockIdx.y, e = a.e0 + el;
+    const int t = threadIdx.x, row = t >> 1, half = t & 1;
+    const int w = tile * TC_M + row;
+    const bool wvalid = w < a.nw;
+    const int mw = a.mw;
+    const size_t slot = (size_t)el * a.n_tiles + tile;
+
+    for (int q = t; q < TC_M * mw; q += kPrepThreads) {
+        const int m = q / mw, j = q - m * mw;
+        const int wm = tile * TC_M + m;
+        mask_s[q] = (wm < a.nw) ? a.masks[((size_t)wm * s.n_elec + e) * mw + j] : 0u;
+    }
+    __syncthreads();
+    for (int j = t; j < mw; j += kPrepThreads) {
+        uint32_t u = 0;
+        for (int m = 0; m < TC_M; ++m) u |= mask_s[m * mw + j];
+        union_s[j] = u;
+    }
+    __syncthreads();
+    const int K = aos_from_mask_n(s, union_s, mw, ao_s, warp_s);
+    const int nks = (K + TC_K - 1) / TC_K;
+    for (int q = K + t; q < nks * TC_K; q += kPrepThreads) ao_s[q] = -1;
+    __syncthreads();
+    int *lst = a.ao_list + slot * (size_t)a.kmax_steps * TC_K;
+    for (int q = t; q < nks * TC_K; q += kPrepThreads) lst[q] = ao_s[q];
+    if (t == 0) a.nks[slot] = nks;
+
+    const double *rw = a.R + ((size_t)(wvalid ? w : 0) * s.n_elec + e) * 3;
+    const float2 r2[3] = {ff::from_double(rw[0]), ff::from_double(rw[1]), ff::from_double(rw[2])};
+    const uint32_t *my_mask = mask_s + row * mw;
+    auto active = [&](int mu, int &sh) {
+        if (mu < 0 || !wvalid) return false;
+        sh = s.ao_shell[mu];
+        return ((my_mask[sh >> 5] >> (sh & 31)) & 1u) != 0;
+    };
+
+    // pass 1: bounds of |value| and |Laplacian| over the row (FP32)
+    float vmax = 0.f, lmax = 0.f;
+    for (int ks = 0; ks < nks; ++ks)
+        for (int c8 = half * 4; c8 < half * 4 + 4; ++c8)
+            for (int q = 0; q < 8; ++q) {
+                const int mu = ao_s[ks * TC_K + c8 * 8 + q];
+                int sh;
+                if (!active(mu, sh)) continue;
+                float v, lp;
+                ao_val_lap_f32(s, a, mu, sh, r2[0].x, r2[0].y, r2[1].x, r2[1].y, r2[2].x, r2[2].y, v, lp);
+                vmax = fmaxf(vmax, fabsf(v));
+                lmax = fmaxf(lmax, fabsf(lp));
+            }
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
+    lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, 1));
+    const int Ev = exp_bound(vmax), El = exp_bound(lmax);
+    if (half == 0) {
+        a.rexp[(slot * TC_M + row) * 2] = Ev;
+        a.rexp[(slot * TC_M + row) * 2 + 1] = El;
+    }
+
+    // pass 2: float-float values and Laplacians, sliced into the operand planes
+    unsigned char *pl = a.planes + slot * (size_t)a.kmax_steps * kStepBytes;
+    for (int ks = 0; ks < nks; ++ks)
+        for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
+            uint32_t wv[kC15Slices][4], wl[kC15Slices][4];
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) {
+                float sv[2][kC15Slices], sl[2][kC15Slices];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int mu = ao_s[ks * TC_K + c8 * 8 + 2 * q2 + h];
+                    int sh;
+                    float2 v = make_float2(0.f, 0.f), lp = make_float2(0.f, 0.f);
+                    if (active(mu, sh)) ao_val_lap_ff(s, a.fb, mu, r2, v, lp);
+                    slice6(v, Ev, sv[h]);
+                    slice6(lp, El, sl[h]);
+                }
+#pragma unroll
+                for (int j = 0; j < kC15Slices; ++j) {
+                    wv[j][q2] = bf16_pair(sv[0][j], sv[1][j]);
+                    wl[j][q2] = bf16_pair(sl[0][j], sl[1][j]);
+                }
+            }
+            const uint32_t off = a_off(row, c8);
+            unsigned char *stp = pl + (size_t)ks * kStepBytes;
+#pragma unroll
+            for (int j = 0; j < kC15Slices; ++j) {
+                *reinterpret_cast<uint4 *>(stp + (size_t)j * kAPlaneBytes + off) =
+                    make_uint4(wv[j][0], wv[j][1], wv[j][2], wv[j][3]);
+                *reinterpret_cast<uint4 *>(stp + (size_t)(kC15Slices + j) * kAPlaneBytes + off) =
+                    make_uint4(wl[j][0], wl[j][1], wl[j][2], wl[j][3]);
+            }
+        }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, bool valid)
+{
+    const int n = valid ? 16 : 0;   // 0: the 16 bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(saddr), "l"(g), "r"(n) : "memory");
+}
+
+__global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char *base = tc_smem + ((1024 - (smem_u32(tc_smem) & 1023)) & 1023);
+    unsigned char *As = base;                                          // [slice] 16 KB K-major
+    unsigned char *Bs = base + kC15Slices * kAPlaneBytes;              // [slice] 16 KB MN-major
+    int *ao_s = reinterpret_cast<int *>(Bs + kC15Slices * kBPlaneBytes);   // [kmax_steps * 64]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+
+    const SysDev &s = a.s;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int mt = blockIdx.x, tile = blockIdx.y, el = blockIdx.z >> 1, o = blockIdx.z & 1;
+    const int e = a.e0 + el;
+    const int spin = e >= s.n_up;
+    const int ei = spin ? e - s.n_up : e;
+    const int ns = spin ? s.n_dn : s.n_up;
+    const int k0 = mt * TC_N;
+    if (k0 >= ns) return;
+    const int nspad = a.ns_pad[spin];
+    const int ncols = min(TC_N, nspad - k0);
+    const size_t slot = (size_t)el * a.n_tiles + tile;
+    const int nks = a.nks[slot];
+    const int *lst = a.ao_list + slot * (size_t)a.kmax_steps * TC_K;
+    for (int q = t; q < nks * TC_K; q += kMmaThreads) ao_s[q] = lst[q];
+    if (t == 0) s_abort = 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
+                     :: "r"(smem_u32(&tmem_slot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t mbar_a = smem_u32(&mbar);
+    const uint32_t idesc = umma_idesc_f16(TC_M, ncols, 1);
+    const uint64_t kWait = 2000000000ull;
+    const uint16_t *__restrict__ Bsl = a.slice[spin];
+    const unsigned char *Ag = a.planes + slot * (size_t)a.kmax_steps * kStepBytes +
+                              (size_t)o * kC15Slices * kAPlaneBytes;
+    const size_t slice_stride = (size_t)s.n_ao * nspad;
+    int ncommit = 0;
+    bool ok = true;
+
+    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+    double *outp = o ? a.L5 : a.X;
+    const int row = (warp & 3) * 32 + lane;            // TMEM lane = walker row of this thread
+    const int w = tile * TC_M + row;
+
+    for (int c0 = 0; c0 < max(nks, 1); c0 += kChunkSteps) {
+        const int c1 = min(nks, c0 + kChunkSteps);
+        for (int ks = c0; ks < c1; ++ks) {
+            if (ncommit > 0 && !mbar_wait(mbar_a, (ncommit - 1) & 1, kWait)) s_abort = 1;
+            __syncthreads();
+            if (s_abort) break;
+            // A: the 6 slice planes of this output (contiguous, already swizzled)
+            const unsigned char *ag = Ag + (size_t)ks * kStepBytes;
+            for (int q = t; q < kC15Slices * (int)kAPlaneBytes / 16; q += kMmaThreads)
+                cp_async16(smem_u32(As + 16 * q), ag + 16 * (size_t)q, true);
+            // B: rows A_slice[j][mu][k0 .. k0+127], gathered by AO index
+            for (int q = t; q < kC15Slices * TC_K * (TC_N / 8); q += kMmaThreads) {
+                const int j = q / (TC_K * (TC_N / 8));
+                const int rem = q - j * (TC_K * (TC_N / 8));
+                const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
+                const int mu = ao_s[ks * TC_K + r];
+                const bool v = mu >= 0 && 8 * c < ncols;
+                const uint16_t *src = Bsl + j * slice_stride + (size_t)(v ? mu : 0) * nspad + k0 + (v ? 8 * c : 0);
+                cp_async16(smem_u32(Bs + j * kBPlaneBytes + b_off(r, 8 * c)), src, v);
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (t == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+                for (int kk = 0; kk < TC_K / 16; ++kk) {
+#pragma unroll
+                    for (int d = 0; d < kC15Slices; ++d) {
+                        const int acc = d < kAcc - 1 ? d : kAcc - 1;
+#pragma unroll
+                        for (int i = 0; i <= d; ++i) {
+                            const int j = d - i;
+                            const uint64_t ad = umma_desc(a0 + i * kAPlaneBytes + 32 * kk, 16, 1024);
+                            const uint64_t bd = umma_desc(b0 + j * kBPlaneBytes + 2 * kk * kBSbo, kBLbo, kBSbo);
+                            const bool first = ks == c0 && kk == 0 && i == 0 && d <= kAcc - 1;
+                            umma_bf16(tmem + acc * TC_N, ad, bd, idesc, first ? 0u : 1u);
+                        }
+                    }
+                }
+                umma_commit(mbar_a);
+            }
+            ++ncommit;
+        }
+        if (!s_abort && ncommit > 0 && !mbar_wait(mbar_a, (ncommit - 1) & 1, kWait)) s_abort = 1;
+        __syncthreads();
+        ok = !s_abort;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: sum of the four accumulators, scaled by 2^(E_w + F_k), added in FP64
+        const int E = (w < a.nw) ? a.rexp[(slot * TC_M + row) * 2 + o] : 0;
+        double *dst = outp + (size_t)(w < a.nw ? w : 0) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
+                      (size_t)ei * ns;
+        for (int cb = (warp >> 2) * 32; cb < ncols; cb += 32 * (kMmaThreads / 128)) {
+            double sum[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) sum[q] = 0.0;
+#pragma unroll
+            for (int acc = 0; acc < kAcc; ++acc) {
+                uint32_t v[32];
+                const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * TC_N + cb);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                               "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+                               "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+                               "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+                               "=r"(v[31])
+                             : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) sum[q] += (double)__uint_as_float(v[q]);
+            }
+            if (w < a.nw && nks > 0) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int k = k0 + cb + q;
+                    if (k >= ns) break;
+                    const double sc = __longlong_as_double((long long)(1023 + E + a.fexp[spin][k]) << 52);
+                    const double val = sum[q] * sc;
+                    if (c0 == 0) dst[k] = val;
+                    else dst[k] += val;
+                }
+            } else if (w < a.nw) {
+                for (int q = 0; q < 32 && k0 + cb + q < ns; ++q) dst[k0 + cb + q] = 0.0;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok) {
+        if (w < a.nw && (warp >> 2) == 0) atomicOr(a.wstatus + w, (uint32_t)QMC_STATUS_TIMEOUT);
+        if (ncommit > 0) mbar_wait(mbar_a, (ncommit - 1) & 1, kWait);   // let MMAs in flight drain
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
+}
+
+bool c15tc_fits(const SysDev &s, int mw)
+{
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const size_t kmax = (size_t)(s.n_ao + TC_K - 1) / TC_K;
+    const size_t sm_mma = 1024 + (size_t)kC15Slices * (kAPlaneBytes + kBPlaneBytes) + sizeof(int) * kmax * TC_K;
+    const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
+    return nmax <= 1024 && mw <= 256 && sm_mma <= 227 * 1024 && sm_prep <= 227 * 1024;
+}
+
+size_t c15tc_batch(int n_elec)
+{
+    return n_elec < 32 ? (size_t)(n_elec > 0 ? n_elec : 1) : 32;
+}
+
+size_t c15tc_bytes(const SysDev &s, int nw)
+{
+    const size_t tiles = (size_t)(nw + TC_M - 1) / TC_M;
+    const size_t kmax = (size_t)(s.n_ao + TC_K - 1) / TC_K;
+    const size_t per = kmax * kStepBytes + kmax * TC_K * 4 + 4 + TC_M * 2 * 4;
+    return c15tc_batch(s.n_elec) * tiles * per + 4096;
+}
+
+cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
+                          const uint32_t *masks, int mw, double *X, double *L5, uint32_t *wstatus, void *scratch,
+                          cudaStream_t st)
+{
+    if (nw == 0) return cudaSuccess;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    if (nmax > 1024 || mw > 256) return cudaErrorInvalidValue;
+    C15TcArgs a;
+    a.s = s; a.fb = fb;
+    a.pgf = mt.pgf; a.pcf = mt.pcf; a.scf = mt.scf; a.Qhi = mt.Qhi; a.Qlo = mt.Qlo;
+    a.R = R; a.masks = masks; a.mw = mw; a.nw = nw;
+    a.n_tiles = (nw + TC_M - 1) / TC_M;
+    a.kmax_steps = (s.n_ao + TC_K - 1) / TC_K;
+    const size_t nb = c15tc_batch(s.n_elec);
+    char *p = static_cast<char *>(scratch);
+    const size_t ntl = nb * a.n_tiles;
+    a.planes = reinterpret_cast<unsigned char *>(p);
+    p += ntl * a.kmax_steps * kStepBytes;
+    a.ao_list = reinterpret_cast<int *>(p);
+    p += ntl * a.kmax_steps * TC_K * 4;
+    a.nks = reinterpret_cast<int *>(p);
+    p += ((ntl * 4 + 255) / 256) * 256;
+    a.rexp = reinterpret_cast<int *>(p);
+    for (int spin = 0; spin < 2; ++spin) {
+        a.slice[spin] = mt.slice[spin];
+        a.fexp[spin] = mt.fexp[spin];
+        a.ns_pad[spin] = mt.ns_pad[spin];
+    }
+    a.X = X; a.L5 = L5; a.wstatus = wstatus;
+    const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
+    const size_t sm_mma = 1024 + (size_t)kC15Slices * (kAPlaneBytes + kBPlaneBytes) +
+                          sizeof(int) * (size_t)a.kmax_steps * TC_K;
+    if (sm_mma > 227 * 1024 || sm_prep > 227 * 1024) return cudaErrorInvalidConfiguration;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_c15_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_c15_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mma)) !=
+        cudaSuccess)
+        return e;
+    const int mtiles = (nmax + TC_N - 1) / TC_N;
+    for (int e0 = 0; e0 < s.n_elec; e0 += (int)nb) {
+        const int ne = s.n_elec - e0 < (int)nb ? s.n_elec - e0 : (int)nb;
+        a.e0 = e0;
+        k_c15_prep<<<dim3(a.n_tiles, ne), kPrepThreads, sm_prep, st>>>(a);
+        k_c15_mma<<<dim3(mtiles, a.n_tiles, 2 * ne), kMmaThreads, sm_mma, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace qmc

@@ -38,8 +38,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "ao_ff.cuh"
 #include "ff_math.cuh"
 #include "qmc_device.cuh"
+#include "umma.cuh"
 
 namespace qmc {
 
@@ -149,102 +151,6 @@ __device__ __forceinline__ float pow2_above(float x)   // smallest power of two 
     int ex;
     const float m = frexpf(x, &ex);                     // x = m 2^ex, m in [0.5, 1)
     return ldexpf(1.f, m == 0.5f ? ex - 1 : ex);
-}
-
-__device__ __forceinline__ float2 ff_ipow(float2 x, int n)   // x^n, n <= 4
-{
-    switch (n) {
-    case 0: return make_float2(1.f, 0.f);
-    case 1: return x;
-    case 2: return ff::mul(x, x);
-    case 3: return ff::mul(ff::mul(x, x), x);
-    case 4: { const float2 y = ff::mul(x, x); return ff::mul(y, y); }
-    default: return make_float2(0.f, 0.f);
-    }
-}
-
-// Value and Laplacian of AO mu (the two quantities C1 and C5 need) at the
-// position r (three float pairs), in float-float arithmetic:
-//   chi = c P(d) g(d2),  g = sum_p c_p e^{-gamma_p d2},  P = dx^nx dy^ny dz^nz
-//   lap chi = c (lap P g + P (gl - 4 L gd)),  gd = sum_p c_p gamma_p e_p,
-//                                            gl = sum_p c_p (4 gamma_p d2 - 6) gamma_p e_p
-// (the FP64 formulas of the other paths, each operation on float pairs).
-__device__ __forceinline__ void ao_val_lap_ff(const SysDev &s, const FfBasis &fb, int mu, const float2 *r,
-                                              float2 &val, float2 &lap)
-{
-    const int sh = s.ao_shell[mu];
-    const int a = s.sh_atom[sh];
-    const float2 dx = ff::sub(r[0], fb.Q[3 * a]), dy = ff::sub(r[1], fb.Q[3 * a + 1]),
-                 dz = ff::sub(r[2], fb.Q[3 * a + 2]);
-    const float2 d2 = ff::add(ff::add(ff::mul(dx, dx), ff::mul(dy, dy)), ff::mul(dz, dz));
-    float2 g = make_float2(0.f, 0.f), gd = g, gl = g;
-    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
-    for (int p = 0; p < np; ++p) {
-        const float2 gam = fb.pg[p0 + p];
-        const float2 x = ff::mul(gam, d2);
-        const float2 ce = ff::mul(fb.pc[p0 + p], ff::exp_neg(x, fb.expj));
-        g = ff::add(g, ce);
-        const float2 gce = ff::mul(gam, ce);
-        gd = ff::add(gd, gce);
-        const float2 t = ff::add(make_float2(4.f * x.x, 4.f * x.y), make_float2(-6.f, 0.f));
-        gl = ff::fma2(gl, t, gce);
-    }
-    const int pw = s.ao_pow[mu];
-    const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
-    const int L = nx + ny + nz;
-    const float2 c = fb.sc[mu];
-    if (L == 0) {
-        val = ff::mul(c, g);
-        lap = ff::mul(c, gl);
-        return;
-    }
-    const float2 px = ff_ipow(dx, nx), py = ff_ipow(dy, ny), pz = ff_ipow(dz, nz);
-    const float2 pyz = ff::mul(py, pz);
-    const float2 P = ff::mul(px, pyz);
-    float2 lapP = make_float2(0.f, 0.f);
-    if (nx > 1) lapP = ff::mulf(ff::mul(ff_ipow(dx, nx - 2), pyz), (float)(nx * (nx - 1)));
-    if (ny > 1) lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, ff_ipow(dy, ny - 2)), pz), (float)(ny * (ny - 1))));
-    if (nz > 1) lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, py), ff_ipow(dz, nz - 2)), (float)(nz * (nz - 1))));
-    val = ff::mul(c, ff::mul(P, g));
-    const float2 inner = ff::fma2(ff::mul(lapP, g), P, ff::sub(gl, ff::mulf(gd, (float)(4 * L))));
-    lap = ff::mul(c, inner);
-}
-
-// Ordered list of the AOs of the shells set in `bits` for a block of any
-// size (a multiple of 32 threads).  Returns the count; idx_s receives the AO indices.
-__device__ int aos_from_mask_n(const SysDev &s, const uint32_t *bits, int mw, int *idx_s, int *warp_s)
-{
-    const int nthr = blockDim.x, nwarps = nthr >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int words_per = (mw + nthr - 1) / nthr;
-    const int w0 = min((int)threadIdx.x * words_per, mw), w1 = min(w0 + words_per, mw);
-    int nao = 0;
-    for (int j = w0; j < w1; ++j)
-        for (uint32_t b = bits[j]; b; b &= b - 1) nao += ncart(s.sh_L[j * 32 + __ffs(b) - 1]);
-    // exclusive block scan of nao
-    int x = nao;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_s[wid] = x;
-    __syncthreads();
-    int base = 0, total = 0;
-    for (int q = 0; q < nwarps; ++q) {
-        const int v = warp_s[q];
-        if (q < wid) base += v;
-        total += v;
-    }
-    __syncthreads();
-    int off = base + x - nao;
-    for (int j = w0; j < w1; ++j)
-        for (uint32_t b = bits[j]; b; b &= b - 1) {
-            const int sh = j * 32 + __ffs(b) - 1;
-            const int a0 = s.sh_ao0[sh], nc = ncart(s.sh_L[sh]);
-            for (int c = 0; c < nc; ++c, ++off) idx_s[off] = a0 + c;
-        }
-    __syncthreads();
-    return total;
 }
 
 // One CTA per (electron index e, group of G walkers).  The float-float MO
@@ -606,105 +512,6 @@ __global__ void __launch_bounds__(kC15MaxThreads, 2) k_c15_ff(C15Args a)
 }
 
 // ------------------------------------------------------------ tcgen05 path
-constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
-constexpr int kTcThreads = 512;   // four threads per walker row
-constexpr uint32_t kAPlaneBytes = TC_M * TC_K * 2;     // 16 KB, one output x one split
-constexpr uint32_t kBPlaneBytes = TC_K * TC_N * 2;     // 16 KB, one split
-constexpr uint32_t kBLbo = 1024;                        // MN-major: next 64-column atom
-constexpr uint32_t kBSbo = 2048;                        // MN-major: next group of 8 K rows
-constexpr int TC_OUT = 3;                               // C2, C3, C4
-constexpr uint32_t kTcSmemFixed = 2 * TC_OUT * kAPlaneBytes + 2 * kBPlaneBytes;   // 128 KB of operands
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// tcgen05 shared-memory matrix descriptor, 128-byte swizzle.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;    // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;    // SWIZZLE_128B
-    return d;
-}
-
-// kind::f16 instruction descriptor: D = F32, A and B both FP16 (format 0) or
-// both BF16 (format 1), A K-major, B MN-major, shape M x N.
-__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N, int bf16)
-{
-    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | (0u << 15) | (1u << 16) |
-           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
-                 : "memory");
-}
-
-__device__ __forceinline__ uint64_t globaltimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait for the mbarrier phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64_t limit_ns)
-{
-    const uint64_t t0 = globaltimer();
-    while (true) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-        if (globaltimer() - t0 > limit_ns) return false;
-    }
-}
-
-// hi/lo split of two values into packed 16-bit pairs: hi = rn(x), lo = rn(x - hi)
-__device__ __forceinline__ void split2(float a, float b, int f16, uint32_t &hi, uint32_t &lo)
-{
-    if (f16) {
-        const __half2 h = __floats2half2_rn(a, b);
-        const float2 hf = __half22float2(h);
-        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-        hi = *reinterpret_cast<const uint32_t *>(&h);
-        lo = *reinterpret_cast<const uint32_t *>(&l);
-    } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-        hi = *reinterpret_cast<const uint32_t *>(&h);
-        lo = *reinterpret_cast<const uint32_t *>(&l);
-    }
-}
-
-// K-major, 128B swizzle: byte offset of element (row m, k) in an [128][64] bf16 plane
-__device__ __forceinline__ uint32_t a_off(int m, int chunk16)
-{
-    return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((chunk16 ^ (m & 7)) << 4));
-}
-
-// MN-major, 128B swizzle: byte offset of the 16-byte chunk holding columns
-// n0..n0+7 (n0 multiple of 8) of K row r in a [64 K][128 N] bf16 plane
-__device__ __forceinline__ uint32_t b_off(int r, int n0)
-{
-    const int c = (n0 & 63) >> 3;
-    return (uint32_t)((r >> 3) * kBSbo + (n0 >> 6) * kBLbo + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-}
-
 struct TcArgs {
     SysDev s;
     const double *R;

@@ -126,7 +126,7 @@ struct Blob {
 // and FP16 hi/lo planes of A * 2^a_exp, [n_ao][n_s padded to 64]; float-float
 // planes [n_ao][n_s].  a_exp is chosen so that max |A| * 2^a_exp <= 8192.
 struct MoLayout {
-    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oF[2], oCm[2];
+    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oF[2], oCm[2], oSl[2], oFe[2];
     int ns_pad[2], ns32[2], a_exp[2];
 };
 
@@ -175,6 +175,26 @@ static void build_mo(int nao, int nu, int nd, int a_dtype, const void *A_up, con
         for (int mu = 0; mu < nao; ++mu)
             for (int k = 0; k < ns; ++k) cm[k] = std::max(cm[k], (float)fabs(A64[(size_t)mu * ns + k]));
         L.oCm[spin] = b.add(cm.data(), 4 * cm.size());
+        // exact BF16 slices of A[mu][k] 2^-F_k, F_k = the column's exponent bound
+        std::vector<int> fe(np, 0);
+        for (int k = 0; k < ns; ++k) {
+            double m = 0.0;
+            for (int mu = 0; mu < nao; ++mu) m = std::max(m, fabs(A64[(size_t)mu * ns + k]));
+            fe[k] = m > 0.0 ? ilogb(m) + 1 : 0;
+        }
+        std::vector<uint16_t> sl((size_t)kC15Slices * nao * np, 0);
+        for (int mu = 0; mu < nao; ++mu)
+            for (int k = 0; k < ns; ++k) {
+                double r = ldexp(A64[(size_t)mu * ns + k], -fe[k]);
+                for (int j = 0; j < kC15Slices; ++j) {
+                    const int sh = kC15SliceBits * (j + 1);
+                    const double sj = ldexp(nearbyint(ldexp(r, sh)), -sh);
+                    sl[((size_t)j * nao + mu) * np + k] = bf16_bits((float)sj);
+                    r -= sj;
+                }
+            }
+        L.oSl[spin] = b.add(sl.data(), 2 * sl.size());
+        L.oFe[spin] = b.add(fe.data(), 4 * fe.size());
     }
 }
 
@@ -190,6 +210,8 @@ static void point_mo(qmc_system *sys, char *dev, const MoLayout &L)
         mt.ff[spin] = reinterpret_cast<const float2 *>(dev + L.oF[spin]);
         mt.ns32[spin] = L.ns32[spin];
         mt.colmax[spin] = reinterpret_cast<const float *>(dev + L.oCm[spin]);
+        mt.slice[spin] = reinterpret_cast<const uint16_t *>(dev + L.oSl[spin]);
+        mt.fexp[spin] = reinterpret_cast<const int *>(dev + L.oFe[spin]);
         mt.ns_pad[spin] = L.ns_pad[spin];
         mt.a_exp[spin] = L.a_exp[spin];
     }
@@ -376,6 +398,7 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     mt.scf = reinterpret_cast<const float *>(dev + oScf);
     mt.Qhi = reinterpret_cast<const float *>(dev + oQh);
     mt.Qlo = reinterpret_cast<const float *>(dev + oQl);
+    sys->tiles.c15_mode = c15tc_fits(s, mt.mask_words) ? QMC_C15_TENSOR : QMC_C15_FLOAT_FLOAT;
     mt.atom_R2f = reinterpret_cast<const float *>(dev + oAR2f);
     mt.sh_R2f = reinterpret_cast<const float *>(dev + oSR2f);
     mt.ffb.pg = reinterpret_cast<const float2 *>(dev + oPg2);
@@ -414,6 +437,10 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
         return invalid("qmc_system_set_tiles: c15_walkers must be 2 or 4");
     if (tiles->a4_mode != QMC_A4_FP64 && tiles->a4_mode != QMC_A4_FLOAT_FLOAT)
         return invalid("qmc_system_set_tiles: a4_mode");
+    if (tiles->c15_mode != QMC_C15_FLOAT_FLOAT && tiles->c15_mode != QMC_C15_TENSOR)
+        return invalid("qmc_system_set_tiles: c15_mode");
+    if (tiles->c15_mode == QMC_C15_TENSOR && !c15tc_fits(sys->d, sys->mixed.mask_words))
+        return invalid("qmc_system_set_tiles: c15_mode tensor exceeds the kernel's shared-memory limits");
     if (!(tiles->a4_kappa_max > 0.0)) return invalid("qmc_system_set_tiles: a4_kappa_max must be > 0");
     sys->tiles = *tiles;
     return QMC_OK;
@@ -459,7 +486,9 @@ struct Plan {
     size_t cd_bytes;   // per walker: FP64 path C2..C5 in FP64; mixed C2..C4 FP32 + C5 FP64
     size_t mask_bytes; // per walker (mixed path): N x mask_words x 4
     size_t redo_bytes; // per chunk (float-float a4): list and state of the FP64 recomputation
+    bool c15tc;        // C1/C5 on the tensor cores (staging buffer per chunk)
     bool dinv;
+    const SysDev *sd;  // the system's sizes
 };
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
@@ -474,6 +503,8 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
     p.dinv = need_dinv;
     p.ffgj = p.mixed && sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT;
     p.redo_bytes = p.ffgj ? redo_scratch_bytes(std::max(sys->d.n_up, sys->d.n_dn)) : 0;
+    p.c15tc = p.mixed && sys->tiles.c15_mode == QMC_C15_TENSOR;
+    p.sd = &sys->d;
     p.per_walker = p.msz * 8 + p.cd_bytes + (need_dinv ? p.msz * 8 : 0) + 36 + p.mask_bytes +
                    (p.ffgj ? p.msz * 8 + 2 : 0);
     return p;
@@ -481,7 +512,7 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
 
 struct Carve {
     double *X; void *Cd; double *L5; double *D; double *la; double *sg; uint32_t *st; uint32_t *masks;
-    float2 *work; uint8_t *redo; void *redo_scratch;
+    float2 *work; uint8_t *redo; void *redo_scratch; void *c15tc;
 };
 
 // Arrays for `nw` walkers laid out array by array inside ws.
@@ -506,6 +537,7 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
     c.work = p.ffgj ? reinterpret_cast<float2 *>(take(p.msz * 8 * nw)) : nullptr;
     c.redo = p.ffgj ? reinterpret_cast<uint8_t *>(take(2 * (size_t)nw)) : nullptr;
     c.redo_scratch = p.ffgj ? take(p.redo_bytes) : nullptr;
+    c.c15tc = p.c15tc ? take(c15tc_bytes(*p.sd, nw)) : nullptr;
     return o <= ws_bytes;
 }
 
@@ -517,6 +549,7 @@ size_t bytes_for(const Plan &p, int nw)
     o += al(16 * (size_t)nw) * 2 + al(4 * (size_t)nw);
     o += p.mask_bytes ? al(p.mask_bytes * nw) : 0;
     o += p.ffgj ? al(p.msz * 8 * nw) + al(2 * (size_t)nw) + al(p.redo_bytes) : 0;
+    o += p.c15tc ? al(c15tc_bytes(*p.sd, nw)) : 0;
     return o;
 }
 
@@ -557,8 +590,11 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     cudaError_t e = launch_shell_mask(s, mt, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.ff, mt.ns32, mt.colmax, c.X, c.L5, st,
-                      sys->tiles.c15_walkers);
+    if (sys->tiles.c15_mode == QMC_C15_TENSOR)
+        e = launch_c15_tc(s, mt.ffb, mt, nw, Rc, c.masks, mt.mask_words, c.X, c.L5, c.st, c.c15tc, st);
+    else
+        e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.ff, mt.ns32, mt.colmax, c.X, c.L5, st,
+                          sys->tiles.c15_walkers);
     if (e != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     TcTables tt;

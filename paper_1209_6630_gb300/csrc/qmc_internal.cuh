@@ -46,6 +46,12 @@ struct FfBasis {
     const float2 *expj;                // exp(-j/32) for j = -12..12 (index j + 12)
 };
 
+// Exact slices for the tensor-core C1/C5 products: a value x with |x| < 2^E
+// is x = 2^E (s_0 + ... + s_5 + r), s_j = q_j 2^(-7 (j + 1)), q_j integer
+// (|q_0| <= 128, |q_j| <= 64 + 1 for j >= 1, so each s_j is exact in BF16), |r| < 2^-42.
+constexpr int kC15Slices = 6;
+constexpr int kC15SliceBits = 7;
+
 // Split-precision copies of the MO coefficients for the mixed path, per spin.
 struct MixedTables {
     const uint16_t *bhi[2], *blo[2];   // BF16 hi/lo planes [n_ao][ns_pad], ns_pad = ns rounded up to 64
@@ -53,6 +59,8 @@ struct MixedTables {
     const float2 *ff[2];               // float-float (hi, lo) plane [n_ao][ns32], zero beyond ns
     int ns32[2];                       // ns rounded up to 32
     const float *colmax[2];            // max over AOs of |A[mu][k]| per MO column k [ns32], zero beyond ns
+    const uint16_t *slice[2];          // BF16 slices s_j of A[mu][k] 2^-F_k: [kC15Slices][n_ao][ns_pad]
+    const int *fexp[2];                // F_k per MO column [ns_pad] (|A[.][k]| < 2^F_k)
     int ns_pad[2];
     int a_exp[2];                      // FP16 planes hold A * 2^a_exp
     int b_exp;                         // FP16 path: AO gradients enter scaled by 2^b_exp
@@ -127,6 +135,11 @@ cudaError_t launch_shell_mask(const SysDev &s, const MixedTables &mt, int nw, co
 cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const double *R, const uint32_t *masks,
                           int mw, const float2 *const *A, const int *ns32, const float *const *colmax,
                           double *X, double *L5, cudaStream_t st, int walkers_per_cta);
+bool c15tc_fits(const SysDev &s, int mw);
+size_t c15tc_bytes(const SysDev &s, int nw);
+cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
+                          const uint32_t *masks, int mw, double *X, double *L5, uint32_t *wstatus, void *scratch,
+                          cudaStream_t st);
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                                const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
 cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,

@@ -1,0 +1,113 @@
+// tcgen05 / mbarrier helpers and the shared-memory operand layouts used by
+// the tensor-core kernels (inline PTX for sm_103a).
+//
+// A operand: K-major, 128-byte swizzle, [128 rows][64 K] 16-bit elements
+// (16 KB per plane); B operand: MN-major, 128-byte swizzle, [64 K][128 N]
+// 16-bit elements (two 64-column atoms); accumulators FP32 in TMEM.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace qmc {
+constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
+constexpr int kTcThreads = 512;   // four threads per walker row
+constexpr uint32_t kAPlaneBytes = TC_M * TC_K * 2;     // 16 KB, one output x one split
+constexpr uint32_t kBPlaneBytes = TC_K * TC_N * 2;     // 16 KB, one split
+constexpr uint32_t kBLbo = 1024;                        // MN-major: next 64-column atom
+constexpr uint32_t kBSbo = 2048;                        // MN-major: next group of 8 K rows
+constexpr int TC_OUT = 3;                               // C2, C3, C4
+constexpr uint32_t kTcSmemFixed = 2 * TC_OUT * kAPlaneBytes + 2 * kBPlaneBytes;   // 128 KB of operands
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// tcgen05 shared-memory matrix descriptor, 128-byte swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;    // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;    // SWIZZLE_128B
+    return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A and B both FP16 (format 0) or
+// both BF16 (format 1), A K-major, B MN-major, shape M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N, int bf16)
+{
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | (0u << 15) | (1u << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the mbarrier phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+// hi/lo split of two values into packed 16-bit pairs: hi = rn(x), lo = rn(x - hi)
+__device__ __forceinline__ void split2(float a, float b, int f16, uint32_t &hi, uint32_t &lo)
+{
+    if (f16) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+// K-major, 128B swizzle: byte offset of element (row m, k) in an [128][64] bf16 plane
+__device__ __forceinline__ uint32_t a_off(int m, int chunk16)
+{
+    return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((chunk16 ^ (m & 7)) << 4));
+}
+
+// MN-major, 128B swizzle: byte offset of the 16-byte chunk holding columns
+// n0..n0+7 (n0 multiple of 8) of K row r in a [64 K][128 N] bf16 plane
+__device__ __forceinline__ uint32_t b_off(int r, int n0)
+{
+    const int c = (n0 & 63) >> 3;
+    return (uint32_t)((r >> 3) * kBSbo + (n0 >> 6) * kBLbo + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+}  // namespace qmc
