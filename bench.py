@@ -464,8 +464,20 @@ def main():
 
     # the plain FP64 GPU path on the same batch (the metric's comparison)
     if prec != "f64" and not a.no_compare:
+        mixed_lp = out["logpsi"].clone()
+        mixed_el = out["e_loc"].clone()
+        mixed_st = out["status"].clone()
         ws64 = q.workspace(W, "f64")
         q.eval(R, precision="f64", out=out, ws=ws64)
+        # accuracy of the timed mixed-precision step over the whole batch, against the FP64 path
+        ok = (mixed_st == 0) & (out["status"] == 0)
+        dlp = (mixed_lp - out["logpsi"]).abs()[ok]
+        del_ = ((mixed_el - out["e_loc"]).abs() / out["e_loc"].abs())[ok]
+        line["accuracy_vs_fp64_path"] = {
+            "walkers": int(ok.sum().item()), "max_abs_logpsi_err": float(dlp.max().item()),
+            "p99_abs_logpsi_err": float(torch.quantile(dlp, 0.99).item()),
+            "max_rel_eloc_err": float(del_.max().item()),
+            "status_mismatch": int((mixed_st != out["status"]).sum().item())}
         t64 = []
         for _ in range(2):
             flush.zero_()

@@ -148,7 +148,10 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      significand, FP32 pipes) whose matrices with
  *                      kappa_inf = ||X||_inf ||X^-1||_inf above a4_kappa_max (near a
  *                      nodal surface), with a zero pivot or a non-finite result
- *                      are recomputed in FP64
+ *                      are recomputed in FP64 -- their C1 from the positions
+ *                      (FP64 AO values and products) and then the elimination,
+ *                      since there log|det| amplifies the mixed C1's ~2^-40 error
+ *                      by kappa
  *   a4_kappa_max       that threshold (> 0)
  *   c15_mode           arithmetic of C1/C5 on the mixed paths:
  *                      QMC_C15_FLOAT_FLOAT = float-float products on the FP32
@@ -158,7 +161,7 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      ~2^-40 normwise), with a staging buffer in the workspace
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT,
- * a4_kappa_max = 1e9, c15_mode = QMC_C15_TENSOR where the system fits that
+ * a4_kappa_max = 1e8, c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
  * QMC_C15_FLOAT_FLOAT.  qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous

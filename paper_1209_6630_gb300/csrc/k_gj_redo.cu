@@ -17,7 +17,7 @@
 // through k_gj.  With nothing flagged every CTA exits at once.
 #include <math.h>
 
-#include "qmc_internal.cuh"
+#include "qmc_device.cuh"
 
 namespace qmc {
 
@@ -46,6 +46,7 @@ struct RedoArgs {
     char *state;           // kRedoMax entries of state_stride bytes
     size_t state_stride;
     int nmax;
+    int e_off[2];          // first electron of each job's spin
 };
 
 __device__ __forceinline__ RedoState *rstate(const RedoArgs &a, int b)
@@ -313,6 +314,58 @@ __global__ void __launch_bounds__(kRThreads) k_redo_final(RedoArgs a)
     }
 }
 
+// C1 rows of every listed matrix recomputed in FP64 (exact screening, FP64 AO
+// values and products): near a nodal surface the mixed-precision C1 (~2^-40
+// normwise) perturbs log|det| by up to kappa times that.  One CTA per
+// (row, listed matrix); thread t owns MO columns t, t + 128, ...
+constexpr int kC1Threads = 128;
+constexpr int kC1Chunk = 512;
+
+__global__ void __launch_bounds__(kC1Threads) k_redo_c1(SysDev s, RedoArgs a, const double *__restrict__ R)
+{
+    const int b = blockIdx.y;
+    if (b >= a.list->count) return;
+    const RedoEntry en = a.list->e[b];
+    const GjJob &J = a.j[en.job];
+    const int n = J.n, i = blockIdx.x;
+    if (i >= n) return;
+    const int e = a.e_off[en.job] + i;
+    const int spin = e >= s.n_up;
+    const double *__restrict__ A = s.A64[spin];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *b_s = reinterpret_cast<double *>(smem_raw);             // [kC1Chunk]
+    int *idx_s = reinterpret_cast<int *>(b_s + kC1Chunk);            // [n_ao]
+    __shared__ int warp_s[kC1Threads / 32];
+    const double *r = R + ((size_t)en.m * s.n_elec + e) * 3;
+    const double rx = r[0], ry = r[1], rz = r[2];
+    const int K = screen_electron<kC1Threads>(s, rx, ry, rz, idx_s, s.n_ao, warp_s);
+    double *__restrict__ Xrow = J.X + (size_t)en.m * J.x_stride + (size_t)i * n;
+    constexpr int kMaxCols = 1024 / kC1Threads;
+    double acc[kMaxCols];
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) acc[j] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += kC1Chunk) {
+        const int kc = min(kC1Chunk, K - k0);
+        for (int q = threadIdx.x; q < kc; q += kC1Threads) b_s[q] = ao_value_f64(s, idx_s[k0 + q], rx, ry, rz);
+        __syncthreads();
+        for (int q = 0; q < kc; ++q) {
+            const double bv = b_s[q];
+            const double *Arow = A + (size_t)idx_s[k0 + q] * n;
+#pragma unroll
+            for (int j = 0; j < kMaxCols; ++j) {
+                const int k = threadIdx.x + kC1Threads * j;
+                if (k < n) acc[j] = fma(bv, Arow[k], acc[j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) {
+        const int k = threadIdx.x + kC1Threads * j;
+        if (k < n) Xrow[k] = acc[j];
+    }
+}
+
 template <int NB>
 static cudaError_t launch_redo_panels(const RedoArgs &a, int nmax, cudaStream_t st)
 {
@@ -333,8 +386,11 @@ static cudaError_t launch_redo_panels(const RedoArgs &a, int nmax, cudaStream_t 
     return cudaGetLastError();
 }
 
-// nb: panel width, the same as the FP64 k_gj of this system (identical results)
-cudaError_t launch_gj_redo(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, int nb)
+// nb: panel width, the same as the FP64 k_gj of this system (identical results).
+// With R given, the listed matrices' C1 is first recomputed in FP64 from the
+// walkers' positions (e_off: first electron of each job's spin).
+cudaError_t launch_gj_redo(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, int nb, const SysDev *s,
+                           const double *R, const int *e_off)
 {
     RedoArgs a;
     int nmax = 0;
@@ -349,9 +405,18 @@ cudaError_t launch_gj_redo(const GjJob *jobs, int n_jobs, void *scratch, cudaStr
     a.list = static_cast<RedoList *>(scratch);
     a.state = static_cast<char *>(scratch) + ((sizeof(RedoList) + 255) & ~size_t(255));
     a.state_stride = (16 + 4 * (size_t)nmax + 255) & ~size_t(255);
+    a.e_off[0] = e_off ? e_off[0] : 0;
+    a.e_off[1] = e_off ? e_off[1] : 0;
     k_redo_list<<<1, 1024, 0, st>>>(a, n_jobs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (R && s) {
+        const size_t sm = sizeof(double) * kC1Chunk + sizeof(int) * (size_t)s->n_ao;
+        if ((e = cudaFuncSetAttribute(k_redo_c1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
+            return e;
+        k_redo_c1<<<dim3(nmax, kRedoMax), kC1Threads, sm, st>>>(*s, a, R);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     switch (nb) {
     case 8: e = launch_redo_panels<8>(a, nmax, st); break;
     case 16: e = launch_redo_panels<16>(a, nmax, st); break;

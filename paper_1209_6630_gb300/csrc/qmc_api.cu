@@ -283,7 +283,7 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     sys->tiles.gj_panel = (d->n_up > 640 || d->n_dn > 640) ? 8 : 16;
     sys->tiles.c15_walkers = 4;
     sys->tiles.a4_mode = QMC_A4_FLOAT_FLOAT;
-    sys->tiles.a4_kappa_max = 1e9;
+    sys->tiles.a4_kappa_max = 1e8;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
     std::vector<double> atom_R2(na, 0.0);
@@ -708,7 +708,10 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             for (int q = 0; q < nj; ++q) ffj[q].flag = nullptr;
             e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, sys->tiles.a4_kappa_max);
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: float-float Gauss-Jordan launch");
-            e = launch_gj_redo(jobs, nj, c.redo_scratch, st, sys->tiles.gj_panel);
+            int e_off[2], q = 0;
+            for (int spin = 0; spin < 2; ++spin)
+                if (spin ? s.n_dn : s.n_up) e_off[q++] = spin ? s.n_up : 0;
+            e = launch_gj_redo(jobs, nj, c.redo_scratch, st, sys->tiles.gj_panel, &s, Rc, e_off);
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: FP64 recomputation launch");
             for (int q = 0; q < nj; ++q) jobs[q].only_redo = 1;
         }

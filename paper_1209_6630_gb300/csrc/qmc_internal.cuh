@@ -110,9 +110,10 @@ cudaError_t launch_screen_ao(const SysDev &s, int nw, const double *R, int cap, 
                              int32_t *idx, double *B, cudaStream_t st);
 cudaError_t launch_gj(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb);
 // Multi-CTA FP64 recomputation of up to kRedoMax flagged matrices (redo 1 -> 2).
-constexpr int kRedoMax = 64;
+constexpr int kRedoMax = 256;
 size_t redo_scratch_bytes(int nmax);
-cudaError_t launch_gj_redo(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, int nb);
+cudaError_t launch_gj_redo(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, int nb, const SysDev *s,
+                           const double *R, const int *e_off);
 cudaError_t launch_gj_ff(const GjJob *jobs, int n_jobs, cudaStream_t st, int nb, double kappa_max);
 // Where the gradient (C2..C4) and Laplacian (C5) matrices of a walker chunk live:
 // component c of spin s, electron row ei: base + w*wstride + (s ? ncomp*n_up^2 : 0) + c*ns^2 + ei*ns

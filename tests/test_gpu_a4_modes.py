@@ -24,11 +24,12 @@ def test_float_float_matches_fp64_and_oracle(sysq):
     R = make_walkers(s, 24, first=321)
     Rd = torch.from_numpy(R).to(dev)
     ref = Oracle(s).eval(R)
-    q.set_tiles(a4_mode="float_float", a4_kappa_max=1e9)
+    # no recomputation here: the comparison is of the two a4 arithmetics on the same C1
+    q.set_tiles(a4_mode="float_float", a4_kappa_max=1e30)
     ff = q.eval(Rd, precision="mixed", want_dinv=True)
     q.set_tiles(a4_mode="fp64")
     fp = q.eval(Rd, precision="mixed", want_dinv=True)
-    q.set_tiles(a4_mode="float_float")
+    q.set_tiles(a4_mode="float_float", a4_kappa_max=1e8)
     for o in (ff, fp):
         lp, el = o["logpsi"].cpu().numpy(), o["e_loc"].cpu().numpy()
         assert np.abs(lp - ref["logpsi"]).max() < 1e-6
@@ -40,17 +41,21 @@ def test_float_float_matches_fp64_and_oracle(sysq):
 
 
 def test_threshold_one_recomputes_every_matrix_in_fp64(sysq):
+    """Every matrix flagged: C1 and the elimination are recomputed in FP64, so
+    log|Psi| and D^-1 are those of the FP64 path (same screening, FP64 AO
+    values and products, the same Gauss-Jordan arithmetic and panel width)."""
     s, q = sysq
     Rd = torch.from_numpy(make_walkers(s, 10, first=55)).to(dev)
-    q.set_tiles(a4_mode="fp64")
-    fp = q.eval(Rd, precision="mixed", want_dinv=True)
+    f64 = q.eval(Rd, precision="f64", want_dinv=True)
     q.set_tiles(a4_mode="float_float", a4_kappa_max=1.0)   # every kappa_inf >= 1: all flagged
     try:
         rec = q.eval(Rd, precision="mixed", want_dinv=True)
     finally:
-        q.set_tiles(a4_kappa_max=1e9)
-    for k in ("logpsi", "sign", "e_loc", "drift", "dinv", "status"):
-        assert torch.equal(rec[k], fp[k]), k
+        q.set_tiles(a4_kappa_max=1e8)
+    assert torch.equal(rec["status"], f64["status"]) and torch.equal(rec["sign"], f64["sign"])
+    assert ((rec["logpsi"] - f64["logpsi"]).abs() / f64["logpsi"].abs()).max().item() < 1e-12
+    assert (rec["dinv"] - f64["dinv"]).abs().max().item() <= 1e-10 * f64["dinv"].abs().max().item()
+    assert ((rec["e_loc"] - f64["e_loc"]).abs() / f64["e_loc"].abs()).max().item() < 1e-5
 
 
 def test_singular_walker_decided_in_fp64(sysq):
@@ -58,7 +63,7 @@ def test_singular_walker_decided_in_fp64(sysq):
     R = make_walkers(s, 6, first=99)
     R[2, 7] = [2e3, 0.0, 0.0]                    # alpha electron without AOs: exactly singular Det_up
     R[4, s.n_up + 3] = [0.0, 2e3, 0.0]           # beta electron without AOs
-    q.set_tiles(a4_mode="float_float", a4_kappa_max=1e9)
+    q.set_tiles(a4_mode="float_float", a4_kappa_max=1e8)
     o = q.eval(torch.from_numpy(R).to(dev), precision="mixed")
     st = o["status"].cpu().numpy()
     assert st[2] == 1 and st[4] == 2 and (st[[0, 1, 3, 5]] == 0).all()
