@@ -32,19 +32,20 @@ WORKLOAD = "1056e"
 METRIC = "walker-steps/s at 1056 e, mixed-prec vs FP64 GPU path, at <=1e-6 log|Psi| err"
 
 
-def launches_per_step(q, prec):
+def launches_per_step(q, prec, n_walk):
     """Library kernels launched by one qmc_walkers_eval of a single walker chunk."""
     if prec == "f64":
         return 3                      # contraction, Gauss-Jordan, energy
     t = q.tiles()
     n = 3                             # masks, tensor cores (C2..C4), energy
     if t["c15_mode"] == "tensor":
-        n += 2 * -(-q.N // 32)         # slice producer + MMA kernel per batch of 32 electrons
+        b = 64 if n_walk > 7 * 128 else (32 if n_walk > 128 else 16)
+        n += 2 * -(-q.N // b)          # slice producer + MMA kernel per batch of electrons
     else:
         n += 1
     if t["a4_mode"] == "float_float":
         panels = -(-max(q.n_up, q.n_dn) // t["gj_panel"])
-        n += 1 + 1 + 2 * panels + 1 + 1   # float-float GJ, list, panel+update per panel, final, FP64 pass
+        n += 1 + 1 + 1 + 2 * panels + 1 + 1   # float-float GJ, list, FP64 C1 rows, panel+update per panel, final, FP64 pass
     else:
         n += 1
     return n
@@ -369,7 +370,7 @@ def main():
     t_step, value = aggregate(sum(step_ms) / len(step_ms), W, ws, dist, dev)
     st = np.array(stages)            # [K, 8]
     stage_mean = st.mean(axis=0)
-    n_launch = launches_per_step(q, prec)   # one walker chunk
+    n_launch = launches_per_step(q, prec, W)   # one walker chunk
 
     # screening statistics of this batch (a1 on a sample, outside the timed region)
     ns = 16

@@ -25,14 +25,18 @@ __device__ __forceinline__ float2 ff_ipow(float2 x, int n)   // x^n, n <= 4
 //   lap chi = c (lap P g + P (gl - 4 L gd)),  gd = sum_p c_p gamma_p e_p,
 //                                            gl = sum_p c_p (4 gamma_p d2 - 6) gamma_p e_p
 // (the FP64 formulas of the other paths, each operation on float pairs).
-__device__ __forceinline__ void ao_val_lap_ff(const SysDev &s, const FfBasis &fb, int mu, const float2 *r,
-                                              float2 &val, float2 &lap)
+// The radial part (d, g, gd, gl) is shared by the AOs of a shell.
+struct FfRadial {
+    float2 dx, dy, dz, g, gd, gl;
+};
+
+__device__ __forceinline__ void ff_radial(const SysDev &s, const FfBasis &fb, int sh, const float2 *r, FfRadial &o)
 {
-    const int sh = s.ao_shell[mu];
     const int a = s.sh_atom[sh];
-    const float2 dx = ff::sub(r[0], fb.Q[3 * a]), dy = ff::sub(r[1], fb.Q[3 * a + 1]),
-                 dz = ff::sub(r[2], fb.Q[3 * a + 2]);
-    const float2 d2 = ff::add(ff::add(ff::mul(dx, dx), ff::mul(dy, dy)), ff::mul(dz, dz));
+    o.dx = ff::sub(r[0], fb.Q[3 * a]);
+    o.dy = ff::sub(r[1], fb.Q[3 * a + 1]);
+    o.dz = ff::sub(r[2], fb.Q[3 * a + 2]);
+    const float2 d2 = ff::add(ff::add(ff::mul(o.dx, o.dx), ff::mul(o.dy, o.dy)), ff::mul(o.dz, o.dz));
     float2 g = make_float2(0.f, 0.f), gd = g, gl = g;
     const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
     for (int p = 0; p < np; ++p) {
@@ -45,25 +49,43 @@ __device__ __forceinline__ void ao_val_lap_ff(const SysDev &s, const FfBasis &fb
         const float2 t = ff::add(make_float2(4.f * x.x, 4.f * x.y), make_float2(-6.f, 0.f));
         gl = ff::fma2(gl, t, gce);
     }
+    o.g = g;
+    o.gd = gd;
+    o.gl = gl;
+}
+
+__device__ __forceinline__ void ff_angular(const SysDev &s, const FfBasis &fb, int mu, const FfRadial &rd,
+                                           float2 &val, float2 &lap)
+{
     const int pw = s.ao_pow[mu];
     const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
     const int L = nx + ny + nz;
     const float2 c = fb.sc[mu];
     if (L == 0) {
-        val = ff::mul(c, g);
-        lap = ff::mul(c, gl);
+        val = ff::mul(c, rd.g);
+        lap = ff::mul(c, rd.gl);
         return;
     }
-    const float2 px = ff_ipow(dx, nx), py = ff_ipow(dy, ny), pz = ff_ipow(dz, nz);
+    const float2 px = ff_ipow(rd.dx, nx), py = ff_ipow(rd.dy, ny), pz = ff_ipow(rd.dz, nz);
     const float2 pyz = ff::mul(py, pz);
     const float2 P = ff::mul(px, pyz);
     float2 lapP = make_float2(0.f, 0.f);
-    if (nx > 1) lapP = ff::mulf(ff::mul(ff_ipow(dx, nx - 2), pyz), (float)(nx * (nx - 1)));
-    if (ny > 1) lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, ff_ipow(dy, ny - 2)), pz), (float)(ny * (ny - 1))));
-    if (nz > 1) lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, py), ff_ipow(dz, nz - 2)), (float)(nz * (nz - 1))));
-    val = ff::mul(c, ff::mul(P, g));
-    const float2 inner = ff::fma2(ff::mul(lapP, g), P, ff::sub(gl, ff::mulf(gd, (float)(4 * L))));
+    if (nx > 1) lapP = ff::mulf(ff::mul(ff_ipow(rd.dx, nx - 2), pyz), (float)(nx * (nx - 1)));
+    if (ny > 1)
+        lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, ff_ipow(rd.dy, ny - 2)), pz), (float)(ny * (ny - 1))));
+    if (nz > 1)
+        lapP = ff::add(lapP, ff::mulf(ff::mul(ff::mul(px, py), ff_ipow(rd.dz, nz - 2)), (float)(nz * (nz - 1))));
+    val = ff::mul(c, ff::mul(P, rd.g));
+    const float2 inner = ff::fma2(ff::mul(lapP, rd.g), P, ff::sub(rd.gl, ff::mulf(rd.gd, (float)(4 * L))));
     lap = ff::mul(c, inner);
+}
+
+__device__ __forceinline__ void ao_val_lap_ff(const SysDev &s, const FfBasis &fb, int mu, const float2 *r,
+                                              float2 &val, float2 &lap)
+{
+    FfRadial rd;
+    ff_radial(s, fb, s.ao_shell[mu], r, rd);
+    ff_angular(s, fb, mu, rd, val, lap);
 }
 
 // Ordered list of the AOs of the shells set in `bits` for a block of any

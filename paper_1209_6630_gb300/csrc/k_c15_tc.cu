@@ -69,16 +69,19 @@ __device__ __forceinline__ int exp_bound(float x)   // 2^E > 1.001 x (x >= 0)
     return ((__float_as_int(y) >> 23) & 0xff) - 126;
 }
 
-// Value and Laplacian of AO mu in FP32 (for the row bounds only).
-__device__ __forceinline__ void ao_val_lap_f32(const SysDev &s, const C15TcArgs &a, int mu, int sh, float rxh,
-                                               float rxl, float ryh, float ryl, float rzh, float rzl, float &v,
-                                               float &lp)
+// Radial part and AO value / Laplacian in FP32 (for the row bounds only).
+struct F32Radial {
+    float dx, dy, dz, g, gd, gl;
+};
+
+__device__ __forceinline__ void f32_radial(const SysDev &s, const C15TcArgs &a, int sh, float rxh, float rxl,
+                                           float ryh, float ryl, float rzh, float rzl, F32Radial &o)
 {
     const int at = s.sh_atom[sh];
-    const float dx = (rxh - a.Qhi[3 * at]) + (rxl - a.Qlo[3 * at]);
-    const float dy = (ryh - a.Qhi[3 * at + 1]) + (ryl - a.Qlo[3 * at + 1]);
-    const float dz = (rzh - a.Qhi[3 * at + 2]) + (rzl - a.Qlo[3 * at + 2]);
-    const float d2 = dx * dx + dy * dy + dz * dz;
+    o.dx = (rxh - a.Qhi[3 * at]) + (rxl - a.Qlo[3 * at]);
+    o.dy = (ryh - a.Qhi[3 * at + 1]) + (ryl - a.Qlo[3 * at + 1]);
+    o.dz = (rzh - a.Qhi[3 * at + 2]) + (rzl - a.Qlo[3 * at + 2]);
+    const float d2 = o.dx * o.dx + o.dy * o.dy + o.dz * o.dz;
     float g = 0.f, gd = 0.f, gl = 0.f;
     const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
     for (int p = 0; p < np; ++p) {
@@ -88,6 +91,14 @@ __device__ __forceinline__ void ao_val_lap_f32(const SysDev &s, const C15TcArgs 
         gd += gam * ce;
         gl += (4.f * gam * d2 - 6.f) * gam * ce;
     }
+    o.g = g;
+    o.gd = gd;
+    o.gl = gl;
+}
+
+__device__ __forceinline__ void f32_angular(const SysDev &s, const C15TcArgs &a, int mu, const F32Radial &rd,
+                                            float &v, float &lp)
+{
     const int pw = s.ao_pow[mu];
     const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
     auto ip = [](float x, int n) {
@@ -95,14 +106,14 @@ __device__ __forceinline__ void ao_val_lap_f32(const SysDev &s, const C15TcArgs 
         for (int i = 0; i < n; ++i) y *= x;
         return y;
     };
-    const float px = ip(dx, nx), py = ip(dy, ny), pz = ip(dz, nz);
+    const float px = ip(rd.dx, nx), py = ip(rd.dy, ny), pz = ip(rd.dz, nz);
     const float P = px * py * pz;
-    const float ddx = nx > 1 ? nx * (nx - 1) * ip(dx, nx - 2) : 0.f;
-    const float ddy = ny > 1 ? ny * (ny - 1) * ip(dy, ny - 2) : 0.f;
-    const float ddz = nz > 1 ? nz * (nz - 1) * ip(dz, nz - 2) : 0.f;
+    const float ddx = nx > 1 ? nx * (nx - 1) * ip(rd.dx, nx - 2) : 0.f;
+    const float ddy = ny > 1 ? ny * (ny - 1) * ip(rd.dy, ny - 2) : 0.f;
+    const float ddz = nz > 1 ? nz * (nz - 1) * ip(rd.dz, nz - 2) : 0.f;
     const float c = a.scf[mu];
-    v = c * P * g;
-    lp = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * g + P * (gl - 4.f * (nx + ny + nz) * gd));
+    v = c * P * rd.g;
+    lp = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * rd.g + P * (rd.gl - 4.f * (nx + ny + nz) * rd.gd));
 }
 
 // Slices of the float pair x with |x| < 2^E: s_j = rint(r 2^(7(j+1))) 2^(-7(j+1)),
@@ -173,19 +184,27 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
         return ((my_mask[sh >> 5] >> (sh & 31)) & 1u) != 0;
     };
 
-    // pass 1: bounds of |value| and |Laplacian| over the row (FP32)
+    // pass 1: bounds of |value| and |Laplacian| over the row (FP32; radial part once per shell)
     float vmax = 0.f, lmax = 0.f;
-    for (int ks = 0; ks < nks; ++ks)
-        for (int c8 = half * 4; c8 < half * 4 + 4; ++c8)
-            for (int q = 0; q < 8; ++q) {
-                const int mu = ao_s[ks * TC_K + c8 * 8 + q];
-                int sh;
-                if (!active(mu, sh)) continue;
-                float v, lp;
-                ao_val_lap_f32(s, a, mu, sh, r2[0].x, r2[0].y, r2[1].x, r2[1].y, r2[2].x, r2[2].y, v, lp);
-                vmax = fmaxf(vmax, fabsf(v));
-                lmax = fmaxf(lmax, fabsf(lp));
-            }
+    {
+        F32Radial rd;
+        int last_sh = -1;
+        for (int ks = 0; ks < nks; ++ks)
+            for (int c8 = half * 4; c8 < half * 4 + 4; ++c8)
+                for (int q = 0; q < 8; ++q) {
+                    const int mu = ao_s[ks * TC_K + c8 * 8 + q];
+                    int sh;
+                    if (!active(mu, sh)) continue;
+                    if (sh != last_sh) {
+                        last_sh = sh;
+                        f32_radial(s, a, sh, r2[0].x, r2[0].y, r2[1].x, r2[1].y, r2[2].x, r2[2].y, rd);
+                    }
+                    float v, lp;
+                    f32_angular(s, a, mu, rd, v, lp);
+                    vmax = fmaxf(vmax, fabsf(v));
+                    lmax = fmaxf(lmax, fabsf(lp));
+                }
+    }
     vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
     lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, 1));
     const int Ev = exp_bound(vmax), El = exp_bound(lmax);
@@ -195,6 +214,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
     }
 
     // pass 2: float-float values and Laplacians, sliced into the operand planes
+    // (the float-float radial part is recomputed per AO here: caching it per shell,
+    // as in pass 1, keeps 12 more registers live across the slicing and measured slower)
     unsigned char *pl = a.planes + slot * (size_t)a.kmax_steps * kStepBytes;
     for (int ks = 0; ks < nks; ++ks)
         for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
@@ -402,9 +423,12 @@ bool c15tc_fits(const SysDev &s, int mw)
     return nmax <= 1024 && mw <= 256 && sm_mma <= 227 * 1024 && sm_prep <= 227 * 1024;
 }
 
-size_t c15tc_batch(int n_elec)
+// Electrons per producer / MMA launch pair: enough CTAs per launch for large
+// batches of walkers, a small staging buffer for small ones.
+size_t c15tc_batch(int n_elec, int n_tiles)
 {
-    return n_elec < 32 ? (size_t)(n_elec > 0 ? n_elec : 1) : 32;
+    const int b = n_tiles >= 8 ? 64 : (n_tiles >= 2 ? 32 : 16);
+    return (size_t)(n_elec < b ? (n_elec > 0 ? n_elec : 1) : b);
 }
 
 size_t c15tc_bytes(const SysDev &s, int nw)
@@ -412,7 +436,7 @@ size_t c15tc_bytes(const SysDev &s, int nw)
     const size_t tiles = (size_t)(nw + TC_M - 1) / TC_M;
     const size_t kmax = (size_t)(s.n_ao + TC_K - 1) / TC_K;
     const size_t per = kmax * kStepBytes + kmax * TC_K * 4 + 4 + TC_M * 2 * 4;
-    return c15tc_batch(s.n_elec) * tiles * per + 4096;
+    return c15tc_batch(s.n_elec, (int)tiles) * tiles * per + 4096;
 }
 
 cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
@@ -428,7 +452,7 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
     a.R = R; a.masks = masks; a.mw = mw; a.nw = nw;
     a.n_tiles = (nw + TC_M - 1) / TC_M;
     a.kmax_steps = (s.n_ao + TC_K - 1) / TC_K;
-    const size_t nb = c15tc_batch(s.n_elec);
+    const size_t nb = c15tc_batch(s.n_elec, a.n_tiles);
     char *p = static_cast<char *>(scratch);
     const size_t ntl = nb * a.n_tiles;
     a.planes = reinterpret_cast<unsigned char *>(p);

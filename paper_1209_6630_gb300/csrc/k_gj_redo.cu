@@ -316,15 +316,14 @@ __global__ void __launch_bounds__(kRThreads) k_redo_final(RedoArgs a)
 
 // C1 rows of every listed matrix recomputed in FP64 (exact screening, FP64 AO
 // values and products): near a nodal surface the mixed-precision C1 (~2^-40
-// normwise) perturbs log|det| by up to kappa times that.  One CTA per
-// (row, listed matrix); thread t owns MO columns t, t + 128, ...
+// normwise) perturbs log|det| by up to kappa times that.  Each CTA computes
+// one row (blockIdx.x) of every 32nd listed matrix; thread t owns MO columns
+// t, t + 128, ...
 constexpr int kC1Threads = 128;
 constexpr int kC1Chunk = 512;
 
-__global__ void __launch_bounds__(kC1Threads) k_redo_c1(SysDev s, RedoArgs a, const double *__restrict__ R)
+__device__ __forceinline__ void redo_c1_row(const SysDev &s, const RedoArgs &a, const double *__restrict__ R, int b)
 {
-    const int b = blockIdx.y;
-    if (b >= a.list->count) return;
     const RedoEntry en = a.list->e[b];
     const GjJob &J = a.j[en.job];
     const int n = J.n, i = blockIdx.x;
@@ -364,6 +363,13 @@ __global__ void __launch_bounds__(kC1Threads) k_redo_c1(SysDev s, RedoArgs a, co
         const int k = threadIdx.x + kC1Threads * j;
         if (k < n) Xrow[k] = acc[j];
     }
+}
+
+constexpr int kC1Slots = 32;   // CTAs per row; each loops over the listed matrices
+
+__global__ void __launch_bounds__(kC1Threads) k_redo_c1(SysDev s, RedoArgs a, const double *__restrict__ R)
+{
+    for (int b = blockIdx.y; b < a.list->count; b += kC1Slots) redo_c1_row(s, a, R, b);
 }
 
 template <int NB>
@@ -414,7 +420,7 @@ cudaError_t launch_gj_redo(const GjJob *jobs, int n_jobs, void *scratch, cudaStr
         const size_t sm = sizeof(double) * kC1Chunk + sizeof(int) * (size_t)s->n_ao;
         if ((e = cudaFuncSetAttribute(k_redo_c1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
             return e;
-        k_redo_c1<<<dim3(nmax, kRedoMax), kC1Threads, sm, st>>>(*s, a, R);
+        k_redo_c1<<<dim3(nmax, kC1Slots), kC1Threads, sm, st>>>(*s, a, R);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     switch (nb) {
