@@ -22,7 +22,14 @@
 // per K step of 64 AOs ([output][slice], K-major 128-byte swizzle, the
 // layout the MMA reads) to a staging buffer in HBM.
 //
-// k_c15_mma (one CTA per MO tile of 128, walker tile, electron and output):
+// The producer's FP32 pass also evaluates the AO gradients and writes them as
+// FP16 (or BF16) hi/lo planes scaled by exact powers of two, the operands of
+// C2..C4 (three products hi.hi + hi.lo + lo.hi per output, FP32 accumulation,
+// as in k_tc_contract), so the gradients are evaluated once per (electron,
+// walker tile) instead of once per MO tile.
+//
+// k_c15_mma (one CTA per MO tile of 128, walker tile, electron and output
+// class: C1, C5, or C2..C4 together):
 // per K step, the 6 slice planes of its output (copied with cp.async) and the
 // 6 slice planes of the MO coefficient rows gathered by AO index (MN-major);
 // one thread issues the 21 slice-pair MMAs of each K16 sub-step into the four
@@ -37,7 +44,8 @@ namespace qmc {
 
 constexpr int kPrepThreads = 256;                              // two threads per walker row
 constexpr int kMmaThreads = 512;
-constexpr int kPlanesPerStep = 2 * kC15Slices;                 // [output][slice]
+constexpr int kGradPlane0 = 2 * kC15Slices;                    // first C2..C4 plane of a step
+constexpr int kPlanesPerStep = 2 * kC15Slices + 6;             // [C1 slice][C5 slice][gradient l][hi, lo]
 constexpr size_t kStepBytes = (size_t)kPlanesPerStep * kAPlaneBytes;
 constexpr int kChunkSteps = 16;                                // 1024 AOs per exact accumulation
 constexpr int kAcc = 4;                                        // accumulators per output
@@ -60,6 +68,8 @@ struct C15TcArgs {
     const int *fexp[2];
     int ns_pad[2];
     double *X, *L5;
+    float *Cg;                     // C2..C4, FP32 [W][3][...]
+    TcTables tt;
     uint32_t *wstatus;
 };
 
@@ -97,7 +107,7 @@ __device__ __forceinline__ void f32_radial(const SysDev &s, const C15TcArgs &a, 
 }
 
 __device__ __forceinline__ void f32_angular(const SysDev &s, const C15TcArgs &a, int mu, const F32Radial &rd,
-                                            float &v, float &lp)
+                                            float &v, float &lp, float &g1, float &g2, float &g3)
 {
     const int pw = s.ao_pow[mu];
     const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
@@ -108,12 +118,19 @@ __device__ __forceinline__ void f32_angular(const SysDev &s, const C15TcArgs &a,
     };
     const float px = ip(rd.dx, nx), py = ip(rd.dy, ny), pz = ip(rd.dz, nz);
     const float P = px * py * pz;
+    const float dpx = nx ? nx * ip(rd.dx, nx - 1) : 0.f;
+    const float dpy = ny ? ny * ip(rd.dy, ny - 1) : 0.f;
+    const float dpz = nz ? nz * ip(rd.dz, nz - 1) : 0.f;
     const float ddx = nx > 1 ? nx * (nx - 1) * ip(rd.dx, nx - 2) : 0.f;
     const float ddy = ny > 1 ? ny * (ny - 1) * ip(rd.dy, ny - 2) : 0.f;
     const float ddz = nz > 1 ? nz * (nz - 1) * ip(rd.dz, nz - 2) : 0.f;
     const float c = a.scf[mu];
+    const float m2gd = -2.f * rd.gd;
     v = c * P * rd.g;
     lp = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * rd.g + P * (rd.gl - 4.f * (nx + ny + nz) * rd.gd));
+    g1 = c * (dpx * py * pz * rd.g + m2gd * rd.dx * P);
+    g2 = c * (px * dpy * pz * rd.g + m2gd * rd.dy * P);
+    g3 = c * (px * py * dpz * rd.g + m2gd * rd.dz * P);
 }
 
 // Slices of the float pair x with |x| < 2^E: s_j = rint(r 2^(7(j+1))) 2^(-7(j+1)),
@@ -184,14 +201,20 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
         return ((my_mask[sh >> 5] >> (sh & 31)) & 1u) != 0;
     };
 
-    // pass 1: bounds of |value| and |Laplacian| over the row (FP32; radial part once per shell)
+    unsigned char *pl = a.planes + slot * (size_t)a.kmax_steps * kStepBytes;
+    // pass 1 (FP32; radial part once per shell): bounds of |value| and
+    // |Laplacian| over the row, and the gradient planes of C2..C4
     float vmax = 0.f, lmax = 0.f;
     {
         F32Radial rd;
         int last_sh = -1;
+        const int f16 = a.tt.f16;
         for (int ks = 0; ks < nks; ++ks)
-            for (int c8 = half * 4; c8 < half * 4 + 4; ++c8)
+            for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
+                float gv[3][8];
+#pragma unroll
                 for (int q = 0; q < 8; ++q) {
+                    gv[0][q] = gv[1][q] = gv[2][q] = 0.f;
                     const int mu = ao_s[ks * TC_K + c8 * 8 + q];
                     int sh;
                     if (!active(mu, sh)) continue;
@@ -200,10 +223,24 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
                         f32_radial(s, a, sh, r2[0].x, r2[0].y, r2[1].x, r2[1].y, r2[2].x, r2[2].y, rd);
                     }
                     float v, lp;
-                    f32_angular(s, a, mu, rd, v, lp);
+                    f32_angular(s, a, mu, rd, v, lp, gv[0][q], gv[1][q], gv[2][q]);
                     vmax = fmaxf(vmax, fabsf(v));
                     lmax = fmaxf(lmax, fabsf(lp));
                 }
+                const uint32_t off = a_off(row, c8);
+                unsigned char *stp = pl + (size_t)ks * kStepBytes + (size_t)kGradPlane0 * kAPlaneBytes;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    uint32_t hi[4], lo[4];
+                    const float isc = a.tt.in_scale[l];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) split2(gv[l][2 * q] * isc, gv[l][2 * q + 1] * isc, f16, hi[q], lo[q]);
+                    *reinterpret_cast<uint4 *>(stp + (size_t)(2 * l) * kAPlaneBytes + off) =
+                        make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(stp + (size_t)(2 * l + 1) * kAPlaneBytes + off) =
+                        make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
     }
     vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
     lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, 1));
@@ -216,7 +253,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
     // pass 2: float-float values and Laplacians, sliced into the operand planes
     // (the float-float radial part is recomputed per AO here: caching it per shell,
     // as in pass 1, keeps 12 more registers live across the slicing and measured slower)
-    unsigned char *pl = a.planes + slot * (size_t)a.kmax_steps * kStepBytes;
     for (int ks = 0; ks < nks; ++ks)
         for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
             uint32_t wv[kC15Slices][4], wl[kC15Slices][4];
@@ -269,7 +305,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
 
     const SysDev &s = a.s;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int mt = blockIdx.x, tile = blockIdx.y, el = blockIdx.z >> 1, o = blockIdx.z & 1;
+    const int mt = blockIdx.x, tile = blockIdx.y, el = blockIdx.z / 3, o = blockIdx.z % 3;   // o: C1, C5, C2..C4
     const int e = a.e0 + el;
     const int spin = e >= s.n_up;
     const int ei = spin ? e - s.n_up : e;
@@ -298,12 +334,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
     const uint32_t mbar_a = smem_u32(&mbar);
-    const uint32_t idesc = umma_idesc_f16(TC_M, ncols, 1);
+    const bool grad = o == 2;
+    const uint32_t idesc = umma_idesc_f16(TC_M, ncols, grad ? (a.tt.f16 ? 0 : 1) : 1);
     const uint64_t kWait = 2000000000ull;
     const uint16_t *__restrict__ Bsl = a.slice[spin];
     const unsigned char *Ag = a.planes + slot * (size_t)a.kmax_steps * kStepBytes +
-                              (size_t)o * kC15Slices * kAPlaneBytes;
+                              (size_t)o * kC15Slices * kAPlaneBytes;     // o = 2: the gradient planes
     const size_t slice_stride = (size_t)s.n_ao * nspad;
+    const int nbplanes = grad ? 2 : kC15Slices;
     int ncommit = 0;
     bool ok = true;
 
@@ -322,14 +360,16 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
             const unsigned char *ag = Ag + (size_t)ks * kStepBytes;
             for (int q = t; q < kC15Slices * (int)kAPlaneBytes / 16; q += kMmaThreads)
                 cp_async16(smem_u32(As + 16 * q), ag + 16 * (size_t)q, true);
-            // B: rows A_slice[j][mu][k0 .. k0+127], gathered by AO index
-            for (int q = t; q < kC15Slices * TC_K * (TC_N / 8); q += kMmaThreads) {
+            // B: rows of the MO slices (C1, C5) or of the hi/lo planes (C2..C4)
+            // [mu][k0 .. k0+127], gathered by AO index
+            for (int q = t; q < nbplanes * TC_K * (TC_N / 8); q += kMmaThreads) {
                 const int j = q / (TC_K * (TC_N / 8));
                 const int rem = q - j * (TC_K * (TC_N / 8));
                 const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
                 const int mu = ao_s[ks * TC_K + r];
                 const bool v = mu >= 0 && 8 * c < ncols;
-                const uint16_t *src = Bsl + j * slice_stride + (size_t)(v ? mu : 0) * nspad + k0 + (v ? 8 * c : 0);
+                const uint16_t *base = grad ? (j ? a.tt.lo[spin] : a.tt.hi[spin]) : Bsl + j * slice_stride;
+                const uint16_t *src = base + (size_t)(v ? mu : 0) * nspad + k0 + (v ? 8 * c : 0);
                 cp_async16(smem_u32(Bs + j * kBPlaneBytes + b_off(r, 8 * c)), src, v);
             }
             asm volatile("cp.async.wait_all;" ::: "memory");
@@ -338,6 +378,22 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+                if (grad) {
+#pragma unroll
+                    for (int kk = 0; kk < TC_K / 16; ++kk) {
+                        const uint64_t bh = umma_desc(b0 + 2 * kk * kBSbo, kBLbo, kBSbo);
+                        const uint64_t bl = umma_desc(b0 + kBPlaneBytes + 2 * kk * kBSbo, kBLbo, kBSbo);
+#pragma unroll
+                        for (int l = 0; l < 3; ++l) {
+                            const uint64_t ah = umma_desc(a0 + (2 * l) * kAPlaneBytes + 32 * kk, 16, 1024);
+                            const uint64_t al = umma_desc(a0 + (2 * l + 1) * kAPlaneBytes + 32 * kk, 16, 1024);
+                            const uint32_t dd = tmem + l * TC_N;
+                            umma_bf16(dd, ah, bh, idesc, (ks > c0 || kk > 0) ? 1u : 0u);
+                            umma_bf16(dd, ah, bl, idesc, 1u);
+                            umma_bf16(dd, al, bh, idesc, 1u);
+                        }
+                    }
+                } else
 #pragma unroll
                 for (int kk = 0; kk < TC_K / 16; ++kk) {
 #pragma unroll
@@ -362,7 +418,45 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
         ok = !s_abort;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: sum of the four accumulators, scaled by 2^(E_w + F_k), added in FP64
+        if (grad) {
+            // epilogue C2..C4: FP32 accumulators times the power-of-two output scale
+            const size_t nss = (size_t)ns * ns;
+            float *crow = a.Cg + (size_t)(w < a.nw ? w : 0) * 3 * msz +
+                          (spin ? 3 * (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+            for (int l = 0; l < 3; ++l) {
+                const float osc = a.tt.out_scale[spin][l];
+                for (int cb = (warp >> 2) * 32; cb < ncols; cb += 32 * (kMmaThreads / 128)) {
+                    uint32_t v[32];
+                    const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(l * TC_N + cb);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                                   "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+                                   "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+                                   "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+                                   "=r"(v[31])
+                                 : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (w < a.nw) {
+                        float *dst = crow + (size_t)l * nss;
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const int k = k0 + cb + q;
+                            if (k >= ns) break;
+                            const float val = nks > 0 ? __uint_as_float(v[q]) * osc : 0.f;
+                            if (c0 == 0) dst[k] = val;
+                            else dst[k] += val;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            continue;
+        }
+        // epilogue C1 / C5: sum of the four accumulators, scaled by 2^(E_w + F_k), added in FP64
         const int E = (w < a.nw) ? a.rexp[(slot * TC_M + row) * 2 + o] : 0;
         double *dst = outp + (size_t)(w < a.nw ? w : 0) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
                       (size_t)ei * ns;
@@ -439,9 +533,9 @@ size_t c15tc_bytes(const SysDev &s, int nw)
     return c15tc_batch(s.n_elec, (int)tiles) * tiles * per + 4096;
 }
 
-cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
-                          const uint32_t *masks, int mw, double *X, double *L5, uint32_t *wstatus, void *scratch,
-                          cudaStream_t st)
+cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, const TcTables &tt, int nw,
+                          const double *R, const uint32_t *masks, int mw, double *X, double *L5, float *Cg,
+                          uint32_t *wstatus, void *scratch, cudaStream_t st)
 {
     if (nw == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
@@ -467,7 +561,7 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
         a.fexp[spin] = mt.fexp[spin];
         a.ns_pad[spin] = mt.ns_pad[spin];
     }
-    a.X = X; a.L5 = L5; a.wstatus = wstatus;
+    a.X = X; a.L5 = L5; a.Cg = Cg; a.tt = tt; a.wstatus = wstatus;
     const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
     const size_t sm_mma = 1024 + (size_t)kC15Slices * (kAPlaneBytes + kBPlaneBytes) +
                           sizeof(int) * (size_t)a.kmax_steps * TC_K;
@@ -484,7 +578,7 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
         const int ne = s.n_elec - e0 < (int)nb ? s.n_elec - e0 : (int)nb;
         a.e0 = e0;
         k_c15_prep<<<dim3(a.n_tiles, ne), kPrepThreads, sm_prep, st>>>(a);
-        k_c15_mma<<<dim3(mtiles, a.n_tiles, 2 * ne), kMmaThreads, sm_mma, st>>>(a);
+        k_c15_mma<<<dim3(mtiles, a.n_tiles, 3 * ne), kMmaThreads, sm_mma, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -590,13 +590,6 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     cudaError_t e = launch_shell_mask(s, mt, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    if (sys->tiles.c15_mode == QMC_C15_TENSOR)
-        e = launch_c15_tc(s, mt.ffb, mt, nw, Rc, c.masks, mt.mask_words, c.X, c.L5, c.st, c.c15tc, st);
-    else
-        e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.ff, mt.ns32, mt.colmax, c.X, c.L5, st,
-                          sys->tiles.c15_walkers);
-    if (e != cudaSuccess) return e;
-    if ((e = mark(5)) != cudaSuccess) return e;
     TcTables tt;
     tt.f16 = precision == QMC_PREC_MIXED ? 1 : 0;
     for (int spin = 0; spin < 2; ++spin) {
@@ -608,6 +601,17 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     }
     for (int l = 0; l < 3; ++l) tt.in_scale[l] = tt.f16 ? (float)ldexp(1.0, mt.b_exp) : 1.0f;
     tt.pgf = mt.pgf; tt.pcf = mt.pcf; tt.scf = mt.scf; tt.Qhi = mt.Qhi; tt.Qlo = mt.Qlo;
+    if (sys->tiles.c15_mode == QMC_C15_TENSOR) {
+        // C1, C5 and C2..C4 from one producer pass per (electron, walker tile)
+        e = launch_c15_tc(s, mt.ffb, mt, tt, nw, Rc, c.masks, mt.mask_words, c.X, c.L5,
+                          static_cast<float *>(c.Cd), c.st, c.c15tc, st);
+        if (e != cudaSuccess) return e;
+        return mark(5);
+    }
+    e = launch_c15_ff(s, mt.ffb, nw, Rc, c.masks, mt.mask_words, mt.ff, mt.ns32, mt.colmax, c.X, c.L5, st,
+                      sys->tiles.c15_walkers);
+    if (e != cudaSuccess) return e;
+    if ((e = mark(5)) != cudaSuccess) return e;
     return launch_tc_contract(s, nw, Rc, c.masks, mt.mask_words, tt, static_cast<float *>(c.Cd), c.st, st);
 }
 

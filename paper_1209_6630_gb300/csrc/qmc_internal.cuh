@@ -138,9 +138,9 @@ cudaError_t launch_c15_ff(const SysDev &s, const FfBasis &fb, int nw, const doub
                           double *X, double *L5, cudaStream_t st, int walkers_per_cta);
 bool c15tc_fits(const SysDev &s, int mw);
 size_t c15tc_bytes(const SysDev &s, int nw);
-cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
-                          const uint32_t *masks, int mw, double *X, double *L5, uint32_t *wstatus, void *scratch,
-                          cudaStream_t st);
+cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, const TcTables &tt, int nw,
+                          const double *R, const uint32_t *masks, int mw, double *X, double *L5, float *Cg,
+                          uint32_t *wstatus, void *scratch, cudaStream_t st);
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                                const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
 cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
