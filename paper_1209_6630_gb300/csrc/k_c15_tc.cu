@@ -44,9 +44,15 @@ namespace qmc {
 
 constexpr int kPrepThreads = 256;                              // two threads per walker row
 constexpr int kMmaThreads = 512;
-constexpr int kGradPlane0 = 2 * kC15Slices;                    // first C2..C4 plane of a step
+constexpr int kGradPlane0 = 2 * kC15Slices;                    // first C2..C4 plane of a stage
 constexpr int kPlanesPerStep = 2 * kC15Slices + 6;             // [C1 slice][C5 slice][gradient l][hi, lo]
-constexpr size_t kStepBytes = (size_t)kPlanesPerStep * kAPlaneBytes;
+// A K step of 64 AOs is staged as two stages of 32 (the MMA kernel double-buffers
+// stages): per stage and plane [128 rows][32 K] 16-bit, K-major, 64-byte swizzle.
+constexpr int SK = 32;
+constexpr uint32_t kSPlaneBytes = TC_M * SK * 2;               // 8 KB
+constexpr uint32_t kSBPlaneBytes = SK * TC_N * 2;              // 8 KB, MN-major, 128-byte swizzle
+constexpr size_t kStageBytes = (size_t)kPlanesPerStep * kSPlaneBytes;
+constexpr size_t kStepBytes = 2 * kStageBytes;
 constexpr int kChunkSteps = 16;                                // 1024 AOs per exact accumulation
 constexpr int kAcc = 4;                                        // accumulators per output
 
@@ -227,17 +233,19 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
                     vmax = fmaxf(vmax, fabsf(v));
                     lmax = fmaxf(lmax, fabsf(lp));
                 }
-                const uint32_t off = a_off(row, c8);
-                unsigned char *stp = pl + (size_t)ks * kStepBytes + (size_t)kGradPlane0 * kAPlaneBytes;
+                // stage 2 ks + c8 / 4 (this thread's half), chunk c8 % 4 within it
+                const uint32_t off = a_off64(row, c8 & 3);
+                unsigned char *stp = pl + (size_t)(2 * ks + (c8 >> 2)) * kStageBytes +
+                                     (size_t)kGradPlane0 * kSPlaneBytes;
 #pragma unroll
                 for (int l = 0; l < 3; ++l) {
                     uint32_t hi[4], lo[4];
                     const float isc = a.tt.in_scale[l];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) split2(gv[l][2 * q] * isc, gv[l][2 * q + 1] * isc, f16, hi[q], lo[q]);
-                    *reinterpret_cast<uint4 *>(stp + (size_t)(2 * l) * kAPlaneBytes + off) =
+                    *reinterpret_cast<uint4 *>(stp + (size_t)(2 * l) * kSPlaneBytes + off) =
                         make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    *reinterpret_cast<uint4 *>(stp + (size_t)(2 * l + 1) * kAPlaneBytes + off) =
+                    *reinterpret_cast<uint4 *>(stp + (size_t)(2 * l + 1) * kSPlaneBytes + off) =
                         make_uint4(lo[0], lo[1], lo[2], lo[3]);
                 }
             }
@@ -274,13 +282,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
                     wl[j][q2] = bf16_pair(sl[0][j], sl[1][j]);
                 }
             }
-            const uint32_t off = a_off(row, c8);
-            unsigned char *stp = pl + (size_t)ks * kStepBytes;
+            const uint32_t off = a_off64(row, c8 & 3);
+            unsigned char *stp = pl + (size_t)(2 * ks + (c8 >> 2)) * kStageBytes;
 #pragma unroll
             for (int j = 0; j < kC15Slices; ++j) {
-                *reinterpret_cast<uint4 *>(stp + (size_t)j * kAPlaneBytes + off) =
+                *reinterpret_cast<uint4 *>(stp + (size_t)j * kSPlaneBytes + off) =
                     make_uint4(wv[j][0], wv[j][1], wv[j][2], wv[j][3]);
-                *reinterpret_cast<uint4 *>(stp + (size_t)(kC15Slices + j) * kAPlaneBytes + off) =
+                *reinterpret_cast<uint4 *>(stp + (size_t)(kC15Slices + j) * kSPlaneBytes + off) =
                     make_uint4(wl[j][0], wl[j][1], wl[j][2], wl[j][3]);
             }
         }
@@ -296,10 +304,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char *base = tc_smem + ((1024 - (smem_u32(tc_smem) & 1023)) & 1023);
-    unsigned char *As = base;                                          // [slice] 16 KB K-major
-    unsigned char *Bs = base + kC15Slices * kAPlaneBytes;              // [slice] 16 KB MN-major
-    int *ao_s = reinterpret_cast<int *>(Bs + kC15Slices * kBPlaneBytes);   // [kmax_steps * 64]
-    __shared__ __align__(8) uint64_t mbar;
+    // two stage buffers, each [A: 6 planes x 8 KB][B: 6 planes x 8 KB]
+    constexpr uint32_t kBufBytes = kC15Slices * (kSPlaneBytes + kSBPlaneBytes);
+    int *ao_s = reinterpret_cast<int *>(base + 2 * kBufBytes);     // [kmax_steps * 64]
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
 
@@ -326,23 +334,24 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t mbar_a = smem_u32(&mbar);
+    const uint32_t mbs[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
     const bool grad = o == 2;
     const uint32_t idesc = umma_idesc_f16(TC_M, ncols, grad ? (a.tt.f16 ? 0 : 1) : 1);
     const uint64_t kWait = 2000000000ull;
     const uint16_t *__restrict__ Bsl = a.slice[spin];
     const unsigned char *Ag = a.planes + slot * (size_t)a.kmax_steps * kStepBytes +
-                              (size_t)o * kC15Slices * kAPlaneBytes;     // o = 2: the gradient planes
+                              (size_t)o * kC15Slices * kSPlaneBytes;     // o = 2: the gradient planes
     const size_t slice_stride = (size_t)s.n_ao * nspad;
     const int nbplanes = grad ? 2 : kC15Slices;
-    int ncommit = 0;
+    int ncb[2] = {0, 0};                                 // commits per stage buffer
     bool ok = true;
 
     const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
@@ -350,70 +359,91 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     const int row = (warp & 3) * 32 + lane;            // TMEM lane = walker row of this thread
     const int w = tile * TC_M + row;
 
-    for (int c0 = 0; c0 < max(nks, 1); c0 += kChunkSteps) {
-        const int c1 = min(nks, c0 + kChunkSteps);
-        for (int ks = c0; ks < c1; ++ks) {
-            if (ncommit > 0 && !mbar_wait(mbar_a, (ncommit - 1) & 1, kWait)) s_abort = 1;
-            __syncthreads();
-            if (s_abort) break;
-            // A: the 6 slice planes of this output (contiguous, already swizzled)
-            const unsigned char *ag = Ag + (size_t)ks * kStepBytes;
-            for (int q = t; q < kC15Slices * (int)kAPlaneBytes / 16; q += kMmaThreads)
-                cp_async16(smem_u32(As + 16 * q), ag + 16 * (size_t)q, true);
-            // B: rows of the MO slices (C1, C5) or of the hi/lo planes (C2..C4)
-            // [mu][k0 .. k0+127], gathered by AO index
-            for (int q = t; q < nbplanes * TC_K * (TC_N / 8); q += kMmaThreads) {
-                const int j = q / (TC_K * (TC_N / 8));
-                const int rem = q - j * (TC_K * (TC_N / 8));
-                const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
-                const int mu = ao_s[ks * TC_K + r];
-                const bool v = mu >= 0 && 8 * c < ncols;
-                const uint16_t *base = grad ? (j ? a.tt.lo[spin] : a.tt.hi[spin]) : Bsl + j * slice_stride;
-                const uint16_t *src = base + (size_t)(v ? mu : 0) * nspad + k0 + (v ? 8 * c : 0);
-                cp_async16(smem_u32(Bs + j * kBPlaneBytes + b_off(r, 8 * c)), src, v);
+    // copies of stage sg (AO positions 32 sg .. 32 sg + 31) into stage buffer buf
+    auto issue_loads = [&](int sg, int buf) {
+        unsigned char *Ab = base + buf * kBufBytes, *Bb = Ab + kC15Slices * kSPlaneBytes;
+        const unsigned char *ag = Ag + (size_t)sg * kStageBytes;
+        for (int q = t; q < kC15Slices * (int)kSPlaneBytes / 16; q += kMmaThreads)
+            cp_async16(smem_u32(Ab + 16 * q), ag + 16 * (size_t)q, true);
+        for (int q = t; q < nbplanes * SK * (TC_N / 8); q += kMmaThreads) {
+            const int j = q / (SK * (TC_N / 8));
+            const int rem = q - j * (SK * (TC_N / 8));
+            const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
+            const int mu = ao_s[sg * SK + r];
+            const bool v = mu >= 0 && 8 * c < ncols;
+            const uint16_t *bsrc = grad ? (j ? a.tt.lo[spin] : a.tt.hi[spin]) : Bsl + j * slice_stride;
+            const uint16_t *src = bsrc + (size_t)(v ? mu : 0) * nspad + k0 + (v ? 8 * c : 0);
+            cp_async16(smem_u32(Bb + j * kSBPlaneBytes + b_off(r, 8 * c)), src, v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    const int nst = 2 * nks;                             // stages of 32 AOs
+    for (int s0 = 0; s0 < max(nst, 1); s0 += 2 * kChunkSteps) {
+        const int s1 = min(nst, s0 + 2 * kChunkSteps);
+        const int c0 = s0;                               // 0 for the first chunk
+        if (s0 < s1) issue_loads(s0, s0 & 1);
+        for (int sg = s0; sg < s1; ++sg) {
+            const int buf = sg & 1;
+            if (sg + 1 < s1) {
+                const int nb = buf ^ 1;
+                // the MMAs of stage sg - 1 read buffer nb: wait before overwriting it
+                if (ncb[nb] > 0 && !mbar_wait(mbs[nb], (ncb[nb] - 1) & 1, kWait)) s_abort = 1;
+                issue_loads(sg + 1, nb);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
-            asm volatile("cp.async.wait_all;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
+            if (s_abort) break;
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+                // descriptors of the buffer's first A and B planes; the others differ only in
+                // the start-address field (address / 16 in the low bits), by constants
+                const uint32_t a0 = smem_u32(base + buf * kBufBytes);
+                const uint64_t dA = umma_desc_sw64(a0, 512);
+                const uint64_t dB = umma_desc(a0 + kC15Slices * kSPlaneBytes, kBLbo, kBSbo);
+                const bool fresh = sg == s0;                  // first stage of a chunk
                 if (grad) {
 #pragma unroll
-                    for (int kk = 0; kk < TC_K / 16; ++kk) {
-                        const uint64_t bh = umma_desc(b0 + 2 * kk * kBSbo, kBLbo, kBSbo);
-                        const uint64_t bl = umma_desc(b0 + kBPlaneBytes + 2 * kk * kBSbo, kBLbo, kBSbo);
+                    for (int kk = 0; kk < SK / 16; ++kk) {
+                        const uint64_t bh = dB + ((2 * kk * kBSbo) >> 4);
+                        const uint64_t bl = dB + ((kSBPlaneBytes + 2 * kk * kBSbo) >> 4);
 #pragma unroll
                         for (int l = 0; l < 3; ++l) {
-                            const uint64_t ah = umma_desc(a0 + (2 * l) * kAPlaneBytes + 32 * kk, 16, 1024);
-                            const uint64_t al = umma_desc(a0 + (2 * l + 1) * kAPlaneBytes + 32 * kk, 16, 1024);
+                            const uint64_t ah = dA + (((2 * l) * kSPlaneBytes + 32 * kk) >> 4);
+                            const uint64_t al = dA + (((2 * l + 1) * kSPlaneBytes + 32 * kk) >> 4);
                             const uint32_t dd = tmem + l * TC_N;
-                            umma_bf16(dd, ah, bh, idesc, (ks > c0 || kk > 0) ? 1u : 0u);
+                            umma_bf16(dd, ah, bh, idesc, (!fresh || kk > 0) ? 1u : 0u);
                             umma_bf16(dd, ah, bl, idesc, 1u);
                             umma_bf16(dd, al, bh, idesc, 1u);
                         }
                     }
-                } else
+                } else {
 #pragma unroll
-                for (int kk = 0; kk < TC_K / 16; ++kk) {
+                    for (int kk = 0; kk < SK / 16; ++kk) {
 #pragma unroll
-                    for (int d = 0; d < kC15Slices; ++d) {
-                        const int acc = d < kAcc - 1 ? d : kAcc - 1;
+                        for (int d = 0; d < kC15Slices; ++d) {
+                            const int acc = d < kAcc - 1 ? d : kAcc - 1;
 #pragma unroll
-                        for (int i = 0; i <= d; ++i) {
-                            const int j = d - i;
-                            const uint64_t ad = umma_desc(a0 + i * kAPlaneBytes + 32 * kk, 16, 1024);
-                            const uint64_t bd = umma_desc(b0 + j * kBPlaneBytes + 2 * kk * kBSbo, kBLbo, kBSbo);
-                            const bool first = ks == c0 && kk == 0 && i == 0 && d <= kAcc - 1;
-                            umma_bf16(tmem + acc * TC_N, ad, bd, idesc, first ? 0u : 1u);
+                            for (int i = 0; i <= d; ++i) {
+                                const int j = d - i;
+                                const uint64_t ad = dA + ((i * kSPlaneBytes + 32 * kk) >> 4);
+                                const uint64_t bd = dB + ((j * kSBPlaneBytes + 2 * kk * kBSbo) >> 4);
+                                const bool first = fresh && kk == 0 && i == 0 && d <= kAcc - 1;
+                                umma_bf16(tmem + acc * TC_N, ad, bd, idesc, first ? 0u : 1u);
+                            }
                         }
                     }
                 }
-                umma_commit(mbar_a);
+                umma_commit(mbs[buf]);
             }
-            ++ncommit;
+            ++ncb[buf];
         }
-        if (!s_abort && ncommit > 0 && !mbar_wait(mbar_a, (ncommit - 1) & 1, kWait)) s_abort = 1;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        for (int bq = 0; bq < 2; ++bq)
+            if (!s_abort && ncb[bq] > 0 && !mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kWait)) s_abort = 1;
         __syncthreads();
         ok = !s_abort;
         if (!ok) break;
@@ -501,7 +531,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     }
     if (!ok) {
         if (w < a.nw && (warp >> 2) == 0) atomicOr(a.wstatus + w, (uint32_t)QMC_STATUS_TIMEOUT);
-        if (ncommit > 0) mbar_wait(mbar_a, (ncommit - 1) & 1, kWait);   // let MMAs in flight drain
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        for (int bq = 0; bq < 2; ++bq)                  // let MMAs in flight drain
+            if (ncb[bq] > 0) mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kWait);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -512,7 +544,7 @@ bool c15tc_fits(const SysDev &s, int mw)
 {
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const size_t kmax = (size_t)(s.n_ao + TC_K - 1) / TC_K;
-    const size_t sm_mma = 1024 + (size_t)kC15Slices * (kAPlaneBytes + kBPlaneBytes) + sizeof(int) * kmax * TC_K;
+    const size_t sm_mma = 1024 + 2 * (size_t)kC15Slices * (kSPlaneBytes + kSBPlaneBytes) + sizeof(int) * kmax * TC_K;
     const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
     return nmax <= 1024 && mw <= 256 && sm_mma <= 227 * 1024 && sm_prep <= 227 * 1024;
 }
@@ -563,7 +595,7 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
     }
     a.X = X; a.L5 = L5; a.Cg = Cg; a.tt = tt; a.wstatus = wstatus;
     const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
-    const size_t sm_mma = 1024 + (size_t)kC15Slices * (kAPlaneBytes + kBPlaneBytes) +
+    const size_t sm_mma = 1024 + 2 * (size_t)kC15Slices * (kSPlaneBytes + kSBPlaneBytes) +
                           sizeof(int) * (size_t)a.kmax_steps * TC_K;
     if (sm_mma > 227 * 1024 || sm_prep > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e;

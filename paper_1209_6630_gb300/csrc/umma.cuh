@@ -97,6 +97,25 @@ __device__ __forceinline__ void split2(float a, float b, int f16, uint32_t &hi, 
 }
 
 // K-major, 128B swizzle: byte offset of element (row m, k) in an [128][64] bf16 plane
+// Same descriptor with the 64-byte swizzle (K-major rows of 32 16-bit elements).
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;    // leading byte offset: unused for swizzled K-major
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;    // SWIZZLE_64B
+    return d;
+}
+
+// K-major, 64B swizzle: byte offset of the 16-byte chunk (0..3) of row m in an
+// [128][32] 16-bit plane (8-row atoms of 512 bytes; chunk XOR bits 1-2 of the row)
+__device__ __forceinline__ uint32_t a_off64(int m, int chunk16)
+{
+    return (uint32_t)((m >> 3) * 512 + (m & 7) * 64 + ((chunk16 ^ ((m & 7) >> 1)) << 4));
+}
+
 __device__ __forceinline__ uint32_t a_off(int m, int chunk16)
 {
     return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((chunk16 ^ (m & 7)) << 4));
