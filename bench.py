@@ -75,6 +75,7 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=0, help="walkers in the oracle sample")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--adjoint-walkers", type=int, default=512, help="walkers of the adjoint's 1731e workload")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep default tiles (no autotuner)")
     return p.parse_args()
@@ -193,6 +194,60 @@ def cpu_oracle_sample(system, R, n_sample):
     ref = o.eval(R[:n_sample], nthreads=cores)
     dt = time.perf_counter() - t0
     return ref, dt, cores
+
+
+def adjoint_bench(a, prec, flush, e0, e1, pk, fp64_peak):
+    import torch
+    from paper_1209_6630_gb300 import QmcSystem
+    from synth import config_system, make_walkers
+    s = config_system("1731e")
+    q = QmcSystem(s, 0)
+    W = a.adjoint_walkers
+    R = torch.from_numpy(make_walkers(s, W, first=7000)).cuda()
+    o = q.eval(R, precision=prec, want_dinv=True)
+    el = o["e_loc"]
+    g = torch.where(o["status"] == 0, 2.0 * (el - el.mean()) / W, torch.zeros_like(el)).contiguous()
+    cnt, _, _ = q.screen_ao(R[:8], cap=0, want_B=False)
+    kbar = float(cnt.float().mean().item())
+    flop = 2.0 * kbar * (s.n_up ** 2 + s.n_dn ** 2) * W
+    aprec = "f64" if prec == "f64" else "mixed"
+
+    def timed(p, reps):
+        q.backward(R, o["dinv"], g, precision=p)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0.record()
+            q.backward(R, o["dinv"], g, precision=p)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts)
+
+    t_a = timed(aprec, 3 if aprec == "mixed" else 1)
+    adj = {"workload": "1731e synthetic open-shell chain (866+865 e, 4985 AOs), E_L-weighted g",
+           "walkers": W, "precision": aprec, "ms": t_a, "walkers_per_s": W / (t_a / 1e3), "kbar_active_aos": kbar,
+           "work": "2 sum_s N_s Kbar N_s flop per walker (the sparse contraction's own products)"}
+    ach = flop / (t_a / 1e3) / 1e12
+    if aprec == "mixed":
+        # six BF16 slice products per FP32-accurate product: the tensor peak / 6 bounds it
+        pk6 = pk.get("bf16_tflops_sustained") / 6.0 if pk.get("bf16_tflops_sustained") else None
+        adj["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk6, "unit": "TFLOP/s",
+                           "peak_source": "measured dense bf16 sustained / 6 slice products",
+                           "frac": ach / pk6 if pk6 else None}
+        if not a.no_compare:
+            adj["fp64_adjoint_ms"] = timed("f64", 1)
+            n = min(W, 64)
+            m_up, m_dn = q.backward(R[:n], o["dinv"][:n], g[:n], precision="mixed")
+            f_up, f_dn = q.backward(R[:n], o["dinv"][:n], g[:n], precision="f64")
+            err = max(float(((m - f).abs().max() / f.abs().max()).item()) for m, f in ((m_up, f_up), (m_dn, f_dn)))
+            adj["vs_fp64_adjoint"] = {"walkers": n, "normwise_rel_err": err}
+    else:
+        adj["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                           "peak_source": "FP64: 152 SMs x 4 flop/clk x sm_max_mhz",
+                           "frac": ach / fp64_peak if fp64_peak else None}
+    return adj
 
 
 def reference_arm(a, ws, rank):
@@ -490,18 +545,11 @@ def main():
         m64 = sum(t64) / len(t64)
         line["fp64_path"] = {"value": ws * W / (m64 / 1e3), "ms_per_step": m64}
 
-    # adjoint d log|Psi| / dA (E_L-weighted) on the same batch
+    # adjoint d log|Psi| / dA (E_L-weighted) on its own workload: the 1731-electron
+    # open-shell system with 512 walkers; FP64 after the FP64 path, the tensor-core
+    # contraction after the mixed one, the FP64 adjoint timed beside it
     if not a.no_adjoint:
-        o2 = q.eval(R, precision=prec, want_dinv=True, ws=wsbuf)
-        el = o2["e_loc"]
-        g = (2.0 * (el - el.mean()) / W).contiguous()
-        q.backward(R, o2["dinv"], g)
-        torch.cuda.synchronize()
-        e0.record()
-        q.backward(R, o2["dinv"], g)
-        e1.record()
-        e1.synchronize()
-        line["adjoint_ms"] = e0.elapsed_time(e1)
+        line["adjoint"] = adjoint_bench(a, prec, flush, e0, e1, pk, fp64_peak)
 
     # parity on a sample and the CPU baseline (rank 0 only, N = 1 only)
     if rank == 0 and ws == 1 and not a.no_cpu:

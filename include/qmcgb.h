@@ -69,13 +69,14 @@ enum {
 /* arithmetic of the products a3 (a4..a6 are always FP64) */
 enum {
     QMC_PREC_F64 = 0,        /* plain FP64 path: AO values, products, LU, energies in FP64 */
-    QMC_PREC_MIXED = 1,      /* C1 (the Slater matrix) and C5 (its Laplacian) from FP64 AO
-                                values with exact float-float products; C2..C4 (gradient
-                                matrices) on the tcgen05 tensor cores from FP16 hi/lo split
-                                operands (3 products, FP32 accumulation, exact power-of-two
-                                scaling); a4 per qmc_tiles.a4_mode (float-float Gauss-Jordan
-                                with FP64 recomputation near nodal surfaces, or FP64);
-                                energies FP64 */
+    QMC_PREC_MIXED = 1,      /* C1 (the Slater matrix) and C5 (its Laplacian) per
+                                qmc_tiles.c15_mode (tcgen05 MMAs on exact BF16 slices of
+                                float-float AO values and of A, or float-float products);
+                                C2..C4 (gradient matrices) on the tcgen05 tensor cores from
+                                FP16 hi/lo split operands (3 products, FP32 accumulation,
+                                exact power-of-two scaling); a4 per qmc_tiles.a4_mode
+                                (float-float Gauss-Jordan with FP64 recomputation near
+                                nodal surfaces, or FP64); energies FP64 */
     QMC_PREC_MIXED_BF16 = 2  /* as QMC_PREC_MIXED with BF16 hi/lo splits for C2..C5 */
 };
 
@@ -159,11 +160,17 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      slices of both operands (six each, per-row / per-column
  *                      power-of-two scaling, four FP32 accumulators per output,
  *                      ~2^-40 normwise), with a staging buffer in the workspace
+ *   bw_walkers         walkers per CTA of the tensor-core adjoint
+ *                      (qmc_logpsi_backward_ex, QMC_PREC_MIXED): 2, 4, 8, 16 or
+ *                      32.  A CTA's FP32 accumulators sum over its walkers'
+ *                      pairs only and the CTAs' partials are added in FP64:
+ *                      fewer walkers = shorter FP32 sums (smaller rounding
+ *                      error), more partials written and read
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT,
  * a4_kappa_max = 1e8, c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
- * QMC_C15_FLOAT_FLOAT.  qmc_system_set_tiles returns QMC_ERR_INVALID for
+ * QMC_C15_FLOAT_FLOAT, bw_walkers = 8.  qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous
  * choice.
  */
@@ -175,6 +182,7 @@ typedef struct {
     int a4_mode;
     double a4_kappa_max;
     int c15_mode;
+    int bw_walkers;
 } qmc_tiles;
 int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles);
 int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles);
@@ -302,6 +310,38 @@ int qmc_graph_free(qmc_graph *g);
  */
 int qmc_logpsi_backward(const qmc_system *sys, int n_walk, const double *R, const double *dinv,
                         const double *g, double *dA_up, double *dA_dn, qmc_stream_t stream);
+
+/*
+ * qmc_backward_workspace_size -- device scratch (bytes) that
+ * qmc_logpsi_backward_ex needs to process `n_walk` walkers in one pass at
+ * `precision` (0 for QMC_PREC_F64; passes hold at most 512 walkers).
+ */
+int qmc_backward_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes);
+
+/*
+ * qmc_logpsi_backward_ex -- a7 with a choice of arithmetic.
+ *   QMC_PREC_F64    exactly qmc_logpsi_backward (ws unused).
+ *   QMC_PREC_MIXED  the same sum as a contraction over the (walker, electron)
+ *                   pairs inside the screening radius of an AO block, on the
+ *                   tcgen05 tensor cores: D^-1 rounded to FP32 and g_w chi_mu
+ *                   evaluated in FP32, both split exactly into three BF16
+ *                   slices, the six slice products of order <= 2 accumulated
+ *                   in FP32 per block of qmc_tiles.bw_walkers walkers (8 by
+ *                   default), the blocks summed in FP64.
+ *                   Each term carries a relative error of a few 2^-24.
+ * Arguments as qmc_logpsi_backward, plus
+ *   ws, ws_bytes  device scratch (qmc_backward_workspace_size); a smaller
+ *                 workspace processes the walkers in several passes, down to
+ *                 one walker (below that: QMC_ERR_CAPACITY).
+ * Layouts and ownership as qmc_logpsi_backward; asynchronous on `stream`.  A
+ * bounded device wait that expires (2 s) leaves NaN in the rows of dA that
+ * the waiting CTA owned.
+ * Errors: QMC_ERR_INVALID (unknown precision, NULL pointer), QMC_ERR_CAPACITY,
+ *         QMC_ERR_CUDA.
+ */
+int qmc_logpsi_backward_ex(const qmc_system *sys, int n_walk, const double *R, const double *dinv,
+                           const double *g, int precision, double *dA_up, double *dA_dn, void *ws,
+                           size_t ws_bytes, qmc_stream_t stream);
 
 /*
  * qmc_screen_ao -- steps a1+a2 alone, for inspection and parity tests.

@@ -37,7 +37,7 @@ class EvalOut(C.Structure):
 
 class Tiles(C.Structure):
     _fields_ = [("gj_panel", _i), ("c15_walkers", _i), ("a4_mode", _i), ("a4_kappa_max", C.c_double),
-                ("c15_mode", _i)]
+                ("c15_mode", _i), ("bw_walkers", _i)]
 
 
 A4_MODE = {"fp64": 0, "float_float": 1}
@@ -86,6 +86,8 @@ def lib():
                                                  C.POINTER(C.c_float)]
             L.qmc_walkers_eval_static.argtypes = [_vp, _i, _vp, _i, C.POINTER(EvalOut), _vp]
             L.qmc_logpsi_backward.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.qmc_backward_workspace_size.argtypes = [_vp, _i, _i, C.POINTER(C.c_size_t)]
+            L.qmc_logpsi_backward_ex.argtypes = [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, C.c_size_t, _vp]
             L.qmc_screen_ao.argtypes = [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]
             L.qmc_shell_masks.argtypes = [_vp, _i, _vp, _vp, C.POINTER(_i), _vp]
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
@@ -95,8 +97,8 @@ def lib():
                          "qmc_batch_eval", "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
                          "qmc_workspace_size",
                          "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static",
-                         "qmc_logpsi_backward", "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices",
-                         "qmc_det_inverse"):
+                         "qmc_logpsi_backward", "qmc_backward_workspace_size", "qmc_logpsi_backward_ex",
+                         "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices", "qmc_det_inverse"):
                 getattr(L, name).restype = _i
             _lib = L
     return _lib
@@ -112,5 +114,6 @@ def check(rc):
 EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo", "qmc_workspace_size",
             "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size", "qmc_batch_eval",
             "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
-            "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward", "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices",
+            "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward",
+            "qmc_backward_workspace_size", "qmc_logpsi_backward_ex", "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices",
             "qmc_det_inverse", "qmc_last_error", "qmc_version")

@@ -97,15 +97,16 @@ class QmcSystem:
         check(lib().qmc_system_get_tiles(self._h, C.byref(t)))
         return {"gj_panel": t.gj_panel, "c15_walkers": t.c15_walkers,
                 "a4_mode": "float_float" if t.a4_mode == 1 else "fp64", "a4_kappa_max": t.a4_kappa_max,
-                "c15_mode": "tensor" if t.c15_mode == 1 else "float_float"}
+                "c15_mode": "tensor" if t.c15_mode == 1 else "float_float", "bw_walkers": t.bw_walkers}
 
-    def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None, c15_mode=None):
+    def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None, c15_mode=None,
+                  bw_walkers=None):
         from ._lib import A4_MODE, C15_MODE
         cur = self.tiles()
         t = Tiles(gj_panel=gj_panel or cur["gj_panel"], c15_walkers=c15_walkers or cur["c15_walkers"],
                   a4_mode=A4_MODE[a4_mode or cur["a4_mode"]],
                   a4_kappa_max=a4_kappa_max if a4_kappa_max is not None else cur["a4_kappa_max"],
-                  c15_mode=C15_MODE[c15_mode or cur["c15_mode"]])
+                  c15_mode=C15_MODE[c15_mode or cur["c15_mode"]], bw_walkers=bw_walkers or cur["bw_walkers"])
         check(lib().qmc_system_set_tiles(self._h, C.byref(t)))
 
     def set_mo(self, A_up, A_dn):
@@ -199,16 +200,33 @@ class QmcSystem:
         dn = Cm[:, 5 * nu2:].reshape(W, 5, self.n_dn, self.n_dn)
         return up, dn
 
-    def backward(self, R, dinv, g):
-        """Step a7 (qmc_logpsi_backward): dA_up [n_ao, n_up], dA_dn [n_ao, n_dn], FP64."""
+    def backward_workspace_size(self, n_walk: int, precision: str = "mixed") -> int:
+        b = C.c_size_t()
+        check(lib().qmc_backward_workspace_size(self._h, n_walk, PREC[precision], C.byref(b)))
+        return int(b.value)
+
+    def backward(self, R, dinv, g, precision: str = "f64", ws=None):
+        """Step a7: dA_up [n_ao, n_up], dA_dn [n_ao, n_dn], FP64 arrays.
+        precision "f64": qmc_logpsi_backward; "mixed": the tensor-core
+        contraction of qmc_logpsi_backward_ex (ws: optional uint8 scratch)."""
         W = int(R.shape[0])
         _req_cuda(R, torch.float64, "R", (W, self.N, 3))
         _req_cuda(dinv, torch.float64, "dinv", (W, self.n_up ** 2 + self.n_dn ** 2))
         _req_cuda(g, torch.float64, "g", (W,))
         dA_up = torch.empty(self.n_ao, self.n_up, dtype=torch.float64, device=self.device)
         dA_dn = torch.empty(self.n_ao, self.n_dn, dtype=torch.float64, device=self.device)
-        check(lib().qmc_logpsi_backward(self._h, W, _ptr(R), _ptr(dinv), _ptr(g), _ptr(dA_up), _ptr(dA_dn),
-                                        _stream(self.device)))
+        if precision == "f64":
+            check(lib().qmc_logpsi_backward(self._h, W, _ptr(R), _ptr(dinv), _ptr(g), _ptr(dA_up), _ptr(dA_dn),
+                                            _stream(self.device)))
+            return dA_up, dA_dn
+        if ws is None:
+            need = self.backward_workspace_size(W, precision)
+            ws = self._ws.get("backward")
+            if ws is None or ws.numel() < need:
+                ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+                self._ws["backward"] = ws
+        check(lib().qmc_logpsi_backward_ex(self._h, W, _ptr(R), _ptr(dinv), _ptr(g), PREC[precision],
+                                           _ptr(dA_up), _ptr(dA_dn), _ptr(ws), ws.numel(), _stream(self.device)))
         return dA_up, dA_dn
 
 
@@ -287,13 +305,15 @@ class LogPsi(torch.autograd.Function):
     forward(A_up, A_dn, R, qsys, precision): qsys must hold the same A values
     (the library keeps its own copy); returns (logpsi, e_loc).  backward
     receives d L / d logpsi (E_L is treated as constant) and returns
-    d L / d A_up, d L / d A_dn through qmc_logpsi_backward.
+    d L / d A_up, d L / d A_dn through qmc_logpsi_backward_ex, in FP64 after
+    an FP64 forward and on the tensor cores after a mixed one.
     """
 
     @staticmethod
     def forward(ctx, A_up, A_dn, R, qsys, precision="f64"):
         o = qsys.eval(R, precision=precision, want_dinv=True)
         ctx.qsys = qsys
+        ctx.precision = "f64" if precision == "f64" else "mixed"
         ctx.save_for_backward(R, o["dinv"], o["status"])
         ctx.a_dtypes = (A_up.dtype, A_dn.dtype)
         ctx.mark_non_differentiable(o["e_loc"])
@@ -303,5 +323,5 @@ class LogPsi(torch.autograd.Function):
     def backward(ctx, g_logpsi, g_eloc):
         R, dinv, status = ctx.saved_tensors
         g = torch.where(status == 0, g_logpsi.to(torch.float64), torch.zeros_like(g_logpsi, dtype=torch.float64))
-        dA_up, dA_dn = ctx.qsys.backward(R, dinv, g.contiguous())
+        dA_up, dA_dn = ctx.qsys.backward(R, dinv, g.contiguous(), precision=ctx.precision)
         return dA_up.to(ctx.a_dtypes[0]), dA_dn.to(ctx.a_dtypes[1]), None, None, None

@@ -294,12 +294,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
         }
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, bool valid)
-{
-    const int n = valid ? 16 : 0;   // 0: the 16 bytes are zero-filled
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(saddr), "l"(g), "r"(n) : "memory");
-}
-
 __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];

@@ -340,6 +340,26 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     for (int a = 0; a < na; ++a) ar2f[a] = (float)atom_R2[a];
     for (int sh = 0; sh < nsh; ++sh) sr2f[sh] = (float)sys->R2_host[sh];
     const size_t oAR2f = b.add(ar2f.data(), 4 * ar2f.size()), oSR2f = b.add(sr2f.data(), 4 * sr2f.size());
+    // AO blocks of the tensor-core adjoint: consecutive atoms, at most nb AOs per block
+    const int nb_bw = bwtc_block_width(std::max(nu, nd));
+    std::vector<int> bw_ao0, bw_sh0;
+    {
+        int cnt = 0;
+        for (int a = 0; a < na; ++a) {
+            const int s0 = atom_sh0[a], s1 = atom_sh0[a + 1];
+            if (s1 == s0) continue;
+            const int n_a = sh_ao0[s1 - 1] + ncart_h(d->shell_L[s1 - 1]) - sh_ao0[s0];
+            if (bw_ao0.empty() || cnt + n_a > nb_bw) {
+                bw_ao0.push_back(sh_ao0[s0]);
+                bw_sh0.push_back(s0);
+                cnt = 0;
+            }
+            cnt += n_a;
+        }
+        bw_ao0.push_back(nao);
+        bw_sh0.push_back(nsh);
+    }
+    const size_t oBA = b.add(bw_ao0.data(), 4 * bw_ao0.size()), oBS = b.add(bw_sh0.data(), 4 * bw_sh0.size());
     // AO derivative values enter the FP16 split scaled by 2^b_exp (bound * 2^b_exp <= 8192)
     double dbound[2] = {0.0, 0.0};
     for (int sh = 0; sh < nsh; ++sh) {
@@ -399,6 +419,11 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     mt.Qhi = reinterpret_cast<const float *>(dev + oQh);
     mt.Qlo = reinterpret_cast<const float *>(dev + oQl);
     sys->tiles.c15_mode = c15tc_fits(s, mt.mask_words) ? QMC_C15_TENSOR : QMC_C15_FLOAT_FLOAT;
+    sys->tiles.bw_walkers = 8;
+    sys->bw.nblk = (int)bw_ao0.size() - 1;
+    sys->bw.nb = nb_bw;
+    sys->bw.ao0 = reinterpret_cast<const int *>(dev + oBA);
+    sys->bw.sh0 = reinterpret_cast<const int *>(dev + oBS);
     mt.atom_R2f = reinterpret_cast<const float *>(dev + oAR2f);
     mt.sh_R2f = reinterpret_cast<const float *>(dev + oSR2f);
     mt.ffb.pg = reinterpret_cast<const float2 *>(dev + oPg2);
@@ -442,6 +467,9 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
     if (tiles->c15_mode == QMC_C15_TENSOR && !c15tc_fits(sys->d, sys->mixed.mask_words))
         return invalid("qmc_system_set_tiles: c15_mode tensor exceeds the kernel's shared-memory limits");
     if (!(tiles->a4_kappa_max > 0.0)) return invalid("qmc_system_set_tiles: a4_kappa_max must be > 0");
+    if (tiles->bw_walkers != 2 && tiles->bw_walkers != 4 && tiles->bw_walkers != 8 && tiles->bw_walkers != 16 &&
+        tiles->bw_walkers != 32)
+        return invalid("qmc_system_set_tiles: bw_walkers must be 2, 4, 8, 16 or 32");
     sys->tiles = *tiles;
     return QMC_OK;
 }
@@ -876,6 +904,40 @@ extern "C" int qmc_logpsi_backward(const qmc_system *sys, int n_walk, const doub
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_backward_f64(sys->d, n_walk, R, dinv, g, dA_up, dA_dn, st, sys->max_shell_per_atom);
     if (e != cudaSuccess) return cuda_fail(e, "qmc_logpsi_backward: launch");
+    return QMC_OK;
+}
+
+extern "C" int qmc_backward_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes)
+{
+    if (!sys || n_walk < 0 || !bytes) return invalid("qmc_backward_workspace_size: bad argument");
+    if (precision == QMC_PREC_F64) {
+        *bytes = 0;
+        return QMC_OK;
+    }
+    if (precision != QMC_PREC_MIXED) return invalid("qmc_backward_workspace_size: precision");
+    *bytes = bwtc_bytes(sys->d, sys->mixed.mask_words, n_walk, sys->tiles.bw_walkers);
+    return QMC_OK;
+}
+
+extern "C" int qmc_logpsi_backward_ex(const qmc_system *sys, int n_walk, const double *R, const double *dinv,
+                                      const double *g, int precision, double *dA_up, double *dA_dn, void *ws,
+                                      size_t ws_bytes, qmc_stream_t stream)
+{
+    if (precision == QMC_PREC_F64) return qmc_logpsi_backward(sys, n_walk, R, dinv, g, dA_up, dA_dn, stream);
+    if (!sys || n_walk < 0) return invalid("qmc_logpsi_backward_ex: bad argument");
+    if (precision != QMC_PREC_MIXED) return invalid("qmc_logpsi_backward_ex: precision");
+    if (!dA_up || !dA_dn || (n_walk > 0 && (!R || !dinv || !g || !ws)))
+        return invalid("qmc_logpsi_backward_ex: null pointer");
+    if (sys->bw.nb == 0 || sys->bw.nblk == 0) return invalid("qmc_logpsi_backward_ex: no AO blocks");
+    cudaError_t e = cudaSetDevice(sys->device);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_logpsi_backward_ex: cudaSetDevice");
+    e = launch_backward_tc(sys->d, sys->mixed, sys->bw, sys->tiles.bw_walkers, n_walk, R, dinv, g, dA_up, dA_dn,
+                           ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+    if (e == cudaErrorMemoryAllocation) {
+        set_error("qmc_logpsi_backward_ex: workspace smaller than one walker");
+        return QMC_ERR_CAPACITY;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_logpsi_backward_ex: launch");
     return QMC_OK;
 }
 

@@ -145,6 +145,19 @@ cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const u
                                const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
 cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
                          cudaStream_t st);
+// AO blocks of the tensor-core adjoint: runs of consecutive whole atoms with at
+// most nb AOs (nb = TMEM columns per MO tile).
+struct BwBlocks {
+    int nblk = 0, nb = 0;
+    const int *ao0 = nullptr, *sh0 = nullptr;   // [nblk + 1] first AO / first shell of each block
+};
+constexpr int kBwtChunk = 512;                  // walkers per pass of the tensor-core adjoint
+int bwtc_block_width(int nmax);
+size_t bwtc_bytes(const SysDev &s, int mw, int nw, int wb);
+cudaError_t launch_backward_tc(const SysDev &s, const MixedTables &mt, const BwBlocks &bb, int wb, int nw,
+                               const double *R,
+                               const double *dinv, const double *g, double *dA_up, double *dA_dn, void *ws,
+                               size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_backward_f64(const SysDev &s, int nw, const double *R, const double *dinv,
                                 const double *g, double *dA_up, double *dA_dn, cudaStream_t st,
                                 int max_ao_per_atom);
@@ -159,6 +172,7 @@ struct qmc_system {
     std::vector<double> R2_host;
     qmc::MixedTables mixed;
     int max_shell_per_atom;
+    qmc::BwBlocks bw;                 // AO blocks of the tensor-core adjoint
     void *mo_dev = nullptr;           // device tables derived from the MO coefficients
     size_t mo_bytes = 0;
     int a_dtype = 0;

@@ -3,7 +3,8 @@ AOs, FP32 MO coefficients): forward parity on sampled walkers against the
 FP64 oracle, and the adjoint d log|Psi| / dA (plain and E_L-weighted) against
 the oracle's analytic gradient and against central finite differences with
 h = 1e-4 on 64 sampled coefficients (32 of A_up, 32 of A_dn), the objective
-L = sum_w g_w log|Psi_w| evaluated by the FP64 GPU path with E_L frozen.
+L = sum_w g_w log|Psi_w| evaluated by the FP64 GPU path with E_L frozen; the
+same differences check the tensor-core adjoint of the mixed path.
 """
 import numpy as np
 import pytest
@@ -71,10 +72,13 @@ def test_adjoint_vs_central_differences(big, weighting):
     gd = torch.from_numpy(g).to(dev)
     dA_up, dA_dn = q.backward(Rd, base["dinv"], gd)
     dA = {"up": dA_up.cpu().numpy(), "dn": dA_dn.cpu().numpy()}
+    mixed = q.eval(Rd, precision="mixed", want_dinv=True)
+    mA_up, mA_dn = q.backward(Rd, mixed["dinv"], gd, precision="mixed")
+    mA = {"up": mA_up.cpu().numpy(), "dn": mA_dn.cpu().numpy()}
     rng = np.random.default_rng(1731)
     h = 1e-4
     A = {"up": s.A_up.copy(), "dn": s.A_dn.copy()}
-    errs = []
+    errs, errs_m = [], []
     try:
         for spin in ("up", "dn"):
             for _ in range(32):
@@ -92,8 +96,11 @@ def test_adjoint_vs_central_differences(big, weighting):
                 A[spin][mu, k] = a0
                 fd = (vals[0] - vals[1]) / (steps[0] - steps[1])
                 errs.append(abs(fd - dA[spin][mu, k]))
+                errs_m.append(abs(fd - mA[spin][mu, k]))
     finally:
         q.set_mo(s.A_up, s.A_dn)
     scale = max(np.abs(dA["up"]).max(), np.abs(dA["dn"]).max())
     # FD truncation ~h^2 and FP64 rounding of L / h: well below 1e-6 of the gradient scale
     assert max(errs) <= 1e-6 * scale, (max(errs), scale)
+    # the tensor-core adjoint: FP32 accumulation per block of walkers (normwise ~1e-5)
+    assert max(errs_m) <= 5e-5 * scale, (max(errs_m), scale)
