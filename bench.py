@@ -37,15 +37,20 @@ def launches_per_step(q, prec, n_walk):
     if prec == "f64":
         return 3                      # contraction, Gauss-Jordan, energy
     t = q.tiles()
-    n = 3                             # masks, tensor cores (C2..C4), energy
+    n = 2                             # masks, energy
     if t["c15_mode"] == "tensor":
         b = 64 if n_walk > 7 * 128 else (32 if n_walk > 128 else 16)
-        n += 2 * -(-q.N // b)          # slice producer + MMA kernel per batch of electrons
+        n += 2 * -(-q.N // b)          # slice producer + MMA kernel per batch of electrons (C1..C5)
     else:
-        n += 1
-    if t["a4_mode"] == "float_float":
-        panels = -(-max(q.n_up, q.n_dn) // t["gj_panel"])
-        n += 1 + 1 + 1 + 2 * panels + 1 + 1   # float-float GJ, list, FP64 C1 rows, panel+update per panel, final, FP64 pass
+        n += 2                        # float-float C1/C5, tensor-core C2..C4
+    nmax = max(q.n_up, q.n_dn)
+    if t["a4_mode"] in ("float_float", "tensor"):
+        panels = -(-nmax // t["gj_panel"])
+        redo = 1 + 1 + 2 * panels + 1 + 1     # list, FP64 C1 rows, panel+update per panel, final, FP64 pass
+        if t["a4_mode"] == "float_float":
+            n += 1 + redo                      # float-float GJ
+        else:
+            n += 1 + 2 * -(-nmax // 32) + 1 + redo   # init, panel + tensor-core update per 32 columns, final
     else:
         n += 1
     return n
@@ -59,7 +64,8 @@ def dtype_of(q, prec):
     t = q.tiles()
     c15 = "bf16 exact slices on tcgen05" if t["c15_mode"] == "tensor" else "float-float FP32 pipes"
     c24 = "fp16x3" if prec == "mixed" else "bf16x3"
-    a4 = "float-float + FP64 near nodes" if t["a4_mode"] == "float_float" else "FP64"
+    a4 = {"float_float": "float-float + FP64 near nodes",
+          "tensor": "float-float panels, bf16 exact-slice tcgen05 updates + FP64 near nodes"}.get(t["a4_mode"], "FP64")
     return f"f64 (C1,C5 {c15}; C2-C4 {c24} tcgen05; a4 {a4})"
 
 
@@ -442,7 +448,7 @@ def main():
     if prec == "f64":
         kern_ms = {"k_contract_f64": stage_mean[0], "k_gj": stage_mean[1], "k_drift_energy": stage_mean[2]}
     else:
-        a4_kern = "k_gj_ff+k_gj" if q.tiles()["a4_mode"] == "float_float" else "k_gj"
+        a4_kern = {"float_float": "k_gj_ff+k_gj", "tensor": "k_gt_panel+k_gt_update+k_gj"}.get(q.tiles()["a4_mode"], "k_gj")
         c15_kern = "k_c15_prep+k_c15_mma" if q.tiles()["c15_mode"] == "tensor" else "k_c15_ff"
         kern_ms = {"k_shell_mask": stage_mean[4], c15_kern: stage_mean[5], "k_tc_contract": stage_mean[6],
                    a4_kern: stage_mean[1], "k_drift_energy": stage_mean[2]}
@@ -458,6 +464,12 @@ def main():
         roof = {"bound": "alu", "achieved": 12.0 * (n_up ** 3 + n_dn ** 3) * W / t_k / 1e12, "peak": fp32_inst_peak,
                 "unit": "Tinst/s", "peak_source": "FP32 pipe: 152 SMs x 128 lanes x sm_max_mhz",
                 "work": "12 FP32 instructions per float-float multiply-add, N_up^3 + N_dn^3 per walker"}
+    elif kern == "k_gt_panel+k_gt_update+k_gj":
+        # the rank-32 updates issue 28 BF16 slice-pair products per multiply-add, n^3 per matrix
+        roof = {"bound": "tensor", "achieved": 28 * 2.0 * (n_up ** 3 + n_dn ** 3) * W / t_k / 1e12,
+                "peak": pk.get("bf16_tflops_sustained"), "unit": "TFLOP/s",
+                "peak_source": "measured dense bf16 sustained, MEASURED_PEAKS.json",
+                "work": "28 BF16 slice-pair products x 2 (N_up^3 + N_dn^3) flop per walker (panel elimination excluded)"}
     elif kern == "k_contract_f64":
         roof = {"bound": "alu", "achieved": 10.0 * prod / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                 "peak_source": "FP64: 152 SMs x 4 flop/clk x sm_max_mhz",

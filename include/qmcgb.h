@@ -152,7 +152,12 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      are recomputed in FP64 -- their C1 from the positions
  *                      (FP64 AO values and products) and then the elimination,
  *                      since there log|det| amplifies the mixed C1's ~2^-40 error
- *                      by kappa
+ *                      by kappa; or QMC_A4_TENSOR = the same elimination and
+ *                      recomputation with panels of 32 columns whose rank-32
+ *                      updates run on the tcgen05 tensor cores (panel and pivot
+ *                      rows in six exact BF16 slices, per-row / per-column
+ *                      power-of-two scaling, four FP32 accumulators added to
+ *                      the float-pair matrix; at most 880 electrons per spin)
  *   a4_kappa_max       that threshold (> 0)
  *   c15_mode           arithmetic of C1/C5 on the mixed paths:
  *                      QMC_C15_FLOAT_FLOAT = float-float products on the FP32
@@ -167,14 +172,15 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      fewer walkers = shorter FP32 sums (smaller rounding
  *                      error), more partials written and read
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
- * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT,
+ * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT (QMC_A4_TENSOR
+ * if an electron count exceeds 640 and fits the panel kernel),
  * a4_kappa_max = 1e8, c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
  * QMC_C15_FLOAT_FLOAT, bw_walkers = 8.  qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous
  * choice.
  */
-enum { QMC_A4_FP64 = 0, QMC_A4_FLOAT_FLOAT = 1 };
+enum { QMC_A4_FP64 = 0, QMC_A4_FLOAT_FLOAT = 1, QMC_A4_TENSOR = 2 };
 enum { QMC_C15_FLOAT_FLOAT = 0, QMC_C15_TENSOR = 1 };
 typedef struct {
     int gj_panel;

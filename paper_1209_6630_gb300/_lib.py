@@ -40,7 +40,7 @@ class Tiles(C.Structure):
                 ("c15_mode", _i), ("bw_walkers", _i)]
 
 
-A4_MODE = {"fp64": 0, "float_float": 1}
+A4_MODE = {"fp64": 0, "float_float": 1, "tensor": 2}
 C15_MODE = {"float_float": 0, "tensor": 1}
 
 

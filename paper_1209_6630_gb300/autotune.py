@@ -1,10 +1,12 @@
 """Tile-shape autotuner for a loaded system.
 
 Candidates (see qmc_tiles in include/qmcgb.h): the Gauss-Jordan panel width
-(8, 16, 32 columns) and, on the mixed path, the walkers per CTA of the C1/C5
-kernel (2, 4).  Each candidate is timed with the library's own per-stage CUDA
-events (qmc_walkers_eval_timed) on a sample batch; the two choices act on
-different stages and are picked independently.  Results are cached in JSON,
+(8, 16, 32 columns), on the mixed path the a4 arithmetic (float-float
+elimination with that panel width, or panels of 32 with the updates on the
+tensor cores) and the walkers per CTA of the float-float C1/C5 kernel (2, 4).
+Each candidate is timed with the library's own per-stage CUDA events
+(qmc_walkers_eval_timed) on a sample batch; the choices act on different
+stages and are picked one after the other.  Results are cached in JSON,
 keyed by the size class (N_up, N_dn, n_ao, mean active AOs per electron
 rounded to 32, precision).
 """
@@ -47,20 +49,33 @@ def autotune(q, R, precision="mixed", cache=DEFAULT_CACHE, force=False, verbose=
     if key in table and not force:
         q.set_tiles(**table[key]["tiles"])
         return table[key]
-    start = {k: v for k, v in q.tiles().items() if k in ("gj_panel", "c15_walkers")}
+    start = {k: v for k, v in q.tiles().items() if k in ("gj_panel", "c15_walkers", "a4_mode")}
     timings = {}
+    mixed = precision != "f64"
     best_gj, best_gj_ms = start["gj_panel"], float("inf")
     for nb in (8, 16, 32):
         try:
-            q.set_tiles(gj_panel=nb, c15_walkers=start["c15_walkers"])
+            q.set_tiles(gj_panel=nb, c15_walkers=start["c15_walkers"], a4_mode="float_float" if mixed else None)
             ms = _time(q, R, precision)
         except QmcError:                       # e.g. shared memory above the limit for this size
             continue
         timings[f"gj_panel={nb}"] = ms[1]
         if ms[1] < best_gj_ms:
             best_gj, best_gj_ms = nb, ms[1]
+    best_a4 = start["a4_mode"]
+    if mixed:
+        best_a4, best_a4_ms = "float_float", best_gj_ms
+        try:
+            q.set_tiles(gj_panel=best_gj, a4_mode="tensor")
+            ms = _time(q, R, precision)
+            timings["a4_mode=tensor"] = ms[1]
+            if ms[1] < best_a4_ms:
+                best_a4, best_a4_ms = "tensor", ms[1]
+        except QmcError:                       # the panel kernel's shared memory: at most 880 per spin
+            pass
+        q.set_tiles(a4_mode=best_a4)
     best_g = start["c15_walkers"]
-    if precision != "f64":
+    if mixed:
         best_g_ms = float("inf")
         for g in (2, 4):
             try:
@@ -71,8 +86,8 @@ def autotune(q, R, precision="mixed", cache=DEFAULT_CACHE, force=False, verbose=
             timings[f"c15_walkers={g}"] = ms[5]
             if ms[5] < best_g_ms:
                 best_g, best_g_ms = g, ms[5]
-    q.set_tiles(gj_panel=best_gj, c15_walkers=best_g)
-    entry = {"tiles": {"gj_panel": best_gj, "c15_walkers": best_g}, "stage_ms": timings,
+    q.set_tiles(gj_panel=best_gj, c15_walkers=best_g, a4_mode=best_a4)
+    entry = {"tiles": {"gj_panel": best_gj, "c15_walkers": best_g, "a4_mode": best_a4}, "stage_ms": timings,
              "sample_walkers": int(R.shape[0])}
     if verbose:
         print("autotune", key, entry)

@@ -38,6 +38,7 @@
 // are accumulated in chunks of 1024, each added to the output in FP64.
 #include "ao_ff.cuh"
 #include "qmc_internal.cuh"
+#include "slices.cuh"
 #include "umma.cuh"
 
 namespace qmc {
@@ -78,12 +79,6 @@ struct C15TcArgs {
     TcTables tt;
     uint32_t *wstatus;
 };
-
-__device__ __forceinline__ int exp_bound(float x)   // 2^E > 1.001 x (x >= 0)
-{
-    const float y = x * 1.001f;
-    return ((__float_as_int(y) >> 23) & 0xff) - 126;
-}
 
 // Radial part and AO value / Laplacian in FP32 (for the row bounds only).
 struct F32Radial {
@@ -137,29 +132,6 @@ __device__ __forceinline__ void f32_angular(const SysDev &s, const C15TcArgs &a,
     g1 = c * (dpx * py * pz * rd.g + m2gd * rd.dx * P);
     g2 = c * (px * dpy * pz * rd.g + m2gd * rd.dy * P);
     g3 = c * (px * py * dpz * rd.g + m2gd * rd.dz * P);
-}
-
-// Slices of the float pair x with |x| < 2^E: s_j = rint(r 2^(7(j+1))) 2^(-7(j+1)),
-// r the remainder, computed exactly in float pairs.
-__device__ __forceinline__ void slice6(float2 x, int E, float (&s)[kC15Slices])
-{
-    E = min(max(E, -125), 126);
-    const float sc = __int_as_float((127 - E) << 23);
-    float2 r = make_float2(x.x * sc, x.y * sc);
-#pragma unroll
-    for (int j = 0; j < kC15Slices; ++j) {
-        const int sh = kC15SliceBits * (j + 1);
-        const float q = rintf(r.x * __int_as_float((127 + sh) << 23));
-        const float sj = q * __int_as_float((127 - sh) << 23);
-        s[j] = sj;
-        r = ff::sub(r, make_float2(sj, 0.f));
-    }
-}
-
-__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi)   // exact: both have <= 8 significant bits
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
@@ -480,39 +452,52 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
             __syncthreads();
             continue;
         }
-        // epilogue C1 / C5: sum of the four accumulators, scaled by 2^(E_w + F_k), added in FP64
+        // epilogue C1 / C5: the four accumulators (orders 0, 1, 2 exact; 3..5 rounded at
+        // 2^-45) summed as float pairs on the FP32 pipes (each addition exact but the last
+        // two lo additions, 2^-47 of the sum), scaled by 2^(E_w + F_k) and converted once:
+        // two conversions and one FP64 addition per element instead of nine FP64 operations
         const int E = (w < a.nw) ? a.rexp[(slot * TC_M + row) * 2 + o] : 0;
         double *dst = outp + (size_t)(w < a.nw ? w : 0) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
                       (size_t)ei * ns;
         for (int cb = (warp >> 2) * 32; cb < ncols; cb += 32 * (kMmaThreads / 128)) {
-            double sum[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) sum[q] = 0.0;
-#pragma unroll
-            for (int acc = 0; acc < kAcc; ++acc) {
+            float hs[32], ls[32];
+            {
                 uint32_t v[32];
-                const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * TC_N + cb);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                               "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-                               "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-                               "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-                               "=r"(v[31])
-                             : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) sum[q] += (double)__uint_as_float(v[q]);
+                for (int q = 0; q < 32; ++q) {
+                    hs[q] = __uint_as_float(v[q]);
+                    ls[q] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int acc = 1; acc < kAcc; ++acc) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * TC_N + cb), v);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    float sh, se;
+                    ff::two_sum(hs[q], __uint_as_float(v[q]), sh, se);
+                    hs[q] = sh;
+                    ls[q] = __fadd_rn(ls[q], se);
+                }
             }
             if (w < a.nw && nks > 0) {
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     const int k = k0 + cb + q;
                     if (k >= ns) break;
-                    const double sc = __longlong_as_double((long long)(1023 + E + a.fexp[spin][k]) << 52);
-                    const double val = sum[q] * sc;
+                    float h2, l2;
+                    ff::fast_two_sum(hs[q], ls[q], h2, l2);
+                    const int ex = E + a.fexp[spin][k];
+                    double val;
+                    if (ex > -60 && ex < 60) {   // exact power-of-two scaling in FP32, both parts normal
+                        const float sc = __int_as_float((127 + ex) << 23);
+                        val = (double)__fmul_rn(h2, sc) + (double)__fmul_rn(l2, sc);
+                    } else {
+                        const double sc = __longlong_as_double((long long)(1023 + ex) << 52);
+                        val = ((double)h2 + (double)l2) * sc;
+                    }
                     if (c0 == 0) dst[k] = val;
                     else dst[k] += val;
                 }

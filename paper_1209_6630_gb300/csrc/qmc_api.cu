@@ -282,7 +282,8 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     sys->device = device;
     sys->tiles.gj_panel = (d->n_up > 640 || d->n_dn > 640) ? 8 : 16;
     sys->tiles.c15_walkers = 4;
-    sys->tiles.a4_mode = QMC_A4_FLOAT_FLOAT;
+    // the tensor-core panel updates win where the float-float elimination drops to 8-column panels
+    sys->tiles.a4_mode = (std::max(nu, nd) > 640 && gjtc_fits(std::max(nu, nd))) ? QMC_A4_TENSOR : QMC_A4_FLOAT_FLOAT;
     sys->tiles.a4_kappa_max = 1e8;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
@@ -460,8 +461,10 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
         return invalid("qmc_system_set_tiles: gj_panel must be 8, 16 or 32");
     if (tiles->c15_walkers != 2 && tiles->c15_walkers != 4)
         return invalid("qmc_system_set_tiles: c15_walkers must be 2 or 4");
-    if (tiles->a4_mode != QMC_A4_FP64 && tiles->a4_mode != QMC_A4_FLOAT_FLOAT)
+    if (tiles->a4_mode != QMC_A4_FP64 && tiles->a4_mode != QMC_A4_FLOAT_FLOAT && tiles->a4_mode != QMC_A4_TENSOR)
         return invalid("qmc_system_set_tiles: a4_mode");
+    if (tiles->a4_mode == QMC_A4_TENSOR && !gjtc_fits(std::max(sys->d.n_up, sys->d.n_dn)))
+        return invalid("qmc_system_set_tiles: a4_mode tensor exceeds the panel kernel's shared memory");
     if (tiles->c15_mode != QMC_C15_FLOAT_FLOAT && tiles->c15_mode != QMC_C15_TENSOR)
         return invalid("qmc_system_set_tiles: c15_mode");
     if (tiles->c15_mode == QMC_C15_TENSOR && !c15tc_fits(sys->d, sys->mixed.mask_words))
@@ -511,6 +514,7 @@ struct Plan {
     size_t per_walker; // bytes
     bool mixed;
     bool ffgj;         // a4 on float pairs (+ FP64 recompute flags)
+    bool tcgj;         // ... with the panel updates on the tensor cores (scratch per chunk)
     size_t cd_bytes;   // per walker: FP64 path C2..C5 in FP64; mixed C2..C4 FP32 + C5 FP64
     size_t mask_bytes; // per walker (mixed path): N x mask_words x 4
     size_t redo_bytes; // per chunk (float-float a4): list and state of the FP64 recomputation
@@ -529,7 +533,8 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
     p.cd_bytes = p.mixed ? p.msz * (3 * 4 + 8) : p.msz * 4 * 8;
     p.mask_bytes = p.mixed ? (size_t)sys->d.n_elec * sys->mixed.mask_words * 4 : 0;
     p.dinv = need_dinv;
-    p.ffgj = p.mixed && sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT;
+    p.ffgj = p.mixed && (sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT || sys->tiles.a4_mode == QMC_A4_TENSOR);
+    p.tcgj = p.mixed && sys->tiles.a4_mode == QMC_A4_TENSOR;
     p.redo_bytes = p.ffgj ? redo_scratch_bytes(std::max(sys->d.n_up, sys->d.n_dn)) : 0;
     p.c15tc = p.mixed && sys->tiles.c15_mode == QMC_C15_TENSOR;
     p.sd = &sys->d;
@@ -540,7 +545,7 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
 
 struct Carve {
     double *X; void *Cd; double *L5; double *D; double *la; double *sg; uint32_t *st; uint32_t *masks;
-    float2 *work; uint8_t *redo; void *redo_scratch; void *c15tc;
+    float2 *work; uint8_t *redo; void *redo_scratch; void *c15tc; void *gjtc;
 };
 
 // Arrays for `nw` walkers laid out array by array inside ws.
@@ -566,6 +571,7 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
     c.redo = p.ffgj ? reinterpret_cast<uint8_t *>(take(2 * (size_t)nw)) : nullptr;
     c.redo_scratch = p.ffgj ? take(p.redo_bytes) : nullptr;
     c.c15tc = p.c15tc ? take(c15tc_bytes(*p.sd, nw)) : nullptr;
+    c.gjtc = p.tcgj ? take(gjtc_bytes(p.sd->n_up, p.sd->n_dn, nw)) : nullptr;
     return o <= ws_bytes;
 }
 
@@ -578,6 +584,7 @@ size_t bytes_for(const Plan &p, int nw)
     o += p.mask_bytes ? al(p.mask_bytes * nw) : 0;
     o += p.ffgj ? al(p.msz * 8 * nw) + al(2 * (size_t)nw) + al(p.redo_bytes) : 0;
     o += p.c15tc ? al(c15tc_bytes(*p.sd, nw)) : 0;
+    o += p.tcgj ? al(gjtc_bytes(p.sd->n_up, p.sd->n_dn, nw)) : 0;
     return o;
 }
 
@@ -738,7 +745,8 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
             GjJob ffj[2] = {jobs[0], jobs[1]};
             for (int q = 0; q < nj; ++q) ffj[q].flag = nullptr;
-            e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, sys->tiles.a4_kappa_max);
+            if (p.tcgj) e = launch_gj_tc(ffj, nj, c.gjtc, st, sys->tiles.a4_kappa_max);
+            else e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, sys->tiles.a4_kappa_max);
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: float-float Gauss-Jordan launch");
             int e_off[2], q = 0;
             for (int spin = 0; spin < 2; ++spin)

@@ -158,6 +158,10 @@ cudaError_t launch_backward_tc(const SysDev &s, const MixedTables &mt, const BwB
                                const double *R,
                                const double *dinv, const double *g, double *dA_up, double *dA_dn, void *ws,
                                size_t ws_bytes, cudaStream_t st);
+// a4 of the mixed path with the panel updates on the tensor cores
+bool gjtc_fits(int nmax);
+size_t gjtc_bytes(int n_up, int n_dn, int nw);
+cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, double kappa_max);
 cudaError_t launch_backward_f64(const SysDev &s, int nw, const double *R, const double *dinv,
                                 const double *g, double *dA_up, double *dA_dn, cudaStream_t st,
                                 int max_ao_per_atom);
