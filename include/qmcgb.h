@@ -173,8 +173,9 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      error), more partials written and read
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT (QMC_A4_TENSOR
- * if an electron count exceeds 640 and fits the panel kernel),
- * a4_kappa_max = 1e8, c15_mode = QMC_C15_TENSOR where the system fits that
+ * from 512 electrons of one spin on, where it fits the panel kernel),
+ * a4_kappa_max = 1e8 (1e7 up to 256 electrons of one spin),
+ * c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
  * QMC_C15_FLOAT_FLOAT, bw_walkers = 8.  qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous

@@ -51,7 +51,7 @@ constexpr int kGtThreads = 256;                      // init and final kernels
 constexpr int kGtWarps = kGtThreads / 32;
 constexpr int kGpThreads = 512;                      // panel kernel: one warp per row, 16 rows at a time
 constexpr int kGpWarps = kGpThreads / 32;
-constexpr int kGtUpThreads = 256;                    // update kernel: 4 lane quadrants x 2 column groups
+constexpr int kGtUpThreads = 512;                    // update kernel: 4 lane quadrants x 4 column groups
 constexpr int kGtN = 64;                             // columns per update tile
 constexpr int kGtSl = 7;                             // slices per operand
 constexpr int kGtAcc = kGtSl;                        // one TMEM accumulator per order 0..6
@@ -259,14 +259,15 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
                 const int i = i0 + u * kGpWarps;
                 live[u] = i < n && i != p;
                 mf[u] = live[u] ? ff::neg(P[i * kGtB + c]) : make_float2(0.f, 0.f);
-                a[u] = live[u] ? P[i * kGtB + cc] : make_float2(0.f, 0.f);
+                // lane c: 0 + m * pinv (its prow is pinv), the same expression as the other lanes
+                a[u] = (live[u] && cc != c) ? P[i * kGtB + cc] : make_float2(0.f, 0.f);
             }
             __syncwarp();                                 // every lane has read the rows' column c
 #pragma unroll
             for (int u = 0; u < RU; ++u) {
                 const int i = i0 + u * kGpWarps;
                 if (!live[u]) continue;
-                const float2 x = (cc != c) ? ff::fma2(a[u], mf[u], prow) : ff::mul(mf[u], pinv);
+                const float2 x = ff::fma2(a[u], mf[u], prow);
                 P[i * kGtB + cc] = x;
                 if (cc == cn && cn < w && !used[i]) gt_argmax_merge(nbv, nbi, fabsf(x.x), i);
             }
@@ -341,7 +342,8 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
 // column tile: MMAs into the seven accumulators; once they complete, the
 // accumulators are read into registers (summed as float pairs), TMEM is
 // released to the next tile's MMAs, and the float-pair read-modify-write of
-// the tile's rows runs while those MMAs execute.
+// the tile's rows runs while those MMAs execute.  512 threads: TMEM lane
+// quadrant x four groups of 16 columns.
 __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0)
 {
     extern __shared__ __align__(1024) unsigned char gt_smem[];
@@ -400,80 +402,27 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
     const uint32_t tmem = tmem_slot;
     const uint32_t mb = smem_u32(&mbar);
     const uint32_t idesc = umma_idesc_f16(128, kGtN, 1);
+    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
 
     const int i = rt * 128 + (warp & 3) * 32 + lane;             // this thread's row (TMEM lane)
-    const int cb = (warp >> 2) * 32;                             // its 32 columns of a tile
+    const int cb = (warp >> 2) * 16;                             // its 16 columns of a tile
     const bool row_ok = i < n;
     const int E = row_ok ? Erow[i] : 0;
     const bool is_piv = row_ok && piv[i] != 0;
     float2 *row = Wk + (size_t)(row_ok ? i : 0) * n;
-    float hs[32], ls[32];
+    float hs[16], ls[16];
     int ncommit = 0;
 
-    // add the float-pair update held in hs/ls to columns ct*64 + cb .. + 31 of this row:
-    // the 32 old values are loaded first (16-byte loads, all in flight), then updated and stored
-    auto rmw = [&](int ct) {
-        if (!row_ok) return;
-        const int c0 = ct * kGtN + cb;
-        float2 x[32];
-        // 16-byte loads only where the segment starts on a 16-byte boundary (matrices and
-        // rows of odd size start on 8-byte ones) and lies inside the row
-        const bool vec = ((reinterpret_cast<uintptr_t>(row + c0) & 15) == 0) && c0 + 32 <= n;
-        if (vec) {
-            const float4 *r4 = reinterpret_cast<const float4 *>(row + c0);
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float4 v4 = is_piv ? make_float4(0.f, 0.f, 0.f, 0.f) : r4[k];
-                x[2 * k] = make_float2(v4.x, v4.y);
-                x[2 * k + 1] = make_float2(v4.z, v4.w);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 32; ++k)
-                x[k] = (!is_piv && c0 + k < n) ? row[c0 + k] : make_float2(0.f, 0.f);
+    for (int ct = 0; ct <= nc; ++ct) {
+        if (ct < nc) {
+            // B(ct) (and A) have landed: groups complete in order, one may stay in flight
+            if (ct + 1 < nc) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const int col = c0 + k;
-            if (col >= jb && col < jb + w) continue;      // the panel's columns are final
-            float h2, l2;
-            ff::fast_two_sum(hs[k], ls[k], h2, l2);
-            const int ex = E + Fs[col < n ? col : 0];
-            float2 corr;
-            if (ex > -60 && ex < 60) {
-                const float s2 = __int_as_float((127 + ex) << 23);
-                corr = make_float2(__fmul_rn(h2, s2), __fmul_rn(l2, s2));
-            } else {
-                corr = ff::from_double(((double)h2 + (double)l2) * ldexp(1.0, ex));
-            }
-            x[k] = ff::add(x[k], corr);
-        }
-        if (vec) {
-            float4 *r4 = reinterpret_cast<float4 *>(row + c0);
-            const bool in_panel = c0 < jb + w && c0 + 32 > jb;
-            if (!in_panel) {
-#pragma unroll
-                for (int k = 0; k < 16; ++k) r4[k] = make_float4(x[2 * k].x, x[2 * k].y, x[2 * k + 1].x, x[2 * k + 1].y);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    if (!(c0 + k >= jb && c0 + k < jb + w)) row[c0 + k] = x[k];
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 32; ++k)
-                if (c0 + k < n && !(c0 + k >= jb && c0 + k < jb + w)) row[c0 + k] = x[k];
-        }
-    };
-
-    for (int ct = 0; ct < nc; ++ct) {
-        // B(ct) (and A) have landed: groups complete in order, one may stay in flight
-        if (ct + 1 < nc) asm volatile("cp.async.wait_group 1;" ::: "memory");
-        else asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();                                         // also: TMEM of tile ct-1 has been read
         if (s_abort) break;
-        if (t == 0) {
+        if (ct < nc && t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t dA = umma_desc_sw64(smem_u32(As), 512);
             const uint64_t dB = umma_desc(smem_u32(Bs0 + (size_t)(ct & 1) * kGtSl * kGtBPlane), kGtBSbo, kGtBSbo);
@@ -490,40 +439,93 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
                     }
             umma_commit(mb);
         }
+        // read-modify-write of tile ct-1 (its update is in hs/ls), overlapping the MMAs of tile ct:
+        // the 16 old values are loaded first (16-byte loads where aligned), then updated and stored
+        if (ct > 0 && row_ok) {
+            const int c0 = (ct - 1) * kGtN + cb;
+            float2 x[16];
+            const bool vec = ((reinterpret_cast<uintptr_t>(row + c0) & 15) == 0) && c0 + 16 <= n;
+            if (vec) {
+                const float4 *r4 = reinterpret_cast<const float4 *>(row + c0);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float4 v4 = is_piv ? make_float4(0.f, 0.f, 0.f, 0.f) : r4[k];
+                    x[2 * k] = make_float2(v4.x, v4.y);
+                    x[2 * k + 1] = make_float2(v4.z, v4.w);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    x[k] = (!is_piv && c0 + k < n) ? row[c0 + k] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int ex = E + Fs[c0 + k < n ? c0 + k : 0];
+                float2 corr;
+                if (ex > -60 && ex < 60) {
+                    const float s2 = __int_as_float((127 + ex) << 23);
+                    corr = make_float2(__fmul_rn(hs[k], s2), __fmul_rn(ls[k], s2));
+                } else {
+                    corr = ff::from_double(((double)hs[k] + (double)ls[k]) * ldexp(1.0, ex));
+                }
+                x[k] = ff::add(x[k], corr);
+            }
+            const bool in_panel = c0 < jb + w && c0 + 16 > jb;   // the panel's columns are final
+            if (vec && !in_panel) {
+                float4 *r4 = reinterpret_cast<float4 *>(row + c0);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) r4[k] = make_float4(x[2 * k].x, x[2 * k].y, x[2 * k + 1].x, x[2 * k + 1].y);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (c0 + k < n && !(c0 + k >= jb && c0 + k < jb + w)) row[c0 + k] = x[k];
+            }
+        }
+        if (ct == nc) break;
         ++ncommit;
-        if (ct > 0) rmw(ct - 1);                                 // overlaps the MMAs just issued
         if (!mbar_wait(mb, (ncommit - 1) & 1, 2000000000ull)) s_abort = 1;   // all leave at the next barrier
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ct + 2 < nc) load_b(ct + 2);                         // B buffer ct & 1 is free again
-        {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
+        // the seven order sums, exact integers in their units: orders 0..3 added as float
+        // pairs, orders 4..6 (below 2^-21 of the update) first in FP32 (rounding ~2^-46)
+        uint32_t v0[16], v1[16];
+        tmem_ld16(tmem + tlane + (uint32_t)cb, v0);
+        tmem_ld16(tmem + tlane + (uint32_t)(kGtN + cb), v1);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                hs[k] = __uint_as_float(v[k]);
-                ls[k] = 0.f;
-            }
+        for (int k = 0; k < 16; ++k) ff::two_sum(__uint_as_float(v0[k]), __uint_as_float(v1[k]), hs[k], ls[k]);
+        tmem_ld16(tmem + tlane + (uint32_t)(2 * kGtN + cb), v0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float sh, se;
+            ff::two_sum(hs[k], __uint_as_float(v0[k]), sh, se);
+            hs[k] = sh;
+            ls[k] = __fadd_rn(ls[k], se);
         }
+        tmem_ld16(tmem + tlane + (uint32_t)(3 * kGtN + cb), v0);
 #pragma unroll
-        for (int acc = 1; acc < kGtAcc; ++acc) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * kGtN + cb), v);
+        for (int k = 0; k < 16; ++k) {
+            float sh, se;
+            ff::two_sum(hs[k], __uint_as_float(v0[k]), sh, se);
+            hs[k] = sh;
+            ls[k] = __fadd_rn(ls[k], se);
+        }
+        tmem_ld16(tmem + tlane + (uint32_t)(4 * kGtN + cb), v0);
+        tmem_ld16(tmem + tlane + (uint32_t)(5 * kGtN + cb), v1);
+        uint32_t v2[16];
+        tmem_ld16(tmem + tlane + (uint32_t)(6 * kGtN + cb), v2);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                float sh, se;
-                ff::two_sum(hs[k], __uint_as_float(v[k]), sh, se);
-                hs[k] = sh;
-                ls[k] = __fadd_rn(ls[k], se);
-            }
+        for (int k = 0; k < 16; ++k) {
+            const float t456 = __fadd_rn(__uint_as_float(v0[k]),
+                                         __fadd_rn(__uint_as_float(v1[k]), __uint_as_float(v2[k])));
+            ls[k] = __fadd_rn(ls[k], t456);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (ct + 1 == nc) rmw(ct);
     }
     __syncthreads();
     if (s_abort) {                                               // recomputed in FP64
         if (t == 0 && J.redo) J.redo[m * J.redo_stride] = 1;
         asm volatile("cp.async.wait_all;" ::: "memory");
-        mbar_wait(mb, (ncommit - 1) & 1, 2000000000ull);         // let MMAs in flight drain
+        if (ncommit > 0) mbar_wait(mb, (ncommit - 1) & 1, 2000000000ull);   // let MMAs in flight drain
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -282,9 +282,12 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     sys->device = device;
     sys->tiles.gj_panel = (d->n_up > 640 || d->n_dn > 640) ? 8 : 16;
     sys->tiles.c15_walkers = 4;
-    // the tensor-core panel updates win where the float-float elimination drops to 8-column panels
-    sys->tiles.a4_mode = (std::max(nu, nd) > 640 && gjtc_fits(std::max(nu, nd))) ? QMC_A4_TENSOR : QMC_A4_FLOAT_FLOAT;
-    sys->tiles.a4_kappa_max = 1e8;
+    // the tensor-core panel updates win from ~500 electrons per spin on (measured at 434 / 528 / 866)
+    sys->tiles.a4_mode = (std::max(nu, nd) >= 512 && gjtc_fits(std::max(nu, nd))) ? QMC_A4_TENSOR : QMC_A4_FLOAT_FLOAT;
+    // kappa_inf overstates the 2-norm condition by up to ~n: small matrices need a lower bar
+    // (158 electrons x 4096 walkers: 1e8 left one walker at |dlog|Psi|| = 1.4e-6, 1e7 at most
+    // 6e-8 for 7% more a4 time); their FP64 recomputation is cheap
+    sys->tiles.a4_kappa_max = std::max(nu, nd) <= 256 ? 1e7 : 1e8;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
     std::vector<double> atom_R2(na, 0.0);
