@@ -489,15 +489,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
                     if (k >= ns) break;
                     float h2, l2;
                     ff::fast_two_sum(hs[q], ls[q], h2, l2);
-                    const int ex = E + a.fexp[spin][k];
-                    double val;
-                    if (ex > -60 && ex < 60) {   // exact power-of-two scaling in FP32, both parts normal
-                        const float sc = __int_as_float((127 + ex) << 23);
-                        val = (double)__fmul_rn(h2, sc) + (double)__fmul_rn(l2, sc);
-                    } else {
-                        const double sc = __longlong_as_double((long long)(1023 + ex) << 52);
-                        val = ((double)h2 + (double)l2) * sc;
-                    }
+                    const int ex = E + a.fexp[spin][k];   // exact power-of-two scaling in FP32
+                    const double val = (double)scale_pow2(h2, ex) + (double)scale_pow2(l2, ex);
                     if (c0 == 0) dst[k] = val;
                     else dst[k] += val;
                 }

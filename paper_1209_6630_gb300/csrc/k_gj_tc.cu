@@ -461,13 +461,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const int ex = E + Fs[c0 + k < n ? c0 + k : 0];
-                float2 corr;
-                if (ex > -60 && ex < 60) {
-                    const float s2 = __int_as_float((127 + ex) << 23);
-                    corr = make_float2(__fmul_rn(hs[k], s2), __fmul_rn(ls[k], s2));
-                } else {
-                    corr = ff::from_double(((double)hs[k] + (double)ls[k]) * ldexp(1.0, ex));
-                }
+                const float2 corr = make_float2(scale_pow2(hs[k], ex), scale_pow2(ls[k], ex));
                 x[k] = ff::add(x[k], corr);
             }
             const bool in_panel = c0 < jb + w && c0 + 16 > jb;   // the panel's columns are final

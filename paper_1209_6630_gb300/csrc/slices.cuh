@@ -51,6 +51,15 @@ __device__ __forceinline__ void slice_n(float2 x, int E, float (&s)[S])
     }
 }
 
+// x * 2^e exactly (barring underflow or overflow of the result) for |e| <= 250,
+// as two multiplications by powers of two that are normal FP32 numbers
+__device__ __forceinline__ float scale_pow2(float x, int e)
+{
+    e = min(max(e, -250), 250);
+    const int e1 = e / 2, e2 = e - e1;
+    return __fmul_rn(__fmul_rn(x, __int_as_float((127 + e1) << 23)), __int_as_float((127 + e2) << 23));
+}
+
 __device__ __forceinline__ uint32_t bf16_pair(float lo, float hi)   // exact: both have <= 8 significant bits
 {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
