@@ -134,7 +134,8 @@ __device__ __forceinline__ void f32_angular(const SysDev &s, const C15TcArgs &a,
     g3 = c * (px * py * dpz * rd.g + m2gd * rd.dz * P);
 }
 
-__global__ void __launch_bounds__(kPrepThreads) k_c15_prep(C15TcArgs a)
+// three CTAs per SM (80 registers; a small spill costs less than the latency it hides)
+__global__ void __launch_bounds__(kPrepThreads, 3) k_c15_prep(C15TcArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *mask_s = reinterpret_cast<uint32_t *>(smem_raw);           // [128][mw]
