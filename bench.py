@@ -343,19 +343,25 @@ def mixed_batch_arm(a, ws, rank, local):
     if clocks:
         line["clocks"] = clocks
     if rank == 0 and not a.no_cpu:
-        import oracle
+        # the CPU baseline leg: the oracle timed on two walkers of each system; its results
+        # double as the reference of the per-system errors
         errs = {}
         outs = b.eval()
         torch.cuda.synchronize()
+        t_cpu, n_cpu, cores = 0.0, 0, os.cpu_count() or 1
         for k, s, Rh, o in zip(keys, systems, hosts, outs):
             sample = [0, W - 1]
-            ref = oracle.Oracle(s).eval(Rh[sample], nthreads=os.cpu_count() or 1)
+            ref, dt, cores = cpu_oracle_sample(s, Rh[sample], len(sample))
+            t_cpu += dt
+            n_cpu += len(sample)
             lp = o["logpsi"].cpu().numpy()[sample]
             el = o["e_loc"].cpu().numpy()[sample]
             errs[k] = {"max_abs_logpsi_err": float(np.abs(lp - ref["logpsi"]).max()),
                        "max_rel_eloc_err": float((np.abs(el - ref["e_loc"]) / np.abs(ref["e_loc"])).max()),
                        "walkers": len(sample)}
         line["parity"] = errs
+        line["cpu_baseline"] = {"value": n_cpu / t_cpu, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": "first and last walker of each of the four systems, FP64 oracle"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
