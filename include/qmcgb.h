@@ -66,7 +66,8 @@ enum {
                                       for this walker's tile: its results are invalid */
 };
 
-/* arithmetic of the products a3 (a4..a6 are always FP64) */
+/* arithmetic of an evaluation (the screening decisions a1 are the exact FP64
+ * ones in both) */
 enum {
     QMC_PREC_F64 = 0,        /* plain FP64 path: AO values, products, LU, energies in FP64 */
     QMC_PREC_MIXED = 1,      /* C1 (the Slater matrix) and C5 (its Laplacian) per
@@ -75,9 +76,11 @@ enum {
                                 C2..C4 (gradient matrices) on the tcgen05 tensor cores from
                                 FP16 hi/lo split operands (3 products, FP32 accumulation,
                                 exact power-of-two scaling); a4 per qmc_tiles.a4_mode
-                                (float-float Gauss-Jordan with FP64 recomputation near
-                                nodal surfaces, or FP64); energies FP64 */
-    QMC_PREC_MIXED_BF16 = 2  /* as QMC_PREC_MIXED with BF16 hi/lo splits for C2..C5 */
+                                (float-float Gauss-Jordan, alone or with its rank-32 updates
+                                on the tensor cores, with FP64 recomputation near nodal
+                                surfaces; or FP64); drift dots in FP32 and the Laplacian dot
+                                in FP64, Coulomb sums in float-float, results in FP64 */
+    QMC_PREC_MIXED_BF16 = 2  /* as QMC_PREC_MIXED with BF16 hi/lo splits for C2..C4 */
 };
 
 enum { QMC_DTYPE_F64 = 0, QMC_DTYPE_F32 = 1 };
