@@ -26,9 +26,10 @@
 //                sums at most 7 x 32 products of at most 128 x 65 units of
 //                2^-7(d+2), below 2^24 units, so every kept product is added
 //                exactly; the dropped orders d >= 7 are below ~2^-47 of the
-//                update (float pairs: 2^-48).  The epilogue sums the seven
-//                as float pairs, scales by 2^(E_i + F_j) and adds the result
-//                to the float-pair X
+//                update (float pairs: 2^-48).  The epilogue adds orders 0..3
+//                as float pairs and 4..6 (below 2^-21 of the update) first in
+//                FP32 (rounding ~2^-46), scales by 2^(E_i + F_j) as two exact
+//                FP32 multiplications and adds the result to the float-pair X
 //   k_gt_final   ||X^-1||_inf, kappa_inf, log|det| and its sign, D^-1 = X^-T
 //
 // Matrices with kappa_inf above the threshold, a zero pivot, a non-finite
