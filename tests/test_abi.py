@@ -51,3 +51,26 @@ def test_oracle_and_library_share_no_code():
         assert "import oracle" not in open(p).read() and "from oracle" not in open(p).read(), p
     osrc = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
     assert "paper_1209_6630_gb300" not in osrc
+
+
+def _header_enums():
+    vals = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(QMC_[A-Z0-9_]+)\s*=\s*(-?\d+)u?\b", src):
+            vals[m.group(1)] = int(m.group(2))
+    return vals
+
+
+def test_binding_constants_match_header_enums():
+    from paper_1209_6630_gb300 import _lib as L
+    e = _header_enums()
+    assert {k: e["QMC_PREC_" + k.upper()] for k in L.PREC} == L.PREC
+    assert {k: e["QMC_A4_" + k.upper()] for k in L.A4_MODE} == L.A4_MODE
+    assert {k: e["QMC_C15_" + k.upper()] for k in L.C15_MODE} == L.C15_MODE
+    assert (L.STATUS_SINGULAR_UP, L.STATUS_SINGULAR_DN, L.STATUS_NONFINITE, L.STATUS_TIMEOUT) == (
+        e["QMC_STATUS_SINGULAR_UP"], e["QMC_STATUS_SINGULAR_DN"], e["QMC_STATUS_NONFINITE"], e["QMC_STATUS_TIMEOUT"])
+    assert (L.DTYPE_F64, L.DTYPE_F32) == (e["QMC_DTYPE_F64"], e["QMC_DTYPE_F32"])
+    assert (L.QMC_OK, L.QMC_ERR_INVALID, L.QMC_ERR_CUDA, L.QMC_ERR_TIMEOUT, L.QMC_ERR_CAPACITY, L.QMC_ERR_NOMEM) == (
+        e["QMC_OK"], e["QMC_ERR_INVALID"], e["QMC_ERR_CUDA"], e["QMC_ERR_TIMEOUT"], e["QMC_ERR_CAPACITY"],
+        e["QMC_ERR_NOMEM"])
