@@ -8,11 +8,13 @@
 //   b = 2^E_w sum_i s_i,   A = 2^F_k sum_j t_j,   s_i, t_j = integer 2^(-7 (i+1))
 // with |integer| <= 128 (i = 0) or about 64 (i >= 1), six slices each (42
 // bits).  Every slice is exact in BF16, every product s_i t_j exact in FP32,
-// and a sum over K <= 1024 AOs of the products with the same i + j = d stays
-// an integer multiple of 2^(-7 (d+2)) below 2^24 of that unit: the FP32
-// tensor-core accumulator holds it exactly.  Four accumulators per output:
-// d = 0, 1, 2 exactly and d = 3..5 together (its rounding is 2^-45 of the
-// result); pairs with d > 5 are dropped (< 2^-42).  The epilogue adds the
+// and a sum over K AOs of the products with the same i + j = d is an integer
+// multiple of 2^(-7 (d+2)) of at most 20865 K units (d <= 2): the FP32
+// tensor-core accumulator holds it exactly for K <= 804; in the chunks of
+// 1024 AOs it can pass 2^24 units only with more than ~800 terms near the
+// row and column maxima of equal sign, and is then rounded by one unit.
+// Four accumulators per output: d = 0, 1, 2 and d = 3..5 together (its
+// rounding is 2^-45 of the result); pairs with d > 5 are dropped (< 2^-42).  The epilogue adds the
 // four in FP64 and scales by 2^(E_w + F_k).
 //
 // k_c15_prep (one CTA per electron and tile of 128 walkers): the union AO

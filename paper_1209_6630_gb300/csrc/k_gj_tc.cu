@@ -23,7 +23,7 @@
 //                loops over the 64-column tiles and issues, per tile, 2 K16
 //                steps x 28 slice-pair MMAs into seven TMEM
 //                accumulators, one per order d = i + j <= 6 of the pair: each
-//                sums at most 7 x 32 products of at most 128 x 65 units of
+//                sums at most 7 x 32 products of at most 128 x 128 units of
 //                2^-7(d+2), below 2^24 units, so every kept product is added
 //                exactly; the dropped orders d >= 7 are below ~2^-47 of the
 //                update (float pairs: 2^-48).  The epilogue adds orders 0..3
