@@ -101,3 +101,25 @@ def test_exact_order_sums():
     # and the dropped orders d >= S contribute below ~2^-47 of the update (worst case 2^-42)
     dropped = sum(_order_bound(S_GT, K_GT, d) * 2.0 ** (-BITS * (d + 2)) for d in range(S_GT, 2 * S_GT - 1))
     assert dropped < 2.0 ** -42, dropped
+
+
+def _bf16_rn(x):
+    """Round an FP32 value to BF16 (8 significant bits), ties to even, from the definition."""
+    b = np.array([x], dtype=np.float32).view(np.uint32)[0]
+    lsb = (b >> 16) & 1
+    r = (b + 0x7FFF + lsb) & 0xFFFF0000
+    return np.array([r], dtype=np.uint32).view(np.float32)[0]
+
+
+def test_three_way_bf16_split_is_exact():
+    # the adjoint's operands: hi = rn(x), mid = rn(x - hi), lo = rn(x - hi - mid), x = hi + mid + lo
+    rng = np.random.default_rng(11)
+    for _ in range(20000):
+        x = np.float32(rng.standard_normal() * 10.0 ** rng.uniform(-20, 20))
+        hi = _bf16_rn(x)
+        r1 = np.float32(x - hi)                          # exact in FP32
+        mid = _bf16_rn(r1)
+        r2 = np.float32(r1 - mid)
+        lo = _bf16_rn(r2)
+        assert np.float64(hi) + np.float64(mid) + np.float64(lo) == np.float64(x), x
+        assert np.float32(lo) == r2                      # the last slice loses nothing
