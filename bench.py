@@ -84,6 +84,8 @@ def parse():
     p.add_argument("--adjoint-walkers", type=int, default=512, help="walkers of the adjoint's 1731e workload")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep default tiles (no autotuner)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the 1731-electron forward comparison and the mixed batch")
     return p.parse_args()
 
 
@@ -191,6 +193,119 @@ def kernel_traffic(kernel, workload):
     return None
 
 
+def stage_roofline(q, prec, stage_mean, kbar, W, pk):
+    """Roofline of the dominant stage of one step.  `achieved` counts the
+    method's own work (the algorithmic flop of the paper's formulation:
+    2 sum_s N_s^3 for log|det| + inverse, 10 sum_s N_s^2 Kbar for the five
+    products), divided by the stage's CUDA-event time, against the measured
+    peak of the pipe that executes it; `frac_issued` counts what the kernels
+    issue on that pipe (the exact-slice products of the emulated FP64-class
+    arithmetic), and `fp64_equiv_ratio` compares the achieved rate with the
+    measured FP64 DFMA rate."""
+    n_up, n_dn = q.n_up, q.n_dn
+    prod = kbar * (n_up * n_up + n_dn * n_dn) * W          # sum_s N_s Kbar N_s multiply-adds per output
+    flop_a4 = 2.0 * (n_up ** 3 + n_dn ** 3) * W
+    flop_a3 = 10.0 * prod
+    bf16 = pk.get("bf16_tflops_sustained")
+    fp64_peak = fp64_peak_tflops(pk)
+    fp32_inst_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12      # T instructions/s
+    t = q.tiles()
+    if prec == "f64":
+        kern_ms = {"k_contract_f64": stage_mean[0], "k_gj": stage_mean[1], "k_drift_energy": stage_mean[2]}
+    else:
+        a4_kern = {"float_float": "k_gj_ff+k_gj", "tensor": "k_gt_panel+k_gt_update+k_gj"}.get(t["a4_mode"], "k_gj")
+        c15_kern = "k_c15_prep+k_c15_mma" if t["c15_mode"] == "tensor" else "k_c15_ff"
+        kern_ms = {"k_shell_mask": stage_mean[4], c15_kern: stage_mean[5], "k_tc_contract": stage_mean[6],
+                   a4_kern: stage_mean[1], "k_drift_energy": stage_mean[2]}
+    kern = max(kern_ms, key=kern_ms.get)
+    ts = kern_ms[kern] / 1e3
+    fp64_src = "FP64 DFMA: 152 SMs x 4 flop/clk x sm_max_mhz (the measured DFMA rate is 1.20 TFLOP/s)"
+    if kern == "k_gj":
+        roof = {"bound": "alu", "achieved": flop_a4 / ts / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_source": fp64_src, "work": "2 (N_up^3 + N_dn^3) flop per walker"}
+    elif kern == "k_contract_f64":
+        roof = {"bound": "alu", "achieved": flop_a3 / ts / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_source": fp64_src, "work": "10 sum_s N_s^2 Kbar flop per walker"}
+    elif kern == "k_gj_ff+k_gj":
+        roof = {"bound": "alu", "achieved": flop_a4 / ts / 1e12, "peak": fp32_inst_peak / 6.0, "unit": "TFLOP/s",
+                "peak_source": "FP32 pipe (152 SMs x 128 lanes x sm_max_mhz) / 6: 12 FP32 instructions "
+                               "per float-float multiply-add",
+                "work": "2 (N_up^3 + N_dn^3) flop per walker (float-float elimination + FP64 near nodes)"}
+    elif kern == "k_gt_panel+k_gt_update+k_gj":
+        roof = {"bound": "tensor", "achieved": flop_a4 / ts / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "peak_source": "measured dense bf16 sustained (MEASURED_PEAKS.json), the pipe that executes the "
+                               "rank-32 updates",
+                "work": "2 (N_up^3 + N_dn^3) flop per walker (the LU + inverse of the paper's accounting)",
+                "issued": "28 BF16 slice-pair products per multiply-add of the updates"}
+        roof["frac_issued"] = 28 * flop_a4 / ts / 1e12 / bf16 if bf16 else None
+    elif kern == "k_c15_prep+k_c15_mma":
+        roof = {"bound": "tensor", "achieved": flop_a3 / ts / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "peak_source": "measured dense bf16 sustained (MEASURED_PEAKS.json)",
+                "work": "10 sum_s N_s^2 Kbar flop per walker (the five products C1..C5)",
+                "issued": "C1, C5: 21 BF16 slice-pair products each; C2..C4: 3 fp16 split products each"}
+        roof["frac_issued"] = (2 * 21 + 3 * 3) * 2.0 * prod / ts / 1e12 / bf16 if bf16 else None
+    elif kern == "k_c15_ff":
+        roof = {"bound": "alu", "achieved": 4.0 * prod / ts / 1e12, "peak": fp32_inst_peak / 4.5, "unit": "TFLOP/s",
+                "peak_source": "FP32 pipe / 4.5: 9 FP32 instructions per float-float product",
+                "work": "2 outputs x 2 sum_s N_s^2 Kbar flop per walker (C1, C5)"}
+    elif kern == "k_tc_contract":
+        roof = {"bound": "tensor", "achieved": 6.0 * prod / ts / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "peak_source": "measured dense bf16 (= fp16) sustained", "work": "3 outputs x 2 sum_s N_s^2 Kbar flop"}
+        roof["frac_issued"] = 3 * 6.0 * prod / ts / 1e12 / bf16 if bf16 else None
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s"}
+    roof["kernel"] = kern
+    roof["kernel_ms_per_launch_region"] = kern_ms[kern]
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") and roof.get("achieved") else None
+    if roof.get("achieved") and roof.get("unit") == "TFLOP/s":
+        roof["fp64_equiv_ratio"] = roof["achieved"] / 1.20     # against the measured FP64 DFMA rate
+    return roof, kern_ms
+
+
+def config4_forward(a, flush, e0, e1):
+    """The 1731-electron open-shell chain (866 + 865 electrons, 4985 AOs, FP32
+    MO coefficients) with 512 walkers: the mixed path against the plain FP64
+    GPU path on the same batch, with the accuracy of every walker against the
+    FP64 path."""
+    import torch
+    from paper_1209_6630_gb300 import QmcSystem
+    from synth import config_system, make_walkers
+    s = config_system("1731e")
+    q = QmcSystem(s, 0)
+    W = 512
+    R = torch.from_numpy(make_walkers(s, W, first=9000)).cuda()
+
+    def timed(prec, reps):
+        ws = q.workspace(W, prec)
+        out = q.alloc_out(W)
+        q.eval(R, precision=prec, out=out, ws=ws)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0.record()
+            q.eval(R, precision=prec, out=out, ws=ws)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts), out
+
+    t_m, om = timed("mixed", 3)
+    t_f, of = timed("f64", 1)
+    ok = (om["status"] == 0) & (of["status"] == 0)
+    dlp = (om["logpsi"] - of["logpsi"]).abs()[ok]
+    del_ = ((om["e_loc"] - of["e_loc"]).abs() / of["e_loc"].abs())[ok]
+    q.close()
+    return {"workload": "1731e synthetic open-shell chain (866+865 e, 4985 AOs, FP32 A), 512 walkers",
+            "mixed": {"walker_steps_per_s": W / (t_m / 1e3), "ms_per_step": t_m},
+            "fp64_path": {"walker_steps_per_s": W / (t_f / 1e3), "ms_per_step": t_f},
+            "speedup_vs_fp64_path": t_f / t_m,
+            "accuracy_vs_fp64_path": {"walkers": int(ok.sum().item()), "max_abs_logpsi_err": float(dlp.max().item()),
+                                      "p99_abs_logpsi_err": float(torch.quantile(dlp, 0.99).item()),
+                                      "max_rel_eloc_err": float(del_.max().item()),
+                                      "status_mismatch": int((om["status"] != of["status"]).sum().item())}}
+
+
 # ---------------------------------------------------------------------------
 def cpu_oracle_sample(system, R, n_sample):
     import oracle
@@ -237,11 +352,13 @@ def adjoint_bench(a, prec, flush, e0, e1, pk, fp64_peak):
            "work": "2 sum_s N_s Kbar N_s flop per walker (the sparse contraction's own products)"}
     ach = flop / (t_a / 1e3) / 1e12
     if aprec == "mixed":
-        # six BF16 slice products per FP32-accurate product: the tensor peak / 6 bounds it
-        pk6 = pk.get("bf16_tflops_sustained") / 6.0 if pk.get("bf16_tflops_sustained") else None
-        adj["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk6, "unit": "TFLOP/s",
-                           "peak_source": "measured dense bf16 sustained / 6 slice products",
-                           "frac": ach / pk6 if pk6 else None}
+        # the method's flop against the executed pipe's measured peak; the six BF16 slice
+        # products issued per FP32-accurate product are reported as frac_issued
+        bf = pk.get("bf16_tflops_sustained")
+        adj["roofline"] = {"bound": "tensor", "achieved": ach, "peak": bf, "unit": "TFLOP/s",
+                           "peak_source": "measured dense bf16 sustained (MEASURED_PEAKS.json)",
+                           "frac": ach / bf if bf else None, "frac_issued": 6 * ach / bf if bf else None,
+                           "fp64_equiv_ratio": ach / 1.20}
         if not a.no_compare:
             adj["fp64_adjoint_ms"] = timed("f64", 1)
             n = min(W, 64)
@@ -287,44 +404,45 @@ def reference_arm(a, ws, rank):
 
 
 # ---------------------------------------------------------------------------
-def mixed_batch_arm(a, ws, rank, local):
-    """The mixed batch: 1024 walkers of each of the 158-, 434-, 1056- and
+def mixed_batch_run(W, local, rank, precision, tune, steps, warmup, oracle_sample):
+    """The mixed batch: W walkers of each of the 158-, 434-, 1056- and
     1731-electron systems (walker seeds interleaved: global walker 4j + s is
-    walker j of system s), tiles chosen by the autotuner per system, the
-    whole batch replayed as one CUDA graph per step."""
+    walker j of system s), replayed as one CUDA graph per step.  Returns the
+    step time, the clocks, the tiles and (rank 0, oracle_sample) the
+    per-system errors against the oracle on the first and last walker of each
+    system, with the oracle's time as the CPU baseline."""
     import numpy as np
     import torch
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1209_6630_gb300 import QmcBatch, QmcSystem
-    from paper_1209_6630_gb300.autotune import autotune
     from synth import config_system, make_walkers
     keys = ["158e", "434e", "1056e", "1731e"]
-    W = a.walkers or 1024
     parts, systems, hosts, tiles = [], [], [], {}
     for k in keys:
         s = config_system(k)
         q = QmcSystem(s, local)
         Rh = make_walkers(s, W, first=rank * W)
         R = torch.from_numpy(Rh).to(dev)
-        if not a.no_tune:
-            tiles[k] = autotune(q, R, precision=a.precision)["tiles"]
+        if tune:
+            from paper_1209_6630_gb300.autotune import autotune
+            tiles[k] = autotune(q, R, precision=precision)["tiles"]
         else:
             tiles[k] = q.tiles()
         parts.append((q, R))
         systems.append(s)
         hosts.append(Rh)
-    b = QmcBatch(parts, precision=a.precision, graph=True)
+    b = QmcBatch(parts, precision=precision, graph=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(max(a.warmup, 0)):
+    for _ in range(max(warmup, 0)):
         b.launch()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
-    for _ in range(a.steps):
+    for _ in range(steps):
         flush.zero_()
         e0.record()
         b.launch()
@@ -332,21 +450,12 @@ def mixed_batch_arm(a, ws, rank, local):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     clocks = clk.stop()
-    t, value = aggregate(sum(times) / len(times), 4 * W, ws)
-    line = {"metric": "walker-steps/s, mixed batch of 158/434/1056/1731-electron systems in one CUDA graph",
-            "value": value, "unit": "walker-steps/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE[a.precision], "data": "synthetic",
-            "config": {"workload": "mixed batch 4 x 1024 walkers (158, 434, 1056, 1731 e)", "walkers_per_system": W,
-                       "precision": a.precision, "l2": "flushed between timed steps", "tiles": tiles},
-            "gpu_launches": "one CUDA graph per step"}
-    if clocks:
-        line["clocks"] = clocks
-    if rank == 0 and not a.no_cpu:
-        # the CPU baseline leg: the oracle timed on two walkers of each system; its results
-        # double as the reference of the per-system errors
+    res = {"ms": sum(times) / len(times), "clocks": clocks, "tiles": tiles}
+    if rank == 0 and oracle_sample:
+        # the oracle on the first and last walker of each system: the per-system errors of
+        # the graph's results, and its time as the CPU baseline
         errs = {}
-        outs = b.eval()
+        outs = b.launch()
         torch.cuda.synchronize()
         t_cpu, n_cpu, cores = 0.0, 0, os.cpu_count() or 1
         for k, s, Rh, o in zip(keys, systems, hosts, outs):
@@ -356,12 +465,35 @@ def mixed_batch_arm(a, ws, rank, local):
             n_cpu += len(sample)
             lp = o["logpsi"].cpu().numpy()[sample]
             el = o["e_loc"].cpu().numpy()[sample]
+            st = o["status"].cpu().numpy()[sample]
             errs[k] = {"max_abs_logpsi_err": float(np.abs(lp - ref["logpsi"]).max()),
                        "max_rel_eloc_err": float((np.abs(el - ref["e_loc"]) / np.abs(ref["e_loc"])).max()),
-                       "walkers": len(sample)}
-        line["parity"] = errs
-        line["cpu_baseline"] = {"value": n_cpu / t_cpu, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
-                                "sample": "first and last walker of each of the four systems, FP64 oracle"}
+                       "status_mismatch": int((st != ref["status"]).sum()), "walkers": len(sample)}
+        res["parity"] = errs
+        res["cpu_baseline"] = {"value": n_cpu / t_cpu, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
+                               "sample": "first and last walker of each of the four systems, FP64 oracle"}
+    del b, parts
+    torch.cuda.synchronize()
+    return res
+
+
+def mixed_batch_arm(a, ws, rank, local):
+    """The mixed batch as its own bench line (--workload mixed4)."""
+    W = a.walkers or 1024
+    r = mixed_batch_run(W, local, rank, a.precision, not a.no_tune, a.steps, a.warmup, not a.no_cpu)
+    t, value = aggregate(r["ms"], 4 * W, ws)
+    line = {"metric": "walker-steps/s, mixed batch of 158/434/1056/1731-electron systems in one CUDA graph",
+            "value": value, "unit": "walker-steps/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[a.precision], "data": "synthetic",
+            "config": {"workload": "mixed batch 4 x 1024 walkers (158, 434, 1056, 1731 e)", "walkers_per_system": W,
+                       "precision": a.precision, "l2": "flushed between timed steps", "tiles": r["tiles"]},
+            "gpu_launches": "one CUDA graph per step"}
+    if r["clocks"]:
+        line["clocks"] = r["clocks"]
+    for k in ("parity", "cpu_baseline"):
+        if k in r:
+            line[k] = r[k]
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -446,59 +578,12 @@ def main():
 
     n_up, n_dn = s.n_up, s.n_dn
     pk = peaks()
-    # algorithmic work per launch (whole batch); sum_s N_s * Kbar * N_s products per output
-    prod = kbar * (n_up * n_up + n_dn * n_dn) * W
-    flop_gj = 2.0 * (n_up ** 3 + n_dn ** 3) * W
     fp64_peak = fp64_peak_tflops(pk)
-    fp32_inst_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12      # T instructions/s
-    if prec == "f64":
-        kern_ms = {"k_contract_f64": stage_mean[0], "k_gj": stage_mean[1], "k_drift_energy": stage_mean[2]}
-    else:
-        a4_kern = {"float_float": "k_gj_ff+k_gj", "tensor": "k_gt_panel+k_gt_update+k_gj"}.get(q.tiles()["a4_mode"], "k_gj")
-        c15_kern = "k_c15_prep+k_c15_mma" if q.tiles()["c15_mode"] == "tensor" else "k_c15_ff"
-        kern_ms = {"k_shell_mask": stage_mean[4], c15_kern: stage_mean[5], "k_tc_contract": stage_mean[6],
-                   a4_kern: stage_mean[1], "k_drift_energy": stage_mean[2]}
-    kern = max(kern_ms, key=kern_ms.get)
-    t_k = kern_ms[kern] / 1e3
-    if kern == "k_gj":
-        roof = {"bound": "alu", "achieved": flop_gj / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                "peak_source": "FP64: 152 SMs x 4 flop/clk (measured DFMA rate, profiles/fp64_rate_gb300.md) "
-                               "x sm_max_mhz", "work": "2 (N_up^3 + N_dn^3) flop per walker"}
-    elif kern == "k_gj_ff+k_gj":
-        # float-float elimination (FP32 pipes) plus the FP64 recomputation of the
-        # few matrices it flags; counted as the float-float work alone
-        roof = {"bound": "alu", "achieved": 12.0 * (n_up ** 3 + n_dn ** 3) * W / t_k / 1e12, "peak": fp32_inst_peak,
-                "unit": "Tinst/s", "peak_source": "FP32 pipe: 152 SMs x 128 lanes x sm_max_mhz",
-                "work": "12 FP32 instructions per float-float multiply-add, N_up^3 + N_dn^3 per walker"}
-    elif kern == "k_gt_panel+k_gt_update+k_gj":
-        # the rank-32 updates issue 28 BF16 slice-pair products per multiply-add, n^3 per matrix
-        roof = {"bound": "tensor", "achieved": 28 * 2.0 * (n_up ** 3 + n_dn ** 3) * W / t_k / 1e12,
-                "peak": pk.get("bf16_tflops_sustained"), "unit": "TFLOP/s",
-                "peak_source": "measured dense bf16 sustained, MEASURED_PEAKS.json",
-                "work": "28 BF16 slice-pair products x 2 (N_up^3 + N_dn^3) flop per walker (panel elimination excluded)"}
-    elif kern == "k_contract_f64":
-        roof = {"bound": "alu", "achieved": 10.0 * prod / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                "peak_source": "FP64: 152 SMs x 4 flop/clk x sm_max_mhz",
-                "work": "10 sum_s N_s Kbar N_s flop per walker"}
-    elif kern == "k_c15_ff":
-        # two outputs, 9 FP32 instructions per exactly accumulated float-float product
-        roof = {"bound": "alu", "achieved": 18.0 * prod / t_k / 1e12, "peak": fp32_inst_peak, "unit": "Tinst/s",
-                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x sm_max_mhz",
-                "work": "2 outputs x 9 FP32 instructions per product, sum_s N_s Kbar N_s products per walker"}
-    elif kern == "k_c15_prep+k_c15_mma":
-        roof = {"bound": "tensor", "achieved": 21 * 2 * 2.0 * prod / t_k / 1e12,
-                "peak": pk.get("bf16_tflops_sustained"), "unit": "TFLOP/s",
-                "peak_source": "measured dense bf16 sustained, MEASURED_PEAKS.json",
-                "work": "2 outputs x 21 BF16 slice-pair products x 2 sum_s N_s Kbar N_s flop per walker"}
-    elif kern == "k_tc_contract":
-        roof = {"bound": "tensor", "achieved": 3 * 3 * 2.0 * prod / t_k / 1e12, "peak": pk.get("bf16_tflops_sustained"),
-                "unit": "TFLOP/s", "peak_source": "measured dense bf16 (= fp16) sustained, MEASURED_PEAKS.json",
-                "work": "3 outputs x 3 split products x 2 sum_s N_s Kbar N_s flop per walker"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s"}
-    roof["kernel"] = kern
-    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") and roof.get("achieved") else None
+    roof, kern_ms = stage_roofline(q, prec, stage_mean, kbar, W, pk)
+    kern = roof["kernel"]
     roof["traffic"] = kernel_traffic(kern, a.workload)
+    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel's unchanged source, "
+                              "scaled to this launch (profiles/ncu_traffic.txt)") if roof["traffic"] else None
     roof["kernel_ms"] = kern_ms
     roof["stage_ms"] = {"a1_a3": stage_mean[0], "a4": stage_mean[1], "a5_a6": stage_mean[2]}
 
@@ -562,6 +647,9 @@ def main():
             t64.append(e0.elapsed_time(e1))
         m64 = sum(t64) / len(t64)
         line["fp64_path"] = {"value": ws * W / (m64 / 1e3), "ms_per_step": m64}
+        del ws64
+        q._ws.pop("f64", None)
+        torch.cuda.empty_cache()
 
     # adjoint d log|Psi| / dA (E_L-weighted) on its own workload: the 1731-electron
     # open-shell system with 512 walkers; FP64 after the FP64 path, the tensor-core
@@ -584,6 +672,21 @@ def main():
                           "status_mismatch": int((got["status"].cpu().numpy() != ref["status"]).sum())}
         line["cpu_baseline"] = {"value": n_s / dt, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{n_s} walkers of the same batch, FP64 oracle, OpenMP over walkers"}
+
+    # the other configurations the comparison names, as extra keys (1 GPU): the 1731-electron
+    # forward pass against the FP64 path, and the mixed batch in one CUDA graph
+    if prec != "f64" and ws == 1 and not a.no_configs:
+        q.close()
+        q._ws.clear()
+        del wsbuf, out
+        torch.cuda.empty_cache()
+        line["config4_forward"] = config4_forward(a, flush, e0, e1)
+        torch.cuda.empty_cache()
+        r5 = mixed_batch_run(1024, local, rank, prec, False, 3, 3, not a.no_cpu)
+        line["config5_mixed_batch"] = {
+            "workload": "1024 walkers each of the 158/434/1056/1731-electron systems, one CUDA graph per step",
+            "walker_steps_per_s": 4096 / (r5["ms"] / 1e3), "ms_per_step": r5["ms"], "tiles": "library defaults",
+            "clocks": r5["clocks"], "parity_vs_oracle": r5.get("parity"), "cpu_baseline": r5.get("cpu_baseline")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -114,6 +114,15 @@ typedef struct {
     const void *A_up;            /* [n_ao][n_up] MO coefficients, row = AO */
     const void *A_dn;            /* [n_ao][n_dn] */
     double eps;                  /* screening threshold on g (paper: 1e-8) */
+    uint32_t crc32;              /* CRC-32 key of the critical data (Sec. V.C, error
+                                    checking): the CRC-32 of ISO 3309 / ITU-T V.42 (the
+                                    one zlib computes; reflected polynomial 0xEDB88320,
+                                    initial value and final XOR 0xFFFFFFFF) over the bytes
+                                    of Z, Q, shell_atom, shell_L, shell_nprim,
+                                    shell_pstart, prim_gamma, prim_coef, ao_shell,
+                                    ao_pow, ao_scale, A_up, A_dn (in this order, as
+                                    stored in these arrays) and then eps (8 bytes,
+                                    IEEE binary64, host byte order) */
 } qmc_system_desc;
 
 /*
@@ -123,10 +132,18 @@ typedef struct {
  * bisection on the IEEE bit patterns of non-negative doubles), each atom's
  * radius (max over its shells, the paper's early exit), V_nn, and the
  * device tables (FP64 A and the split planes the mixed path reads).
+ * The CRC-32 of the description is computed first (Sec. V.C: the key checks
+ * that the input data reached the computing node intact); if it differs from
+ * desc->crc32 nothing is loaded and the call returns QMC_ERR_INVALID with a
+ * message giving both values.
  * The library owns the returned system until qmc_system_free.  Blocking.
  */
 int qmc_system_load(const qmc_system_desc *desc, int device, qmc_system **out);
 int qmc_system_free(qmc_system *sys);
+
+/* The CRC-32 key of a loaded system's critical data (as checked at load;
+ * qmc_system_set_mo recomputes it over the new coefficients). */
+int qmc_system_crc32(const qmc_system *sys, uint32_t *crc);
 
 /*
  * qmc_system_set_mo -- replace the MO coefficients a_{k mu} of a loaded
@@ -134,7 +151,8 @@ int qmc_system_free(qmc_system *sys);
  * driven by qmc_logpsi_backward.  A_up [n_ao][n_up], A_dn [n_ao][n_dn] host
  * arrays of a_dtype.  Rebuilds the library's device copies (FP64 and the
  * split planes of the mixed path) in place.  Blocking: it synchronises the
- * device first, so no evaluation still reads the old coefficients.
+ * device first, so no evaluation still reads the old coefficients.  The
+ * system's CRC-32 key (qmc_system_crc32) is recomputed over the new ones.
  */
 int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void *A_dn);
 
@@ -174,13 +192,32 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      pairs only and the CTAs' partials are added in FP64:
  *                      fewer walkers = shorter FP32 sums (smaller rounding
  *                      error), more partials written and read
+ *   wait_s             limit, in seconds, of each bounded device wait of the
+ *                      tcgen05 kernels for the copies and MMAs that feed their
+ *                      next step (1e-6 .. 60).  A wait that runs out does not
+ *                      hang the call: the C1..C5 kernels set QMC_STATUS_TIMEOUT
+ *                      on the walkers of their tile of 128, the tensor-core a4
+ *                      hands its matrix to the FP64 recomputation (the result
+ *                      stays correct), the tensor-core adjoint leaves NaN in
+ *                      the rows of dA its CTA owned.  After such a wait the CTA
+ *                      waits at most 2 s more for its own MMAs, then frees its
+ *                      tensor memory and returns.  (The paper's principle for
+ *                      failures, Sec. V: lose only the affected block of work.)
+ *   expire_walker      test hook, -1 = off.  For w >= 0 the tcgen05 kernels that
+ *                      work on walker w (index within the call) make one of
+ *                      their waits run out deliberately: it waits wait_s on a
+ *                      flag that nothing sets.  C1..C5: the C1 CTA of electron 0
+ *                      and MO tile 0 of w's walker tile; a4 (tensor mode): the
+ *                      first update CTA of w's spin-up and spin-down matrices;
+ *                      adjoint: the spin-up CTAs of w's block of bw_walkers.
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT (QMC_A4_TENSOR
  * from 512 electrons of one spin on, where it fits the panel kernel),
  * a4_kappa_max = 1e8 (1e7 up to 256 electrons of one spin),
  * c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
- * QMC_C15_FLOAT_FLOAT, bw_walkers = 8.  qmc_system_set_tiles returns QMC_ERR_INVALID for
+ * QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1.
+ * qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous
  * choice.
  */
@@ -193,6 +230,8 @@ typedef struct {
     double a4_kappa_max;
     int c15_mode;
     int bw_walkers;
+    double wait_s;
+    int expire_walker;
 } qmc_tiles;
 int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles);
 int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles);
@@ -266,7 +305,11 @@ int qmc_walkers_eval_timed(const qmc_system *sys, int n_walk, const double *R, i
  *     QMC_PREC_F64) is rejected with QMC_ERR_CAPACITY and a message giving
  *     the size.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress), and so does the first call after that device's
+ *     CUDA context was destroyed and created again; make that first call
+ *     before any stream capture.
+ *   - n_walk == 0 returns QMC_OK at once (after checking sys and out), as
+ *     qmc_walkers_eval does.
  *   - All calls share the one array and it keeps the last call's contents:
  *     calls that overlap on the GPU (other streams, other threads) race and
  *     corrupt each other's results; serialise them.

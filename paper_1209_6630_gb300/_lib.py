@@ -26,7 +26,7 @@ class SystemDesc(C.Structure):
         ("n_prim", _i), ("prim_gamma", _vp), ("prim_coef", _vp),
         ("n_ao", _i), ("ao_shell", _vp), ("ao_pow", _vp), ("ao_scale", _vp),
         ("n_up", _i), ("n_dn", _i), ("a_dtype", _i), ("A_up", _vp), ("A_dn", _vp),
-        ("eps", C.c_double),
+        ("eps", C.c_double), ("crc32", C.c_uint32),
     ]
 
 
@@ -37,7 +37,7 @@ class EvalOut(C.Structure):
 
 class Tiles(C.Structure):
     _fields_ = [("gj_panel", _i), ("c15_walkers", _i), ("a4_mode", _i), ("a4_kappa_max", C.c_double),
-                ("c15_mode", _i), ("bw_walkers", _i)]
+                ("c15_mode", _i), ("bw_walkers", _i), ("wait_s", C.c_double), ("expire_walker", _i)]
 
 
 A4_MODE = {"fp64": 0, "float_float": 1, "tensor": 2}
@@ -73,6 +73,7 @@ def lib():
             L.qmc_system_free.argtypes = [_vp]
             L.qmc_system_shell_r2.argtypes = [_vp, _vp]
             L.qmc_system_set_mo.argtypes = [_vp, _i, _vp, _vp]
+            L.qmc_system_crc32.argtypes = [_vp, C.POINTER(C.c_uint32)]
             L.qmc_system_set_tiles.argtypes = [_vp, C.POINTER(Tiles)]
             L.qmc_system_get_tiles.argtypes = [_vp, C.POINTER(Tiles)]
             L.qmc_batch_workspace_size.argtypes = [C.POINTER(Segment), _i, _i, C.POINTER(C.c_size_t)]
@@ -93,6 +94,7 @@ def lib():
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo",
+                         "qmc_system_crc32",
                          "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size",
                          "qmc_batch_eval", "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
                          "qmc_workspace_size",
@@ -111,7 +113,8 @@ def check(rc):
 
 
 # every symbol include/qmcgb.h declares
-EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo", "qmc_workspace_size",
+EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo", "qmc_system_crc32",
+            "qmc_workspace_size",
             "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size", "qmc_batch_eval",
             "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
             "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward",

@@ -6,6 +6,7 @@ torch provides device memory and the current stream.
 from __future__ import annotations
 
 import ctypes as C
+import zlib
 
 import numpy as np
 import torch
@@ -23,6 +24,17 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def desc_crc32(arrays, eps):
+    """CRC-32 key of a system description (the qmc_system_desc.crc32 rule):
+    zlib's CRC-32 over the arrays' bytes in declaration order, then eps as an
+    8-byte IEEE double in host byte order."""
+    c = 0
+    for a in arrays:
+        c = zlib.crc32(memoryview(np.ascontiguousarray(a)).cast("B"), c)
+    c = zlib.crc32(np.array([eps], dtype=np.float64).tobytes(), c)
+    return c & 0xFFFFFFFF
+
+
 def _req_cuda(t, dtype, name, shape=None):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
@@ -35,6 +47,40 @@ def _req_cuda(t, dtype, name, shape=None):
     return t
 
 
+def system_desc(s):
+    """qmc_system_desc of a synthetic system (host arrays kept alive in the
+    returned list) with its CRC-32 key; returns (desc, keep, A dtype)."""
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        if a.ndim > 1:
+            a = a.reshape(-1)
+        keep.append(a)
+        return C.c_void_p(a.ctypes.data)
+
+    d = SystemDesc()
+    d.n_atom = s.n_atom
+    d.Z, d.Q = arr(s.Z, np.float64), arr(s.Q, np.float64)
+    d.n_shell = s.n_shell
+    d.shell_atom, d.shell_L = arr(s.shell_atom, np.int32), arr(s.shell_L, np.int32)
+    d.shell_nprim, d.shell_pstart = arr(s.shell_nprim, np.int32), arr(s.shell_pstart, np.int32)
+    d.n_prim = int(np.asarray(s.prim_gamma).size)
+    d.prim_gamma, d.prim_coef = arr(s.prim_gamma, np.float64), arr(s.prim_coef, np.float64)
+    d.n_ao = s.n_ao
+    d.ao_shell, d.ao_pow, d.ao_scale = arr(s.ao_shell, np.int32), arr(s.ao_pow, np.int32), arr(s.ao_scale, np.float64)
+    d.n_up, d.n_dn = s.n_up, s.n_dn
+    f32 = np.asarray(s.A_up).dtype == np.float32
+    a_dtype = np.float32 if f32 else np.float64
+    d.a_dtype = DTYPE_F32 if f32 else DTYPE_F64
+    d.A_up, d.A_dn = arr(s.A_up, a_dtype), arr(s.A_dn, a_dtype)
+    d.eps = float(s.eps)
+    # keep[] holds Z, Q, shell_atom, shell_L, shell_nprim, shell_pstart, prim_gamma, prim_coef,
+    # ao_shell, ao_pow, ao_scale, A_up, A_dn: the order of the key
+    d.crc32 = desc_crc32(keep, d.eps)
+    return d, keep, a_dtype
+
+
 class QmcSystem:
     """A molecular system resident on one GPU (qmc_system_load)."""
 
@@ -44,29 +90,7 @@ class QmcSystem:
         self.n_up, self.n_dn, self.n_ao = int(s.n_up), int(s.n_dn), int(s.n_ao)
         self.N = self.n_up + self.n_dn
         self.n_atom, self.n_shell = int(s.n_atom), int(s.n_shell)
-        keep = []
-
-        def arr(a, dt):
-            a = np.ascontiguousarray(a, dtype=dt)
-            keep.append(a)
-            return C.c_void_p(a.ctypes.data)
-
-        d = SystemDesc()
-        d.n_atom = s.n_atom
-        d.Z, d.Q = arr(s.Z, np.float64), arr(s.Q, np.float64)
-        d.n_shell = s.n_shell
-        d.shell_atom, d.shell_L = arr(s.shell_atom, np.int32), arr(s.shell_L, np.int32)
-        d.shell_nprim, d.shell_pstart = arr(s.shell_nprim, np.int32), arr(s.shell_pstart, np.int32)
-        d.n_prim = int(np.asarray(s.prim_gamma).size)
-        d.prim_gamma, d.prim_coef = arr(s.prim_gamma, np.float64), arr(s.prim_coef, np.float64)
-        d.n_ao = s.n_ao
-        d.ao_shell, d.ao_pow, d.ao_scale = arr(s.ao_shell, np.int32), arr(s.ao_pow, np.int32), arr(s.ao_scale, np.float64)
-        d.n_up, d.n_dn = s.n_up, s.n_dn
-        f32 = np.asarray(s.A_up).dtype == np.float32
-        self.a_dtype = np.float32 if f32 else np.float64
-        d.a_dtype = DTYPE_F32 if f32 else DTYPE_F64
-        d.A_up, d.A_dn = arr(s.A_up, self.a_dtype), arr(s.A_dn, self.a_dtype)
-        d.eps = float(s.eps)
+        d, self._keep, self.a_dtype = system_desc(s)
         h = C.c_void_p()
         check(lib().qmc_system_load(C.byref(d), device, C.byref(h)))
         self._h = h
@@ -92,21 +116,30 @@ class QmcSystem:
         check(lib().qmc_system_shell_r2(self._h, C.c_void_p(out.ctypes.data)))
         return out
 
+    def crc32(self) -> int:
+        """The system's CRC-32 key (qmc_system_crc32)."""
+        c = C.c_uint32()
+        check(lib().qmc_system_crc32(self._h, C.byref(c)))
+        return int(c.value)
+
     def tiles(self):
         t = Tiles()
         check(lib().qmc_system_get_tiles(self._h, C.byref(t)))
         return {"gj_panel": t.gj_panel, "c15_walkers": t.c15_walkers,
                 "a4_mode": {0: "fp64", 1: "float_float", 2: "tensor"}[t.a4_mode], "a4_kappa_max": t.a4_kappa_max,
-                "c15_mode": "tensor" if t.c15_mode == 1 else "float_float", "bw_walkers": t.bw_walkers}
+                "c15_mode": "tensor" if t.c15_mode == 1 else "float_float", "bw_walkers": t.bw_walkers,
+                "wait_s": t.wait_s, "expire_walker": t.expire_walker}
 
     def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None, c15_mode=None,
-                  bw_walkers=None):
+                  bw_walkers=None, wait_s=None, expire_walker=None):
         from ._lib import A4_MODE, C15_MODE
         cur = self.tiles()
         t = Tiles(gj_panel=gj_panel or cur["gj_panel"], c15_walkers=c15_walkers or cur["c15_walkers"],
                   a4_mode=A4_MODE[a4_mode or cur["a4_mode"]],
                   a4_kappa_max=a4_kappa_max if a4_kappa_max is not None else cur["a4_kappa_max"],
-                  c15_mode=C15_MODE[c15_mode or cur["c15_mode"]], bw_walkers=bw_walkers or cur["bw_walkers"])
+                  c15_mode=C15_MODE[c15_mode or cur["c15_mode"]], bw_walkers=bw_walkers or cur["bw_walkers"],
+                  wait_s=wait_s if wait_s is not None else cur["wait_s"],
+                  expire_walker=expire_walker if expire_walker is not None else cur["expire_walker"])
         check(lib().qmc_system_set_tiles(self._h, C.byref(t)))
 
     def set_mo(self, A_up, A_dn):

@@ -70,6 +70,8 @@ struct BwTcArgs {
     int nb;                    // AO block width = TMEM columns per MO tile
     const int *blk_ao0, *blk_sh0;
     float *part[2];            // [walker block][n_ao][ns] FP32 partials
+    unsigned long long wait_ns;  // limit of each wait (WaitCfg)
+    int expire_w;              // test hook: spin-up CTAs of this walker (in the pass) let their last wait run out
 };
 
 __device__ __forceinline__ float ipowf(float x, int n)
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_bw_mma(BwTcArgs a)
     __shared__ int warp_s[kBtThreads / 32];
     __shared__ __align__(8) uint64_t mbar[kBtABufs];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_npend, s_abort;
+    __shared__ int s_npend, s_abort, s_never;
 
     const SysDev &s = a.s;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_bw_mma(BwTcArgs a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_npend = 0;
         s_abort = 0;
+        s_never = 0;
     }
     // rows nb..: never written again; rows < nao are rewritten every stage
     for (uint32_t q = t; q < 2 * kBtSlices * xplane / 16; q += kBtThreads)
@@ -197,7 +200,8 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_bw_mma(BwTcArgs a)
     const uint32_t tmem = tmem_slot;
     uint32_t mbs[kBtABufs];
     for (int b = 0; b < kBtABufs; ++b) mbs[b] = smem_u32(&mbar[b]);
-    const uint64_t kWait = 2000000000ull;
+    const uint64_t kWait = a.wait_ns;
+    const bool expire = spin == 0 && a.expire_w >= w_lo && a.expire_w < w_lo + nwl;
     const uint32_t idesc = umma_idesc_f16_major(TC_M, a.nb, 1, 1, 0);   // A = D^-1 rows MN-major, B = X K-major
 
     // next stage of up to 64 hits into hits_s[buf]; returns their number
@@ -391,7 +395,8 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_bw_mma(BwTcArgs a)
         }
         if (ok) {
             const int last = ncommit - 1;
-            if (!mbar_wait(mbs[last % kBtABufs], (last / kBtABufs) & 1, kWait)) s_abort = 1;
+            if (expire ? !flag_wait(&s_never, kWait) : !mbar_wait(mbs[last % kBtABufs], (last / kBtABufs) & 1, kWait))
+                s_abort = 1;
         }
         __syncthreads();
         ok = ok && !s_abort;
@@ -416,7 +421,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_bw_mma(BwTcArgs a)
         asm volatile("cp.async.wait_all;" ::: "memory");
         for (int b = 0; b < kBtABufs; ++b) {   // let MMAs in flight drain before TMEM is released
             const int x = ncommit - 1 - (((ncommit - 1 - b) % kBtABufs) + kBtABufs) % kBtABufs;
-            if (x >= 0) mbar_wait(mbs[b], (x / kBtABufs) & 1, kWait);
+            if (x >= 0) mbar_wait(mbs[b], (x / kBtABufs) & 1, kDrainNs);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -463,7 +468,7 @@ size_t bwtc_bytes(const SysDev &s, int mw, int nw, int wb)
 
 cudaError_t launch_backward_tc(const SysDev &s, const MixedTables &mt, const BwBlocks &bb, int wb, int nw,
                                const double *R, const double *dinv, const double *g, double *dA_up, double *dA_dn, void *ws,
-                               size_t ws_bytes, cudaStream_t st)
+                               size_t ws_bytes, cudaStream_t st, const WaitCfg &wcfg)
 {
     cudaError_t e;
     if (nw == 0) {
@@ -520,6 +525,8 @@ cudaError_t launch_backward_tc(const SysDev &s, const MixedTables &mt, const BwB
         a.plane = (size_t)n * msz8;
         a.nw = n;
         a.g = g + c0;
+        a.wait_ns = wcfg.limit_ns;
+        a.expire_w = wcfg.expire_w >= c0 && wcfg.expire_w < c0 + n ? wcfg.expire_w - c0 : -1;
         const size_t work = (size_t)n * (msz8 / 8);
         const int pblocks = (int)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
         k_bw_prep<<<pblocks, 256, 0, st>>>(dinv + (size_t)c0 * msz, n, s.n_up, s.n_dn, ns8u, ns8d, msz8, sl, a.plane,

@@ -80,6 +80,8 @@ struct C15TcArgs {
     float *Cg;                     // C2..C4, FP32 [W][3][...]
     TcTables tt;
     uint32_t *wstatus;
+    unsigned long long wait_ns;    // limit of each wait (WaitCfg)
+    int expire_tile;               // test hook: walker tile whose first CTA's wait runs out (-1: none)
 };
 
 // Radial part and AO value / Laplacian in FP32 (for the row bounds only).
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     int *ao_s = reinterpret_cast<int *>(base + 2 * kBufBytes);     // [kmax_steps * 64]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_never;
 
     const SysDev &s = a.s;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     const int nks = a.nks[slot];
     const int *lst = a.ao_list + slot * (size_t)a.kmax_steps * TC_K;
     for (int q = t; q < nks * TC_K; q += kMmaThreads) ao_s[q] = lst[q];
-    if (t == 0) s_abort = 0;
+    if (t == 0) { s_abort = 0; s_never = 0; }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
@@ -314,7 +316,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     const uint32_t mbs[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
     const bool grad = o == 2;
     const uint32_t idesc = umma_idesc_f16(TC_M, ncols, grad ? (a.tt.f16 ? 0 : 1) : 1);
-    const uint64_t kWait = 2000000000ull;
+    const uint64_t kWait = a.wait_ns;
+    // test hook: the C1 CTA of electron 0, MO tile 0 of the chosen walker tile
+    const bool expire = tile == a.expire_tile && e == 0 && mt == 0 && o == 0;
     const uint16_t *__restrict__ Bsl = a.slice[spin];
     const unsigned char *Ag = a.planes + slot * (size_t)a.kmax_steps * kStepBytes +
                               (size_t)o * kC15Slices * kSPlaneBytes;     // o = 2: the gradient planes
@@ -411,6 +415,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
             ++ncb[buf];
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
+        if (expire && !flag_wait(&s_never, kWait)) s_abort = 1;
         for (int bq = 0; bq < 2; ++bq)
             if (!s_abort && ncb[bq] > 0 && !mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kWait)) s_abort = 1;
         __syncthreads();
@@ -508,7 +513,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
         if (w < a.nw && (warp >> 2) == 0) atomicOr(a.wstatus + w, (uint32_t)QMC_STATUS_TIMEOUT);
         asm volatile("cp.async.wait_all;" ::: "memory");
         for (int bq = 0; bq < 2; ++bq)                  // let MMAs in flight drain
-            if (ncb[bq] > 0) mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kWait);
+            if (ncb[bq] > 0) mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kDrainNs);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -542,7 +547,7 @@ size_t c15tc_bytes(const SysDev &s, int nw)
 
 cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, const TcTables &tt, int nw,
                           const double *R, const uint32_t *masks, int mw, double *X, double *L5, float *Cg,
-                          uint32_t *wstatus, void *scratch, cudaStream_t st)
+                          uint32_t *wstatus, void *scratch, cudaStream_t st, const WaitCfg &wc)
 {
     if (nw == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
@@ -569,6 +574,8 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
         a.ns_pad[spin] = mt.ns_pad[spin];
     }
     a.X = X; a.L5 = L5; a.Cg = Cg; a.tt = tt; a.wstatus = wstatus;
+    a.wait_ns = wc.limit_ns;
+    a.expire_tile = wc.expire_w >= 0 && wc.expire_w < nw ? wc.expire_w / TC_M : -1;
     const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
     const size_t sm_mma = 1024 + 2 * (size_t)kC15Slices * (kSPlaneBytes + kSBPlaneBytes) +
                           sizeof(int) * (size_t)a.kmax_steps * TC_K;

@@ -102,6 +102,8 @@ struct GtJobs {
     unsigned char *scr[2];                           // scratch of matrix m: scr + m * per
     int nj;
     int jb;                                          // current panel
+    unsigned long long wait_ns;                      // limit of each wait (WaitCfg)
+    int expire_m;                                    // test hook: matrix whose first update wait runs out
 };
 
 __device__ __forceinline__ void gt_argmax_merge(float &v, int &i, float v2, int i2)
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
     unsigned char *base = gt_smem + ((1024 - (smem_u32(gt_smem) & 1023)) & 1023);
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_never;
 
     const int z = z0 + blockIdx.z;
     const int q = z % js.nj, m = z / js.nj;
@@ -396,6 +398,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
+        s_never = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -478,7 +481,10 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
         }
         if (ct == nc) break;
         ++ncommit;
-        if (!mbar_wait(mb, (ncommit - 1) & 1, 2000000000ull)) s_abort = 1;   // all leave at the next barrier
+        // all leave at the next barrier; the test hook replaces the first panel's first wait of
+        // the chosen matrix by one that runs out
+        const bool expire = m == js.expire_m && jb == 0 && rt == 0 && ct == 0;
+        if (expire ? !flag_wait(&s_never, js.wait_ns) : !mbar_wait(mb, (ncommit - 1) & 1, js.wait_ns)) s_abort = 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ct + 2 < nc) load_b(ct + 2);                         // B buffer ct & 1 is free again
         // the seven order sums, exact integers in their units: orders 0..3 added as float
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
     if (s_abort) {                                               // recomputed in FP64
         if (t == 0 && J.redo) J.redo[m * J.redo_stride] = 1;
         asm volatile("cp.async.wait_all;" ::: "memory");
-        if (ncommit > 0) mbar_wait(mb, (ncommit - 1) & 1, 2000000000ull);   // let MMAs in flight drain
+        if (ncommit > 0) mbar_wait(mb, (ncommit - 1) & 1, kDrainNs);   // let MMAs in flight drain
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -610,7 +616,8 @@ size_t gjtc_bytes(int n_up, int n_dn, int nw)
     return b + 256;
 }
 
-cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, double kappa_max)
+cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, double kappa_max,
+                         const WaitCfg &wc)
 {
     GtJobs js;
     int nmax = 0, cmax = 0;
@@ -625,6 +632,8 @@ cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStrea
     }
     js.nj = n_jobs;
     js.jb = 0;
+    js.wait_ns = wc.limit_ns;
+    js.expire_m = wc.expire_w;
     if (cmax == 0 || n_jobs == 0) return cudaSuccess;
     if (!gjtc_fits(nmax)) return cudaErrorInvalidConfiguration;
     const size_t sm_panel = sizeof(float2) * (size_t)nmax * kGtB + sizeof(short) * (size_t)nmax;

@@ -521,6 +521,7 @@ struct TcArgs {
     TcTables tt;             // 16-bit hi/lo planes of A [n_ao][ns_pad] and scales
     float *Cg;               // [nw][3][msz] FP32 (C2..C4)
     uint32_t *wstatus;       // [nw] per-walker status (QMC_STATUS_TIMEOUT on a timed-out wait)
+    unsigned long long wait_ns;   // limit of each wait for the MMAs
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     const uint32_t tmem = tmem_slot;
     const uint32_t mbar_a = smem_u32(&mbar);
     const uint32_t idesc = umma_idesc_f16(TC_M, ncols, f16 ? 0 : 1);
-    const uint64_t kWait = 2000000000ull;   // 2 s per wait
+    const uint64_t kWait = p.wait_ns;
 
     // this walker's position as float pairs (hi + lo)
     const double *rw = p.R + ((size_t)(wvalid ? w : 0) * s.n_elec + e) * 3;
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
     if (!ok) {
         if (wvalid) atomicOr(p.wstatus + w, (uint32_t)QMC_STATUS_TIMEOUT);
         // let any MMA still in flight drain (bounded) before freeing TMEM
-        if (nks > 0) mbar_wait(mbar_a, (nks - 1) & 1, kWait);
+        if (nks > 0) mbar_wait(mbar_a, (nks - 1) & 1, kDrainNs);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
@@ -867,13 +868,14 @@ size_t tc_smem_bytes(const SysDev &s, int mw)
 }
 
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
-                               const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st)
+                               const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st, const WaitCfg &wc)
 {
     if (nw == 0) return cudaSuccess;
     TcArgs a;
     a.s = s; a.R = R; a.masks = masks; a.mw = mw; a.nw = nw;
     a.tt = tt;
     a.Cg = Cg; a.wstatus = wstatus;
+    a.wait_ns = wc.limit_ns;
     const size_t sm = tc_smem_bytes(s, mw);
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;   // system too large for one tile
     cudaError_t e = cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

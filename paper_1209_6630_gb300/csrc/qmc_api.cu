@@ -1,12 +1,16 @@
 // Host side of libqmcgb: system loading, workspace planning and the C ABI
 // entry points declared in include/qmcgb.h.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "qmc_internal.cuh"
@@ -30,6 +34,55 @@ static int invalid(const std::string &msg)
 }
 
 static int ncart_h(int L) { return (L + 1) * (L + 2) / 2; }
+
+// CRC-32 of ISO 3309 / ITU-T V.42 (reflected polynomial 0xEDB88320), the key
+// the paper attaches to a simulation's critical data (Sec. V.C).  crc32_update
+// advances the register over `n` bytes (table built from the polynomial on
+// first use); a key is crc32_update(0xFFFFFFFF, ...) ^ 0xFFFFFFFF.
+static uint32_t crc32_update(uint32_t reg, const void *data, size_t n)
+{
+    static uint32_t table[256];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1u) ? (0xEDB88320u ^ (c >> 1)) : (c >> 1);
+            table[i] = c;
+        }
+    });
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) reg = table[(reg ^ p[i]) & 0xFFu] ^ (reg >> 8);
+    return reg;
+}
+
+// Register after the basis part of a description (Z .. ao_scale).
+static uint32_t desc_crc_prefix(const qmc_system_desc *d)
+{
+    uint32_t r = 0xFFFFFFFFu;
+    r = crc32_update(r, d->Z, sizeof(double) * (size_t)d->n_atom);
+    r = crc32_update(r, d->Q, sizeof(double) * 3 * (size_t)d->n_atom);
+    r = crc32_update(r, d->shell_atom, sizeof(int32_t) * (size_t)d->n_shell);
+    r = crc32_update(r, d->shell_L, sizeof(int32_t) * (size_t)d->n_shell);
+    r = crc32_update(r, d->shell_nprim, sizeof(int32_t) * (size_t)d->n_shell);
+    r = crc32_update(r, d->shell_pstart, sizeof(int32_t) * (size_t)d->n_shell);
+    r = crc32_update(r, d->prim_gamma, sizeof(double) * (size_t)d->n_prim);
+    r = crc32_update(r, d->prim_coef, sizeof(double) * (size_t)d->n_prim);
+    r = crc32_update(r, d->ao_shell, sizeof(int32_t) * (size_t)d->n_ao);
+    r = crc32_update(r, d->ao_pow, sizeof(int32_t) * 3 * (size_t)d->n_ao);
+    r = crc32_update(r, d->ao_scale, sizeof(double) * (size_t)d->n_ao);
+    return r;
+}
+
+// Key from the prefix register, the MO coefficients and eps.
+static uint32_t desc_crc_finish(uint32_t r, int nao, int nu, int nd, int a_dtype, const void *A_up, const void *A_dn,
+                                double eps)
+{
+    const size_t es = a_dtype == QMC_DTYPE_F64 ? 8 : 4;
+    if (nu) r = crc32_update(r, A_up, es * (size_t)nao * nu);
+    if (nd) r = crc32_update(r, A_dn, es * (size_t)nao * nd);
+    r = crc32_update(r, &eps, sizeof(double));
+    return r ^ 0xFFFFFFFFu;
+}
 
 // Radial part of shell sh at squared distance x: sum_p c_p exp(-gamma_p x),
 // summed in primitive order (the same operations on every call).
@@ -240,6 +293,15 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     if (!d->Z || !d->Q || !d->shell_atom || !d->shell_L || !d->shell_nprim || !d->shell_pstart || !d->prim_gamma ||
         !d->prim_coef || !d->ao_shell || !d->ao_pow || !d->ao_scale || (d->n_up && !d->A_up) || (d->n_dn && !d->A_dn))
         return invalid("qmc_system_load: null array");
+    // Sec. V.C: the CRC-32 key checks that the critical data arrived intact
+    const uint32_t crc_pre = desc_crc_prefix(d);
+    const uint32_t crc = desc_crc_finish(crc_pre, d->n_ao, d->n_up, d->n_dn, d->a_dtype, d->A_up, d->A_dn, d->eps);
+    if (crc != d->crc32) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "qmc_system_load: CRC-32 of the description is 0x%08x, desc->crc32 is 0x%08x",
+                 crc, d->crc32);
+        return invalid(msg);
+    }
 
     const int na = d->n_atom, nsh = d->n_shell, nao = d->n_ao, nu = d->n_up, nd = d->n_dn;
     std::vector<int> atom_sh0(na + 1, 0), sh_ao0(nsh, -1);
@@ -280,6 +342,11 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
 
     qmc_system *sys = new qmc_system();
     sys->device = device;
+    sys->crc_prefix = crc_pre;
+    sys->crc = crc;
+    sys->eps = d->eps;
+    sys->tiles.wait_s = 2.0;
+    sys->tiles.expire_walker = -1;
     sys->tiles.gj_panel = (d->n_up > 640 || d->n_dn > 640) ? 8 : 16;
     sys->tiles.c15_walkers = 4;
     // the tensor-core panel updates win from ~500 electrons per spin on (measured at 434 / 528 / 866)
@@ -454,6 +521,14 @@ extern "C" int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up,
     if (e != cudaSuccess) return cuda_fail(e, "qmc_system_set_mo");
     sys->a_dtype = a_dtype;
     point_mo(sys, static_cast<char *>(sys->mo_dev), mo);
+    sys->crc = desc_crc_finish(sys->crc_prefix, sys->d.n_ao, sys->d.n_up, sys->d.n_dn, a_dtype, A_up, A_dn, sys->eps);
+    return QMC_OK;
+}
+
+extern "C" int qmc_system_crc32(const qmc_system *sys, uint32_t *crc)
+{
+    if (!sys || !crc) return invalid("qmc_system_crc32: null argument");
+    *crc = sys->crc;
     return QMC_OK;
 }
 
@@ -476,6 +551,9 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
     if (tiles->bw_walkers != 2 && tiles->bw_walkers != 4 && tiles->bw_walkers != 8 && tiles->bw_walkers != 16 &&
         tiles->bw_walkers != 32)
         return invalid("qmc_system_set_tiles: bw_walkers must be 2, 4, 8, 16 or 32");
+    if (!(tiles->wait_s >= 1e-6 && tiles->wait_s <= 60.0))
+        return invalid("qmc_system_set_tiles: wait_s must be within 1e-6 .. 60 seconds");
+    if (tiles->expire_walker < -1) return invalid("qmc_system_set_tiles: expire_walker must be >= -1");
     sys->tiles = *tiles;
     return QMC_OK;
 }
@@ -618,9 +696,19 @@ CView cview(const Plan &p, const Carve &c)
 // Steps a1-a3 for one chunk of walkers: C1 -> c.X (FP64), C2..C5 -> c.Cd
 // (FP64 in the FP64 path, FP32 in the mixed path).
 // `mark(q)` (if set) records event q after product kernel q-4 (mask, C1/C5, tensor cores).
+// The bounded-wait settings of one walker chunk starting at walker w0.
+WaitCfg wait_cfg(const qmc_system *sys, int w0, int nw)
+{
+    WaitCfg wc;
+    wc.limit_ns = (unsigned long long)(sys->tiles.wait_s * 1e9);
+    const int x = sys->tiles.expire_walker;
+    wc.expire_w = (x >= w0 && x < w0 + nw) ? x - w0 : -1;
+    return wc;
+}
+
 template <typename Mark>
 cudaError_t run_products(const qmc_system *sys, int precision, int nw, const double *Rc, const Carve &c,
-                         cudaStream_t st, Mark mark)
+                         cudaStream_t st, Mark mark, const WaitCfg &wc)
 {
     const SysDev &s = sys->d;
     if (precision == QMC_PREC_F64) return launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
@@ -642,7 +730,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     if (sys->tiles.c15_mode == QMC_C15_TENSOR) {
         // C1, C5 and C2..C4 from one producer pass per (electron, walker tile)
         e = launch_c15_tc(s, mt.ffb, mt, tt, nw, Rc, c.masks, mt.mask_words, c.X, c.L5,
-                          static_cast<float *>(c.Cd), c.st, c.c15tc, st);
+                          static_cast<float *>(c.Cd), c.st, c.c15tc, st, wc);
         if (e != cudaSuccess) return e;
         return mark(5);
     }
@@ -650,7 +738,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
                       sys->tiles.c15_walkers);
     if (e != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
-    return launch_tc_contract(s, nw, Rc, c.masks, mt.mask_words, tt, static_cast<float *>(c.Cd), c.st, st);
+    return launch_tc_contract(s, nw, Rc, c.masks, mt.mask_words, tt, static_cast<float *>(c.Cd), c.st, st, wc);
 }
 
 
@@ -724,7 +812,8 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
         if ((e = mark(0)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
-        e = run_products(sys, precision, nw, Rc, c, st, mark);
+        const WaitCfg wc = wait_cfg(sys, w0, nw);
+        e = run_products(sys, precision, nw, Rc, c, st, mark, wc);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: products launch");
         if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         GjJob jobs[2] = {GjJob(), GjJob()};
@@ -748,7 +837,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
             GjJob ffj[2] = {jobs[0], jobs[1]};
             for (int q = 0; q < nj; ++q) ffj[q].flag = nullptr;
-            if (p.tcgj) e = launch_gj_tc(ffj, nj, c.gjtc, st, sys->tiles.a4_kappa_max);
+            if (p.tcgj) e = launch_gj_tc(ffj, nj, c.gjtc, st, sys->tiles.a4_kappa_max, wc);
             else e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, sys->tiles.a4_kappa_max);
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: float-float Gauss-Jordan launch");
             int e_off[2], q = 0;
@@ -831,7 +920,7 @@ extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const doub
         const double *Rc = R + (size_t)w0 * s.n_elec * 3;
         e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: memset");
-        e = run_products(sys, precision, nw, Rc, c, st, [](int) { return cudaSuccess; });
+        e = run_products(sys, precision, nw, Rc, c, st, [](int) { return cudaSuccess; }, wait_cfg(sys, w0, nw));
         if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: products launch");
         char *o = reinterpret_cast<char *>(C + (size_t)w0 * 5 * p.msz);
         // per walker: [C1 up][C2..C5 up][C1 dn][C2..C5 dn]
@@ -943,7 +1032,7 @@ extern "C" int qmc_logpsi_backward_ex(const qmc_system *sys, int n_walk, const d
     cudaError_t e = cudaSetDevice(sys->device);
     if (e != cudaSuccess) return cuda_fail(e, "qmc_logpsi_backward_ex: cudaSetDevice");
     e = launch_backward_tc(sys->d, sys->mixed, sys->bw, sys->tiles.bw_walkers, n_walk, R, dinv, g, dA_up, dA_dn,
-                           ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+                           ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), wait_cfg(sys, 0, n_walk));
     if (e == cudaErrorMemoryAllocation) {
         set_error("qmc_logpsi_backward_ex: workspace smaller than one walker");
         return QMC_ERR_CAPACITY;
@@ -969,19 +1058,53 @@ constexpr size_t kStaticScratchBytes = (size_t)QMC_STATIC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void *g_static_ptr[kMaxDevices] = {nullptr};   // device address of the array, per device
+
+// Device address of the array per device, with the id of the CUDA context it
+// was looked up in: if the context is destroyed and recreated (a
+// cudaDeviceReset elsewhere in the process), the module is loaded again and the
+// array may move, so a changed id means looking it up again.
+struct StaticSlot {
+    unsigned long long ctx_id = 0;
+    void *ptr = nullptr;
+};
+StaticSlot g_static_slot[kMaxDevices];
+std::mutex g_static_mutex;
+
+// Id of the calling thread's current CUDA context, through driver entry points
+// the runtime hands out (so the library needs no link against libcuda).
+cudaError_t current_ctx_id(unsigned long long *id)
+{
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+        get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 }  // namespace
 
 extern "C" int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const double *R, int precision,
                                        const qmc_eval_out *out, qmc_stream_t stream)
 {
-    if (!sys) return invalid("qmc_walkers_eval_static: null system");
+    if (!sys || !out) return invalid("qmc_walkers_eval_static: null argument");
+    if (n_walk < 0) return invalid("qmc_walkers_eval_static: n_walk < 0");
+    if (n_walk == 0) return QMC_OK;
     const int dev = sys->device;
     if (dev < 0 || dev >= kMaxDevices) return invalid("qmc_walkers_eval_static: device index out of range");
     if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16)
         return invalid("qmc_walkers_eval_static: precision");
-    const Plan p = make_plan(sys, precision, out == nullptr || out->dinv == nullptr);
+    const Plan p = make_plan(sys, precision, out->dinv == nullptr);
     if (bytes_for(p, 1) > kStaticScratchBytes) {
         set_error("qmc_walkers_eval_static: one walker of this system needs " + std::to_string(bytes_for(p, 1)) +
                   " bytes of scratch, more than the library's fixed " + std::to_string(kStaticScratchBytes) +
@@ -990,15 +1113,26 @@ extern "C" int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const 
     }
     cudaError_t e = cudaSetDevice(dev);
     if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval_static: cudaSetDevice");
-    if (!g_static_ptr[dev]) {
-        // first call on this device: the host-side symbol is only a stand-in,
-        // the kernels need the array's device address
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval_static: cudaGetSymbolAddress");
-        g_static_ptr[dev] = ptr;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        // the context now current for this device (cudaSetDevice made its primary context current)
+        unsigned long long ctx_id = 0;
+        e = current_ctx_id(&ctx_id);
+        if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval_static: current context id");
+        StaticSlot &slot = g_static_slot[dev];
+        if (!slot.ptr || slot.ctx_id != ctx_id) {
+            // first call on this device (or in a new context): the host-side
+            // symbol is only a stand-in, the kernels need the array's device address
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval_static: cudaGetSymbolAddress");
+            slot.ptr = ptr;
+            slot.ctx_id = ctx_id;
+        }
+        scratch = slot.ptr;
     }
-    return eval_impl(sys, n_walk, R, precision, out, g_static_ptr[dev], kStaticScratchBytes,
+    return eval_impl(sys, n_walk, R, precision, out, scratch, kStaticScratchBytes,
                      reinterpret_cast<cudaStream_t>(stream), nullptr);
 }
 

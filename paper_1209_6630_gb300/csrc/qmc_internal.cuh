@@ -16,6 +16,17 @@ constexpr int kMaxPrim = 16;      // primitives per shell
 constexpr int kGjPanel = 16;      // Gauss-Jordan panel width
 constexpr int kMaxN = 1024;       // largest Slater matrix
 
+// Bounded device waits of the tensor-core kernels.  limit_ns bounds each wait
+// for a copy or an MMA that feeds the next step; after a wait gives up, a CTA
+// waits at most kDrainNs for its own MMAs still in flight, then frees its TMEM.
+// expire_w >= 0 is a test hook: the CTAs that work on that walker (index within
+// the launch) wait on a flag that nothing sets instead, so their wait runs out.
+constexpr unsigned long long kDrainNs = 2000000000ull;
+struct WaitCfg {
+    unsigned long long limit_ns = 2000000000ull;
+    int expire_w = -1;
+};
+
 // Device view of a system, passed by value to kernels.
 struct SysDev {
     int n_atom, n_shell, n_ao, n_up, n_dn, n_elec;
@@ -140,9 +151,9 @@ bool c15tc_fits(const SysDev &s, int mw);
 size_t c15tc_bytes(const SysDev &s, int nw);
 cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, const TcTables &tt, int nw,
                           const double *R, const uint32_t *masks, int mw, double *X, double *L5, float *Cg,
-                          uint32_t *wstatus, void *scratch, cudaStream_t st);
+                          uint32_t *wstatus, void *scratch, cudaStream_t st, const WaitCfg &wc);
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
-                               const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st);
+                               const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st, const WaitCfg &wc);
 cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
                          cudaStream_t st);
 // AO blocks of the tensor-core adjoint: runs of consecutive whole atoms with at
@@ -157,11 +168,12 @@ size_t bwtc_bytes(const SysDev &s, int mw, int nw, int wb);
 cudaError_t launch_backward_tc(const SysDev &s, const MixedTables &mt, const BwBlocks &bb, int wb, int nw,
                                const double *R,
                                const double *dinv, const double *g, double *dA_up, double *dA_dn, void *ws,
-                               size_t ws_bytes, cudaStream_t st);
+                               size_t ws_bytes, cudaStream_t st, const WaitCfg &wc);
 // a4 of the mixed path with the panel updates on the tensor cores
 bool gjtc_fits(int nmax);
 size_t gjtc_bytes(int n_up, int n_dn, int nw);
-cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, double kappa_max);
+cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, double kappa_max,
+                         const WaitCfg &wc);
 cudaError_t launch_backward_f64(const SysDev &s, int nw, const double *R, const double *dinv,
                                 const double *g, double *dA_up, double *dA_dn, cudaStream_t st,
                                 int max_ao_per_atom);
@@ -180,4 +192,7 @@ struct qmc_system {
     void *mo_dev = nullptr;           // device tables derived from the MO coefficients
     size_t mo_bytes = 0;
     int a_dtype = 0;
+    uint32_t crc_prefix = 0;          // CRC-32 register after the basis arrays (before A_up)
+    uint32_t crc = 0;                 // CRC-32 key of the critical data
+    double eps = 0.0;
 };

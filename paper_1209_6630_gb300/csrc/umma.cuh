@@ -87,6 +87,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64
     }
 }
 
+// Bounded wait on a flag that nothing in the kernel sets (the test hook that
+// makes a CTA's wait run out, WaitCfg::expire_w); returns false after limit_ns.
+__device__ __forceinline__ bool flag_wait(const volatile int *f, uint64_t limit_ns)
+{
+    const uint64_t t0 = globaltimer();
+    while (!*f)
+        if (globaltimer() - t0 > limit_ns) return false;
+    return true;
+}
+
 // 16-byte cp.async global -> shared (L2 only); valid = false zero-fills the 16 bytes
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, bool valid)
 {

@@ -74,3 +74,43 @@ def test_binding_constants_match_header_enums():
     assert (L.QMC_OK, L.QMC_ERR_INVALID, L.QMC_ERR_CUDA, L.QMC_ERR_TIMEOUT, L.QMC_ERR_CAPACITY, L.QMC_ERR_NOMEM) == (
         e["QMC_OK"], e["QMC_ERR_INVALID"], e["QMC_ERR_CUDA"], e["QMC_ERR_TIMEOUT"], e["QMC_ERR_CAPACITY"],
         e["QMC_ERR_NOMEM"])
+
+
+def test_crc32_key_checked_at_load():
+    """Sec. V.C (error checking): the CRC-32 key of the critical data.  The
+    binding computes it with zlib; the library recomputes it with its own
+    table-driven CRC before any device call, so a corrupted byte is caught on
+    the host (QMC_ERR_INVALID) and an intact description passes the check
+    (then QMC_OK on a GPU, QMC_ERR_CUDA without one)."""
+    import ctypes as C
+    import zlib
+
+    import numpy as np
+
+    from paper_1209_6630_gb300._lib import lib
+    from paper_1209_6630_gb300.api import desc_crc32, system_desc
+    from synth import tiny_system
+
+    L = lib()
+    s = tiny_system("mini_chain")
+    d, keep, _ = system_desc(s)
+    # the key is zlib's CRC-32 of the arrays' bytes in declaration order, then eps
+    blob = b"".join(a.tobytes() for a in keep) + np.array([s.eps]).tobytes()
+    assert d.crc32 == zlib.crc32(blob) & 0xFFFFFFFF
+    h = C.c_void_p()
+    rc = L.qmc_system_load(C.byref(d), 0, C.byref(h))
+    assert rc in (0, -2), L.qmc_last_error()         # passed the CRC check
+    if rc == 0:
+        L.qmc_system_free(h)
+    # one flipped bit in an MO coefficient: rejected on the host, nothing loaded
+    keep[11].view(np.uint8)[5] ^= 0x10
+    rc = L.qmc_system_load(C.byref(d), 0, C.byref(h))
+    assert rc == -1
+    msg = L.qmc_last_error().decode()
+    assert "CRC-32" in msg
+    got = int(msg.split("description is ")[1].split(",")[0], 16)
+    assert got == desc_crc32(keep, d.eps) != d.crc32      # the library's CRC = zlib's on the corrupted bytes
+    # a wrong key with intact data is rejected the same way
+    keep[11].view(np.uint8)[5] ^= 0x10
+    d.crc32 ^= 1
+    assert L.qmc_system_load(C.byref(d), 0, C.byref(h)) == -1

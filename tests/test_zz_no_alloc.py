@@ -6,7 +6,8 @@ is a fixed array inside the library instead of a caller workspace.
 
 Checked through the C ABI against qmc_walkers_eval with a caller workspace,
 on two calls in a row (the array keeps the previous call's contents), with
-batches that need more than one pass through the array: the FP64 path to
+batches that need several passes through the array (checked against the
+workspace size): the FP64 path to
 1e-10 relative; the mixed path within its parity tolerances (log|Psi| 1e-6,
 E_L 1e-5 relative, drift 1e-4 normwise), because its tensor-core products
 group walkers into tiles by pass and their last accumulator rounds at ~2^-45
@@ -38,8 +39,11 @@ def test_static_scratch_matches_caller_workspace_twice(precision):
     from synth import config_system, make_walkers
     s = config_system("158e")
     q = QmcSystem(s, 0)
+    W = 400
+    # several passes through the fixed array in both precisions: the batch needs more than
+    # twice its size of scratch
+    assert q.workspace_size(W, precision) > 2 * (64 << 20), q.workspace_size(W, precision)
     for call, first in enumerate((5000, 6000)):            # two calls in a row, different walkers
-        W = 150                                            # more walkers than fit the array at once
         R = torch.from_numpy(make_walkers(s, W, first=first)).cuda()
         got = _eval_static(q, R, precision, want_dinv=(call == 1))
         ref = q.eval(R, precision=precision, want_dinv=(call == 1))
