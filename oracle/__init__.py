@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qmc_oracle.c")
+_SRC_MC = os.path.join(_HERE, "qmc_oracle_mc.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -44,10 +45,11 @@ class _OSys(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (idempotent)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_MC))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11",
+               "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_MC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -71,6 +73,14 @@ def lib():
             L.oracle_screen_points.argtypes = [vp, C.c_int, _d, C.c_int, _i, _i]
             L.oracle_vnn.argtypes = [vp]
             L.oracle_vnn.restype = C.c_double
+            u64 = C.c_uint64
+            pu64 = C.POINTER(u64)
+            L.oracle_philox4x64.argtypes = [pu64, pu64, pu64]
+            L.oracle_move_normals.argtypes = [C.c_int, C.c_int, C.c_int, u64, u64, _d]
+            L.oracle_dmc_move.argtypes = [C.c_int, C.c_int, _d, _d, C.c_double, u64, u64, _d]
+            L.oracle_dmc_weight.argtypes = [C.c_int, _d, _d, C.POINTER(C.c_uint), _d, _d, C.POINTER(C.c_uint),
+                                            C.c_double, C.c_double, _d, C.POINTER(C.c_uint)]
+            L.oracle_srmc.argtypes = [C.c_int, _d, u64, u64, _i, _d]
             _lib = L
     return _lib
 
@@ -203,3 +213,86 @@ def lu_inverse(M):
     inv = np.zeros((n, n))
     rc = lib().oracle_lu_inverse(n, _p(M), _p(la), _p(sg), _p(inv))
     return float(la[0]), float(sg[0]), (inv if rc == 0 else None)
+
+
+# --- the Monte Carlo step around the evaluation (qmc_oracle_mc.c) -----------
+def philox4x64(ctr, key):
+    """One Philox4x64-10 block: four uint64 outputs of counter ctr[4], key key[2]."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, np.uint64)
+    pu = C.POINTER(C.c_uint64)
+    lib().oracle_philox4x64(c.ctypes.data_as(pu), k.ctypes.data_as(pu), out.ctypes.data_as(pu))
+    return out
+
+
+def move_normals(W, n_comp, seed, step, w0=0):
+    """The move's Gaussian noise eta [W, n_comp] (Box-Muller on Philox)."""
+    eta = np.zeros((W, n_comp))
+    lib().oracle_move_normals(W, w0, n_comp, seed, step, _p(eta))
+    return eta
+
+
+def dmc_move(R, drift, tau, seed, step):
+    """Eq. (1): R' = R + tau b + sqrt(tau) eta.  R, drift [W, N, 3]."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    drift = np.ascontiguousarray(drift, dtype=np.float64)
+    out = np.zeros_like(R)
+    lib().oracle_dmc_move(R.shape[0], R.shape[1], _p(R), _p(drift), tau, seed, step, _p(out))
+    return out
+
+
+def dmc_weight(e_old, sign_old, status_old, e_new, sign_new, status_new, tau, e_trial):
+    """Eq. (3) with the fixed-node rule: (weight [W], accept [W])."""
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    u = lambda a: np.ascontiguousarray(a, dtype=np.uint32)
+    e_old, sign_old, e_new, sign_new = f(e_old), f(sign_old), f(e_new), f(sign_new)
+    status_old, status_new = u(status_old), u(status_new)
+    W = e_old.shape[0]
+    wt = np.zeros(W)
+    acc = np.zeros(W, np.uint32)
+    pu = C.POINTER(C.c_uint)
+    lib().oracle_dmc_weight(W, _p(e_old), _p(sign_old), status_old.ctypes.data_as(pu), _p(e_new), _p(sign_new),
+                            status_new.ctypes.data_as(pu), tau, e_trial, _p(wt), acc.ctypes.data_as(pu))
+    return wt, acc
+
+
+def srmc(weight, seed, step):
+    """Sec. II.B reconfiguration: (idx [W] int32, sum of weights, alive count, all_zero)."""
+    w = np.ascontiguousarray(weight, dtype=np.float64)
+    W = w.shape[0]
+    idx = np.zeros(W, np.int32)
+    ws = np.zeros(2)
+    rc = lib().oracle_srmc(W, _p(w), seed, step, _p(idx, _i), _p(ws))
+    if rc < 0:
+        raise MemoryError("oracle_srmc")
+    return idx, float(ws[0]), int(ws[1]), rc == 1
+
+
+def dmc_step(oracle, state, tau, e_trial, seed, step, nthreads=0):
+    """One fixed-node DMC step with constant population (Eqs. 1-4, Sec. II.B),
+    in the paper's order: move every walker (Eq. 1), evaluate the proposed
+    positions (drift Eq. 2, E_L Eq. 4), keep or reject each move (fixed node),
+    weigh it (Eq. 3), then draw the new population (reconfiguration).
+    state: dict R [W,N,3], drift, e_loc, logpsi, sign, status of the current
+    walkers.  Returns (new state, info) with info = weights, accept, idx,
+    sum_w, sum_w_eloc (the weighted local energy of the generation, before the
+    draw), alive."""
+    R_new = dmc_move(state["R"], state["drift"], tau, seed, step)
+    ev = oracle.eval(R_new, nthreads=nthreads)
+    wt, acc = dmc_weight(state["e_loc"], state["sign"], state["status"], ev["e_loc"], ev["sign"], ev["status"],
+                         tau, e_trial)
+    a = acc.astype(bool)
+    sel = {"R": np.where(a[:, None, None], R_new, state["R"]),
+           "drift": np.where(a[:, None, None], ev["drift"], state["drift"]),
+           "e_loc": np.where(a, ev["e_loc"], state["e_loc"]),
+           "logpsi": np.where(a, ev["logpsi"], state["logpsi"]),
+           "sign": np.where(a, ev["sign"], state["sign"]),
+           "status": np.where(a, ev["status"], state["status"]).astype(np.uint32)}
+    idx, sw, alive, _ = srmc(wt, seed, step)
+    live = np.isfinite(wt) & (wt > 0.0)
+    terms = np.where(live, wt * np.where(live, sel["e_loc"], 0.0), 0.0)
+    swe = float(np.cumsum(terms)[-1]) if terms.size else 0.0      # summed in walker order
+    new = {k: v[idx].copy() for k, v in sel.items()}
+    return new, {"weight": wt, "accept": acc, "idx": idx, "sum_w": sw, "sum_w_eloc": swe, "alive": alive,
+                 "R_proposed": R_new}
