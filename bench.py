@@ -84,6 +84,7 @@ def parse():
     p.add_argument("--adjoint-walkers", type=int, default=512, help="walkers of the adjoint's 1731e workload")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep default tiles (no autotuner)")
+    p.add_argument("--no-dmc", action="store_true", help="skip the full DMC step timing")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the 1731-electron forward comparison and the mixed batch")
     return p.parse_args()
@@ -304,6 +305,42 @@ def config4_forward(a, flush, e0, e1):
                                       "p99_abs_logpsi_err": float(torch.quantile(dlp, 0.99).item()),
                                       "max_rel_eloc_err": float(del_.max().item()),
                                       "status_mismatch": int((om["status"] != of["status"]).sum().item())}}
+
+
+def dmc_bench(q, R, prec, flush, e0, e1, t_eval_ms):
+    """One fixed-node DMC step with constant population (qmc_dmc_step: move
+    Eq. 1, evaluation, weight Eq. 3, reconfiguration Sec. II.B, copy of the
+    drawn walkers) on the same batch, timed like the evaluation; the MC
+    kernels' share is the difference to the evaluation alone."""
+    import torch
+    W = int(R.shape[0])
+    a = q.init_state(R, precision=prec)
+    b = q.walker_state(W)
+    e_t = float(a["e_loc"].mean().item())
+    ws = torch.empty(q.dmc_workspace_size(W, prec), dtype=torch.uint8, device=R.device)
+    stats = torch.zeros(4, dtype=torch.float64, device=R.device)
+    tau = 0.005
+    for n in range(2):
+        q.dmc_step(a, b, tau, e_t, 17, n, precision=prec, stats=stats, ws=ws)
+        a, b = b, a
+    torch.cuda.synchronize()
+    ts = []
+    for n in range(2, 5):
+        flush.zero_()
+        e0.record()
+        q.dmc_step(a, b, tau, e_t, 17, n, precision=prec, stats=stats, ws=ws)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        a, b = b, a
+    t = sum(ts) / len(ts)
+    sv = stats.cpu().numpy()
+    res = {"walker_steps_per_s": W / (t / 1e3), "ms_per_step": t, "tau": tau,
+           "mc_kernels_ms": t - t_eval_ms, "accepted": int(sv[3]), "walkers_alive": int(sv[1]),
+           "what": "move (Eq. 1) + evaluation + fixed-node weight (Eq. 3) + SRMC draw (Sec. II.B) + copy"}
+    del a, b, ws
+    torch.cuda.empty_cache()
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -620,6 +657,9 @@ def main():
     line["e2e"] = {"value": v_e2e, "unit": "walker-steps/s",
                    "h2d_bytes_per_step": int(R_pin.numel() * 8),
                    "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host_out.values()))}
+
+    if not a.no_dmc:
+        line["dmc_step"] = dmc_bench(q, R, prec, flush, e0, e1, t_step)
 
     # the plain FP64 GPU path on the same batch (the metric's comparison)
     if prec != "f64" and not a.no_compare:

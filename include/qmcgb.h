@@ -443,6 +443,119 @@ int qmc_slater_matrices(const qmc_system *sys, int n_walk, const double *R, int 
 int qmc_det_inverse(int batch, int n, double *X, double *Dinv, double *logabs, double *sign,
                     uint32_t *singular, qmc_stream_t stream);
 
+/*
+ * ---------------------------------------------------------------------------
+ * The Monte Carlo step around the evaluation (Sec. II.A and II.B): fixed-node
+ * diffusion Monte Carlo with a constant number of walkers.
+ *
+ * Random numbers come from Philox4x64-10 (Salmon, Moraes, Dror and Shaw,
+ * SC'11), a counter-based generator, so a walker's numbers depend only on
+ * (seed, step, walker, component), never on the launch:
+ *   move  key (seed, 0), counter (j, walker, step, 0): block j gives the
+ *         normals of components 4j..4j+3 of the walker's 3N (component 3e + c
+ *         is coordinate c of electron e) through two Box-Muller pairs,
+ *         u1 = ((x0 >> 11) + 1) 2^-53, u2 = (x1 >> 11) 2^-53,
+ *         (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2), then (x2, x3);
+ *   draws key (seed, 1), counter (j >> 2, step, 0, 0): output j & 3 is the
+ *         64-bit uniform integer of draw j of the reconfiguration.
+ * ---------------------------------------------------------------------------
+ */
+
+/* The state of W walkers, device memory: positions and what the evaluation
+ * returned for them. */
+typedef struct {
+    double *R;         /* [W][N][3] */
+    double *drift;     /* [W][N][3] grad Psi / Psi, Eq. (2) */
+    double *e_loc;     /* [W] E_L, Eq. (4) */
+    double *logpsi;    /* [W] */
+    double *sign;      /* [W] */
+    uint32_t *status;  /* [W] QMC_STATUS_* bits */
+} qmc_walker_state;
+
+/*
+ * qmc_dmc_move -- Eq. (1): R_new = R + tau b(R) + sqrt(tau) eta for W walkers
+ * of N electrons, eta the Philox/Box-Muller normals of the "move" stream.
+ * Each component is rounded as written, (R + tau b) + sqrt(tau) eta, without
+ * fused multiply-adds.  R, drift, R_new device [W][N][3] f64 (R_new may not
+ * alias R).  step_ptr: NULL, or a device uint64 read in place of `step` (so a
+ * captured CUDA graph can advance it, see qmc_dmc_step).
+ */
+int qmc_dmc_move(int n_walk, int n_elec, const double *R, const double *drift, double tau, uint64_t seed,
+                 uint64_t step, const uint64_t *step_ptr, double *R_new, qmc_stream_t stream);
+
+/*
+ * qmc_dmc_weight -- Eq. (3) with the fixed-node rule (Sec. II.A: the nodes
+ * of Psi_T are infinitely repulsive barriers).  accept[w] = 1 iff the old
+ * walker is valid (status 0, sign != 0), the proposed one is valid and Psi_T
+ * kept its sign; weight[w] = exp(-(((E' - E_T) + (E_old - E_T)) * (tau / 2)))
+ * with E' = e_new[w] if accepted, else e_old[w]; an invalid old walker gets
+ * weight 0.  All arrays device [W]; e_trial_ptr: NULL or a device double read
+ * in place of e_trial.
+ */
+int qmc_dmc_weight(int n_walk, const double *e_old, const double *sign_old, const uint32_t *status_old,
+                   const double *e_new, const double *sign_new, const uint32_t *status_new, double tau,
+                   double e_trial, const double *e_trial_ptr, double *weight, uint32_t *accept,
+                   qmc_stream_t stream);
+
+/*
+ * qmc_srmc_reconfigure -- Sec. II.B: draw M = W walkers among the W with
+ * probabilities p_k = w_k / sum_i w_i, in exact integer arithmetic:
+ * q_k = floor(2^40 w_k / max_i w_i) (a weight that is not finite or not
+ * positive counts 0), C_k = q_0 + ... + q_k (64-bit, exact), draw j takes the
+ * first k with C_k > floor(U_j C_{W-1} / 2^64), U_j the 64-bit integer of the
+ * "draws" stream.  The indices are thus a function of the weights, seed and
+ * step alone.  If every weight is 0 the population is kept (idx[j] = j).
+ *   weight device [W] f64; idx device [W] i32 (new walker j copies old walker
+ *   idx[j]); stats NULL or device [4] f64: sum of the counted weights, their
+ *   number, 0, 0; ws device scratch of at least 8 W bytes.
+ * One CTA: W up to 2^24.
+ */
+int qmc_srmc_reconfigure(int n_walk, const double *weight, uint64_t seed, uint64_t step, const uint64_t *step_ptr,
+                         int32_t *idx, double *stats, void *ws, size_t ws_bytes, qmc_stream_t stream);
+
+/* Parameters of one DMC step.  step_ptr / e_trial_ptr (device, optional)
+ * replace step / e_trial when not NULL; qmc_dmc_step then adds 1 to *step_ptr
+ * in its last kernel, so a CUDA graph captured from one step replays the
+ * following ones. */
+typedef struct {
+    double tau;
+    double e_trial;
+    uint64_t seed;
+    uint64_t step;
+    int precision;              /* of the evaluation: QMC_PREC_* */
+    uint64_t *step_ptr;
+    const double *e_trial_ptr;
+} qmc_dmc_params;
+
+/* Device scratch (bytes) of qmc_dmc_step for W walkers: the evaluation's
+ * workspace (qmc_workspace_size) plus the proposed walkers, weights, accept
+ * flags, draws and the reconfiguration's sums. */
+int qmc_dmc_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes);
+
+/*
+ * qmc_dmc_step -- one fixed-node DMC step with constant population, in the
+ * paper's order: move every walker (Eq. 1), evaluate the proposed positions
+ * (a1..a6: drift Eq. 2, E_L Eq. 4), keep or reject each move and weigh it
+ * (Eq. 3, qmc_dmc_weight), draw the new population (Sec. II.B,
+ * qmc_srmc_reconfigure), and copy the drawn walkers' state to `out`.
+ *   in   the current walkers (as evaluated: drift, e_loc, logpsi, sign, status
+ *        of their positions); out: the next generation, same layout, must not
+ *        alias `in`.
+ *   stats NULL or device [4] f64: sum_k w_k, the number of walkers with a
+ *        positive weight, sum_k w_k E_L,k (E_L of the kept state, before the
+ *        draw: the numerator of the generation's weighted average), the number
+ *        of accepted moves.  The paper's global weight of a generation is
+ *        stats[0] / W; its product over the preceding generations weighs the
+ *        averages (left to the caller).
+ * Asynchronous on `stream`; nothing is allocated; capturable in a CUDA graph
+ * with step_ptr set (the first call of a system should come before the
+ * capture, as for qmc_walkers_eval).
+ * Errors: QMC_ERR_INVALID (bad arguments, tau <= 0), QMC_ERR_CAPACITY
+ * (workspace below qmc_dmc_workspace_size), QMC_ERR_CUDA.
+ */
+int qmc_dmc_step(const qmc_system *sys, int n_walk, const qmc_walker_state *in, const qmc_walker_state *out,
+                 const qmc_dmc_params *params, double *stats, void *ws, size_t ws_bytes, qmc_stream_t stream);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char *qmc_last_error(void);
 

@@ -44,6 +44,15 @@ A4_MODE = {"fp64": 0, "float_float": 1, "tensor": 2}
 C15_MODE = {"float_float": 0, "tensor": 1}
 
 
+class WalkerState(C.Structure):
+    _fields_ = [("R", _vp), ("drift", _vp), ("e_loc", _vp), ("logpsi", _vp), ("sign", _vp), ("status", _vp)]
+
+
+class DmcParams(C.Structure):
+    _fields_ = [("tau", C.c_double), ("e_trial", C.c_double), ("seed", C.c_uint64), ("step", C.c_uint64),
+                ("precision", _i), ("step_ptr", _vp), ("e_trial_ptr", _vp)]
+
+
 class Segment(C.Structure):
     _fields_ = [("sys", _vp), ("n_walk", _i), ("R", _vp), ("out", EvalOut)]
 
@@ -93,6 +102,14 @@ def lib():
             L.qmc_shell_masks.argtypes = [_vp, _i, _vp, _vp, C.POINTER(_i), _vp]
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
+            u64 = C.c_uint64
+            L.qmc_dmc_move.argtypes = [_i, _i, _vp, _vp, C.c_double, u64, u64, _vp, _vp, _vp]
+            L.qmc_dmc_weight.argtypes = [_i, _vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp,
+                                         _vp]
+            L.qmc_srmc_reconfigure.argtypes = [_i, _vp, u64, u64, _vp, _vp, _vp, _vp, C.c_size_t, _vp]
+            L.qmc_dmc_workspace_size.argtypes = [_vp, _i, _i, C.POINTER(C.c_size_t)]
+            L.qmc_dmc_step.argtypes = [_vp, _i, C.POINTER(WalkerState), C.POINTER(WalkerState),
+                                       C.POINTER(DmcParams), _vp, _vp, C.c_size_t, _vp]
             for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo",
                          "qmc_system_crc32",
                          "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size",
@@ -100,7 +117,9 @@ def lib():
                          "qmc_workspace_size",
                          "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static",
                          "qmc_logpsi_backward", "qmc_backward_workspace_size", "qmc_logpsi_backward_ex",
-                         "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices", "qmc_det_inverse"):
+                         "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices", "qmc_det_inverse",
+                         "qmc_dmc_move", "qmc_dmc_weight", "qmc_srmc_reconfigure", "qmc_dmc_workspace_size",
+                         "qmc_dmc_step"):
                 getattr(L, name).restype = _i
             _lib = L
     return _lib
@@ -119,4 +138,5 @@ EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_sy
             "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
             "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward",
             "qmc_backward_workspace_size", "qmc_logpsi_backward_ex", "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices",
-            "qmc_det_inverse", "qmc_last_error", "qmc_version")
+            "qmc_det_inverse", "qmc_dmc_move", "qmc_dmc_weight", "qmc_srmc_reconfigure", "qmc_dmc_workspace_size",
+            "qmc_dmc_step", "qmc_last_error", "qmc_version")

@@ -11,9 +11,11 @@ import zlib
 import numpy as np
 import torch
 
-from ._lib import PREC, DTYPE_F32, DTYPE_F64, EvalOut, QmcError, Segment, SystemDesc, Tiles, check, lib
+from ._lib import (PREC, DTYPE_F32, DTYPE_F64, DmcParams, EvalOut, QmcError, Segment, SystemDesc, Tiles,
+                   WalkerState, check, lib)
 
-__all__ = ["QmcSystem", "QmcBatch", "det_inverse", "LogPsi", "QmcError"]
+__all__ = ["QmcSystem", "QmcBatch", "det_inverse", "LogPsi", "QmcError", "dmc_move", "dmc_weight",
+           "srmc_reconfigure"]
 
 
 def _stream(device):
@@ -233,6 +235,51 @@ class QmcSystem:
         dn = Cm[:, 5 * nu2:].reshape(W, 5, self.n_dn, self.n_dn)
         return up, dn
 
+    # --- the Monte Carlo step (qmc_dmc_step) --------------------------------
+    def walker_state(self, W: int):
+        """Device buffers of W walkers' state: R, drift, e_loc, logpsi, sign, status."""
+        dev, f64 = self.device, torch.float64
+        return dict(R=torch.empty(W, self.N, 3, dtype=f64, device=dev),
+                    drift=torch.empty(W, self.N, 3, dtype=f64, device=dev),
+                    e_loc=torch.empty(W, dtype=f64, device=dev), logpsi=torch.empty(W, dtype=f64, device=dev),
+                    sign=torch.empty(W, dtype=f64, device=dev), status=torch.empty(W, dtype=torch.int32, device=dev))
+
+    def init_state(self, R, precision: str = "f64"):
+        """The state of walkers at positions R (one evaluation)."""
+        W = int(R.shape[0])
+        st = self.walker_state(W)
+        st["R"].copy_(R)
+        o = self.eval(st["R"], precision=precision)
+        for k in ("drift", "e_loc", "logpsi", "sign", "status"):
+            st[k].copy_(o[k])
+        return st
+
+    def dmc_workspace_size(self, n_walk: int, precision: str = "f64") -> int:
+        b = C.c_size_t()
+        check(lib().qmc_dmc_workspace_size(self._h, n_walk, PREC[precision], C.byref(b)))
+        return int(b.value)
+
+    def dmc_step(self, state_in, state_out, tau, e_trial, seed, step, precision="f64", stats=None, ws=None,
+                 step_ptr=None, e_trial_ptr=None):
+        """One fixed-node DMC step with constant population (qmc_dmc_step):
+        state_in -> state_out (dicts of walker_state buffers).  stats: optional
+        cuda f64 [4] (sum w, walkers with w > 0, sum w E_L, accepted moves)."""
+        W = int(state_in["R"].shape[0])
+        for k, t in list(state_in.items()) + list(state_out.items()):
+            _req_cuda(t, torch.int32 if k == "status" else torch.float64, k)
+        if ws is None:
+            need = self.dmc_workspace_size(W, precision)
+            ws = self._ws.get("dmc")
+            if ws is None or ws.numel() < need:
+                ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+                self._ws["dmc"] = ws
+        si, so = _state_struct(state_in), _state_struct(state_out)
+        p = DmcParams(tau=float(tau), e_trial=float(e_trial), seed=int(seed), step=int(step),
+                      precision=PREC[precision], step_ptr=_ptr(step_ptr), e_trial_ptr=_ptr(e_trial_ptr))
+        check(lib().qmc_dmc_step(self._h, W, C.byref(si), C.byref(so), C.byref(p), _ptr(stats), _ptr(ws),
+                                 ws.numel(), _stream(self.device)))
+        return state_out
+
     def backward_workspace_size(self, n_walk: int, precision: str = "mixed") -> int:
         b = C.c_size_t()
         check(lib().qmc_backward_workspace_size(self._h, n_walk, PREC[precision], C.byref(b)))
@@ -315,6 +362,48 @@ class QmcBatch:
                 lib().qmc_graph_free(self._g)
         except Exception:
             pass
+
+
+def _state_struct(st):
+    return WalkerState(R=_ptr(st["R"]), drift=_ptr(st["drift"]), e_loc=_ptr(st["e_loc"]), logpsi=_ptr(st["logpsi"]),
+                       sign=_ptr(st["sign"]), status=_ptr(st["status"]))
+
+
+def dmc_move(R, drift, tau, seed, step, step_ptr=None):
+    """Eq. (1) on cuda f64 [W, N, 3] (qmc_dmc_move); returns R'."""
+    _req_cuda(R, torch.float64, "R")
+    _req_cuda(drift, torch.float64, "drift", tuple(R.shape))
+    Rn = torch.empty_like(R)
+    check(lib().qmc_dmc_move(int(R.shape[0]), int(R.shape[1]), _ptr(R), _ptr(drift), float(tau), int(seed), int(step),
+                             _ptr(step_ptr), _ptr(Rn), _stream(R.device)))
+    return Rn
+
+
+def dmc_weight(e_old, sign_old, status_old, e_new, sign_new, status_new, tau, e_trial):
+    """Eq. (3) with the fixed-node rule (qmc_dmc_weight): (weight, accept)."""
+    W = int(e_old.shape[0])
+    for name, t in (("e_old", e_old), ("sign_old", sign_old), ("e_new", e_new), ("sign_new", sign_new)):
+        _req_cuda(t, torch.float64, name, (W,))
+    for name, t in (("status_old", status_old), ("status_new", status_new)):
+        _req_cuda(t, torch.int32, name, (W,))
+    w = torch.empty(W, dtype=torch.float64, device=e_old.device)
+    acc = torch.empty(W, dtype=torch.int32, device=e_old.device)
+    check(lib().qmc_dmc_weight(W, _ptr(e_old), _ptr(sign_old), _ptr(status_old), _ptr(e_new), _ptr(sign_new),
+                               _ptr(status_new), float(tau), float(e_trial), None, _ptr(w), _ptr(acc),
+                               _stream(e_old.device)))
+    return w, acc
+
+
+def srmc_reconfigure(weight, seed, step):
+    """Sec. II.B draw (qmc_srmc_reconfigure): (idx int32 [W], stats f64 [4])."""
+    W = int(weight.shape[0])
+    _req_cuda(weight, torch.float64, "weight", (W,))
+    idx = torch.empty(W, dtype=torch.int32, device=weight.device)
+    stats = torch.zeros(4, dtype=torch.float64, device=weight.device)
+    ws = torch.empty(max(8 * W, 8), dtype=torch.uint8, device=weight.device)
+    check(lib().qmc_srmc_reconfigure(W, _ptr(weight), int(seed), int(step), None, _ptr(idx), _ptr(stats), _ptr(ws),
+                                     ws.numel(), _stream(weight.device)))
+    return idx, stats
 
 
 def det_inverse(X):

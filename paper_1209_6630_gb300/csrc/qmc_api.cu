@@ -1137,6 +1137,157 @@ extern "C" int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const 
 }
 
 // ---------------------------------------------------------------------------
+// The Monte Carlo step (Sec. II.A, II.B).
+namespace {
+
+constexpr int kMaxSrmcWalkers = 1 << 24;
+
+struct DmcCarve {
+    double *R, *drift, *e, *lp, *sg, *w;
+    uint32_t *st, *acc;
+    int *idx;
+    unsigned long long *C;
+    char *eval_ws;
+    size_t eval_bytes;
+};
+
+size_t dmc_own_bytes(int W, int n_elec)
+{
+    const size_t nc = (size_t)W * n_elec * 3;
+    return 2 * al(nc * 8) + 4 * al((size_t)W * 8) + 2 * al((size_t)W * 4) + al((size_t)W * 4) + al((size_t)W * 8);
+}
+
+bool dmc_carve(int W, int n_elec, void *ws, size_t ws_bytes, DmcCarve &c)
+{
+    char *b = static_cast<char *>(ws);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { char *r = b + o; o = al(o + bytes); return r; };
+    const size_t nc = (size_t)W * n_elec * 3;
+    c.R = reinterpret_cast<double *>(take(nc * 8));
+    c.drift = reinterpret_cast<double *>(take(nc * 8));
+    c.e = reinterpret_cast<double *>(take((size_t)W * 8));
+    c.lp = reinterpret_cast<double *>(take((size_t)W * 8));
+    c.sg = reinterpret_cast<double *>(take((size_t)W * 8));
+    c.w = reinterpret_cast<double *>(take((size_t)W * 8));
+    c.st = reinterpret_cast<uint32_t *>(take((size_t)W * 4));
+    c.acc = reinterpret_cast<uint32_t *>(take((size_t)W * 4));
+    c.idx = reinterpret_cast<int *>(take((size_t)W * 4));
+    c.C = reinterpret_cast<unsigned long long *>(take((size_t)W * 8));
+    if (o > ws_bytes) return false;
+    c.eval_ws = b + o;
+    c.eval_bytes = ws_bytes - o;
+    return true;
+}
+
+bool state_ok(const qmc_walker_state *s)
+{
+    return s && s->R && s->drift && s->e_loc && s->logpsi && s->sign && s->status;
+}
+
+}  // namespace
+
+extern "C" int qmc_dmc_move(int n_walk, int n_elec, const double *R, const double *drift, double tau, uint64_t seed,
+                            uint64_t step, const uint64_t *step_ptr, double *R_new, qmc_stream_t stream)
+{
+    if (n_walk < 0 || n_elec < 0) return invalid("qmc_dmc_move: negative size");
+    if (!(tau > 0.0) || !isfinite(tau)) return invalid("qmc_dmc_move: tau must be positive and finite");
+    if (n_walk == 0 || n_elec == 0) return QMC_OK;
+    if (!R || !drift || !R_new) return invalid("qmc_dmc_move: null pointer");
+    if (R_new == R) return invalid("qmc_dmc_move: R_new may not alias R");
+    cudaError_t e = launch_dmc_move(n_walk, n_elec, R, drift, tau, seed, step, step_ptr, R_new,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_dmc_move: launch");
+    return QMC_OK;
+}
+
+extern "C" int qmc_dmc_weight(int n_walk, const double *e_old, const double *sign_old, const uint32_t *status_old,
+                              const double *e_new, const double *sign_new, const uint32_t *status_new, double tau,
+                              double e_trial, const double *e_trial_ptr, double *weight, uint32_t *accept,
+                              qmc_stream_t stream)
+{
+    if (n_walk < 0) return invalid("qmc_dmc_weight: n_walk < 0");
+    if (!(tau > 0.0) || !isfinite(tau)) return invalid("qmc_dmc_weight: tau must be positive and finite");
+    if (n_walk == 0) return QMC_OK;
+    if (!e_old || !sign_old || !status_old || !e_new || !sign_new || !status_new || !weight || !accept)
+        return invalid("qmc_dmc_weight: null pointer");
+    cudaError_t e = launch_dmc_weight(n_walk, e_old, sign_old, status_old, e_new, sign_new, status_new, tau, e_trial,
+                                      e_trial_ptr, weight, accept, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_dmc_weight: launch");
+    return QMC_OK;
+}
+
+extern "C" int qmc_srmc_reconfigure(int n_walk, const double *weight, uint64_t seed, uint64_t step,
+                                    const uint64_t *step_ptr, int32_t *idx, double *stats, void *ws, size_t ws_bytes,
+                                    qmc_stream_t stream)
+{
+    if (n_walk < 0 || n_walk > kMaxSrmcWalkers) return invalid("qmc_srmc_reconfigure: need 0 <= n_walk <= 2^24");
+    if (n_walk == 0) return QMC_OK;
+    if (!weight || !idx || !ws) return invalid("qmc_srmc_reconfigure: null pointer");
+    if (ws_bytes < (size_t)n_walk * 8) {
+        set_error("qmc_srmc_reconfigure: scratch below 8 bytes per walker");
+        return QMC_ERR_CAPACITY;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 7) return invalid("qmc_srmc_reconfigure: scratch not 8-byte aligned");
+    cudaError_t e = launch_srmc(n_walk, weight, seed, step, step_ptr, static_cast<unsigned long long *>(ws), idx,
+                                stats, nullptr, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_srmc_reconfigure: launch");
+    return QMC_OK;
+}
+
+extern "C" int qmc_dmc_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes)
+{
+    if (!sys || !bytes || n_walk < 0) return invalid("qmc_dmc_workspace_size: bad argument");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_dmc_workspace_size: precision");
+    const Plan p = make_plan(sys, precision, true);
+    *bytes = dmc_own_bytes(n_walk, sys->d.n_elec) + bytes_for(p, std::min(n_walk, 65535));
+    return QMC_OK;
+}
+
+extern "C" int qmc_dmc_step(const qmc_system *sys, int n_walk, const qmc_walker_state *in,
+                            const qmc_walker_state *out, const qmc_dmc_params *prm, double *stats, void *ws,
+                            size_t ws_bytes, qmc_stream_t stream)
+{
+    if (!sys || !prm) return invalid("qmc_dmc_step: null argument");
+    if (n_walk < 0 || n_walk > kMaxSrmcWalkers) return invalid("qmc_dmc_step: need 0 <= n_walk <= 2^24");
+    if (!(prm->tau > 0.0) || !isfinite(prm->tau)) return invalid("qmc_dmc_step: tau must be positive and finite");
+    if (prm->precision < QMC_PREC_F64 || prm->precision > QMC_PREC_MIXED_BF16) return invalid("qmc_dmc_step: precision");
+    if (n_walk == 0) return QMC_OK;
+    if (!state_ok(in) || !state_ok(out) || !ws) return invalid("qmc_dmc_step: null pointer");
+    if (in->R == out->R || in->drift == out->drift || in->e_loc == out->e_loc || in->status == out->status)
+        return invalid("qmc_dmc_step: out may not alias in");
+    const SysDev &s = sys->d;
+    DmcCarve c;
+    const Plan p = make_plan(sys, prm->precision, true);
+    if (!dmc_carve(n_walk, s.n_elec, ws, ws_bytes, c) || bytes_for(p, 1) > c.eval_bytes) {
+        set_error("qmc_dmc_step: workspace smaller than the step's arrays plus one walker's evaluation");
+        return QMC_ERR_CAPACITY;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(sys->device);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_dmc_step: cudaSetDevice");
+    // Eq. (1)
+    e = launch_dmc_move(n_walk, s.n_elec, in->R, in->drift, prm->tau, prm->seed, prm->step, prm->step_ptr, c.R, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_dmc_step: move launch");
+    // a1..a6 at the proposed positions
+    qmc_eval_out eo;
+    memset(&eo, 0, sizeof eo);
+    eo.logpsi = c.lp; eo.sign = c.sg; eo.drift = c.drift; eo.e_loc = c.e; eo.status = c.st;
+    int rc = eval_impl(sys, n_walk, c.R, prm->precision, &eo, c.eval_ws, c.eval_bytes, st, nullptr);
+    if (rc) return rc;
+    // Eq. (3) with the fixed-node rule, then the reconfiguration of Sec. II.B
+    e = launch_dmc_weight(n_walk, in->e_loc, in->sign, in->status, c.e, c.sg, c.st, prm->tau, prm->e_trial,
+                          prm->e_trial_ptr, c.w, c.acc, st);
+    if (e == cudaSuccess)
+        e = launch_srmc(n_walk, c.w, prm->seed, prm->step, prm->step_ptr, c.C, c.idx, stats, c.e, in->e_loc, c.acc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_dmc_step: weight / reconfiguration launch");
+    qmc_walker_state prop;
+    prop.R = c.R; prop.drift = c.drift; prop.e_loc = c.e; prop.logpsi = c.lp; prop.sign = c.sg; prop.status = c.st;
+    e = launch_dmc_gather(n_walk, s.n_elec, c.idx, c.acc, *in, prop, *out, prm->step_ptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_dmc_step: gather launch");
+    return QMC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Mixed batch: segments of several systems, concurrent on forked streams.
 namespace {
 

@@ -178,6 +178,20 @@ cudaError_t launch_backward_f64(const SysDev &s, int nw, const double *R, const 
                                 const double *g, double *dA_up, double *dA_dn, cudaStream_t st,
                                 int max_ao_per_atom);
 
+// Monte Carlo step (k_dmc.cu)
+cudaError_t launch_dmc_move(int nw, int n_elec, const double *R, const double *drift, double tau, uint64_t seed,
+                            uint64_t step, const uint64_t *step_ptr, double *Rn, cudaStream_t st);
+cudaError_t launch_dmc_weight(int nw, const double *e_old, const double *s_old, const uint32_t *st_old,
+                              const double *e_new, const double *s_new, const uint32_t *st_new, double tau,
+                              double e_trial, const double *e_trial_ptr, double *weight, uint32_t *accept,
+                              cudaStream_t st);
+cudaError_t launch_srmc(int nw, const double *weight, uint64_t seed, uint64_t step, const uint64_t *step_ptr,
+                        unsigned long long *C, int *idx, double *stats, const double *e_new, const double *e_old,
+                        const uint32_t *accept, cudaStream_t st);
+cudaError_t launch_dmc_gather(int nw, int n_elec, const int *idx, const uint32_t *accept, const qmc_walker_state &old,
+                              const qmc_walker_state &prop, const qmc_walker_state &out, uint64_t *step_ptr,
+                              cudaStream_t st);
+
 }  // namespace qmc
 
 struct qmc_system {
