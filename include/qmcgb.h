@@ -210,19 +210,23 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      and MO tile 0 of w's walker tile; a4 (tensor mode): the
  *                      first update CTA of w's spin-up and spin-down matrices;
  *                      adjoint: the spin-up CTAs of w's block of bw_walkers.
+ *   expire_kernels     which kernels the hook applies to: bits QMC_EXPIRE_C15
+ *                      (1), QMC_EXPIRE_A4 (2), QMC_EXPIRE_ADJOINT (4).
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT (QMC_A4_TENSOR
  * from 512 electrons of one spin on, where it fits the panel kernel),
  * a4_kappa_max = 1e8 (1e7 up to 256 electrons of one spin),
  * c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
- * QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1.
+ * QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1,
+ * expire_kernels = 7.
  * qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous
  * choice.
  */
 enum { QMC_A4_FP64 = 0, QMC_A4_FLOAT_FLOAT = 1, QMC_A4_TENSOR = 2 };
 enum { QMC_C15_FLOAT_FLOAT = 0, QMC_C15_TENSOR = 1 };
+enum { QMC_EXPIRE_C15 = 1, QMC_EXPIRE_A4 = 2, QMC_EXPIRE_ADJOINT = 4 };
 typedef struct {
     int gj_panel;
     int c15_walkers;
@@ -232,6 +236,7 @@ typedef struct {
     int bw_walkers;
     double wait_s;
     int expire_walker;
+    int expire_kernels;
 } qmc_tiles;
 int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles);
 int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles);

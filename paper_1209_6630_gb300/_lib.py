@@ -37,11 +37,13 @@ class EvalOut(C.Structure):
 
 class Tiles(C.Structure):
     _fields_ = [("gj_panel", _i), ("c15_walkers", _i), ("a4_mode", _i), ("a4_kappa_max", C.c_double),
-                ("c15_mode", _i), ("bw_walkers", _i), ("wait_s", C.c_double), ("expire_walker", _i)]
+                ("c15_mode", _i), ("bw_walkers", _i), ("wait_s", C.c_double), ("expire_walker", _i),
+                ("expire_kernels", _i)]
 
 
 A4_MODE = {"fp64": 0, "float_float": 1, "tensor": 2}
 C15_MODE = {"float_float": 0, "tensor": 1}
+EXPIRE = {"c15": 1, "a4": 2, "adjoint": 4}
 
 
 class WalkerState(C.Structure):

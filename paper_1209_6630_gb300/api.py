@@ -130,10 +130,10 @@ class QmcSystem:
         return {"gj_panel": t.gj_panel, "c15_walkers": t.c15_walkers,
                 "a4_mode": {0: "fp64", 1: "float_float", 2: "tensor"}[t.a4_mode], "a4_kappa_max": t.a4_kappa_max,
                 "c15_mode": "tensor" if t.c15_mode == 1 else "float_float", "bw_walkers": t.bw_walkers,
-                "wait_s": t.wait_s, "expire_walker": t.expire_walker}
+                "wait_s": t.wait_s, "expire_walker": t.expire_walker, "expire_kernels": t.expire_kernels}
 
     def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None, c15_mode=None,
-                  bw_walkers=None, wait_s=None, expire_walker=None):
+                  bw_walkers=None, wait_s=None, expire_walker=None, expire_kernels=None):
         from ._lib import A4_MODE, C15_MODE
         cur = self.tiles()
         t = Tiles(gj_panel=gj_panel or cur["gj_panel"], c15_walkers=c15_walkers or cur["c15_walkers"],
@@ -141,7 +141,8 @@ class QmcSystem:
                   a4_kappa_max=a4_kappa_max if a4_kappa_max is not None else cur["a4_kappa_max"],
                   c15_mode=C15_MODE[c15_mode or cur["c15_mode"]], bw_walkers=bw_walkers or cur["bw_walkers"],
                   wait_s=wait_s if wait_s is not None else cur["wait_s"],
-                  expire_walker=expire_walker if expire_walker is not None else cur["expire_walker"])
+                  expire_walker=expire_walker if expire_walker is not None else cur["expire_walker"],
+                  expire_kernels=expire_kernels if expire_kernels is not None else cur["expire_kernels"])
         check(lib().qmc_system_set_tiles(self._h, C.byref(t)))
 
     def set_mo(self, A_up, A_dn):

@@ -526,7 +526,8 @@ cudaError_t launch_backward_tc(const SysDev &s, const MixedTables &mt, const BwB
         a.nw = n;
         a.g = g + c0;
         a.wait_ns = wcfg.limit_ns;
-        a.expire_w = wcfg.expire_w >= c0 && wcfg.expire_w < c0 + n ? wcfg.expire_w - c0 : -1;
+        a.expire_w = (wcfg.expire_kernels & QMC_EXPIRE_ADJOINT) && wcfg.expire_w >= c0 && wcfg.expire_w < c0 + n
+                         ? wcfg.expire_w - c0 : -1;
         const size_t work = (size_t)n * (msz8 / 8);
         const int pblocks = (int)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
         k_bw_prep<<<pblocks, 256, 0, st>>>(dinv + (size_t)c0 * msz, n, s.n_up, s.n_dn, ns8u, ns8d, msz8, sl, a.plane,

@@ -575,7 +575,7 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
     }
     a.X = X; a.L5 = L5; a.Cg = Cg; a.tt = tt; a.wstatus = wstatus;
     a.wait_ns = wc.limit_ns;
-    a.expire_tile = wc.expire_w >= 0 && wc.expire_w < nw ? wc.expire_w / TC_M : -1;
+    a.expire_tile = (wc.expire_kernels & QMC_EXPIRE_C15) && wc.expire_w >= 0 && wc.expire_w < nw ? wc.expire_w / TC_M : -1;
     const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
     const size_t sm_mma = 1024 + 2 * (size_t)kC15Slices * (kSPlaneBytes + kSBPlaneBytes) +
                           sizeof(int) * (size_t)a.kmax_steps * TC_K;

@@ -633,7 +633,7 @@ cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStrea
     js.nj = n_jobs;
     js.jb = 0;
     js.wait_ns = wc.limit_ns;
-    js.expire_m = wc.expire_w;
+    js.expire_m = (wc.expire_kernels & QMC_EXPIRE_A4) ? wc.expire_w : -1;
     if (cmax == 0 || n_jobs == 0) return cudaSuccess;
     if (!gjtc_fits(nmax)) return cudaErrorInvalidConfiguration;
     const size_t sm_panel = sizeof(float2) * (size_t)nmax * kGtB + sizeof(short) * (size_t)nmax;

@@ -347,6 +347,7 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     sys->eps = d->eps;
     sys->tiles.wait_s = 2.0;
     sys->tiles.expire_walker = -1;
+    sys->tiles.expire_kernels = QMC_EXPIRE_C15 | QMC_EXPIRE_A4 | QMC_EXPIRE_ADJOINT;
     sys->tiles.gj_panel = (d->n_up > 640 || d->n_dn > 640) ? 8 : 16;
     sys->tiles.c15_walkers = 4;
     // the tensor-core panel updates win from ~500 electrons per spin on (measured at 434 / 528 / 866)
@@ -554,6 +555,8 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
     if (!(tiles->wait_s >= 1e-6 && tiles->wait_s <= 60.0))
         return invalid("qmc_system_set_tiles: wait_s must be within 1e-6 .. 60 seconds");
     if (tiles->expire_walker < -1) return invalid("qmc_system_set_tiles: expire_walker must be >= -1");
+    if (tiles->expire_kernels < 0 || tiles->expire_kernels > 7)
+        return invalid("qmc_system_set_tiles: expire_kernels must be a combination of QMC_EXPIRE_* bits");
     sys->tiles = *tiles;
     return QMC_OK;
 }
@@ -703,6 +706,7 @@ WaitCfg wait_cfg(const qmc_system *sys, int w0, int nw)
     wc.limit_ns = (unsigned long long)(sys->tiles.wait_s * 1e9);
     const int x = sys->tiles.expire_walker;
     wc.expire_w = (x >= w0 && x < w0 + nw) ? x - w0 : -1;
+    wc.expire_kernels = sys->tiles.expire_kernels;
     return wc;
 }
 

@@ -25,6 +25,7 @@ constexpr unsigned long long kDrainNs = 2000000000ull;
 struct WaitCfg {
     unsigned long long limit_ns = 2000000000ull;
     int expire_w = -1;
+    int expire_kernels = 0;     // QMC_EXPIRE_* bits: the kernels the hook applies to
 };
 
 // Device view of a system, passed by value to kernels.

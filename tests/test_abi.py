@@ -68,6 +68,7 @@ def test_binding_constants_match_header_enums():
     assert {k: e["QMC_PREC_" + k.upper()] for k in L.PREC} == L.PREC
     assert {k: e["QMC_A4_" + k.upper()] for k in L.A4_MODE} == L.A4_MODE
     assert {k: e["QMC_C15_" + k.upper()] for k in L.C15_MODE} == L.C15_MODE
+    assert {k: e["QMC_EXPIRE_" + k.upper()] for k in L.EXPIRE} == L.EXPIRE
     assert (L.STATUS_SINGULAR_UP, L.STATUS_SINGULAR_DN, L.STATUS_NONFINITE, L.STATUS_TIMEOUT) == (
         e["QMC_STATUS_SINGULAR_UP"], e["QMC_STATUS_SINGULAR_DN"], e["QMC_STATUS_NONFINITE"], e["QMC_STATUS_TIMEOUT"])
     assert (L.DTYPE_F64, L.DTYPE_F32) == (e["QMC_DTYPE_F64"], e["QMC_DTYPE_F32"])

@@ -33,7 +33,7 @@ def sysq():
 
 
 def _reset(q):
-    q.set_tiles(wait_s=2.0, expire_walker=-1, a4_mode="float_float", a4_kappa_max=1e7)
+    q.set_tiles(wait_s=2.0, expire_walker=-1, expire_kernels=7, a4_mode="float_float", a4_kappa_max=1e7)
 
 
 def test_c15_expired_wait_marks_its_tile_only(sysq):
@@ -43,7 +43,7 @@ def test_c15_expired_wait_marks_its_tile_only(sysq):
     Rd = torch.from_numpy(make_walkers(s, W, first=4100)).to(dev)
     try:
         ref = q.eval(Rd, precision="mixed")
-        q.set_tiles(wait_s=0.01, expire_walker=150)  # a walker of tile 1
+        q.set_tiles(wait_s=0.01, expire_walker=150, expire_kernels=1)  # a walker of tile 1, C1..C5
         got = q.eval(Rd, precision="mixed")
         torch.cuda.synchronize()
     finally:
@@ -68,7 +68,7 @@ def test_a4_tensor_expired_wait_recomputed_in_fp64(sysq):
     try:
         q.set_tiles(a4_mode="tensor", a4_kappa_max=1e30)   # no matrix flagged by its condition
         ref = q.eval(Rd, precision="mixed", want_dinv=True)
-        q.set_tiles(wait_s=0.01, expire_walker=7)
+        q.set_tiles(wait_s=0.01, expire_walker=7, expire_kernels=2)
         got = q.eval(Rd, precision="mixed", want_dinv=True)
         torch.cuda.synchronize()
     finally:
@@ -96,7 +96,7 @@ def test_adjoint_expired_wait_leaves_nan_in_its_rows_only(sysq):
     q.set_tiles(bw_walkers=8)
     try:
         ref_up, ref_dn = q.backward(Rd, o["dinv"], g, precision="mixed")
-        q.set_tiles(wait_s=0.01, expire_walker=9)      # the spin-up CTAs of walkers 8..15
+        q.set_tiles(wait_s=0.01, expire_walker=9, expire_kernels=4)   # spin-up CTAs of walkers 8..15
         got_up, got_dn = q.backward(Rd, o["dinv"], g, precision="mixed")
         torch.cuda.synchronize()
     finally:
