@@ -185,7 +185,17 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      pipes; QMC_C15_TENSOR = tcgen05 BF16 MMAs on exact 7-bit
  *                      slices of both operands (six each, per-row / per-column
  *                      power-of-two scaling, four FP32 accumulators per output,
- *                      ~2^-40 normwise), with a staging buffer in the workspace
+ *                      ~2^-40 normwise), with a staging buffer in the workspace;
+ *                      QMC_C15_CFREE = the "C-free" variant: only C1 is formed (as
+ *                      in QMC_C15_TENSOR), and after a4 the drift and Laplacian
+ *                      come from v_e = D^-1[e,:] A^T (Sec. II.C vector products with
+ *                      the MO expansion Eq. (mo)): drift_e = sum_mu v_e,mu grad chi_mu,
+ *                      lap_e = sum_mu v_e,mu lap chi_mu over e's active AOs, v on the
+ *                      tcgen05 tensor cores from exact BF16 slices of D^-1 and A
+ *                      (as for C1), the AO derivatives evaluated in the epilogue
+ *                      (gradient FP32, Laplacian float-float); C2..C5 are never
+ *                      stored (qmc_slater_matrices still returns all five, formed
+ *                      as in QMC_C15_TENSOR)
  *   bw_walkers         walkers per CTA of the tensor-core adjoint
  *                      (qmc_logpsi_backward_ex, QMC_PREC_MIXED): 2, 4, 8, 16 or
  *                      32.  A CTA's FP32 accumulators sum over its walkers'
@@ -225,7 +235,7 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  * choice.
  */
 enum { QMC_A4_FP64 = 0, QMC_A4_FLOAT_FLOAT = 1, QMC_A4_TENSOR = 2 };
-enum { QMC_C15_FLOAT_FLOAT = 0, QMC_C15_TENSOR = 1 };
+enum { QMC_C15_FLOAT_FLOAT = 0, QMC_C15_TENSOR = 1, QMC_C15_CFREE = 2 };
 enum { QMC_EXPIRE_C15 = 1, QMC_EXPIRE_A4 = 2, QMC_EXPIRE_ADJOINT = 4 };
 typedef struct {
     int gj_panel;

@@ -42,7 +42,7 @@ class Tiles(C.Structure):
 
 
 A4_MODE = {"fp64": 0, "float_float": 1, "tensor": 2}
-C15_MODE = {"float_float": 0, "tensor": 1}
+C15_MODE = {"float_float": 0, "tensor": 1, "cfree": 2}
 EXPIRE = {"c15": 1, "a4": 2, "adjoint": 4}
 
 

@@ -129,7 +129,7 @@ class QmcSystem:
         check(lib().qmc_system_get_tiles(self._h, C.byref(t)))
         return {"gj_panel": t.gj_panel, "c15_walkers": t.c15_walkers,
                 "a4_mode": {0: "fp64", 1: "float_float", 2: "tensor"}[t.a4_mode], "a4_kappa_max": t.a4_kappa_max,
-                "c15_mode": "tensor" if t.c15_mode == 1 else "float_float", "bw_walkers": t.bw_walkers,
+                "c15_mode": {0: "float_float", 1: "tensor", 2: "cfree"}[t.c15_mode], "bw_walkers": t.bw_walkers,
                 "wait_s": t.wait_s, "expire_walker": t.expire_walker, "expire_kernels": t.expire_kernels}
 
     def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None, c15_mode=None,

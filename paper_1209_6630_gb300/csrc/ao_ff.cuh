@@ -88,6 +88,23 @@ __device__ __forceinline__ void ao_val_lap_ff(const SysDev &s, const FfBasis &fb
     ff_angular(s, fb, mu, rd, val, lap);
 }
 
+// Value alone (the C-free variant's C1): the radial sum g without gd and gl.
+__device__ __forceinline__ float2 ao_val_ff(const SysDev &s, const FfBasis &fb, int mu, const float2 *r)
+{
+    const int sh = s.ao_shell[mu];
+    const int a = s.sh_atom[sh];
+    const float2 dx = ff::sub(r[0], fb.Q[3 * a]), dy = ff::sub(r[1], fb.Q[3 * a + 1]), dz = ff::sub(r[2], fb.Q[3 * a + 2]);
+    const float2 d2 = ff::add(ff::add(ff::mul(dx, dx), ff::mul(dy, dy)), ff::mul(dz, dz));
+    float2 g = make_float2(0.f, 0.f);
+    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
+    for (int p = 0; p < np; ++p)
+        g = ff::add(g, ff::mul(fb.pc[p0 + p], ff::exp_neg(ff::mul(fb.pg[p0 + p], d2), fb.expj)));
+    const int pw = s.ao_pow[mu];
+    const int nx = pw & 255, ny = (pw >> 8) & 255, nz = (pw >> 16) & 255;
+    const float2 P = ff::mul(ff_ipow(dx, nx), ff::mul(ff_ipow(dy, ny), ff_ipow(dz, nz)));
+    return ff::mul(fb.sc[mu], ff::mul(P, g));
+}
+
 // Ordered list of the AOs of the shells set in `bits` for a block of any
 // size (a multiple of 32 threads).  Returns the count; idx_s receives the AO indices.
 static __device__ int aos_from_mask_n(const SysDev &s, const uint32_t *bits, int mw, int *idx_s, int *warp_s)

@@ -82,6 +82,7 @@ struct C15TcArgs {
     uint32_t *wstatus;
     unsigned long long wait_ns;    // limit of each wait (WaitCfg)
     int expire_tile;               // test hook: walker tile whose first CTA's wait runs out (-1: none)
+    int c1_only;                   // the C-free variant: C1 alone (value planes only, MMA class C1 only)
 };
 
 // Radial part and AO value / Laplacian in FP32 (for the row bounds only).
@@ -138,7 +139,9 @@ __device__ __forceinline__ void f32_angular(const SysDev &s, const C15TcArgs &a,
     g3 = c * (px * py * dpz * rd.g + m2gd * rd.dz * P);
 }
 
-// three CTAs per SM (80 registers; a small spill costs less than the latency it hides)
+// three CTAs per SM (80 registers; a small spill costs less than the latency it hides).
+// kC1Only: the C-free variant's producer: float-float values alone, six planes per stage.
+template <bool kC1Only>
 __global__ void __launch_bounds__(kPrepThreads, 3) k_c15_prep(C15TcArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -188,7 +191,23 @@ __global__ void __launch_bounds__(kPrepThreads, 3) k_c15_prep(C15TcArgs a)
     // pass 1 (FP32; radial part once per shell): bounds of |value| and
     // |Laplacian| over the row, and the gradient planes of C2..C4
     float vmax = 0.f, lmax = 0.f;
-    {
+    if constexpr (kC1Only) {
+        F32Radial rd;
+        int last_sh = -1;
+        for (int ks = 0; ks < nks; ++ks)
+            for (int q = half * 32; q < half * 32 + 32; ++q) {
+                const int mu = ao_s[ks * TC_K + q];
+                int sh;
+                if (!active(mu, sh)) continue;
+                if (sh != last_sh) {
+                    last_sh = sh;
+                    f32_radial(s, a, sh, r2[0].x, r2[0].y, r2[1].x, r2[1].y, r2[2].x, r2[2].y, rd);
+                }
+                float v, lp, g1, g2, g3;
+                f32_angular(s, a, mu, rd, v, lp, g1, g2, g3);
+                vmax = fmaxf(vmax, fabsf(v));
+            }
+    } else {
         F32Radial rd;
         int last_sh = -1;
         const int f16 = a.tt.f16;
@@ -235,6 +254,32 @@ __global__ void __launch_bounds__(kPrepThreads, 3) k_c15_prep(C15TcArgs a)
         a.rexp[(slot * TC_M + row) * 2 + 1] = El;
     }
 
+    if constexpr (kC1Only) {
+        for (int ks = 0; ks < nks; ++ks)
+            for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
+                uint32_t wv[kC15Slices][4];
+#pragma unroll
+                for (int q2 = 0; q2 < 4; ++q2) {
+                    float sv[2][kC15Slices];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int mu = ao_s[ks * TC_K + c8 * 8 + 2 * q2 + h];
+                        int sh;
+                        const float2 v = active(mu, sh) ? ao_val_ff(s, a.fb, mu, r2) : make_float2(0.f, 0.f);
+                        slice6(v, Ev, sv[h]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < kC15Slices; ++j) wv[j][q2] = bf16_pair(sv[0][j], sv[1][j]);
+                }
+                const uint32_t off = a_off64(row, c8 & 3);
+                unsigned char *stp = pl + (size_t)(2 * ks + (c8 >> 2)) * kStageBytes;
+#pragma unroll
+                for (int j = 0; j < kC15Slices; ++j)
+                    *reinterpret_cast<uint4 *>(stp + (size_t)j * kSPlaneBytes + off) =
+                        make_uint4(wv[j][0], wv[j][1], wv[j][2], wv[j][3]);
+            }
+        return;
+    }
     // pass 2: float-float values and Laplacians, sliced into the operand planes
     // (the float-float radial part is recomputed per AO here: caching it per shell,
     // as in pass 1, keeps 12 more registers live across the slicing and measured slower)
@@ -284,7 +329,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
 
     const SysDev &s = a.s;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int mt = blockIdx.x, tile = blockIdx.y, el = blockIdx.z / 3, o = blockIdx.z % 3;   // o: C1, C5, C2..C4
+    // o: C1, C5, C2..C4 (the C-free variant: C1 alone)
+    const int mt = blockIdx.x, tile = blockIdx.y;
+    const int el = a.c1_only ? (int)blockIdx.z : (int)blockIdx.z / 3, o = a.c1_only ? 0 : (int)blockIdx.z % 3;
     const int e = a.e0 + el;
     const int spin = e >= s.n_up;
     const int ei = spin ? e - s.n_up : e;
@@ -547,7 +594,7 @@ size_t c15tc_bytes(const SysDev &s, int nw)
 
 cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, const TcTables &tt, int nw,
                           const double *R, const uint32_t *masks, int mw, double *X, double *L5, float *Cg,
-                          uint32_t *wstatus, void *scratch, cudaStream_t st, const WaitCfg &wc)
+                          uint32_t *wstatus, void *scratch, cudaStream_t st, const WaitCfg &wc, bool c1_only)
 {
     if (nw == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
@@ -575,14 +622,15 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
     }
     a.X = X; a.L5 = L5; a.Cg = Cg; a.tt = tt; a.wstatus = wstatus;
     a.wait_ns = wc.limit_ns;
+    a.c1_only = c1_only ? 1 : 0;
     a.expire_tile = (wc.expire_kernels & QMC_EXPIRE_C15) && wc.expire_w >= 0 && wc.expire_w < nw ? wc.expire_w / TC_M : -1;
     const size_t sm_prep = sizeof(uint32_t) * TC_M * (size_t)mw + sizeof(int) * ((size_t)s.n_ao + TC_K);
     const size_t sm_mma = 1024 + 2 * (size_t)kC15Slices * (kSPlaneBytes + kSBPlaneBytes) +
                           sizeof(int) * (size_t)a.kmax_steps * TC_K;
     if (sm_mma > 227 * 1024 || sm_prep > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_c15_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(c1_only ? k_c15_prep<true> : k_c15_prep<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_c15_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mma)) !=
         cudaSuccess)
@@ -591,8 +639,9 @@ cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables 
     for (int e0 = 0; e0 < s.n_elec; e0 += (int)nb) {
         const int ne = s.n_elec - e0 < (int)nb ? s.n_elec - e0 : (int)nb;
         a.e0 = e0;
-        k_c15_prep<<<dim3(a.n_tiles, ne), kPrepThreads, sm_prep, st>>>(a);
-        k_c15_mma<<<dim3(mtiles, a.n_tiles, 3 * ne), kMmaThreads, sm_mma, st>>>(a);
+        if (c1_only) k_c15_prep<true><<<dim3(a.n_tiles, ne), kPrepThreads, sm_prep, st>>>(a);
+        else k_c15_prep<false><<<dim3(a.n_tiles, ne), kPrepThreads, sm_prep, st>>>(a);
+        k_c15_mma<<<dim3(mtiles, a.n_tiles, (c1_only ? 1 : 3) * ne), kMmaThreads, sm_mma, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

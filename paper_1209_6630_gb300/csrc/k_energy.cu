@@ -99,7 +99,16 @@ __global__ void __launch_bounds__(kEnThreads) k_drift_energy(SysDev s, const dou
     const double *Rw = R + (size_t)w * N * 3;
 
     double lap_acc = 0.0;
-    for (int e = wid; e < N; e += kEnWarps) {
+    if (cv.vd) {                 // C-free variant: drift and Laplacian per electron already formed
+        for (int e = t; e < N; e += kEnThreads) {
+            const double *v = cv.vd + ((size_t)w * N + e) * 4;
+            double *dr = o.drift + ((size_t)wg * N + e) * 3;
+            dr[0] = v[0]; dr[1] = v[1]; dr[2] = v[2];
+        }
+        if (lane == 0)
+            for (int e = wid; e < N; e += kEnWarps) lap_acc += cv.vd[((size_t)w * N + e) * 4 + 3];
+    }
+    for (int e = wid; e < N && !cv.vd; e += kEnWarps) {
         const int spin = e >= s.n_up;
         const int ei = spin ? e - s.n_up : e;
         const int ns = spin ? s.n_dn : s.n_up;

@@ -1,0 +1,357 @@
+// The C-free variant of steps a3 + a5 (drift and Laplacian without the
+// gradient and Laplacian matrices C2..C5).  From the cofactor identities of
+// Sec. II.C (the two vector products) and the MO expansion Eq. (mo):
+//   drift_{e,l} = sum_k (D^-1)_{ek} d_l phi_k(r_e) = sum_mu v_{e mu} d_l chi_mu(r_e)
+//   lap_e       = sum_k (D^-1)_{ek} lap phi_k(r_e) = sum_mu v_{e mu} lap chi_mu(r_e)
+//   v_{e mu}    = sum_k (D^-1)_{ek} a_{k mu}              (v_e = D^-1[e,:] A^T)
+// with mu over the AOs that are not screened out for r_e.  Only C1 is formed
+// (for the determinant and D^-1); the product v costs sum_s N_s^2 Kbar
+// multiply-adds, against 4 sum_s N_s^2 Kbar for C2..C5.
+//
+// k_vd_rowexp: the exponent bound E of every D^-1 row (|D^-1[e,k]| < 2^E).
+// k_vd_mma (one CTA per walker tile of 128 and electron e): the union of the
+// tile's active AOs for e (from the shell masks), then per AO tile of 128: v
+// on the tcgen05 tensor cores as M = 128 walkers x N = 128 AOs x K = N_s MOs
+// from exact BF16 slices, the split of the C1 products (k_c15_tc.cu) with
+// the roles of the indices exchanged: D^-1 rows scaled by 2^-E_{w,e} (sliced
+// in the kernel from the FP64 inverse), A rows scaled by 2^-G_mu (sliced at
+// load), six slices each, the 21 slice pairs of order <= 5 into four FP32
+// accumulators (orders 0, 1, 2 exact; 3..5 together); K stages of 32 MOs
+// through two buffers (B rows by cp.async, A slices stored by all threads),
+// one thread issuing the MMAs, mbarrier commits, bounded waits.  Epilogue:
+// v = 2^(E + G_mu) (acc0 + acc1 + acc2 + acc3) in FP64, and for every active
+// AO of the walker the gradient (FP32) and Laplacian (float-float) of the AO
+// at r_e, accumulated into the drift (FP64 sums of FP32 products) and the
+// Laplacian (FP64).  Output vd[w][e] = (drift_x, drift_y, drift_z, lap_e).
+#include "ao_ff.cuh"
+#include "qmc_internal.cuh"
+#include "slices.cuh"
+#include "umma.cuh"
+
+namespace qmc {
+
+namespace {
+
+constexpr int kVdThreads = 512;
+constexpr int kVdK = 32;                                      // MOs per stage
+constexpr uint32_t kVdPlane = TC_M * kVdK * 2;                // [128 rows][32 K] 16-bit, 64-byte swizzle: 8 KB
+constexpr uint32_t kVdBuf = 2 * kC15Slices * kVdPlane;        // 6 A planes + 6 B planes: 96 KB
+constexpr int kVdAcc = 4;
+
+struct VdArgs {
+    SysDev s;
+    FfBasis fb;
+    const double *R;
+    const uint32_t *masks;
+    int mw, nw;
+    const double *Dinv;            // [nw][msz] rows = electrons
+    size_t msz;
+    const int *rexp;               // [nw][N] row exponents of D^-1
+    const uint16_t *rslice[2];     // [6][n_ao][ns_pad]
+    const int *gexp[2];            // [n_ao]
+    int ns_pad[2];
+    double *vd;                    // [nw][N][4]
+    uint32_t *wstatus;
+    unsigned long long wait_ns;
+};
+
+__global__ void k_vd_rowexp(int nw, int n_up, int n_dn, size_t msz, const double *__restrict__ Dinv,
+                            int *__restrict__ rexp)
+{
+    const int N = n_up + n_dn;
+    const size_t row = blockIdx.x * (size_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= (size_t)nw * N) return;
+    const int w = (int)(row / N), e = (int)(row - (size_t)w * N);
+    const int spin = e >= n_up, ns = spin ? n_dn : n_up, ei = spin ? e - n_up : e;
+    const double *d = Dinv + (size_t)w * msz + (spin ? (size_t)n_up * n_up : 0) + (size_t)ei * ns;
+    float m = 0.f;
+    for (int k = lane; k < ns; k += 32) m = fmaxf(m, fabsf((float)d[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) rexp[row] = exp_bound(m);
+}
+
+__device__ __forceinline__ double pow2d(int e)   // 2^e, |e| <= 1000
+{
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char vd_smem[];
+    unsigned char *base = vd_smem + ((1024 - (smem_u32(vd_smem) & 1023)) & 1023);
+    int *ao_s = reinterpret_cast<int *>(base + 2 * kVdBuf);    // [n_ao + 128]
+    __shared__ uint32_t un_s[256];
+    __shared__ int warp_s[kVdThreads / 32];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+
+    const SysDev &s = a.s;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int tile = blockIdx.x, e = blockIdx.y;
+    const int N = s.n_elec;
+    const int spin = e >= s.n_up, ei = spin ? e - s.n_up : e, ns = spin ? s.n_dn : s.n_up;
+    const int nspad = a.ns_pad[spin];
+    const int mw = a.mw;
+
+    // union of the tile's active shells for electron e, and its AO list
+    for (int j = t; j < mw; j += kVdThreads) {
+        uint32_t u = 0;
+        for (int m = 0; m < TC_M; ++m) {
+            const int w = tile * TC_M + m;
+            if (w < a.nw) u |= a.masks[((size_t)w * N + e) * mw + j];
+        }
+        un_s[j] = u;
+    }
+    __syncthreads();
+    const int K = aos_from_mask_n(s, un_s, mw, ao_s, warp_s);
+    const int nat = (K + TC_N - 1) / TC_N;
+    for (int q = K + t; q < nat * TC_N; q += kVdThreads) ao_s[q] = -1;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
+                     :: "r"(smem_u32(&tmem_slot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t mbs[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
+    const uint32_t idesc = umma_idesc_f16_major(TC_M, TC_N, 1, 0, 0);   // BF16, A and B K-major
+    const uint64_t kWait = a.wait_ns;
+
+    // producer role of this thread: 8 consecutive MOs (chunk pc) of D^-1 row (walker prow, e)
+    const int prow = t >> 2, pc = t & 3;
+    const int pw = tile * TC_M + prow;
+    const bool pvalid = pw < a.nw;
+    const double *drow = a.Dinv + (size_t)(pvalid ? pw : 0) * a.msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
+                         (size_t)ei * ns;
+    const int Ep = pvalid ? a.rexp[(size_t)pw * N + e] : 0;
+    const uint16_t *Bsl = a.rslice[spin];
+    const size_t bstride = (size_t)s.n_ao * nspad;
+
+    // epilogue role: walker row erow (TMEM lane), columns cg * 32 .. + 32 of an AO tile
+    const int erow = (warp & 3) * 32 + lane, cg = warp >> 2;
+    const int ew = tile * TC_M + erow;
+    const bool evalid = ew < a.nw;
+    const int Ee = evalid ? a.rexp[(size_t)ew * N + e] : 0;
+    const double *rw = a.R + ((size_t)(evalid ? ew : 0) * N + e) * 3;
+    const float2 r2[3] = {ff::from_double(rw[0]), ff::from_double(rw[1]), ff::from_double(rw[2])};
+    const uint32_t *my_mask = a.masks + ((size_t)(evalid ? ew : 0) * N + e) * mw;
+    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
+    double b0 = 0.0, b1 = 0.0, b2 = 0.0, lap = 0.0;
+
+    const int nst = nspad / kVdK;
+    int ncb[2] = {0, 0};
+    bool ok = true;
+
+    auto produce = [&](int at, int sg, int buf) {
+        unsigned char *Ab = base + buf * kVdBuf;
+        unsigned char *Bb = Ab + kC15Slices * kVdPlane;
+        const int k0 = sg * kVdK;
+        // B: rows of A (the union's AOs of this tile), six slice planes
+        for (int q = t; q < kC15Slices * TC_N * 4; q += kVdThreads) {
+            const int j = q / (TC_N * 4), rem = q - j * (TC_N * 4);
+            const int r = rem >> 2, c = rem & 3;
+            const int mu = ao_s[at * TC_N + r];
+            const bool v = mu >= 0;
+            const uint16_t *src = Bsl + j * bstride + (size_t)(v ? mu : 0) * nspad + k0 + 8 * c;
+            cp_async16(smem_u32(Bb + j * kVdPlane + a_off64(r, c)), src, v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // A: this thread's 8 entries of D^-1, cut into six exact slices
+        float sl[8][kC15Slices];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = k0 + 8 * pc + i;
+            const double d = (pvalid && k < ns) ? drow[k] : 0.0;
+            slice6(ff::from_double(d), Ep, sl[i]);
+        }
+#pragma unroll
+        for (int j = 0; j < kC15Slices; ++j)
+            *reinterpret_cast<uint4 *>(Ab + j * kVdPlane + a_off64(prow, pc)) =
+                make_uint4(bf16_pair(sl[0][j], sl[1][j]), bf16_pair(sl[2][j], sl[3][j]), bf16_pair(sl[4][j], sl[5][j]),
+                           bf16_pair(sl[6][j], sl[7][j]));
+    };
+
+    for (int at = 0; at < nat && ok; ++at) {
+        produce(at, 0, 0);
+        for (int sg = 0; sg < nst; ++sg) {
+            const int buf = sg & 1;
+            if (sg + 1 < nst) {
+                const int nb = buf ^ 1;
+                // the MMAs of stage sg - 1 read buffer nb: wait before overwriting it
+                if (ncb[nb] > 0 && !mbar_wait(mbs[nb], (ncb[nb] - 1) & 1, kWait)) s_abort = 1;
+                produce(at, sg + 1, nb);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (s_abort) break;
+            if (t == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(base + buf * kVdBuf);
+                const uint64_t dA = umma_desc_sw64(a0, 512);
+                const uint64_t dB = umma_desc_sw64(a0 + kC15Slices * kVdPlane, 512);
+#pragma unroll
+                for (int kk = 0; kk < kVdK / 16; ++kk)
+#pragma unroll
+                    for (int d = 0; d < kC15Slices; ++d) {
+                        const int acc = d < kVdAcc - 1 ? d : kVdAcc - 1;
+#pragma unroll
+                        for (int i = 0; i <= d; ++i) {
+                            const int j = d - i;
+                            const uint64_t ad = dA + ((i * kVdPlane + 32 * kk) >> 4);
+                            const uint64_t bd = dB + ((j * kVdPlane + 32 * kk) >> 4);
+                            const bool first = sg == 0 && kk == 0 && i == 0 && d <= kVdAcc - 1;
+                            umma_bf16(tmem + acc * TC_N, ad, bd, idesc, first ? 0u : 1u);
+                        }
+                    }
+                umma_commit(mbs[buf]);
+            }
+            ++ncb[buf];
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        for (int bq = 0; bq < 2; ++bq)
+            if (!s_abort && ncb[bq] > 0 && !mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kWait)) s_abort = 1;
+        __syncthreads();
+        ok = !s_abort;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: v for 32 AOs of this walker row, then the AO derivatives at r_e
+        FfRadial rd;
+        int last_sh = -1;
+        double *vbuf = reinterpret_cast<double *>(base);   // [16][512]: the operand buffers are idle here
+        for (int h = 0; h < 2; ++h) {
+            const int c0 = cg * 32 + h * 16;
+            {
+                uint32_t v0[16], v1[16], v2[16], v3[16];
+                tmem_ld16(tmem + tlane + (uint32_t)(0 * TC_N + c0), v0);
+                tmem_ld16(tmem + tlane + (uint32_t)(1 * TC_N + c0), v1);
+                tmem_ld16(tmem + tlane + (uint32_t)(2 * TC_N + c0), v2);
+                tmem_ld16(tmem + tlane + (uint32_t)(3 * TC_N + c0), v3);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    vbuf[q * kVdThreads + t] = (((double)__uint_as_float(v0[q]) + (double)__uint_as_float(v1[q])) +
+                                                (double)__uint_as_float(v2[q])) + (double)__uint_as_float(v3[q]);
+            }
+            if (!evalid) continue;
+#pragma unroll 1
+            for (int q = 0; q < 16; ++q) {
+                const int mu = ao_s[at * TC_N + c0 + q];
+                if (mu < 0) break;
+                const int sh = s.ao_shell[mu];
+                if (!((my_mask[sh >> 5] >> (sh & 31)) & 1u)) continue;
+                const double vmu = vbuf[q * kVdThreads + t] * pow2d(Ee + a.gexp[spin][mu]);
+                if (sh != last_sh) {
+                    last_sh = sh;
+                    ff_radial(s, a.fb, sh, r2, rd);
+                }
+                float2 val, lp;
+                ff_angular(s, a.fb, mu, rd, val, lp);
+                // gradient in FP32 from the same radial part
+                const int pw2 = s.ao_pow[mu];
+                const int nx = pw2 & 255, ny = (pw2 >> 8) & 255, nz = (pw2 >> 16) & 255;
+                const float dx = rd.dx.x + rd.dx.y, dy = rd.dy.x + rd.dy.y, dz = rd.dz.x + rd.dz.y;
+                auto ip = [](float x, int n) {
+                    float y = 1.f;
+                    for (int i = 0; i < n; ++i) y *= x;
+                    return y;
+                };
+                const float px = ip(dx, nx), py = ip(dy, ny), pz = ip(dz, nz);
+                const float P = px * py * pz, g = rd.g.x + rd.g.y, m2gd = -2.f * (rd.gd.x + rd.gd.y);
+                const float c = a.fb.sc[mu].x + a.fb.sc[mu].y;
+                const float g1 = c * ((nx ? nx * ip(dx, nx - 1) : 0.f) * py * pz * g + m2gd * dx * P);
+                const float g2 = c * (px * (ny ? ny * ip(dy, ny - 1) : 0.f) * pz * g + m2gd * dy * P);
+                const float g3 = c * (px * py * (nz ? nz * ip(dz, nz - 1) : 0.f) * g + m2gd * dz * P);
+                b0 += vmu * (double)g1;
+                b1 += vmu * (double)g2;
+                b2 += vmu * (double)g3;
+                lap += vmu * ((double)lp.x + (double)lp.y);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();                                   // TMEM read before the next tile's MMAs
+    }
+    if (!ok) {
+        if (t < TC_M && tile * TC_M + t < a.nw) atomicOr(a.wstatus + tile * TC_M + t, (uint32_t)QMC_STATUS_TIMEOUT);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        for (int bq = 0; bq < 2; ++bq)                     // let MMAs in flight drain
+            if (ncb[bq] > 0) mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kDrainNs);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
+    // the four column groups' partial sums of each row, added in a fixed order
+    double *red = reinterpret_cast<double *>(base);        // [4 groups][128 rows][4]; operands no longer read
+    red[((size_t)cg * TC_M + erow) * 4 + 0] = b0;
+    red[((size_t)cg * TC_M + erow) * 4 + 1] = b1;
+    red[((size_t)cg * TC_M + erow) * 4 + 2] = b2;
+    red[((size_t)cg * TC_M + erow) * 4 + 3] = lap;
+    __syncthreads();
+    if (t < TC_M * 4) {
+        const int r = t >> 2, c = t & 3;
+        const int w = tile * TC_M + r;
+        if (w < a.nw) {
+            double x = 0.0;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) x += red[((size_t)g * TC_M + r) * 4 + c];
+            a.vd[((size_t)w * N + e) * 4 + c] = ok ? x : __longlong_as_double(0x7ff8000000000000ll);
+        }
+    }
+}
+
+}  // namespace
+
+bool vdrift_fits(const SysDev &s)
+{
+    const size_t sm = 1024 + 2 * (size_t)kVdBuf + sizeof(int) * ((size_t)s.n_ao + TC_N);
+    return sm <= 227 * 1024;
+}
+
+size_t vdrift_bytes(const SysDev &s, int nw)
+{
+    return ((sizeof(int) * (size_t)nw * s.n_elec + 255) / 256) * 256;
+}
+
+cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
+                          const uint32_t *masks, int mw, const double *Dinv, double *vd, uint32_t *wstatus,
+                          void *scratch, cudaStream_t st, const WaitCfg &wc)
+{
+    if (nw == 0) return cudaSuccess;
+    if (!vdrift_fits(s)) return cudaErrorInvalidConfiguration;
+    VdArgs a;
+    a.s = s; a.fb = fb; a.R = R; a.masks = masks; a.mw = mw; a.nw = nw; a.Dinv = Dinv;
+    a.msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+    a.rexp = static_cast<const int *>(scratch);
+    for (int spin = 0; spin < 2; ++spin) {
+        a.rslice[spin] = mt.rslice[spin];
+        a.gexp[spin] = mt.gexp[spin];
+        a.ns_pad[spin] = mt.ns_pad[spin];
+    }
+    a.vd = vd;
+    a.wstatus = wstatus;
+    a.wait_ns = wc.limit_ns;
+    const size_t rows = (size_t)nw * s.n_elec;
+    k_vd_rowexp<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(nw, s.n_up, s.n_dn, a.msz, Dinv,
+                                                          static_cast<int *>(scratch));
+    const size_t sm = 1024 + 2 * (size_t)kVdBuf + sizeof(int) * ((size_t)s.n_ao + TC_N);
+    cudaError_t e = cudaFuncSetAttribute(k_vd_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int tiles = (nw + TC_M - 1) / TC_M;
+    k_vd_mma<<<dim3(tiles, s.n_elec), kVdThreads, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace qmc

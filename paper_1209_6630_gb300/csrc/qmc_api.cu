@@ -179,7 +179,7 @@ struct Blob {
 // and FP16 hi/lo planes of A * 2^a_exp, [n_ao][n_s padded to 64]; float-float
 // planes [n_ao][n_s].  a_exp is chosen so that max |A| * 2^a_exp <= 8192.
 struct MoLayout {
-    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oF[2], oCm[2], oSl[2], oFe[2];
+    size_t oA[2], oBh[2], oBl[2], oHh[2], oHl[2], oF[2], oCm[2], oSl[2], oFe[2], oRs[2], oGe[2];
     int ns_pad[2], ns32[2], a_exp[2];
 };
 
@@ -248,6 +248,27 @@ static void build_mo(int nao, int nu, int nd, int a_dtype, const void *A_up, con
             }
         L.oSl[spin] = b.add(sl.data(), 2 * sl.size());
         L.oFe[spin] = b.add(fe.data(), 4 * fe.size());
+        // the same slicing with one exponent per AO row: the operand of v = D^-1 A^T, whose
+        // contraction runs over the MO index k
+        std::vector<int> ge(nao, 0);
+        for (int mu = 0; mu < nao; ++mu) {
+            double m = 0.0;
+            for (int k = 0; k < ns; ++k) m = std::max(m, fabs(A64[(size_t)mu * ns + k]));
+            ge[mu] = m > 0.0 ? ilogb(m) + 1 : 0;
+        }
+        std::vector<uint16_t> rs((size_t)kC15Slices * nao * np, 0);
+        for (int mu = 0; mu < nao; ++mu)
+            for (int k = 0; k < ns; ++k) {
+                double r = ldexp(A64[(size_t)mu * ns + k], -ge[mu]);
+                for (int j = 0; j < kC15Slices; ++j) {
+                    const int sh = kC15SliceBits * (j + 1);
+                    const double sj = ldexp(nearbyint(ldexp(r, sh)), -sh);
+                    rs[((size_t)j * nao + mu) * np + k] = bf16_bits((float)sj);
+                    r -= sj;
+                }
+            }
+        L.oRs[spin] = b.add(rs.data(), 2 * rs.size());
+        L.oGe[spin] = b.add(ge.data(), 4 * ge.size());
     }
 }
 
@@ -265,6 +286,8 @@ static void point_mo(qmc_system *sys, char *dev, const MoLayout &L)
         mt.colmax[spin] = reinterpret_cast<const float *>(dev + L.oCm[spin]);
         mt.slice[spin] = reinterpret_cast<const uint16_t *>(dev + L.oSl[spin]);
         mt.fexp[spin] = reinterpret_cast<const int *>(dev + L.oFe[spin]);
+        mt.rslice[spin] = reinterpret_cast<const uint16_t *>(dev + L.oRs[spin]);
+        mt.gexp[spin] = reinterpret_cast<const int *>(dev + L.oGe[spin]);
         mt.ns_pad[spin] = L.ns_pad[spin];
         mt.a_exp[spin] = L.a_exp[spin];
     }
@@ -544,10 +567,13 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
         return invalid("qmc_system_set_tiles: a4_mode");
     if (tiles->a4_mode == QMC_A4_TENSOR && !gjtc_fits(std::max(sys->d.n_up, sys->d.n_dn)))
         return invalid("qmc_system_set_tiles: a4_mode tensor exceeds the panel kernel's shared memory");
-    if (tiles->c15_mode != QMC_C15_FLOAT_FLOAT && tiles->c15_mode != QMC_C15_TENSOR)
+    if (tiles->c15_mode != QMC_C15_FLOAT_FLOAT && tiles->c15_mode != QMC_C15_TENSOR && tiles->c15_mode != QMC_C15_CFREE)
         return invalid("qmc_system_set_tiles: c15_mode");
-    if (tiles->c15_mode == QMC_C15_TENSOR && !c15tc_fits(sys->d, sys->mixed.mask_words))
+    if ((tiles->c15_mode == QMC_C15_TENSOR || tiles->c15_mode == QMC_C15_CFREE) &&
+        !c15tc_fits(sys->d, sys->mixed.mask_words))
         return invalid("qmc_system_set_tiles: c15_mode tensor exceeds the kernel's shared-memory limits");
+    if (tiles->c15_mode == QMC_C15_CFREE && !vdrift_fits(sys->d))
+        return invalid("qmc_system_set_tiles: c15_mode cfree exceeds the drift kernel's shared-memory limits");
     if (!(tiles->a4_kappa_max > 0.0)) return invalid("qmc_system_set_tiles: a4_kappa_max must be > 0");
     if (tiles->bw_walkers != 2 && tiles->bw_walkers != 4 && tiles->bw_walkers != 8 && tiles->bw_walkers != 16 &&
         tiles->bw_walkers != 32)
@@ -603,24 +629,28 @@ struct Plan {
     size_t mask_bytes; // per walker (mixed path): N x mask_words x 4
     size_t redo_bytes; // per chunk (float-float a4): list and state of the FP64 recomputation
     bool c15tc;        // C1/C5 on the tensor cores (staging buffer per chunk)
+    bool cfree;        // C-free variant: C1 alone, drift and Laplacian from v = D^-1 A^T
     bool dinv;
     const SysDev *sd;  // the system's sizes
 };
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
-Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
+// c15_override >= 0 replaces the system's c15_mode (qmc_slater_matrices needs all five matrices)
+Plan make_plan(const qmc_system *sys, int precision, bool need_dinv, int c15_override = -1)
 {
     Plan p;
+    const int c15 = c15_override >= 0 ? c15_override : sys->tiles.c15_mode;
     p.msz = (size_t)sys->d.n_up * sys->d.n_up + (size_t)sys->d.n_dn * sys->d.n_dn;
     p.mixed = precision != QMC_PREC_F64;
-    p.cd_bytes = p.mixed ? p.msz * (3 * 4 + 8) : p.msz * 4 * 8;
+    p.cfree = p.mixed && c15 == QMC_C15_CFREE;
+    p.cd_bytes = p.cfree ? (size_t)sys->d.n_elec * 4 * 8 : (p.mixed ? p.msz * (3 * 4 + 8) : p.msz * 4 * 8);
     p.mask_bytes = p.mixed ? (size_t)sys->d.n_elec * sys->mixed.mask_words * 4 : 0;
     p.dinv = need_dinv;
     p.ffgj = p.mixed && (sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT || sys->tiles.a4_mode == QMC_A4_TENSOR);
     p.tcgj = p.mixed && sys->tiles.a4_mode == QMC_A4_TENSOR;
     p.redo_bytes = p.ffgj ? redo_scratch_bytes(std::max(sys->d.n_up, sys->d.n_dn)) : 0;
-    p.c15tc = p.mixed && sys->tiles.c15_mode == QMC_C15_TENSOR;
+    p.c15tc = p.mixed && (c15 == QMC_C15_TENSOR || c15 == QMC_C15_CFREE);
     p.sd = &sys->d;
     p.per_walker = p.msz * 8 + p.cd_bytes + (need_dinv ? p.msz * 8 : 0) + 36 + p.mask_bytes +
                    (p.ffgj ? p.msz * 8 + 2 : 0);
@@ -629,7 +659,7 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv)
 
 struct Carve {
     double *X; void *Cd; double *L5; double *D; double *la; double *sg; uint32_t *st; uint32_t *masks;
-    float2 *work; uint8_t *redo; void *redo_scratch; void *c15tc; void *gjtc;
+    float2 *work; uint8_t *redo; void *redo_scratch; void *c15tc; void *gjtc; double *vd; void *vdscr;
 };
 
 // Arrays for `nw` walkers laid out array by array inside ws.
@@ -639,7 +669,14 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
     size_t o = 0;
     auto take = [&](size_t bytes) { char *r = b + o; o = al(o + bytes); return r; };
     c.X = reinterpret_cast<double *>(take(p.msz * 8 * nw));
-    if (p.mixed) {
+    c.vd = nullptr;
+    c.vdscr = nullptr;
+    if (p.cfree) {
+        c.Cd = nullptr;
+        c.L5 = nullptr;
+        c.vd = reinterpret_cast<double *>(take(p.cd_bytes * nw));
+        c.vdscr = take(vdrift_bytes(*p.sd, nw));
+    } else if (p.mixed) {
         c.Cd = take(p.msz * 3 * 4 * nw);
         c.L5 = reinterpret_cast<double *>(take(p.msz * 8 * nw));
     } else {
@@ -662,7 +699,8 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
 size_t bytes_for(const Plan &p, int nw)
 {
     size_t o = al(p.msz * 8 * nw);
-    o += p.mixed ? al(p.msz * 3 * 4 * nw) + al(p.msz * 8 * nw) : al(p.msz * 4 * 8 * nw);
+    if (p.cfree) o += al(p.cd_bytes * nw) + al(vdrift_bytes(*p.sd, nw));
+    else o += p.mixed ? al(p.msz * 3 * 4 * nw) + al(p.msz * 8 * nw) : al(p.msz * 4 * 8 * nw);
     o += p.dinv ? al(p.msz * 8 * nw) : 0;
     o += al(16 * (size_t)nw) * 2 + al(4 * (size_t)nw);
     o += p.mask_bytes ? al(p.mask_bytes * nw) : 0;
@@ -686,7 +724,11 @@ CView cview(const Plan &p, const Carve &c)
 {
     CView v;
     v.g = c.Cd;
-    if (p.mixed) {
+    v.vd = c.vd;
+    if (p.cfree) {
+        v.g_f32 = 1; v.g_wstride = 0; v.g_ncomp = 3;
+        v.l = nullptr; v.l_wstride = 0; v.l_ncomp = 1; v.l_comp = 0;
+    } else if (p.mixed) {
         v.g_f32 = 1; v.g_wstride = 3 * p.msz; v.g_ncomp = 3;
         v.l = c.L5; v.l_wstride = p.msz; v.l_ncomp = 1; v.l_comp = 0;
     } else {
@@ -712,7 +754,7 @@ WaitCfg wait_cfg(const qmc_system *sys, int w0, int nw)
 
 template <typename Mark>
 cudaError_t run_products(const qmc_system *sys, int precision, int nw, const double *Rc, const Carve &c,
-                         cudaStream_t st, Mark mark, const WaitCfg &wc)
+                         cudaStream_t st, Mark mark, const WaitCfg &wc, const Plan &p)
 {
     const SysDev &s = sys->d;
     if (precision == QMC_PREC_F64) return launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
@@ -731,7 +773,14 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
     }
     for (int l = 0; l < 3; ++l) tt.in_scale[l] = tt.f16 ? (float)ldexp(1.0, mt.b_exp) : 1.0f;
     tt.pgf = mt.pgf; tt.pcf = mt.pcf; tt.scf = mt.scf; tt.Qhi = mt.Qhi; tt.Qlo = mt.Qlo;
-    if (sys->tiles.c15_mode == QMC_C15_TENSOR) {
+    if (p.cfree) {
+        // the C-free variant: C1 alone here; drift and Laplacian after a4 (launch_vdrift)
+        e = launch_c15_tc(s, mt.ffb, mt, tt, nw, Rc, c.masks, mt.mask_words, c.X, nullptr, nullptr, c.st, c.c15tc,
+                          st, wc, true);
+        if (e != cudaSuccess) return e;
+        return mark(5);
+    }
+    if (p.c15tc) {
         // C1, C5 and C2..C4 from one producer pass per (electron, walker tile)
         e = launch_c15_tc(s, mt.ffb, mt, tt, nw, Rc, c.masks, mt.mask_words, c.X, c.L5,
                           static_cast<float *>(c.Cd), c.st, c.c15tc, st, wc);
@@ -817,7 +866,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
         e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
         const WaitCfg wc = wait_cfg(sys, w0, nw);
-        e = run_products(sys, precision, nw, Rc, c, st, mark, wc);
+        e = run_products(sys, precision, nw, Rc, c, st, mark, wc, p);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: products launch");
         if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
         GjJob jobs[2] = {GjJob(), GjJob()};
@@ -854,6 +903,11 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
         e = launch_gj(jobs, nj, st, sys->tiles.gj_panel);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: Gauss-Jordan launch");
         if ((e = mark(2)) != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: event");
+        if (p.cfree) {
+            e = launch_vdrift(s, sys->mixed.ffb, sys->mixed, nw, Rc, c.masks, sys->mixed.mask_words, Dinv, c.vd, c.st,
+                              c.vdscr, st, wc);
+            if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: C-free drift launch");
+        }
         e = launch_drift_energy(s, nw, Rc, Dinv, cview(p, c), c.la, c.sg, c.st, *out, w0, st, sys->mixed.ffb.Q);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: energy launch");
         if (stage_ms) {
@@ -905,7 +959,9 @@ extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const doub
     if (n_walk < 0) return invalid("qmc_slater_matrices: n_walk < 0");
     if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_slater_matrices: precision");
     if (n_walk == 0) return QMC_OK;
-    const Plan p = make_plan(sys, precision, false);
+    // all five matrices: the C-free variant's system computes them as the tensor-core mode does
+    const Plan p = make_plan(sys, precision, false,
+                             sys->tiles.c15_mode == QMC_C15_CFREE ? QMC_C15_TENSOR : sys->tiles.c15_mode);
     const int chunk = chunk_walkers(p, n_walk, ws_bytes);
     if (chunk < 1) {
         set_error("qmc_slater_matrices: workspace smaller than one walker");
@@ -924,7 +980,7 @@ extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const doub
         const double *Rc = R + (size_t)w0 * s.n_elec * 3;
         e = cudaMemsetAsync(c.st, 0, 4 * (size_t)nw, st);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: memset");
-        e = run_products(sys, precision, nw, Rc, c, st, [](int) { return cudaSuccess; }, wait_cfg(sys, w0, nw));
+        e = run_products(sys, precision, nw, Rc, c, st, [](int) { return cudaSuccess; }, wait_cfg(sys, w0, nw), p);
         if (e != cudaSuccess) return cuda_fail(e, "qmc_slater_matrices: products launch");
         char *o = reinterpret_cast<char *>(C + (size_t)w0 * 5 * p.msz);
         // per walker: [C1 up][C2..C5 up][C1 dn][C2..C5 dn]

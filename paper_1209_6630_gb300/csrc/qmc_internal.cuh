@@ -73,6 +73,9 @@ struct MixedTables {
     const float *colmax[2];            // max over AOs of |A[mu][k]| per MO column k [ns32], zero beyond ns
     const uint16_t *slice[2];          // BF16 slices s_j of A[mu][k] 2^-F_k: [kC15Slices][n_ao][ns_pad]
     const int *fexp[2];                // F_k per MO column [ns_pad] (|A[.][k]| < 2^F_k)
+    const uint16_t *rslice[2];         // BF16 slices of A[mu][k] 2^-G_mu (per-AO-row exponents, for the
+                                       // C-free product v = D^-1 A^T): [kC15Slices][n_ao][ns_pad]
+    const int *gexp[2];                // G_mu per AO row [n_ao] (|A[mu][.]| < 2^G_mu)
     int ns_pad[2];
     int a_exp[2];                      // FP16 planes hold A * 2^a_exp
     int b_exp;                         // FP16 path: AO gradients enter scaled by 2^b_exp
@@ -138,6 +141,7 @@ struct CView {
     size_t l_wstride;
     int l_ncomp;
     int l_comp;
+    const double *vd;   // C-free variant: drift and Laplacian per electron [W][N][4] (the dots are done)
 };
 
 cudaError_t launch_drift_energy(const SysDev &s, int nw, const double *R, const double *Dinv, const CView &cv,
@@ -152,7 +156,14 @@ bool c15tc_fits(const SysDev &s, int mw);
 size_t c15tc_bytes(const SysDev &s, int nw);
 cudaError_t launch_c15_tc(const SysDev &s, const FfBasis &fb, const MixedTables &mt, const TcTables &tt, int nw,
                           const double *R, const uint32_t *masks, int mw, double *X, double *L5, float *Cg,
-                          uint32_t *wstatus, void *scratch, cudaStream_t st, const WaitCfg &wc);
+                          uint32_t *wstatus, void *scratch, cudaStream_t st, const WaitCfg &wc,
+                          bool c1_only = false);
+// C-free variant: drift and Laplacian from v = D^-1 A^T (k_vdrift.cu)
+bool vdrift_fits(const SysDev &s);
+size_t vdrift_bytes(const SysDev &s, int nw);
+cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
+                          const uint32_t *masks, int mw, const double *Dinv, double *vd, uint32_t *wstatus,
+                          void *scratch, cudaStream_t st, const WaitCfg &wc);
 cudaError_t launch_tc_contract(const SysDev &s, int nw, const double *R, const uint32_t *masks, int mw,
                                const TcTables &tt, float *Cg, uint32_t *wstatus, cudaStream_t st, const WaitCfg &wc);
 cudaError_t launch_widen(const float *src, size_t spitch, double *dst, size_t dpitch, size_t width, int rows,
