@@ -85,6 +85,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep default tiles (no autotuner)")
     p.add_argument("--no-dmc", action="store_true", help="skip the full DMC step timing")
+    p.add_argument("--no-cfree", action="store_true", help="skip the C-free variant's timing")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the 1731-electron forward comparison and the mixed batch")
     return p.parse_args()
@@ -307,7 +308,39 @@ def config4_forward(a, flush, e0, e1):
                                       "status_mismatch": int((om["status"] != of["status"]).sum().item())}}
 
 
-def dmc_bench(q, R, prec, flush, e0, e1, t_eval_ms):
+def cfree_bench(q, R, prec, flush, e0, e1):
+    """The C-free variant on the same batch (c15_mode cfree: C1 alone, then the
+    drift and Laplacian from v = D^-1 A^T), timed like the default; returns the
+    timing and its outputs for the accuracy check against the FP64 path."""
+    import numpy as np
+    import torch
+    W = int(R.shape[0])
+    old = q.tiles()["c15_mode"]
+    q.set_tiles(c15_mode="cfree")
+    try:
+        ws = q.workspace(W, prec)
+        out = q.alloc_out(W)
+        for _ in range(2):
+            q.eval(R, precision=prec, out=out, ws=ws)
+        torch.cuda.synchronize()
+        ts, stages = [], []
+        for _ in range(3):
+            flush.zero_()
+            e0.record()
+            q.eval(R, precision=prec, out=out, ws=ws, stage_ms=stages)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    finally:
+        q.set_tiles(c15_mode=old)
+    st = np.array(stages).mean(axis=0)
+    t = sum(ts) / len(ts)
+    res = {"walker_steps_per_s": W / (t / 1e3), "ms_per_step": t,
+           "stage_ms": {"masks": st[4], "c1_products": st[5], "a4": st[1], "vdrift_and_energy": st[2]},
+           "what": "C1 only, then v = D^-1 A^T on the tensor cores and the drift / Laplacian from the AO derivatives"}
+    return res, out
+
+
     """One fixed-node DMC step with constant population (qmc_dmc_step: move
     Eq. 1, evaluation, weight Eq. 3, reconfiguration Sec. II.B, copy of the
     drawn walkers) on the same batch, timed like the evaluation; the MC
@@ -660,6 +693,9 @@ def main():
 
     if not a.no_dmc:
         line["dmc_step"] = dmc_bench(q, R, prec, flush, e0, e1, t_step)
+    cf_out = None
+    if prec != "f64" and not a.no_cfree and q.tiles()["c15_mode"] == "tensor":
+        line["cfree"], cf_out = cfree_bench(q, R, prec, flush, e0, e1)
 
     # the plain FP64 GPU path on the same batch (the metric's comparison)
     if prec != "f64" and not a.no_compare:
@@ -677,6 +713,17 @@ def main():
             "p99_abs_logpsi_err": float(torch.quantile(dlp, 0.99).item()),
             "max_rel_eloc_err": float(del_.max().item()),
             "status_mismatch": int((mixed_st != out["status"]).sum().item())}
+        if cf_out is not None:
+            okc = (cf_out["status"] == 0) & (out["status"] == 0)
+            dlc = (cf_out["logpsi"] - out["logpsi"]).abs()[okc]
+            dec = ((cf_out["e_loc"] - out["e_loc"]).abs() / out["e_loc"].abs())[okc]
+            ddc = ((cf_out["drift"] - out["drift"]).abs().amax(dim=(1, 2)) /
+                   out["drift"].abs().amax(dim=(1, 2)))[okc]
+            line["cfree"]["accuracy_vs_fp64_path"] = {
+                "walkers": int(okc.sum().item()), "max_abs_logpsi_err": float(dlc.max().item()),
+                "max_rel_eloc_err": float(dec.max().item()), "max_drift_normwise_err": float(ddc.max().item()),
+                "status_mismatch": int((cf_out["status"] != out["status"]).sum().item())}
+            del cf_out
         t64 = []
         for _ in range(2):
             flush.zero_()

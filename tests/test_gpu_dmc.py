@@ -126,7 +126,8 @@ def test_dmc_steps_fp64_vs_oracle(sys158):
         assert (np.abs(g["e_loc"] - st_o["e_loc"]) / np.abs(st_o["e_loc"])).max() <= 1e-9
         sv = stats.cpu().numpy()
         assert sv[1] == info["alive"] and sv[3] == info["accept"].sum()
-        assert abs(sv[0] - info["sum_w"]) <= 1e-12 * info["sum_w"]
+        # the weights carry E_L's 1e-12 relative differences amplified by tau |E_L| / 2
+        assert abs(sv[0] - info["sum_w"]) <= 1e-10 * info["sum_w"]
         assert abs(sv[2] - info["sum_w_eloc"]) <= 1e-9 * abs(info["sum_w_eloc"])
 
 
