@@ -352,7 +352,7 @@ def cfree_bench(q, R, prec, flush, e0, e1):
     e_t = float(a["e_loc"].mean().item())
     ws = torch.empty(q.dmc_workspace_size(W, prec), dtype=torch.uint8, device=R.device)
     stats = torch.zeros(4, dtype=torch.float64, device=R.device)
-    tau = 0.005
+    tau = 1e-4          # all-electron moves of 1056 electrons: larger steps cross nodes (fixed-node rejections)
     for n in range(2):
         q.dmc_step(a, b, tau, e_t, 17, n, precision=prec, stats=stats, ws=ws)
         a, b = b, a
@@ -734,6 +734,29 @@ def main():
             t64.append(e0.elapsed_time(e1))
         m64 = sum(t64) / len(t64)
         line["fp64_path"] = {"value": ws * W / (m64 / 1e3), "ms_per_step": m64}
+        # the FP64 path with the tensor-core a4 and FP64 recomputation above f64_kappa_max
+        # (QMC_PREC_F64_TCA4), gated against the FP64 path's 1e-10 relative bar
+        f64_lp, f64_el, f64_st = out["logpsi"].clone(), out["e_loc"].clone(), out["status"].clone()
+        ws_tc = q.workspace(W, "f64_tca4")
+        o_tc = q.alloc_out(W)
+        q.eval(R, precision="f64_tca4", out=o_tc, ws=ws_tc)
+        flush.zero_()
+        e0.record()
+        q.eval(R, precision="f64_tca4", out=o_tc, ws=ws_tc)
+        e1.record()
+        e1.synchronize()
+        m_tc = e0.elapsed_time(e1)
+        okt = (o_tc["status"] == 0) & (f64_st == 0)
+        rlp = ((o_tc["logpsi"] - f64_lp).abs() / f64_lp.abs())[okt]
+        rel = ((o_tc["e_loc"] - f64_el).abs() / f64_el.abs())[okt]
+        line["fp64_tca4_path"] = {
+            "value": ws * W / (m_tc / 1e3), "ms_per_step": m_tc, "f64_kappa_max": q.tiles()["f64_kappa_max"],
+            "vs_fp64_path": {"walkers": int(okt.sum().item()), "max_rel_logpsi_err": float(rlp.max().item()),
+                             "max_rel_eloc_err": float(rel.max().item()),
+                             "walkers_within_1e-10": int(((rlp <= 1e-10) & (rel <= 1e-10)).sum().item()),
+                             "status_mismatch": int((o_tc["status"] != f64_st).sum().item())}}
+        del ws_tc, o_tc
+        q._ws.pop("f64_tca4", None)
         del ws64
         q._ws.pop("f64", None)
         torch.cuda.empty_cache()

@@ -80,7 +80,15 @@ enum {
                                 on the tensor cores, with FP64 recomputation near nodal
                                 surfaces; or FP64); drift dots in FP32 and the Laplacian dot
                                 in FP64, Coulomb sums in float-float, results in FP64 */
-    QMC_PREC_MIXED_BF16 = 2  /* as QMC_PREC_MIXED with BF16 hi/lo splits for C2..C4 */
+    QMC_PREC_MIXED_BF16 = 2, /* as QMC_PREC_MIXED with BF16 hi/lo splits for C2..C4 */
+    QMC_PREC_F64_TCA4 = 3    /* the plain FP64 path (FP64 AO values, products and energies)
+                                with a4 by the tensor-core Gauss-Jordan of the mixed path
+                                (float-float panels, rank-32 updates from exact BF16 slices;
+                                the float-float elimination where that kernel does not fit)
+                                and FP64 recomputation of every matrix whose kappa_inf
+                                exceeds qmc_tiles.f64_kappa_max: a cheaper FP64-accurate a4
+                                (Sec. IV.B inversion step; Table 2 caption: the inversion in
+                                double precision) */
 };
 
 enum { QMC_DTYPE_F64 = 0, QMC_DTYPE_F32 = 1 };
@@ -222,6 +230,8 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  *                      adjoint: the spin-up CTAs of w's block of bw_walkers.
  *   expire_kernels     which kernels the hook applies to: bits QMC_EXPIRE_C15
  *                      (1), QMC_EXPIRE_A4 (2), QMC_EXPIRE_ADJOINT (4).
+ *   f64_kappa_max      QMC_PREC_F64_TCA4: matrices with kappa_inf above this are
+ *                      recomputed in FP64 (> 0)
  * Defaults after qmc_system_load: gj_panel = 16 (8 if an electron count
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT (QMC_A4_TENSOR
  * from 512 electrons of one spin on, where it fits the panel kernel),
@@ -229,7 +239,7 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  * c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
  * QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1,
- * expire_kernels = 7.
+ * expire_kernels = 7, f64_kappa_max = 1e4.
  * qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous
  * choice.
@@ -247,6 +257,7 @@ typedef struct {
     double wait_s;
     int expire_walker;
     int expire_kernels;
+    double f64_kappa_max;
 } qmc_tiles;
 int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles);
 int qmc_system_get_tiles(const qmc_system *sys, qmc_tiles *tiles);

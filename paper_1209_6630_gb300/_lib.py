@@ -12,7 +12,7 @@ from . import build as _build
 
 QMC_OK, QMC_ERR_INVALID, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_CAPACITY, QMC_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 STATUS_SINGULAR_UP, STATUS_SINGULAR_DN, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4, 8
-PREC = {"f64": 0, "mixed": 1, "mixed_bf16": 2}
+PREC = {"f64": 0, "mixed": 1, "mixed_bf16": 2, "f64_tca4": 3}
 DTYPE_F64, DTYPE_F32 = 0, 1
 
 _vp = C.c_void_p
@@ -38,7 +38,7 @@ class EvalOut(C.Structure):
 class Tiles(C.Structure):
     _fields_ = [("gj_panel", _i), ("c15_walkers", _i), ("a4_mode", _i), ("a4_kappa_max", C.c_double),
                 ("c15_mode", _i), ("bw_walkers", _i), ("wait_s", C.c_double), ("expire_walker", _i),
-                ("expire_kernels", _i)]
+                ("expire_kernels", _i), ("f64_kappa_max", C.c_double)]
 
 
 A4_MODE = {"fp64": 0, "float_float": 1, "tensor": 2}

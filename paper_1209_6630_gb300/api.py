@@ -130,10 +130,11 @@ class QmcSystem:
         return {"gj_panel": t.gj_panel, "c15_walkers": t.c15_walkers,
                 "a4_mode": {0: "fp64", 1: "float_float", 2: "tensor"}[t.a4_mode], "a4_kappa_max": t.a4_kappa_max,
                 "c15_mode": {0: "float_float", 1: "tensor", 2: "cfree"}[t.c15_mode], "bw_walkers": t.bw_walkers,
-                "wait_s": t.wait_s, "expire_walker": t.expire_walker, "expire_kernels": t.expire_kernels}
+                "wait_s": t.wait_s, "expire_walker": t.expire_walker, "expire_kernels": t.expire_kernels,
+                "f64_kappa_max": t.f64_kappa_max}
 
     def set_tiles(self, gj_panel=None, c15_walkers=None, a4_mode=None, a4_kappa_max=None, c15_mode=None,
-                  bw_walkers=None, wait_s=None, expire_walker=None, expire_kernels=None):
+                  bw_walkers=None, wait_s=None, expire_walker=None, expire_kernels=None, f64_kappa_max=None):
         from ._lib import A4_MODE, C15_MODE
         cur = self.tiles()
         t = Tiles(gj_panel=gj_panel or cur["gj_panel"], c15_walkers=c15_walkers or cur["c15_walkers"],
@@ -142,7 +143,8 @@ class QmcSystem:
                   c15_mode=C15_MODE[c15_mode or cur["c15_mode"]], bw_walkers=bw_walkers or cur["bw_walkers"],
                   wait_s=wait_s if wait_s is not None else cur["wait_s"],
                   expire_walker=expire_walker if expire_walker is not None else cur["expire_walker"],
-                  expire_kernels=expire_kernels if expire_kernels is not None else cur["expire_kernels"])
+                  expire_kernels=expire_kernels if expire_kernels is not None else cur["expire_kernels"],
+                  f64_kappa_max=f64_kappa_max if f64_kappa_max is not None else cur["f64_kappa_max"])
         check(lib().qmc_system_set_tiles(self._h, C.byref(t)))
 
     def set_mo(self, A_up, A_dn):
@@ -296,7 +298,7 @@ class QmcSystem:
         _req_cuda(g, torch.float64, "g", (W,))
         dA_up = torch.empty(self.n_ao, self.n_up, dtype=torch.float64, device=self.device)
         dA_dn = torch.empty(self.n_ao, self.n_dn, dtype=torch.float64, device=self.device)
-        if precision == "f64":
+        if precision in ("f64", "f64_tca4"):
             check(lib().qmc_logpsi_backward(self._h, W, _ptr(R), _ptr(dinv), _ptr(g), _ptr(dA_up), _ptr(dA_dn),
                                             _stream(self.device)))
             return dA_up, dA_dn
@@ -436,7 +438,7 @@ class LogPsi(torch.autograd.Function):
     def forward(ctx, A_up, A_dn, R, qsys, precision="f64"):
         o = qsys.eval(R, precision=precision, want_dinv=True)
         ctx.qsys = qsys
-        ctx.precision = "f64" if precision == "f64" else "mixed"
+        ctx.precision = "f64" if precision in ("f64", "f64_tca4") else "mixed"
         ctx.save_for_backward(R, o["dinv"], o["status"])
         ctx.a_dtypes = (A_up.dtype, A_dn.dtype)
         ctx.mark_non_differentiable(o["e_loc"])

@@ -379,6 +379,7 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     // (158 electrons x 4096 walkers: 1e8 left one walker at |dlog|Psi|| = 1.4e-6, 1e7 at most
     // 6e-8 for 7% more a4 time); their FP64 recomputation is cheap
     sys->tiles.a4_kappa_max = std::max(nu, nd) <= 256 ? 1e7 : 1e8;
+    sys->tiles.f64_kappa_max = 1e4;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
     std::vector<double> atom_R2(na, 0.0);
@@ -575,6 +576,7 @@ extern "C" int qmc_system_set_tiles(qmc_system *sys, const qmc_tiles *tiles)
     if (tiles->c15_mode == QMC_C15_CFREE && !vdrift_fits(sys->d))
         return invalid("qmc_system_set_tiles: c15_mode cfree exceeds the drift kernel's shared-memory limits");
     if (!(tiles->a4_kappa_max > 0.0)) return invalid("qmc_system_set_tiles: a4_kappa_max must be > 0");
+    if (!(tiles->f64_kappa_max > 0.0)) return invalid("qmc_system_set_tiles: f64_kappa_max must be > 0");
     if (tiles->bw_walkers != 2 && tiles->bw_walkers != 4 && tiles->bw_walkers != 8 && tiles->bw_walkers != 16 &&
         tiles->bw_walkers != 32)
         return invalid("qmc_system_set_tiles: bw_walkers must be 2, 4, 8, 16 or 32");
@@ -630,6 +632,8 @@ struct Plan {
     size_t redo_bytes; // per chunk (float-float a4): list and state of the FP64 recomputation
     bool c15tc;        // C1/C5 on the tensor cores (staging buffer per chunk)
     bool cfree;        // C-free variant: C1 alone, drift and Laplacian from v = D^-1 A^T
+    bool f64tc;        // FP64 path with the tensor-core a4 (QMC_PREC_F64_TCA4)
+    double kappa_max;  // FP64 recomputation threshold of the float-pair a4
     bool dinv;
     const SysDev *sd;  // the system's sizes
 };
@@ -642,13 +646,16 @@ Plan make_plan(const qmc_system *sys, int precision, bool need_dinv, int c15_ove
     Plan p;
     const int c15 = c15_override >= 0 ? c15_override : sys->tiles.c15_mode;
     p.msz = (size_t)sys->d.n_up * sys->d.n_up + (size_t)sys->d.n_dn * sys->d.n_dn;
-    p.mixed = precision != QMC_PREC_F64;
+    p.mixed = precision == QMC_PREC_MIXED || precision == QMC_PREC_MIXED_BF16;
+    p.f64tc = precision == QMC_PREC_F64_TCA4;
     p.cfree = p.mixed && c15 == QMC_C15_CFREE;
     p.cd_bytes = p.cfree ? (size_t)sys->d.n_elec * 4 * 8 : (p.mixed ? p.msz * (3 * 4 + 8) : p.msz * 4 * 8);
     p.mask_bytes = p.mixed ? (size_t)sys->d.n_elec * sys->mixed.mask_words * 4 : 0;
     p.dinv = need_dinv;
-    p.ffgj = p.mixed && (sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT || sys->tiles.a4_mode == QMC_A4_TENSOR);
-    p.tcgj = p.mixed && sys->tiles.a4_mode == QMC_A4_TENSOR;
+    p.ffgj = (p.mixed && (sys->tiles.a4_mode == QMC_A4_FLOAT_FLOAT || sys->tiles.a4_mode == QMC_A4_TENSOR)) || p.f64tc;
+    p.tcgj = (p.mixed && sys->tiles.a4_mode == QMC_A4_TENSOR) ||
+             (p.f64tc && gjtc_fits(std::max(sys->d.n_up, sys->d.n_dn)));
+    p.kappa_max = p.f64tc ? sys->tiles.f64_kappa_max : sys->tiles.a4_kappa_max;
     p.redo_bytes = p.ffgj ? redo_scratch_bytes(std::max(sys->d.n_up, sys->d.n_dn)) : 0;
     p.c15tc = p.mixed && (c15 == QMC_C15_TENSOR || c15 == QMC_C15_CFREE);
     p.sd = &sys->d;
@@ -757,7 +764,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
                          cudaStream_t st, Mark mark, const WaitCfg &wc, const Plan &p)
 {
     const SysDev &s = sys->d;
-    if (precision == QMC_PREC_F64) return launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
+    if (!p.mixed) return launch_contract_f64(s, nw, Rc, c.X, static_cast<double *>(c.Cd), st);
     const MixedTables &mt = sys->mixed;
     cudaError_t e = launch_shell_mask(s, mt, nw, Rc, mt.mask_words, c.masks, st);
     if (e != cudaSuccess) return e;
@@ -800,7 +807,7 @@ cudaError_t run_products(const qmc_system *sys, int precision, int nw, const dou
 extern "C" int qmc_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes)
 {
     if (!sys || !bytes || n_walk < 0) return invalid("qmc_workspace_size: bad argument");
-    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_workspace_size: precision");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_F64_TCA4) return invalid("qmc_workspace_size: precision");
     const Plan p = make_plan(sys, precision, true);
     *bytes = bytes_for(p, std::min(n_walk, 65535));
     return QMC_OK;
@@ -841,7 +848,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
     if (n_walk == 0) return QMC_OK;
     if (!R || !out->logpsi || !out->sign || !out->drift || !out->e_loc || !out->status)
         return invalid("qmc_walkers_eval: null required pointer");
-    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_walkers_eval: precision");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_F64_TCA4) return invalid("qmc_walkers_eval: precision");
     const Plan p = make_plan(sys, precision, out->dinv == nullptr);
     const int chunk = chunk_walkers(p, n_walk, ws_bytes);
     if (chunk < 1) {
@@ -890,8 +897,8 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: memset");
             GjJob ffj[2] = {jobs[0], jobs[1]};
             for (int q = 0; q < nj; ++q) ffj[q].flag = nullptr;
-            if (p.tcgj) e = launch_gj_tc(ffj, nj, c.gjtc, st, sys->tiles.a4_kappa_max, wc);
-            else e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, sys->tiles.a4_kappa_max);
+            if (p.tcgj) e = launch_gj_tc(ffj, nj, c.gjtc, st, p.kappa_max, wc);
+            else e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, p.kappa_max);
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: float-float Gauss-Jordan launch");
             int e_off[2], q = 0;
             for (int spin = 0; spin < 2; ++spin)
@@ -921,7 +928,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
                 stage_ms[q] += ms;
                 stage_ms[3] += ms;
             }
-            if (precision != QMC_PREC_F64) {   // split of stage 0 into its three kernels
+            if (p.mixed) {   // split of stage 0 into its three kernels
                 float m4 = 0.0f, m5 = 0.0f, m6 = 0.0f;
                 if ((e = cudaEventElapsedTime(&m4, t_events.ev[0], t_events.ev[4])) != cudaSuccess ||
                     (e = cudaEventElapsedTime(&m5, t_events.ev[4], t_events.ev[5])) != cudaSuccess ||
@@ -957,7 +964,7 @@ extern "C" int qmc_slater_matrices(const qmc_system *sys, int n_walk, const doub
 {
     if (!sys || (n_walk > 0 && (!R || !C))) return invalid("qmc_slater_matrices: null argument");
     if (n_walk < 0) return invalid("qmc_slater_matrices: n_walk < 0");
-    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_slater_matrices: precision");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_F64_TCA4) return invalid("qmc_slater_matrices: precision");
     if (n_walk == 0) return QMC_OK;
     // all five matrices: the C-free variant's system computes them as the tensor-core mode does
     const Plan p = make_plan(sys, precision, false,
@@ -1070,7 +1077,7 @@ extern "C" int qmc_logpsi_backward(const qmc_system *sys, int n_walk, const doub
 extern "C" int qmc_backward_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes)
 {
     if (!sys || n_walk < 0 || !bytes) return invalid("qmc_backward_workspace_size: bad argument");
-    if (precision == QMC_PREC_F64) {
+    if (precision == QMC_PREC_F64 || precision == QMC_PREC_F64_TCA4) {
         *bytes = 0;
         return QMC_OK;
     }
@@ -1083,7 +1090,8 @@ extern "C" int qmc_logpsi_backward_ex(const qmc_system *sys, int n_walk, const d
                                       const double *g, int precision, double *dA_up, double *dA_dn, void *ws,
                                       size_t ws_bytes, qmc_stream_t stream)
 {
-    if (precision == QMC_PREC_F64) return qmc_logpsi_backward(sys, n_walk, R, dinv, g, dA_up, dA_dn, stream);
+    if (precision == QMC_PREC_F64 || precision == QMC_PREC_F64_TCA4)
+        return qmc_logpsi_backward(sys, n_walk, R, dinv, g, dA_up, dA_dn, stream);
     if (!sys || n_walk < 0) return invalid("qmc_logpsi_backward_ex: bad argument");
     if (precision != QMC_PREC_MIXED) return invalid("qmc_logpsi_backward_ex: precision");
     if (!dA_up || !dA_dn || (n_walk > 0 && (!R || !dinv || !g || !ws)))
@@ -1162,7 +1170,7 @@ extern "C" int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const 
     if (n_walk == 0) return QMC_OK;
     const int dev = sys->device;
     if (dev < 0 || dev >= kMaxDevices) return invalid("qmc_walkers_eval_static: device index out of range");
-    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16)
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_F64_TCA4)
         return invalid("qmc_walkers_eval_static: precision");
     const Plan p = make_plan(sys, precision, out->dinv == nullptr);
     if (bytes_for(p, 1) > kStaticScratchBytes) {
@@ -1297,7 +1305,7 @@ extern "C" int qmc_srmc_reconfigure(int n_walk, const double *weight, uint64_t s
 extern "C" int qmc_dmc_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t *bytes)
 {
     if (!sys || !bytes || n_walk < 0) return invalid("qmc_dmc_workspace_size: bad argument");
-    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("qmc_dmc_workspace_size: precision");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_F64_TCA4) return invalid("qmc_dmc_workspace_size: precision");
     const Plan p = make_plan(sys, precision, true);
     *bytes = dmc_own_bytes(n_walk, sys->d.n_elec) + bytes_for(p, std::min(n_walk, 65535));
     return QMC_OK;
@@ -1310,7 +1318,7 @@ extern "C" int qmc_dmc_step(const qmc_system *sys, int n_walk, const qmc_walker_
     if (!sys || !prm) return invalid("qmc_dmc_step: null argument");
     if (n_walk < 0 || n_walk > kMaxSrmcWalkers) return invalid("qmc_dmc_step: need 0 <= n_walk <= 2^24");
     if (!(prm->tau > 0.0) || !isfinite(prm->tau)) return invalid("qmc_dmc_step: tau must be positive and finite");
-    if (prm->precision < QMC_PREC_F64 || prm->precision > QMC_PREC_MIXED_BF16) return invalid("qmc_dmc_step: precision");
+    if (prm->precision < QMC_PREC_F64 || prm->precision > QMC_PREC_F64_TCA4) return invalid("qmc_dmc_step: precision");
     if (n_walk == 0) return QMC_OK;
     if (!state_ok(in) || !state_ok(out) || !ws) return invalid("qmc_dmc_step: null pointer");
     if (in->R == out->R || in->drift == out->drift || in->e_loc == out->e_loc || in->status == out->status)
@@ -1381,7 +1389,7 @@ int pool_for(int dev, StreamPool **out)
 int check_segments(const qmc_segment *segs, int n_seg, int precision)
 {
     if (!segs || n_seg < 1) return invalid("batch: need at least one segment");
-    if (precision < QMC_PREC_F64 || precision > QMC_PREC_MIXED_BF16) return invalid("batch: precision");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_F64_TCA4) return invalid("batch: precision");
     for (int i = 0; i < n_seg; ++i) {
         if (!segs[i].sys || segs[i].n_walk < 0) return invalid("batch: bad segment");
         if (segs[i].sys->device != segs[0].sys->device) return invalid("batch: segments on different devices");
