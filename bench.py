@@ -341,6 +341,7 @@ def cfree_bench(q, R, prec, flush, e0, e1):
     return res, out
 
 
+def dmc_bench(q, R, prec, flush, e0, e1, t_eval_ms):
     """One fixed-node DMC step with constant population (qmc_dmc_step: move
     Eq. 1, evaluation, weight Eq. 3, reconfiguration Sec. II.B, copy of the
     drawn walkers) on the same batch, timed like the evaluation; the MC

@@ -239,7 +239,7 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  * c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
  * QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1,
- * expire_kernels = 7, f64_kappa_max = 1e4.
+ * expire_kernels = 7, f64_kappa_max = 1e4 (1e3 up to 256 electrons of one spin).
  * qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous
  * choice.

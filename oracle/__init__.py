@@ -39,6 +39,8 @@ class _OSys(C.Structure):
         ("n_up", C.c_int), ("n_dn", C.c_int), ("A_up", _d), ("A_dn", _d),
         ("eps", C.c_double), ("R2", _d), ("unscreened", C.c_int),
         ("sh_ao0", _i), ("sh_nao", _i),
+        ("jas_on", C.c_int), ("ja_par", C.c_double), ("ja_anti", C.c_double), ("jb_ee", C.c_double),
+        ("ja_en", _d), ("jb_en", _d),
     ]
 
 
@@ -66,7 +68,7 @@ def lib():
             L.oracle_eval.argtypes = [vp, C.c_int, _d, C.c_int, _d, _d, _d, _d, _d, _d,
                                       C.POINTER(C.c_uint), _d]
             L.oracle_eval_debug.argtypes = [vp, _d, C.c_int, _i, _i, _d, _d, _d, _d, _d, _d, _d,
-                                            _d, C.POINTER(C.c_uint)]
+                                            _d, C.POINTER(C.c_uint), _d]
             L.oracle_lu_inverse.argtypes = [C.c_int, _d, _d, _d, _d]
             L.oracle_logpsi_grad.argtypes = [vp, C.c_int, _d, _d, C.c_int, _d, _d]
             L.oracle_ao_points.argtypes = [vp, C.c_int, C.c_int, _d, _d]
@@ -92,7 +94,10 @@ def _p(a, t=_d):
 class Oracle:
     """Oracle bound to one system.  Keeps its own FP64 copies of the inputs."""
 
-    def __init__(self, system, unscreened: bool = False):
+    def __init__(self, system, unscreened: bool = False, jastrow=None):
+        """jastrow: None, or dict(a_par, a_anti, b_ee, a_en [n_atom], b_en [n_atom]) -- the
+        factor e^J with J = sum_{i<j} a r_ij / (1 + b_ee r_ij) (a = a_par for equal
+        spins, a_anti otherwise) - sum_{i,a} a_en[a] r_ia / (1 + b_en[a] r_ia)."""
         s = system
         self.system = s
         self._keep = []
@@ -123,6 +128,11 @@ class Oracle:
         st.A_up, st.A_dn = _p(f64(s.A_up)), _p(f64(s.A_dn))
         st.eps = float(s.eps)
         st.unscreened = 1 if unscreened else 0
+        if jastrow is not None:
+            st.jas_on = 1
+            st.ja_par, st.ja_anti, st.jb_ee = (float(jastrow[k]) for k in ("a_par", "a_anti", "b_ee"))
+            st.ja_en = _p(f64(np.broadcast_to(np.asarray(jastrow["a_en"], np.float64), (s.n_atom,))))
+            st.jb_en = _p(f64(np.broadcast_to(np.asarray(jastrow["b_en"], np.float64), (s.n_atom,))))
         self._sh_ao0 = np.zeros(s.n_shell, np.int32)
         self._sh_nao = np.zeros(s.n_shell, np.int32)
         st.sh_ao0, st.sh_nao = _p(self._sh_ao0, _i), _p(self._sh_nao, _i)
@@ -164,11 +174,11 @@ class Oracle:
                  B=np.zeros((self.N, 5, cap)), C=np.zeros(5 * nu * nu + 5 * nd * nd),
                  logabs=np.zeros(2), sign=np.zeros(2), drift=np.zeros((self.N, 3)),
                  parts=np.zeros(4), e_loc=np.zeros(1), dinv=np.zeros(nu * nu + nd * nd),
-                 status=np.zeros(1, np.uint32))
+                 status=np.zeros(1, np.uint32), jastrow=np.zeros(1))
         rc = lib().oracle_eval_debug(C.byref(self._st), _p(R1), cap, _p(o["cnt"], _i), _p(o["idx"], _i),
                                      _p(o["B"]), _p(o["C"]), _p(o["logabs"]), _p(o["sign"]),
                                      _p(o["drift"]), _p(o["parts"]), _p(o["e_loc"]), _p(o["dinv"]),
-                                     o["status"].ctypes.data_as(C.POINTER(C.c_uint)))
+                                     o["status"].ctypes.data_as(C.POINTER(C.c_uint)), _p(o["jastrow"]))
         assert rc == 0
         o["C_up"] = o["C"][: 5 * nu * nu].reshape(5, nu, nu)
         o["C_dn"] = o["C"][5 * nu * nu:].reshape(5, nd, nd)
@@ -176,6 +186,8 @@ class Oracle:
         o["dinv_dn"] = o["dinv"][nu * nu:].reshape(nd, nd)
         o["e_loc"] = float(o["e_loc"][0])
         o["status"] = int(o["status"][0])
+        o["jastrow"] = float(o["jastrow"][0])
+        o["logpsi"] = float(o["logabs"].sum()) + o["jastrow"]
         return o
 
     def logpsi_grad(self, R, g, nthreads: int = 0):

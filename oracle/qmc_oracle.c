@@ -58,6 +58,14 @@ typedef struct {
     int unscreened;           /* 1: every AO active (no screening) */
     const int *sh_ao0;        /* [n_shell] first AO of each shell (oracle_shell_ranges) */
     const int *sh_nao;        /* [n_shell] number of AOs of each shell */
+    /* Jastrow factor e^J (Sec. II.C, the J of Eq. psit), off unless jas_on:
+     * J = sum_{i<j} U_ee(r_ij) + sum_i sum_a U_en(r_ia),
+     * U_ee(r) = a r / (1 + b_ee r) with a = ja_par (same spins) or ja_anti,
+     * U_en(r) = -ja_en[a] r / (1 + jb_en[a] r).                          */
+    int jas_on;
+    double ja_par, ja_anti, jb_ee;
+    const double *ja_en;      /* [n_atom] */
+    const double *jb_en;      /* [n_atom] */
 } osys;
 
 /* AOs are stored shell by shell; record each shell's contiguous AO range. */
@@ -328,6 +336,47 @@ static double v_ee(const double *R, int N)
 }
 
 /* ------------------------------------------------------------------ */
+/* The Jastrow factor of one walker: J, and per electron its gradient g_i =
+ * grad_i J and Laplacian L_i = lap_i J.  Pade form U(r) = a r / (1 + b r):
+ * U' = a / (1 + b r)^2, U'' = -2 a b / (1 + b r)^3, lap_i U(|r_i - x|) =
+ * U'' + 2 U' / r, grad_i U = U' (r_i - x) / r.  Pairs in natural order.    */
+static double jastrow(const osys *s, const double *R, int N, double *g /*[N][3]*/, double *L /*[N]*/)
+{
+    double J = 0.0;
+    for (int i = 0; i < 3 * N; ++i) g[i] = 0.0;
+    for (int i = 0; i < N; ++i) L[i] = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            const double a = ((i < s->n_up) == (j < s->n_up)) ? s->ja_par : s->ja_anti, b = s->jb_ee;
+            double d[3];
+            for (int l = 0; l < 3; ++l) d[l] = R[3 * i + l] - R[3 * j + l];
+            const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const double q = 1.0 + b * r;
+            const double u = a * r / q, u1 = a / (q * q), u2 = -2.0 * a * b / (q * q * q);
+            J += u;
+            for (int l = 0; l < 3; ++l) {
+                g[3 * i + l] += u1 * d[l] / r;
+                g[3 * j + l] -= u1 * d[l] / r;
+            }
+            L[i] += u2 + 2.0 * u1 / r;
+            L[j] += u2 + 2.0 * u1 / r;
+        }
+    for (int i = 0; i < N; ++i)
+        for (int at = 0; at < s->n_atom; ++at) {
+            const double a = -s->ja_en[at], b = s->jb_en[at];
+            double d[3];
+            for (int l = 0; l < 3; ++l) d[l] = R[3 * i + l] - s->Q[3 * at + l];
+            const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const double q = 1.0 + b * r;
+            const double u = a * r / q, u1 = a / (q * q), u2 = -2.0 * a * b / (q * q * q);
+            J += u;
+            for (int l = 0; l < 3; ++l) g[3 * i + l] += u1 * d[l] / r;
+            L[i] += u2 + 2.0 * u1 / r;
+        }
+    return J;
+}
+
+/* ------------------------------------------------------------------ */
 /* One walker, full evaluation.  Outputs:
  *   logabs[2], sgn[2] per spin; drift[N][3]; parts[4] = T, V_en, V_ee, V_nn;
  *   e_loc; dinv (optional) [n_up*n_up + n_dn*n_dn], D^-1 of each spin with
@@ -342,7 +391,7 @@ typedef struct {
 
 static unsigned eval_one(const osys *s, const double *R, double vnn,
                          double *logabs, double *sgn, double *drift, double *parts,
-                         double *e_loc, double *dinv, const odebug *dbg)
+                         double *e_loc, double *dinv, const odebug *dbg, double *jas_out)
 {
     int N = s->n_up + s->n_dn;
     unsigned status = 0;
@@ -390,6 +439,25 @@ static unsigned eval_one(const osys *s, const double *R, double vnn,
         doff += (size_t)ns * ns;
         free(C); free(D); free(Dinv);
     }
+    /* Jastrow: Psi = e^J Det_up Det_dn, so grad_i Psi / Psi = g_i + b_i and
+     * lap_i Psi / Psi = L_i + |g_i|^2 + 2 g_i . b_i + lap_i Det / Det        */
+    double J = 0.0;
+    if (s->jas_on) {
+        double *g = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+        double *L = (double *)malloc(sizeof(double) * (size_t)N);
+        J = jastrow(s, R, N, g, L);
+        for (int i = 0; i < N; ++i) {
+            double gb = 0.0, gg = 0.0;
+            for (int l = 0; l < 3; ++l) {
+                gg += g[3 * i + l] * g[3 * i + l];
+                gb += g[3 * i + l] * drift[3 * i + l];
+            }
+            T += -0.5 * (L[i] + gg + 2.0 * gb);
+            for (int l = 0; l < 3; ++l) drift[3 * i + l] += g[3 * i + l];
+        }
+        free(g); free(L);
+    }
+    if (jas_out) *jas_out = J;
     double ven = v_en(s, R, N), vee = v_ee(R, N);
     parts[0] = T; parts[1] = ven; parts[2] = vee; parts[3] = vnn;
     *e_loc = T + ven + vee + vnn;
@@ -413,11 +481,11 @@ int oracle_eval(const osys *s, int W, const double *R, int nthreads,
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int w = 0; w < W; ++w) {
-        double la[2], sg[2];
+        double la[2], sg[2], J;
         unsigned st = eval_one(s, &R[(size_t)w * 3 * N], vnn, la, sg, &drift[(size_t)w * 3 * N],
-                               &e_parts[4 * (size_t)w], &e_loc[w], dinv ? &dinv[w * dsz] : NULL, NULL);
+                               &e_parts[4 * (size_t)w], &e_loc[w], dinv ? &dinv[w * dsz] : NULL, NULL, &J);
         logabs[2 * w] = la[0]; logabs[2 * w + 1] = la[1];
-        logpsi[w] = la[0] + la[1];
+        logpsi[w] = la[0] + la[1] + J;
         sign[w] = sg[0] * sg[1];
         status[w] = st;
     }
@@ -426,11 +494,11 @@ int oracle_eval(const osys *s, int W, const double *R, int nthreads,
 
 int oracle_eval_debug(const osys *s, const double *R, int cap, int *cnt, int *idx, double *B,
                       double *C, double *logabs, double *sgn, double *drift, double *parts,
-                      double *e_loc, double *dinv, unsigned *status)
+                      double *e_loc, double *dinv, unsigned *status, double *jas)
 {
     odebug dbg = { cap, cnt, idx, B, C };
     if (cap < s->n_ao) return -1;
-    *status = eval_one(s, R, oracle_vnn(s), logabs, sgn, drift, parts, e_loc, dinv, &dbg);
+    *status = eval_one(s, R, oracle_vnn(s), logabs, sgn, drift, parts, e_loc, dinv, &dbg, jas);
     return 0;
 }
 
@@ -473,7 +541,7 @@ int oracle_logpsi_grad(const osys *s, int W, const double *R, const double *g, i
         for (int w = 0; w < W; ++w) {
             double la[2], sg[2], parts[4], el;
             const double *Rw = &R[(size_t)w * 3 * N];
-            eval_one(s, Rw, vnn, la, sg, drift, parts, &el, dinv, NULL);
+            eval_one(s, Rw, vnn, la, sg, drift, parts, &el, dinv, NULL, NULL);
             size_t doff = 0;
             for (int spin = 0; spin < 2; ++spin) {
                 int ns = spin ? s->n_dn : s->n_up;

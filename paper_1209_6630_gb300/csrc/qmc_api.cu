@@ -379,7 +379,8 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     // (158 electrons x 4096 walkers: 1e8 left one walker at |dlog|Psi|| = 1.4e-6, 1e7 at most
     // 6e-8 for 7% more a4 time); their FP64 recomputation is cheap
     sys->tiles.a4_kappa_max = std::max(nu, nd) <= 256 ? 1e7 : 1e8;
-    sys->tiles.f64_kappa_max = 1e4;
+    // the FP64 path's 1e-10 bar on E_L: at 158 electrons kappa_inf 1e4 left one walker at 1.3e-10
+    sys->tiles.f64_kappa_max = std::max(nu, nd) <= 256 ? 1e3 : 1e4;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
     std::vector<double> atom_R2(na, 0.0);
