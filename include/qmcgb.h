@@ -150,8 +150,34 @@ int qmc_system_load(const qmc_system_desc *desc, int device, qmc_system **out);
 int qmc_system_free(qmc_system *sys);
 
 /* The CRC-32 key of a loaded system's critical data (as checked at load;
- * qmc_system_set_mo recomputes it over the new coefficients). */
+ * qmc_system_set_mo recomputes it over the new coefficients; with a Jastrow
+ * factor set, the key continues over its parameters: a_par, a_anti, b_ee as
+ * three doubles, then a_en[], then b_en[]). */
 int qmc_system_crc32(const qmc_system *sys, uint32_t *crc);
+
+/*
+ * Jastrow factor (Sec. II.C: Psi_T = e^J Det_up Det_dn, the Jastrow of the
+ * trial-function formula with its e-n and e-e terms; the paper leaves the
+ * functions U open, this library takes the Pade form):
+ *   J = sum_{i<j} a r_ij / (1 + b_ee r_ij) - sum_{i,atoms} a_en[at] r / (1 + b_en[at] r),
+ *   a = a_par for two electrons of the same spin, a_anti otherwise
+ *   (a_anti = 1/2, a_par = 1/4 satisfy the electron-electron cusp conditions).
+ * With the factor on, log|Psi| includes J (logabs stays the determinants'),
+ * the drift gains grad J and the kinetic term lap J + |grad J|^2 +
+ * 2 grad J . grad Det / Det; the adjoint d log|Psi| / dA is unchanged (J does
+ * not depend on A).  The Jastrow sums run in FP64 in every precision mode
+ * (O(N^2) per walker).  Off after qmc_system_load and after
+ * qmc_system_set_mo.  enabled = 0 (or j == NULL) switches it off.
+ * Blocking: synchronises the device first.  a_en, b_en: host [n_atom];
+ * b_ee, b_en >= 0.
+ */
+typedef struct {
+    int enabled;
+    double a_par, a_anti, b_ee;
+    const double *a_en;
+    const double *b_en;
+} qmc_jastrow;
+int qmc_system_set_jastrow(qmc_system *sys, const qmc_jastrow *j);
 
 /*
  * qmc_system_set_mo -- replace the MO coefficients a_{k mu} of a loaded
@@ -275,7 +301,7 @@ int qmc_workspace_size(const qmc_system *sys, int n_walk, int precision, size_t 
 
 /* Outputs of one evaluation, device memory owned by the caller. */
 typedef struct {
-    double *logpsi;    /* [W]  log|Psi| = log|Det_up| + log|Det_dn|   (required) */
+    double *logpsi;    /* [W]  log|Psi| = log|Det_up| + log|Det_dn| (+ J)  (required) */
     double *sign;      /* [W]  sign of Psi (0 if singular)            (required) */
     double *logabs;    /* [W][2] log|Det_up|, log|Det_dn|             (optional) */
     double *drift;     /* [W][N][3] grad Psi / Psi, Eq. (2)           (required) */

@@ -46,6 +46,11 @@ C15_MODE = {"float_float": 0, "tensor": 1, "cfree": 2}
 EXPIRE = {"c15": 1, "a4": 2, "adjoint": 4}
 
 
+class Jastrow(C.Structure):
+    _fields_ = [("enabled", _i), ("a_par", C.c_double), ("a_anti", C.c_double), ("b_ee", C.c_double),
+                ("a_en", _vp), ("b_en", _vp)]
+
+
 class WalkerState(C.Structure):
     _fields_ = [("R", _vp), ("drift", _vp), ("e_loc", _vp), ("logpsi", _vp), ("sign", _vp), ("status", _vp)]
 
@@ -85,6 +90,7 @@ def lib():
             L.qmc_system_shell_r2.argtypes = [_vp, _vp]
             L.qmc_system_set_mo.argtypes = [_vp, _i, _vp, _vp]
             L.qmc_system_crc32.argtypes = [_vp, C.POINTER(C.c_uint32)]
+            L.qmc_system_set_jastrow.argtypes = [_vp, C.POINTER(Jastrow)]
             L.qmc_system_set_tiles.argtypes = [_vp, C.POINTER(Tiles)]
             L.qmc_system_get_tiles.argtypes = [_vp, C.POINTER(Tiles)]
             L.qmc_batch_workspace_size.argtypes = [C.POINTER(Segment), _i, _i, C.POINTER(C.c_size_t)]
@@ -113,7 +119,7 @@ def lib():
             L.qmc_dmc_step.argtypes = [_vp, _i, C.POINTER(WalkerState), C.POINTER(WalkerState),
                                        C.POINTER(DmcParams), _vp, _vp, C.c_size_t, _vp]
             for name in ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo",
-                         "qmc_system_crc32",
+                         "qmc_system_crc32", "qmc_system_set_jastrow",
                          "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size",
                          "qmc_batch_eval", "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",
                          "qmc_workspace_size",
@@ -135,6 +141,7 @@ def check(rc):
 
 # every symbol include/qmcgb.h declares
 EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_system_set_mo", "qmc_system_crc32",
+            "qmc_system_set_jastrow",
             "qmc_workspace_size",
             "qmc_system_set_tiles", "qmc_system_get_tiles", "qmc_batch_workspace_size", "qmc_batch_eval",
             "qmc_batch_graph_create", "qmc_graph_launch", "qmc_graph_free",

@@ -11,7 +11,7 @@ import zlib
 import numpy as np
 import torch
 
-from ._lib import (PREC, DTYPE_F32, DTYPE_F64, DmcParams, EvalOut, QmcError, Segment, SystemDesc, Tiles,
+from ._lib import (PREC, DTYPE_F32, DTYPE_F64, DmcParams, EvalOut, Jastrow, QmcError, Segment, SystemDesc, Tiles,
                    WalkerState, check, lib)
 
 __all__ = ["QmcSystem", "QmcBatch", "det_inverse", "LogPsi", "QmcError", "dmc_move", "dmc_weight",
@@ -117,6 +117,18 @@ class QmcSystem:
         out = np.zeros(self.n_shell, np.float64)
         check(lib().qmc_system_shell_r2(self._h, C.c_void_p(out.ctypes.data)))
         return out
+
+    def set_jastrow(self, jastrow=None):
+        """The Jastrow factor (qmc_system_set_jastrow): None switches it off, else a
+        dict(a_par, a_anti, b_ee, a_en, b_en) with a_en, b_en scalars or [n_atom]."""
+        if jastrow is None:
+            check(lib().qmc_system_set_jastrow(self._h, C.byref(Jastrow(enabled=0))))
+            return
+        a_en = np.ascontiguousarray(np.broadcast_to(np.asarray(jastrow["a_en"], np.float64), (self.n_atom,)))
+        b_en = np.ascontiguousarray(np.broadcast_to(np.asarray(jastrow["b_en"], np.float64), (self.n_atom,)))
+        j = Jastrow(enabled=1, a_par=float(jastrow["a_par"]), a_anti=float(jastrow["a_anti"]),
+                    b_ee=float(jastrow["b_ee"]), a_en=C.c_void_p(a_en.ctypes.data), b_en=C.c_void_p(b_en.ctypes.data))
+        check(lib().qmc_system_set_jastrow(self._h, C.byref(j)))
 
     def crc32(self) -> int:
         """The system's CRC-32 key (qmc_system_crc32)."""

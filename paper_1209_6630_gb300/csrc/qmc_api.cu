@@ -367,6 +367,7 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     sys->device = device;
     sys->crc_prefix = crc_pre;
     sys->crc = crc;
+    sys->crc_nojas = crc;
     sys->eps = d->eps;
     sys->tiles.wait_s = 2.0;
     sys->tiles.expire_walker = -1;
@@ -457,6 +458,9 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
         bw_sh0.push_back(nsh);
     }
     const size_t oBA = b.add(bw_ao0.data(), 4 * bw_ao0.size()), oBS = b.add(bw_sh0.data(), 4 * bw_sh0.size());
+    // Jastrow e-n parameters (set by qmc_system_set_jastrow; off at load)
+    std::vector<double> jzero(na, 0.0);
+    const size_t oJa = b.add(jzero.data(), 8 * jzero.size()), oJb = b.add(jzero.data(), 8 * jzero.size());
     // AO derivative values enter the FP16 split scaled by 2^b_exp (bound * 2^b_exp <= 8192)
     double dbound[2] = {0.0, 0.0};
     for (int sh = 0; sh < nsh; ++sh) {
@@ -507,6 +511,10 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     s.ao_shell = reinterpret_cast<const int *>(dev + oAO);
     s.ao_scale = reinterpret_cast<const double *>(dev + oSC);
     s.vnn = vnn;
+    s.jas = 0;
+    s.ja_par = s.ja_anti = s.jb_ee = 0.0;
+    s.ja_en = reinterpret_cast<const double *>(dev + oJa);
+    s.jb_en = reinterpret_cast<const double *>(dev + oJb);
     MixedTables &mt = sys->mixed;
     mt.b_exp = b_exp;
     mt.mask_words = (nsh + 31) / 32;
@@ -548,6 +556,45 @@ extern "C" int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up,
     sys->a_dtype = a_dtype;
     point_mo(sys, static_cast<char *>(sys->mo_dev), mo);
     sys->crc = desc_crc_finish(sys->crc_prefix, sys->d.n_ao, sys->d.n_up, sys->d.n_dn, a_dtype, A_up, A_dn, sys->eps);
+    sys->crc_nojas = sys->crc;
+    sys->d.jas = 0;          // new coefficients: a Jastrow factor must be set again (and keyed again)
+    return QMC_OK;
+}
+
+extern "C" int qmc_system_set_jastrow(qmc_system *sys, const qmc_jastrow *j)
+{
+    if (!sys) return invalid("qmc_system_set_jastrow: null system");
+    const int na = sys->d.n_atom;
+    if (!j || !j->enabled) {
+        sys->d.jas = 0;
+        sys->crc = sys->crc_nojas;
+        return QMC_OK;
+    }
+    if (!j->a_en || !j->b_en) return invalid("qmc_system_set_jastrow: null e-n parameters");
+    const double sc[3] = {j->a_par, j->a_anti, j->b_ee};
+    for (double x : sc)
+        if (!isfinite(x)) return invalid("qmc_system_set_jastrow: non-finite parameter");
+    if (j->b_ee < 0.0) return invalid("qmc_system_set_jastrow: b_ee must be >= 0");
+    for (int a = 0; a < na; ++a)
+        if (!isfinite(j->a_en[a]) || !(j->b_en[a] >= 0.0))
+            return invalid("qmc_system_set_jastrow: e-n parameters must be finite with b_en >= 0");
+    cudaError_t e = cudaSetDevice(sys->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // no evaluation may still read the old values
+    if (e == cudaSuccess)
+        e = cudaMemcpy(const_cast<double *>(sys->d.ja_en), j->a_en, sizeof(double) * na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(const_cast<double *>(sys->d.jb_en), j->b_en, sizeof(double) * na, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_system_set_jastrow");
+    sys->d.jas = 1;
+    sys->d.ja_par = j->a_par;
+    sys->d.ja_anti = j->a_anti;
+    sys->d.jb_ee = j->b_ee;
+    // the Jastrow parameters are critical data too (Sec. V.C): the key continues over them
+    uint32_t r = sys->crc_nojas ^ 0xFFFFFFFFu;
+    r = crc32_update(r, sc, sizeof sc);
+    r = crc32_update(r, j->a_en, sizeof(double) * na);
+    r = crc32_update(r, j->b_en, sizeof(double) * na);
+    sys->crc = r ^ 0xFFFFFFFFu;
     return QMC_OK;
 }
 

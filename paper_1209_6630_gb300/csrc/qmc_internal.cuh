@@ -48,6 +48,11 @@ struct SysDev {
     const double *ao_scale; // [n_ao]
     const double *A64[2];   // [n_ao][n_s] FP64 MO coefficients per spin
     double vnn;
+    // Jastrow factor e^J (off unless jas): U_ee = a r / (1 + jb_ee r), a = ja_par or ja_anti;
+    // U_en = -ja_en[atom] r / (1 + jb_en[atom] r)
+    int jas;
+    double ja_par, ja_anti, jb_ee;
+    const double *ja_en, *jb_en;   // [n_atom]
 };
 
 // Float-pair (hi + lo) copies of the basis for the float-float AO evaluation.
@@ -220,5 +225,6 @@ struct qmc_system {
     int a_dtype = 0;
     uint32_t crc_prefix = 0;          // CRC-32 register after the basis arrays (before A_up)
     uint32_t crc = 0;                 // CRC-32 key of the critical data
+    uint32_t crc_nojas = 0;           // the key without the Jastrow parameters
     double eps = 0.0;
 };
