@@ -38,9 +38,11 @@ def launches_per_step(q, prec, n_walk):
         return 3                      # contraction, Gauss-Jordan, energy
     t = q.tiles()
     n = 2                             # masks, energy
-    if t["c15_mode"] == "tensor":
+    if t["c15_mode"] in ("tensor", "cfree"):
         b = 64 if n_walk > 7 * 128 else (32 if n_walk > 128 else 16)
-        n += 2 * -(-q.N // b)          # slice producer + MMA kernel per batch of electrons (C1..C5)
+        n += 2 * -(-q.N // b)          # slice producer + MMA kernel per batch of electrons (C1..C5, or C1)
+        if t["c15_mode"] == "cfree":
+            n += 2                    # row exponents of D^-1, v = D^-1 A^T with the drift / Laplacian
     else:
         n += 2                        # float-float C1/C5, tensor-core C2..C4
     nmax = max(q.n_up, q.n_dn)
@@ -62,8 +64,10 @@ def dtype_of(q, prec):
     if prec == "f64":
         return "f64"
     t = q.tiles()
-    c15 = "bf16 exact slices on tcgen05" if t["c15_mode"] == "tensor" else "float-float FP32 pipes"
+    c15 = "bf16 exact slices on tcgen05" if t["c15_mode"] in ("tensor", "cfree") else "float-float FP32 pipes"
     c24 = "fp16x3" if prec == "mixed" else "bf16x3"
+    if t["c15_mode"] == "cfree":
+        c24 = "none (C-free: v = D^-1 A^T bf16 exact slices on tcgen05, AO derivatives fp32 / float-float)"
     a4 = {"float_float": "float-float + FP64 near nodes",
           "tensor": "float-float panels, bf16 exact-slice tcgen05 updates + FP64 near nodes"}.get(t["a4_mode"], "FP64")
     return f"f64 (C1,C5 {c15}; C2-C4 {c24} tcgen05; a4 {a4})"
@@ -86,6 +90,8 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="keep default tiles (no autotuner)")
     p.add_argument("--no-dmc", action="store_true", help="skip the full DMC step timing")
     p.add_argument("--no-cfree", action="store_true", help="skip the C-free variant's timing")
+    p.add_argument("--c15-mode", default=None, choices=["float_float", "tensor", "cfree"],
+                   help="override the C1..C5 arithmetic of the timed evaluation")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the 1731-electron forward comparison and the mixed batch")
     return p.parse_args()
@@ -216,9 +222,11 @@ def stage_roofline(q, prec, stage_mean, kbar, W, pk):
         kern_ms = {"k_contract_f64": stage_mean[0], "k_gj": stage_mean[1], "k_drift_energy": stage_mean[2]}
     else:
         a4_kern = {"float_float": "k_gj_ff+k_gj", "tensor": "k_gt_panel+k_gt_update+k_gj"}.get(t["a4_mode"], "k_gj")
-        c15_kern = "k_c15_prep+k_c15_mma" if t["c15_mode"] == "tensor" else "k_c15_ff"
+        c15_kern = {"tensor": "k_c15_prep+k_c15_mma", "cfree": "k_c15_prep+k_c15_mma (C1)"}.get(t["c15_mode"],
+                                                                                           "k_c15_ff")
         kern_ms = {"k_shell_mask": stage_mean[4], c15_kern: stage_mean[5], "k_tc_contract": stage_mean[6],
-                   a4_kern: stage_mean[1], "k_drift_energy": stage_mean[2]}
+                   a4_kern: stage_mean[1],
+                   "k_vd_mma+k_drift_energy" if t["c15_mode"] == "cfree" else "k_drift_energy": stage_mean[2]}
     kern = max(kern_ms, key=kern_ms.get)
     ts = kern_ms[kern] / 1e3
     fp64_src = "FP64 DFMA: 152 SMs x 4 flop/clk x sm_max_mhz (the measured DFMA rate is 1.20 TFLOP/s)"
@@ -246,6 +254,16 @@ def stage_roofline(q, prec, stage_mean, kbar, W, pk):
                 "work": "10 sum_s N_s^2 Kbar flop per walker (the five products C1..C5)",
                 "issued": "C1, C5: 21 BF16 slice-pair products each; C2..C4: 3 fp16 split products each"}
         roof["frac_issued"] = (2 * 21 + 3 * 3) * 2.0 * prod / ts / 1e12 / bf16 if bf16 else None
+    elif kern == "k_c15_prep+k_c15_mma (C1)":
+        roof = {"bound": "tensor", "achieved": 2.0 * prod / ts / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "peak_source": "measured dense bf16 sustained (MEASURED_PEAKS.json)",
+                "work": "2 sum_s N_s^2 Kbar flop per walker (C1)", "issued": "21 BF16 slice-pair products"}
+        roof["frac_issued"] = 21 * 2.0 * prod / ts / 1e12 / bf16 if bf16 else None
+    elif kern == "k_vd_mma+k_drift_energy":
+        roof = {"bound": "tensor", "achieved": 2.0 * prod / ts / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "peak_source": "measured dense bf16 sustained (MEASURED_PEAKS.json)",
+                "work": "2 sum_s N_s^2 Kbar flop per walker (v = D^-1 A^T)", "issued": "21 BF16 slice-pair products"}
+        roof["frac_issued"] = 21 * 2.0 * prod / ts / 1e12 / bf16 if bf16 else None
     elif kern == "k_c15_ff":
         roof = {"bound": "alu", "achieved": 4.0 * prod / ts / 1e12, "peak": fp32_inst_peak / 4.5, "unit": "TFLOP/s",
                 "peak_source": "FP32 pipe / 4.5: 9 FP32 instructions per float-float product",
@@ -602,6 +620,9 @@ def main():
         from paper_1209_6630_gb300.autotune import autotune
         tuned = autotune(q, R[: min(W, 1024)], precision=prec)
         tiles = dict(tuned["tiles"], stage_ms=tuned.get("stage_ms"))
+    if a.c15_mode:
+        q.set_tiles(c15_mode=a.c15_mode)
+        tiles = dict(tiles, c15_mode=a.c15_mode)
     wsbuf = q.workspace(W, prec)
     out = q.alloc_out(W, want_dinv=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)

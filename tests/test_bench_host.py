@@ -52,3 +52,19 @@ def test_traffic_lookup_requires_matching_source():
     assert bench.kernel_traffic("no_such_kernel", "1056e") is None
     v = bench.kernel_traffic("k_gj_ff+k_gj", "1056e")
     assert v is None or v > 1e10
+
+
+def test_bench_calls_only_defined_or_imported_names():
+    """Every plain function name bench.py calls is defined in it, imported, or a builtin
+    (the GPU legs only run on the GPU machine, so a missing helper would surface there first)."""
+    import ast
+    import builtins
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    tree = ast.parse(src)
+    known = {n.name for n in ast.walk(tree) if isinstance(n, (ast.FunctionDef, ast.ClassDef))}
+    for n in ast.walk(tree):
+        if isinstance(n, (ast.Import, ast.ImportFrom)):
+            known |= {(a.asname or a.name).split(".")[0] for a in n.names}
+    calls = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
+    missing = sorted(c for c in calls if c not in known and not hasattr(builtins, c))
+    assert not missing, missing
