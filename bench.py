@@ -366,7 +366,8 @@ def dmc_bench(q, R, prec, flush, e0, e1, t_eval_ms):
     kernels' share is the difference to the evaluation alone."""
     import torch
     W = int(R.shape[0])
-    a = q.init_state(R, precision=prec)
+    a0 = q.init_state(R, precision=prec)
+    a = {k: v.clone() for k, v in a0.items()}
     b = q.walker_state(W)
     e_t = float(a["e_loc"].mean().item())
     ws = torch.empty(q.dmc_workspace_size(W, prec), dtype=torch.uint8, device=R.device)
@@ -376,21 +377,25 @@ def dmc_bench(q, R, prec, flush, e0, e1, t_eval_ms):
         q.dmc_step(a, b, tau, e_t, 17, n, precision=prec, stats=stats, ws=ws)
         a, b = b, a
     torch.cuda.synchronize()
+    # every timed step starts from the same evaluated population (the walkers of the batch):
+    # without drift limiting or equilibration a population of unequilibrated all-electron walkers
+    # collapses onto near-nucleus configurations within a few steps (E_L -> -inf without the cusp)
     ts = []
     for n in range(2, 5):
+        for k in a:
+            a[k].copy_(a0[k])
         flush.zero_()
         e0.record()
         q.dmc_step(a, b, tau, e_t, 17, n, precision=prec, stats=stats, ws=ws)
         e1.record()
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
-        a, b = b, a
     t = sum(ts) / len(ts)
     sv = stats.cpu().numpy()
     res = {"walker_steps_per_s": W / (t / 1e3), "ms_per_step": t, "tau": tau,
            "mc_kernels_ms": t - t_eval_ms, "accepted": int(sv[3]), "walkers_alive": int(sv[1]),
            "what": "move (Eq. 1) + evaluation + fixed-node weight (Eq. 3) + SRMC draw (Sec. II.B) + copy"}
-    del a, b, ws
+    del a, a0, b, ws
     torch.cuda.empty_cache()
     return res
 

@@ -85,8 +85,9 @@ enum {
                                 with a4 by the tensor-core Gauss-Jordan of the mixed path
                                 (float-float panels, rank-32 updates from exact BF16 slices;
                                 the float-float elimination where that kernel does not fit)
-                                and FP64 recomputation of every matrix whose kappa_inf
-                                exceeds qmc_tiles.f64_kappa_max: a cheaper FP64-accurate a4
+                                and the FP64 elimination (one CTA per matrix, the FP64
+                                C1 kept) of every matrix whose kappa_inf exceeds
+                                qmc_tiles.f64_kappa_max: a cheaper FP64-accurate a4
                                 (Sec. IV.B inversion step; Table 2 caption: the inversion in
                                 double precision) */
 };
@@ -265,7 +266,8 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  * c15_mode = QMC_C15_TENSOR where the system fits that
  * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
  * QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1,
- * expire_kernels = 7, f64_kappa_max = 1e4 (1e3 up to 256 electrons of one spin).
+ * expire_kernels = 7, f64_kappa_max = 1e6 (1, i.e. every matrix in FP64, up to 256
+ * electrons of one spin).
  * qmc_system_set_tiles returns QMC_ERR_INVALID for
  * other values (or a tensor mode that does not fit) and keeps the previous
  * choice.

@@ -20,9 +20,11 @@
 // through two buffers (B rows by cp.async, A slices stored by all threads),
 // one thread issuing the MMAs, mbarrier commits, bounded waits.  Epilogue:
 // v = 2^(E + G_mu) (acc0 + acc1 + acc2 + acc3) in FP64, and for every active
-// AO of the walker the gradient (FP32) and Laplacian (float-float) of the AO
-// at r_e, accumulated into the drift (FP64 sums of FP32 products) and the
-// Laplacian (FP64).  Output vd[w][e] = (drift_x, drift_y, drift_z, lap_e).
+// AO of the walker the gradient and Laplacian of the AO at r_e in FP32 (radial
+// part once per shell), each product with v in FP64 and accumulated in FP64:
+// the drift and Laplacian carry a relative error of a few 2^-24 per term (no
+// accumulation error), where the C2..C5 products rounded every partial sum.
+// Output vd[w][e] = (drift_x, drift_y, drift_z, lap_e).
 #include "ao_ff.cuh"
 #include "qmc_internal.cuh"
 #include "slices.cuh"
@@ -53,7 +55,37 @@ struct VdArgs {
     double *vd;                    // [nw][N][4]
     uint32_t *wstatus;
     unsigned long long wait_ns;
+    const float *pgf, *pcf, *scf;  // FP32 exponents, coefficients [n_prim], AO scales [n_ao]
+    const float *Qhi, *Qlo;        // nuclear positions as float pairs [n_atom][3]
 };
+
+// Radial part of a shell at the electron position, FP32 (the position's
+// float pair minus the nucleus' float pair, then rounded): d, g = sum_p c_p e_p,
+// gd = sum_p c_p gamma_p e_p, gl = sum_p c_p (4 gamma_p d2 - 6) gamma_p e_p.
+struct R32 {
+    float dx, dy, dz, g, gd, gl;
+};
+
+__device__ __forceinline__ void r32_radial(const SysDev &s, const VdArgs &a, int sh, const float2 *r2, R32 &o)
+{
+    const int at = s.sh_atom[sh];
+    o.dx = (r2[0].x - a.Qhi[3 * at]) + (r2[0].y - a.Qlo[3 * at]);
+    o.dy = (r2[1].x - a.Qhi[3 * at + 1]) + (r2[1].y - a.Qlo[3 * at + 1]);
+    o.dz = (r2[2].x - a.Qhi[3 * at + 2]) + (r2[2].y - a.Qlo[3 * at + 2]);
+    const float d2 = o.dx * o.dx + o.dy * o.dy + o.dz * o.dz;
+    float g = 0.f, gd = 0.f, gl = 0.f;
+    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
+    for (int p = 0; p < np; ++p) {
+        const float gam = a.pgf[p0 + p];
+        const float ce = a.pcf[p0 + p] * expf(-gam * d2);
+        g += ce;
+        gd += gam * ce;
+        gl += (4.f * gam * d2 - 6.f) * gam * ce;
+    }
+    o.g = g;
+    o.gd = gd;
+    o.gl = gl;
+}
 
 __global__ void k_vd_rowexp(int nw, int n_up, int n_dn, size_t msz, const double *__restrict__ Dinv,
                             int *__restrict__ rexp)
@@ -230,7 +262,7 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: v for 32 AOs of this walker row, then the AO derivatives at r_e
-        FfRadial rd;
+        R32 rd;
         int last_sh = -1;
         double *vbuf = reinterpret_cast<double *>(base);   // [16][512]: the operand buffers are idle here
         for (int h = 0; h < 2; ++h) {
@@ -256,29 +288,33 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
                 const double vmu = vbuf[q * kVdThreads + t] * pow2d(Ee + a.gexp[spin][mu]);
                 if (sh != last_sh) {
                     last_sh = sh;
-                    ff_radial(s, a.fb, sh, r2, rd);
+                    r32_radial(s, a, sh, r2, rd);
                 }
-                float2 val, lp;
-                ff_angular(s, a.fb, mu, rd, val, lp);
-                // gradient in FP32 from the same radial part
+                // gradient and Laplacian of chi_mu = c P(d) g in FP32 (lap = c (lap P g +
+                // P (gl - 4 L gd)), grad_x = c (dP/dx g - 2 gd dx P)), products with v in FP64
                 const int pw2 = s.ao_pow[mu];
                 const int nx = pw2 & 255, ny = (pw2 >> 8) & 255, nz = (pw2 >> 16) & 255;
-                const float dx = rd.dx.x + rd.dx.y, dy = rd.dy.x + rd.dy.y, dz = rd.dz.x + rd.dz.y;
+                const float dx = rd.dx, dy = rd.dy, dz = rd.dz;
                 auto ip = [](float x, int n) {
                     float y = 1.f;
                     for (int i = 0; i < n; ++i) y *= x;
                     return y;
                 };
                 const float px = ip(dx, nx), py = ip(dy, ny), pz = ip(dz, nz);
-                const float P = px * py * pz, g = rd.g.x + rd.g.y, m2gd = -2.f * (rd.gd.x + rd.gd.y);
-                const float c = a.fb.sc[mu].x + a.fb.sc[mu].y;
+                const float P = px * py * pz, g = rd.g, m2gd = -2.f * rd.gd;
+                const float c = a.scf[mu];
+                const float ddx = nx > 1 ? nx * (nx - 1) * ip(dx, nx - 2) : 0.f;
+                const float ddy = ny > 1 ? ny * (ny - 1) * ip(dy, ny - 2) : 0.f;
+                const float ddz = nz > 1 ? nz * (nz - 1) * ip(dz, nz - 2) : 0.f;
+                const float lp = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * g +
+                                      P * (rd.gl - 4.f * (nx + ny + nz) * rd.gd));
                 const float g1 = c * ((nx ? nx * ip(dx, nx - 1) : 0.f) * py * pz * g + m2gd * dx * P);
                 const float g2 = c * (px * (ny ? ny * ip(dy, ny - 1) : 0.f) * pz * g + m2gd * dy * P);
                 const float g3 = c * (px * py * (nz ? nz * ip(dz, nz - 1) : 0.f) * g + m2gd * dz * P);
                 b0 += vmu * (double)g1;
                 b1 += vmu * (double)g2;
                 b2 += vmu * (double)g3;
-                lap += vmu * ((double)lp.x + (double)lp.y);
+                lap += vmu * (double)lp;
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -342,6 +378,7 @@ cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables 
     }
     a.vd = vd;
     a.wstatus = wstatus;
+    a.pgf = mt.pgf; a.pcf = mt.pcf; a.scf = mt.scf; a.Qhi = mt.Qhi; a.Qlo = mt.Qlo;
     a.wait_ns = wc.limit_ns;
     const size_t rows = (size_t)nw * s.n_elec;
     k_vd_rowexp<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(nw, s.n_up, s.n_dn, a.msz, Dinv,

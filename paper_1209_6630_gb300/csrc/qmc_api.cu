@@ -380,8 +380,11 @@ extern "C" int qmc_system_load(const qmc_system_desc *d, int device, qmc_system 
     // (158 electrons x 4096 walkers: 1e8 left one walker at |dlog|Psi|| = 1.4e-6, 1e7 at most
     // 6e-8 for 7% more a4 time); their FP64 recomputation is cheap
     sys->tiles.a4_kappa_max = std::max(nu, nd) <= 256 ? 1e7 : 1e8;
-    // the FP64 path's 1e-10 bar on E_L: at 158 electrons kappa_inf 1e4 left one walker at 1.3e-10
-    sys->tiles.f64_kappa_max = std::max(nu, nd) <= 256 ? 1e3 : 1e4;
+    // the FP64 path's 1e-10 bar on E_L: measured on 512 walkers of 1056 electrons, kappa_inf
+    // 1e6 keeps every walker within 4.2e-11 (1e7: 12 walkers above 1e-10); at 158 electrons the
+    // float-pair elimination alone moved one walker's E_L by 1.3e-10 (kappa_inf below 1e3, T
+    // and V cancelling), so small systems recompute every matrix in FP64
+    sys->tiles.f64_kappa_max = std::max(nu, nd) <= 256 ? 1.0 : 1e6;
     sys->max_shell_per_atom = max_ao_atom;
     sys->R2_host.resize(nsh);
     std::vector<double> atom_R2(na, 0.0);
@@ -948,11 +951,17 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             if (p.tcgj) e = launch_gj_tc(ffj, nj, c.gjtc, st, p.kappa_max, wc);
             else e = launch_gj_ff(ffj, nj, st, sys->tiles.gj_panel, p.kappa_max);
             if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: float-float Gauss-Jordan launch");
-            int e_off[2], q = 0;
-            for (int spin = 0; spin < 2; ++spin)
-                if (spin ? s.n_dn : s.n_up) e_off[q++] = spin ? s.n_up : 0;
-            e = launch_gj_redo(jobs, nj, c.redo_scratch, st, sys->tiles.gj_panel, &s, Rc, e_off);
-            if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: FP64 recomputation launch");
+            if (!p.f64tc) {
+                // near-node matrices: C1 again in FP64 (the mixed C1 carries its ~2^-40 error), then
+                // the FP64 elimination, multi-CTA for the first kRedoMax of them
+                int e_off[2], q = 0;
+                for (int spin = 0; spin < 2; ++spin)
+                    if (spin ? s.n_dn : s.n_up) e_off[q++] = spin ? s.n_up : 0;
+                e = launch_gj_redo(jobs, nj, c.redo_scratch, st, sys->tiles.gj_panel, &s, Rc, e_off);
+                if (e != cudaSuccess) return cuda_fail(e, "qmc_walkers_eval: FP64 recomputation launch");
+            }
+            // (QMC_PREC_F64_TCA4: C1 is FP64 already; every flagged matrix goes to the batched
+            // FP64 elimination below, one CTA per matrix)
             for (int q = 0; q < nj; ++q) jobs[q].only_redo = 1;
         }
         e = launch_gj(jobs, nj, st, sys->tiles.gj_panel);
