@@ -57,35 +57,10 @@ struct VdArgs {
     unsigned long long wait_ns;
     const float *pgf, *pcf, *scf;  // FP32 exponents, coefficients [n_prim], AO scales [n_ao]
     const float *Qhi, *Qlo;        // nuclear positions as float pairs [n_atom][3]
+    int e0;                        // first electron of this launch's batch
+    unsigned char *astage;         // per CTA of the batch: the sliced D^-1 rows, one A image per K stage
+    size_t astage_per;             // bytes per CTA
 };
-
-// Radial part of a shell at the electron position, FP32 (the position's
-// float pair minus the nucleus' float pair, then rounded): d, g = sum_p c_p e_p,
-// gd = sum_p c_p gamma_p e_p, gl = sum_p c_p (4 gamma_p d2 - 6) gamma_p e_p.
-struct R32 {
-    float dx, dy, dz, g, gd, gl;
-};
-
-__device__ __forceinline__ void r32_radial(const SysDev &s, const VdArgs &a, int sh, const float2 *r2, R32 &o)
-{
-    const int at = s.sh_atom[sh];
-    o.dx = (r2[0].x - a.Qhi[3 * at]) + (r2[0].y - a.Qlo[3 * at]);
-    o.dy = (r2[1].x - a.Qhi[3 * at + 1]) + (r2[1].y - a.Qlo[3 * at + 1]);
-    o.dz = (r2[2].x - a.Qhi[3 * at + 2]) + (r2[2].y - a.Qlo[3 * at + 2]);
-    const float d2 = o.dx * o.dx + o.dy * o.dy + o.dz * o.dz;
-    float g = 0.f, gd = 0.f, gl = 0.f;
-    const int p0 = s.sh_pstart[sh], np = s.sh_nprim[sh];
-    for (int p = 0; p < np; ++p) {
-        const float gam = a.pgf[p0 + p];
-        const float ce = a.pcf[p0 + p] * expf(-gam * d2);
-        g += ce;
-        gd += gam * ce;
-        gl += (4.f * gam * d2 - 6.f) * gam * ce;
-    }
-    o.g = g;
-    o.gd = gd;
-    o.gl = gl;
-}
 
 __global__ void k_vd_rowexp(int nw, int n_up, int n_dn, size_t msz, const double *__restrict__ Dinv,
                             int *__restrict__ rexp)
@@ -122,7 +97,8 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
 
     const SysDev &s = a.s;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int tile = blockIdx.x, e = blockIdx.y;
+    const int tile = blockIdx.x, e = a.e0 + (int)blockIdx.y;
+    unsigned char *ast = a.astage + ((size_t)blockIdx.y * gridDim.x + tile) * a.astage_per;
     const int N = s.n_elec;
     const int spin = e >= s.n_up, ei = spin ? e - s.n_up : e, ns = spin ? s.n_dn : s.n_up;
     const int nspad = a.ns_pad[spin];
@@ -199,8 +175,15 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
             const uint16_t *src = Bsl + j * bstride + (size_t)(v ? mu : 0) * nspad + k0 + 8 * c;
             cp_async16(smem_u32(Bb + j * kVdPlane + a_off64(r, c)), src, v);
         }
+        // A: the stage's six slice planes of D^-1, an image of the shared-memory layout
+        const unsigned char *As = ast + (size_t)sg * kC15Slices * kVdPlane;
+        for (int q = t; q < (int)(kC15Slices * kVdPlane / 16); q += kVdThreads)
+            cp_async16(smem_u32(Ab + 16 * q), As + 16 * (size_t)q, true);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        // A: this thread's 8 entries of D^-1, cut into six exact slices
+    };
+    // this CTA's D^-1 rows cut into six exact slices once, for every K stage (the AO tiles reuse them)
+    for (int sg = 0; sg < nst; ++sg) {
+        const int k0 = sg * kVdK;
         float sl[8][kC15Slices];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -208,12 +191,14 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
             const double d = (pvalid && k < ns) ? drow[k] : 0.0;
             slice6(ff::from_double(d), Ep, sl[i]);
         }
+        unsigned char *Ad = ast + (size_t)sg * kC15Slices * kVdPlane;
 #pragma unroll
         for (int j = 0; j < kC15Slices; ++j)
-            *reinterpret_cast<uint4 *>(Ab + j * kVdPlane + a_off64(prow, pc)) =
+            *reinterpret_cast<uint4 *>(Ad + j * kVdPlane + a_off64(prow, pc)) =
                 make_uint4(bf16_pair(sl[0][j], sl[1][j]), bf16_pair(sl[2][j], sl[3][j]), bf16_pair(sl[4][j], sl[5][j]),
                            bf16_pair(sl[6][j], sl[7][j]));
-    };
+    }
+    __syncthreads();                                       // the block's global writes, before its cp.async reads
 
     for (int at = 0; at < nat && ok; ++at) {
         produce(at, 0, 0);
@@ -262,7 +247,7 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: v for 32 AOs of this walker row, then the AO derivatives at r_e
-        R32 rd;
+        FfRadial rd;
         int last_sh = -1;
         double *vbuf = reinterpret_cast<double *>(base);   // [16][512]: the operand buffers are idle here
         for (int h = 0; h < 2; ++h) {
@@ -288,33 +273,31 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
                 const double vmu = vbuf[q * kVdThreads + t] * pow2d(Ee + a.gexp[spin][mu]);
                 if (sh != last_sh) {
                     last_sh = sh;
-                    r32_radial(s, a, sh, r2, rd);
+                    ff_radial(s, a.fb, sh, r2, rd);
                 }
-                // gradient and Laplacian of chi_mu = c P(d) g in FP32 (lap = c (lap P g +
-                // P (gl - 4 L gd)), grad_x = c (dP/dx g - 2 gd dx P)), products with v in FP64
+                // Laplacian in float-float (the kinetic term cancels against the potential: an FP32
+                // Laplacian left E_L at 2e-5 relative on 2048 walkers of 1056 electrons), the
+                // gradient in FP32 from the same radial part; products with v and sums in FP64
+                float2 val, lp;
+                ff_angular(s, a.fb, mu, rd, val, lp);
                 const int pw2 = s.ao_pow[mu];
                 const int nx = pw2 & 255, ny = (pw2 >> 8) & 255, nz = (pw2 >> 16) & 255;
-                const float dx = rd.dx, dy = rd.dy, dz = rd.dz;
+                const float dx = rd.dx.x + rd.dx.y, dy = rd.dy.x + rd.dy.y, dz = rd.dz.x + rd.dz.y;
                 auto ip = [](float x, int n) {
                     float y = 1.f;
                     for (int i = 0; i < n; ++i) y *= x;
                     return y;
                 };
                 const float px = ip(dx, nx), py = ip(dy, ny), pz = ip(dz, nz);
-                const float P = px * py * pz, g = rd.g, m2gd = -2.f * rd.gd;
+                const float P = px * py * pz, g = rd.g.x + rd.g.y, m2gd = -2.f * (rd.gd.x + rd.gd.y);
                 const float c = a.scf[mu];
-                const float ddx = nx > 1 ? nx * (nx - 1) * ip(dx, nx - 2) : 0.f;
-                const float ddy = ny > 1 ? ny * (ny - 1) * ip(dy, ny - 2) : 0.f;
-                const float ddz = nz > 1 ? nz * (nz - 1) * ip(dz, nz - 2) : 0.f;
-                const float lp = c * ((ddx * py * pz + px * ddy * pz + px * py * ddz) * g +
-                                      P * (rd.gl - 4.f * (nx + ny + nz) * rd.gd));
                 const float g1 = c * ((nx ? nx * ip(dx, nx - 1) : 0.f) * py * pz * g + m2gd * dx * P);
                 const float g2 = c * (px * (ny ? ny * ip(dy, ny - 1) : 0.f) * pz * g + m2gd * dy * P);
                 const float g3 = c * (px * py * (nz ? nz * ip(dz, nz - 1) : 0.f) * g + m2gd * dz * P);
                 b0 += vmu * (double)g1;
                 b1 += vmu * (double)g2;
                 b2 += vmu * (double)g3;
-                lap += vmu * (double)lp;
+                lap += vmu * ((double)lp.x + (double)lp.y);
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -356,9 +339,21 @@ bool vdrift_fits(const SysDev &s)
     return sm <= 227 * 1024;
 }
 
+// electrons per launch (the A staging holds one image per CTA of a batch)
+int vdrift_batch(const SysDev &s) { return s.n_elec < 64 ? s.n_elec : 64; }
+
+size_t vdrift_stage_per(const SysDev &s)
+{
+    const int nsmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const size_t nst = (size_t)((nsmax + 63) / 64 * 64) / kVdK;
+    return nst * kC15Slices * kVdPlane;
+}
+
 size_t vdrift_bytes(const SysDev &s, int nw)
 {
-    return ((sizeof(int) * (size_t)nw * s.n_elec + 255) / 256) * 256;
+    const size_t tiles = (size_t)(nw + TC_M - 1) / TC_M;
+    return ((sizeof(int) * (size_t)nw * s.n_elec + 255) / 256) * 256 +
+           tiles * (size_t)vdrift_batch(s) * vdrift_stage_per(s);
 }
 
 cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
@@ -379,6 +374,8 @@ cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables 
     a.vd = vd;
     a.wstatus = wstatus;
     a.pgf = mt.pgf; a.pcf = mt.pcf; a.scf = mt.scf; a.Qhi = mt.Qhi; a.Qlo = mt.Qlo;
+    a.astage = static_cast<unsigned char *>(scratch) + ((sizeof(int) * (size_t)nw * s.n_elec + 255) / 256) * 256;
+    a.astage_per = vdrift_stage_per(s);
     a.wait_ns = wc.limit_ns;
     const size_t rows = (size_t)nw * s.n_elec;
     k_vd_rowexp<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(nw, s.n_up, s.n_dn, a.msz, Dinv,
@@ -387,8 +384,14 @@ cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables 
     cudaError_t e = cudaFuncSetAttribute(k_vd_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int tiles = (nw + TC_M - 1) / TC_M;
-    k_vd_mma<<<dim3(tiles, s.n_elec), kVdThreads, sm, st>>>(a);
-    return cudaGetLastError();
+    const int nb = vdrift_batch(s);
+    for (int e0 = 0; e0 < s.n_elec; e0 += nb) {
+        a.e0 = e0;
+        const int ne = s.n_elec - e0 < nb ? s.n_elec - e0 : nb;
+        k_vd_mma<<<dim3(tiles, ne), kVdThreads, sm, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace qmc
