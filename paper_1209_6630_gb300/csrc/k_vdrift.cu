@@ -34,10 +34,12 @@ namespace qmc {
 
 namespace {
 
-constexpr int kVdThreads = 512;
+constexpr int kVdThreads = 256;
 constexpr int kVdK = 32;                                      // MOs per stage
-constexpr uint32_t kVdPlane = TC_M * kVdK * 2;                // [128 rows][32 K] 16-bit, 64-byte swizzle: 8 KB
-constexpr uint32_t kVdBuf = 2 * kC15Slices * kVdPlane;        // 6 A planes + 6 B planes: 96 KB
+constexpr int kVdN = 64;                                      // AOs per tile (TMEM columns per accumulator)
+constexpr uint32_t kVdPlane = TC_M * kVdK * 2;                // A: [128 rows][32 K] 16-bit, 64-byte swizzle: 8 KB
+constexpr uint32_t kVdBPlane = kVdN * kVdK * 2;               // B: [64 rows][32 K]: 4 KB
+constexpr uint32_t kVdBuf = kC15Slices * (kVdPlane + kVdBPlane);   // 6 A planes + 6 B planes: 72 KB
 constexpr int kVdAcc = 4;
 
 struct VdArgs {
@@ -84,14 +86,17 @@ __device__ __forceinline__ double pow2d(int e)   // 2^e, |e| <= 1000
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-__global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
+// Two CTAs per SM (256 threads, N = 64 AOs per tile, one operand stage of
+// 72 KB, 256 TMEM columns each): one CTA's epilogue (the AO derivatives, the
+// larger part of the work) runs while the other's copies and MMAs proceed.
+__global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
 {
     extern __shared__ __align__(1024) unsigned char vd_smem[];
     unsigned char *base = vd_smem + ((1024 - (smem_u32(vd_smem) & 1023)) & 1023);
-    int *ao_s = reinterpret_cast<int *>(base + 2 * kVdBuf);    // [n_ao + 128]
+    int *ao_s = reinterpret_cast<int *>(base + kVdBuf);       // [n_ao + kVdN]
     __shared__ uint32_t un_s[256];
     __shared__ int warp_s[kVdThreads / 32];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
 
@@ -115,17 +120,16 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
     }
     __syncthreads();
     const int K = aos_from_mask_n(s, un_s, mw, ao_s, warp_s);
-    const int nat = (K + TC_N - 1) / TC_N;
-    for (int q = K + t; q < nat * TC_N; q += kVdThreads) ao_s[q] = -1;
+    const int nat = (K + kVdN - 1) / kVdN;
+    for (int q = K + t; q < nat * kVdN; q += kVdThreads) ao_s[q] = -1;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
                      :: "r"(smem_u32(&tmem_slot)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -133,21 +137,42 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t mbs[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
-    const uint32_t idesc = umma_idesc_f16_major(TC_M, TC_N, 1, 0, 0);   // BF16, A and B K-major
+    const uint32_t mb = smem_u32(&mbar);
+    const uint32_t idesc = umma_idesc_f16_major(TC_M, kVdN, 1, 0, 0);   // BF16, A and B K-major
     const uint64_t kWait = a.wait_ns;
-
-    // producer role of this thread: 8 consecutive MOs (chunk pc) of D^-1 row (walker prow, e)
-    const int prow = t >> 2, pc = t & 3;
-    const int pw = tile * TC_M + prow;
-    const bool pvalid = pw < a.nw;
-    const double *drow = a.Dinv + (size_t)(pvalid ? pw : 0) * a.msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
-                         (size_t)ei * ns;
-    const int Ep = pvalid ? a.rexp[(size_t)pw * N + e] : 0;
     const uint16_t *Bsl = a.rslice[spin];
     const size_t bstride = (size_t)s.n_ao * nspad;
+    const int nst = nspad / kVdK;
 
-    // epilogue role: walker row erow (TMEM lane), columns cg * 32 .. + 32 of an AO tile
+    // this CTA's D^-1 rows cut into six exact slices once, for every K stage (the AO tiles
+    // reuse them): thread -> (row, chunk of 8 MOs), two per thread
+    for (int q = t; q < TC_M * 4; q += kVdThreads) {
+        const int prow = q >> 2, pc = q & 3;
+        const int pw = tile * TC_M + prow;
+        const bool pvalid = pw < a.nw;
+        const double *drow = a.Dinv + (size_t)(pvalid ? pw : 0) * a.msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
+                             (size_t)ei * ns;
+        const int Ep = pvalid ? a.rexp[(size_t)pw * N + e] : 0;
+        for (int sg = 0; sg < nst; ++sg) {
+            const int k0 = sg * kVdK;
+            float sl[8][kC15Slices];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = k0 + 8 * pc + i;
+                const double d = (pvalid && k < ns) ? drow[k] : 0.0;
+                slice6(ff::from_double(d), Ep, sl[i]);
+            }
+            unsigned char *Ad = ast + (size_t)sg * kC15Slices * kVdPlane;
+#pragma unroll
+            for (int j = 0; j < kC15Slices; ++j)
+                *reinterpret_cast<uint4 *>(Ad + j * kVdPlane + a_off64(prow, pc)) =
+                    make_uint4(bf16_pair(sl[0][j], sl[1][j]), bf16_pair(sl[2][j], sl[3][j]),
+                               bf16_pair(sl[4][j], sl[5][j]), bf16_pair(sl[6][j], sl[7][j]));
+        }
+    }
+    __syncthreads();                                       // the block's global writes, before its cp.async reads
+
+    // epilogue role: walker row erow (TMEM lane), columns cg * 32 .. + 32 of an AO tile of 64
     const int erow = (warp & 3) * 32 + lane, cg = warp >> 2;
     const int ew = tile * TC_M + erow;
     const bool evalid = ew < a.nw;
@@ -158,69 +183,33 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
     const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
     double b0 = 0.0, b1 = 0.0, b2 = 0.0, lap = 0.0;
 
-    const int nst = nspad / kVdK;
-    int ncb[2] = {0, 0};
+    int ncommit = 0;
     bool ok = true;
-
-    auto produce = [&](int at, int sg, int buf) {
-        unsigned char *Ab = base + buf * kVdBuf;
-        unsigned char *Bb = Ab + kC15Slices * kVdPlane;
-        const int k0 = sg * kVdK;
-        // B: rows of A (the union's AOs of this tile), six slice planes
-        for (int q = t; q < kC15Slices * TC_N * 4; q += kVdThreads) {
-            const int j = q / (TC_N * 4), rem = q - j * (TC_N * 4);
-            const int r = rem >> 2, c = rem & 3;
-            const int mu = ao_s[at * TC_N + r];
-            const bool v = mu >= 0;
-            const uint16_t *src = Bsl + j * bstride + (size_t)(v ? mu : 0) * nspad + k0 + 8 * c;
-            cp_async16(smem_u32(Bb + j * kVdPlane + a_off64(r, c)), src, v);
-        }
-        // A: the stage's six slice planes of D^-1, an image of the shared-memory layout
-        const unsigned char *As = ast + (size_t)sg * kC15Slices * kVdPlane;
-        for (int q = t; q < (int)(kC15Slices * kVdPlane / 16); q += kVdThreads)
-            cp_async16(smem_u32(Ab + 16 * q), As + 16 * (size_t)q, true);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    // this CTA's D^-1 rows cut into six exact slices once, for every K stage (the AO tiles reuse them)
-    for (int sg = 0; sg < nst; ++sg) {
-        const int k0 = sg * kVdK;
-        float sl[8][kC15Slices];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = k0 + 8 * pc + i;
-            const double d = (pvalid && k < ns) ? drow[k] : 0.0;
-            slice6(ff::from_double(d), Ep, sl[i]);
-        }
-        unsigned char *Ad = ast + (size_t)sg * kC15Slices * kVdPlane;
-#pragma unroll
-        for (int j = 0; j < kC15Slices; ++j)
-            *reinterpret_cast<uint4 *>(Ad + j * kVdPlane + a_off64(prow, pc)) =
-                make_uint4(bf16_pair(sl[0][j], sl[1][j]), bf16_pair(sl[2][j], sl[3][j]), bf16_pair(sl[4][j], sl[5][j]),
-                           bf16_pair(sl[6][j], sl[7][j]));
-    }
-    __syncthreads();                                       // the block's global writes, before its cp.async reads
-
+    unsigned char *Ab = base;
+    unsigned char *Bb = base + kC15Slices * kVdPlane;
     for (int at = 0; at < nat && ok; ++at) {
-        produce(at, 0, 0);
         for (int sg = 0; sg < nst; ++sg) {
-            const int buf = sg & 1;
-            if (sg + 1 < nst) {
-                const int nb = buf ^ 1;
-                // the MMAs of stage sg - 1 read buffer nb: wait before overwriting it
-                if (ncb[nb] > 0 && !mbar_wait(mbs[nb], (ncb[nb] - 1) & 1, kWait)) s_abort = 1;
-                produce(at, sg + 1, nb);
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-            } else {
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            // the stage buffer: A (the staged D^-1 slices) and B (the rows of A of this AO tile)
+            const int k0 = sg * kVdK;
+            const unsigned char *As = ast + (size_t)sg * kC15Slices * kVdPlane;
+            for (int q = t; q < (int)(kC15Slices * kVdPlane / 16); q += kVdThreads)
+                cp_async16(smem_u32(Ab + 16 * q), As + 16 * (size_t)q, true);
+            for (int q = t; q < kC15Slices * kVdN * 4; q += kVdThreads) {
+                const int j = q / (kVdN * 4), rem = q - j * (kVdN * 4);
+                const int r = rem >> 2, c = rem & 3;
+                const int mu = ao_s[at * kVdN + r];
+                const bool v = mu >= 0;
+                const uint16_t *src = Bsl + j * bstride + (size_t)(v ? mu : 0) * nspad + k0 + 8 * c;
+                cp_async16(smem_u32(Bb + j * kVdBPlane + a_off64(r, c)), src, v);
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
-            if (s_abort) break;
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(base + buf * kVdBuf);
-                const uint64_t dA = umma_desc_sw64(a0, 512);
-                const uint64_t dB = umma_desc_sw64(a0 + kC15Slices * kVdPlane, 512);
+                const uint64_t dA = umma_desc_sw64(smem_u32(Ab), 512);
+                const uint64_t dB = umma_desc_sw64(smem_u32(Bb), 512);
 #pragma unroll
                 for (int kk = 0; kk < kVdK / 16; ++kk)
 #pragma unroll
@@ -230,34 +219,35 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
                         for (int i = 0; i <= d; ++i) {
                             const int j = d - i;
                             const uint64_t ad = dA + ((i * kVdPlane + 32 * kk) >> 4);
-                            const uint64_t bd = dB + ((j * kVdPlane + 32 * kk) >> 4);
+                            const uint64_t bd = dB + ((j * kVdBPlane + 32 * kk) >> 4);
                             const bool first = sg == 0 && kk == 0 && i == 0 && d <= kVdAcc - 1;
-                            umma_bf16(tmem + acc * TC_N, ad, bd, idesc, first ? 0u : 1u);
+                            umma_bf16(tmem + acc * kVdN, ad, bd, idesc, first ? 0u : 1u);
                         }
                     }
-                umma_commit(mbs[buf]);
+                umma_commit(mb);
             }
-            ++ncb[buf];
+            ++ncommit;
+            // the buffer is rewritten by the next stage: wait for these MMAs (the other CTA
+            // on the SM keeps the tensor pipe busy meanwhile)
+            if (!mbar_wait(mb, (ncommit - 1) & 1, kWait)) s_abort = 1;
+            __syncthreads();
+            if (s_abort) break;
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        for (int bq = 0; bq < 2; ++bq)
-            if (!s_abort && ncb[bq] > 0 && !mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kWait)) s_abort = 1;
-        __syncthreads();
         ok = !s_abort;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: v for 32 AOs of this walker row, then the AO derivatives at r_e
         FfRadial rd;
         int last_sh = -1;
-        double *vbuf = reinterpret_cast<double *>(base);   // [16][512]: the operand buffers are idle here
+        double *vbuf = reinterpret_cast<double *>(base);   // [16][256]: the stage buffer is idle here
         for (int h = 0; h < 2; ++h) {
             const int c0 = cg * 32 + h * 16;
             {
                 uint32_t v0[16], v1[16], v2[16], v3[16];
-                tmem_ld16(tmem + tlane + (uint32_t)(0 * TC_N + c0), v0);
-                tmem_ld16(tmem + tlane + (uint32_t)(1 * TC_N + c0), v1);
-                tmem_ld16(tmem + tlane + (uint32_t)(2 * TC_N + c0), v2);
-                tmem_ld16(tmem + tlane + (uint32_t)(3 * TC_N + c0), v3);
+                tmem_ld16(tmem + tlane + (uint32_t)(0 * kVdN + c0), v0);
+                tmem_ld16(tmem + tlane + (uint32_t)(1 * kVdN + c0), v1);
+                tmem_ld16(tmem + tlane + (uint32_t)(2 * kVdN + c0), v2);
+                tmem_ld16(tmem + tlane + (uint32_t)(3 * kVdN + c0), v3);
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
                     vbuf[q * kVdThreads + t] = (((double)__uint_as_float(v0[q]) + (double)__uint_as_float(v1[q])) +
@@ -266,7 +256,7 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
             if (!evalid) continue;
 #pragma unroll 1
             for (int q = 0; q < 16; ++q) {
-                const int mu = ao_s[at * TC_N + c0 + q];
+                const int mu = ao_s[at * kVdN + c0 + q];
                 if (mu < 0) break;
                 const int sh = s.ao_shell[mu];
                 if (!((my_mask[sh >> 5] >> (sh & 31)) & 1u)) continue;
@@ -301,31 +291,28 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();                                   // TMEM read before the next tile's MMAs
+        __syncthreads();                                   // TMEM and vbuf read before the next tile
     }
     if (!ok) {
         if (t < TC_M && tile * TC_M + t < a.nw) atomicOr(a.wstatus + tile * TC_M + t, (uint32_t)QMC_STATUS_TIMEOUT);
         asm volatile("cp.async.wait_all;" ::: "memory");
-        for (int bq = 0; bq < 2; ++bq)                     // let MMAs in flight drain
-            if (ncb[bq] > 0) mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kDrainNs);
+        if (ncommit > 0) mbar_wait(mb, (ncommit - 1) & 1, kDrainNs);   // let MMAs in flight drain
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
-    // the four column groups' partial sums of each row, added in a fixed order
-    double *red = reinterpret_cast<double *>(base);        // [4 groups][128 rows][4]; operands no longer read
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
+    // the two column groups' partial sums of each row, added in a fixed order
+    double *red = reinterpret_cast<double *>(base);        // [2 groups][128 rows][4]; operands no longer read
     red[((size_t)cg * TC_M + erow) * 4 + 0] = b0;
     red[((size_t)cg * TC_M + erow) * 4 + 1] = b1;
     red[((size_t)cg * TC_M + erow) * 4 + 2] = b2;
     red[((size_t)cg * TC_M + erow) * 4 + 3] = lap;
     __syncthreads();
-    if (t < TC_M * 4) {
-        const int r = t >> 2, c = t & 3;
+    for (int q = t; q < TC_M * 4; q += kVdThreads) {
+        const int r = q >> 2, c = q & 3;
         const int w = tile * TC_M + r;
         if (w < a.nw) {
-            double x = 0.0;
-#pragma unroll
-            for (int g = 0; g < 4; ++g) x += red[((size_t)g * TC_M + r) * 4 + c];
+            const double x = red[((size_t)0 * TC_M + r) * 4 + c] + red[((size_t)1 * TC_M + r) * 4 + c];
             a.vd[((size_t)w * N + e) * 4 + c] = ok ? x : __longlong_as_double(0x7ff8000000000000ll);
         }
     }
@@ -335,7 +322,7 @@ __global__ void __launch_bounds__(kVdThreads, 1) k_vd_mma(VdArgs a)
 
 bool vdrift_fits(const SysDev &s)
 {
-    const size_t sm = 1024 + 2 * (size_t)kVdBuf + sizeof(int) * ((size_t)s.n_ao + TC_N);
+    const size_t sm = 1024 + (size_t)kVdBuf + sizeof(int) * ((size_t)s.n_ao + kVdN);
     return sm <= 227 * 1024;
 }
 
@@ -380,7 +367,7 @@ cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables 
     const size_t rows = (size_t)nw * s.n_elec;
     k_vd_rowexp<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(nw, s.n_up, s.n_dn, a.msz, Dinv,
                                                           static_cast<int *>(scratch));
-    const size_t sm = 1024 + 2 * (size_t)kVdBuf + sizeof(int) * ((size_t)s.n_ao + TC_N);
+    const size_t sm = 1024 + (size_t)kVdBuf + sizeof(int) * ((size_t)s.n_ao + kVdN);
     cudaError_t e = cudaFuncSetAttribute(k_vd_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int tiles = (nw + TC_M - 1) / TC_M;
