@@ -326,15 +326,16 @@ def config4_forward(a, flush, e0, e1):
                                       "status_mismatch": int((om["status"] != of["status"]).sum().item())}}
 
 
-def cfree_bench(q, R, prec, flush, e0, e1):
-    """The C-free variant on the same batch (c15_mode cfree: C1 alone, then the
-    drift and Laplacian from v = D^-1 A^T), timed like the default; returns the
-    timing and its outputs for the accuracy check against the FP64 path."""
+def cfree_bench(q, R, prec, flush, e0, e1, mode):
+    """The other C1..C5 arithmetic on the same batch (c15_mode tensor: C1..C5 on
+    the tensor cores; cfree: C1 alone, then the drift and Laplacian from
+    v = D^-1 A^T), timed like the default; returns the timing and its outputs
+    for the accuracy check against the FP64 path."""
     import numpy as np
     import torch
     W = int(R.shape[0])
     old = q.tiles()["c15_mode"]
-    q.set_tiles(c15_mode="cfree")
+    q.set_tiles(c15_mode=mode)
     try:
         ws = q.workspace(W, prec)
         out = q.alloc_out(W)
@@ -354,8 +355,10 @@ def cfree_bench(q, R, prec, flush, e0, e1):
     st = np.array(stages).mean(axis=0)
     t = sum(ts) / len(ts)
     res = {"walker_steps_per_s": W / (t / 1e3), "ms_per_step": t,
-           "stage_ms": {"masks": st[4], "c1_products": st[5], "a4": st[1], "vdrift_and_energy": st[2]},
-           "what": "C1 only, then v = D^-1 A^T on the tensor cores and the drift / Laplacian from the AO derivatives"}
+           "stage_ms": {"masks": st[4], "products": st[5], "a4": st[1], "drift_energy": st[2]},
+           "what": {"cfree": "C1 only, then v = D^-1 A^T on the tensor cores and the drift / Laplacian from the "
+                             "AO derivatives",
+                    "tensor": "C1..C5 on the tensor cores (exact slices for C1, C5; fp16x3 for C2..C4)"}[mode]}
     return res, out
 
 
@@ -721,8 +724,9 @@ def main():
     if not a.no_dmc:
         line["dmc_step"] = dmc_bench(q, R, prec, flush, e0, e1, t_step)
     cf_out = None
-    if prec != "f64" and not a.no_cfree and q.tiles()["c15_mode"] == "tensor":
-        line["cfree"], cf_out = cfree_bench(q, R, prec, flush, e0, e1)
+    if prec != "f64" and not a.no_cfree and q.tiles()["c15_mode"] in ("tensor", "cfree"):
+        alt = "tensor" if q.tiles()["c15_mode"] == "cfree" else "cfree"
+        line["c15_mode_" + alt], cf_out = cfree_bench(q, R, prec, flush, e0, e1, alt)
 
     # the plain FP64 GPU path on the same batch (the metric's comparison)
     if prec != "f64" and not a.no_compare:
@@ -746,7 +750,7 @@ def main():
             dec = ((cf_out["e_loc"] - out["e_loc"]).abs() / out["e_loc"].abs())[okc]
             ddc = ((cf_out["drift"] - out["drift"]).abs().amax(dim=(1, 2)) /
                    out["drift"].abs().amax(dim=(1, 2)))[okc]
-            line["cfree"]["accuracy_vs_fp64_path"] = {
+            line["c15_mode_" + alt]["accuracy_vs_fp64_path"] = {
                 "walkers": int(okc.sum().item()), "max_abs_logpsi_err": float(dlc.max().item()),
                 "max_rel_eloc_err": float(dec.max().item()), "max_drift_normwise_err": float(ddc.max().item()),
                 "status_mismatch": int((cf_out["status"] != out["status"]).sum().item())}

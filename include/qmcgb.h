@@ -263,9 +263,9 @@ int qmc_system_set_mo(qmc_system *sys, int a_dtype, const void *A_up, const void
  * exceeds 640), c15_walkers = 4, a4_mode = QMC_A4_FLOAT_FLOAT (QMC_A4_TENSOR
  * from 512 electrons of one spin on, where it fits the panel kernel),
  * a4_kappa_max = 1e8 (1e7 up to 256 electrons of one spin),
- * c15_mode = QMC_C15_TENSOR where the system fits that
- * kernel (at most 1024 electrons per spin, 8192 shells, ~7500 AOs), else
- * QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1,
+ * c15_mode = QMC_C15_CFREE where the system fits the tensor-core kernels
+ * (at most 1024 electrons per spin, 8192 shells, ~7500 AOs; the C-free
+ * kernel: ~36000 AOs), else QMC_C15_FLOAT_FLOAT, bw_walkers = 8, wait_s = 2, expire_walker = -1,
  * expire_kernels = 7, f64_kappa_max = 1e6 (1, i.e. every matrix in FP64, up to 256
  * electrons of one spin).
  * qmc_system_set_tiles returns QMC_ERR_INVALID for

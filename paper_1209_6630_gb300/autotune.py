@@ -3,7 +3,8 @@
 Candidates (see qmc_tiles in include/qmcgb.h): the Gauss-Jordan panel width
 (8, 16, 32 columns), on the mixed path the a4 arithmetic (float-float
 elimination with that panel width, or panels of 32 with the updates on the
-tensor cores) and the walkers per CTA of the float-float C1/C5 kernel (2, 4).
+tensor cores), the walkers per CTA of the float-float C1/C5 kernel (2, 4),
+and the C1..C5 products on the tensor cores against the C-free variant.
 Each candidate is timed with the library's own per-stage CUDA events
 (qmc_walkers_eval_timed) on a sample batch; the choices act on different
 stages and are picked one after the other.  Results are cached in JSON,
@@ -87,7 +88,22 @@ def autotune(q, R, precision="mixed", cache=DEFAULT_CACHE, force=False, verbose=
             if ms[5] < best_g_ms:
                 best_g, best_g_ms = g, ms[5]
     q.set_tiles(gj_panel=best_gj, c15_walkers=best_g, a4_mode=best_a4)
-    entry = {"tiles": {"gj_panel": best_gj, "c15_walkers": best_g, "a4_mode": best_a4}, "stage_ms": timings,
+    # C1..C5 on the tensor cores against the C-free variant, by the whole evaluation's time
+    best_c15 = q.tiles()["c15_mode"]
+    if mixed and best_c15 in ("tensor", "cfree"):
+        best_c15_ms = float("inf")
+        for mode in ("tensor", "cfree"):
+            try:
+                q.set_tiles(c15_mode=mode)
+                ms = _time(q, R, precision)
+            except QmcError:
+                continue
+            timings[f"c15_mode={mode}"] = ms[3]
+            if ms[3] < best_c15_ms:
+                best_c15, best_c15_ms = mode, ms[3]
+        q.set_tiles(c15_mode=best_c15)
+    entry = {"tiles": {"gj_panel": best_gj, "c15_walkers": best_g, "a4_mode": best_a4, "c15_mode": best_c15},
+             "stage_ms": timings,
              "sample_walkers": int(R.shape[0])}
     if verbose:
         print("autotune", key, entry)

@@ -38,7 +38,7 @@ def _reset(q):
 
 def test_c15_expired_wait_marks_its_tile_only(sysq):
     s, q = sysq
-    assert q.tiles()["c15_mode"] == "tensor"
+    assert q.tiles()["c15_mode"] in ("tensor", "cfree")      # both run the C1 MMA kernel with the hook
     W = 300                                         # tiles 0..127, 128..255, 256..299
     Rd = torch.from_numpy(make_walkers(s, W, first=4100)).to(dev)
     try:
