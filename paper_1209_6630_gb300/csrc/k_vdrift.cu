@@ -19,11 +19,11 @@
 // accumulators (orders 0, 1, 2 exact; 3..5 together); K stages of 32 MOs
 // through two buffers (B rows by cp.async, A slices stored by all threads),
 // one thread issuing the MMAs, mbarrier commits, bounded waits.  Epilogue:
-// v = 2^(E + G_mu) (acc0 + acc1 + acc2 + acc3) in FP64, and for every active
-// AO of the walker the gradient and Laplacian of the AO at r_e in FP32 (radial
-// part once per shell), each product with v in FP64 and accumulated in FP64:
-// the drift and Laplacian carry a relative error of a few 2^-24 per term (no
-// accumulation error), where the C2..C5 products rounded every partial sum.
+// v = 2^(E + G_mu) (acc0 + acc1 + acc2 + acc3) as a float pair (the order sums
+// are exact integers in their units; the power of two is applied exactly),
+// and for every active AO of the walker the gradient (FP32) and Laplacian
+// (float-float, radial part once per shell) of the AO at r_e, multiplied by v
+// and accumulated as float pairs on the FP32 pipes.
 // Output vd[w][e] = (drift_x, drift_y, drift_z, lap_e).
 #include "ao_ff.cuh"
 #include "qmc_internal.cuh"
@@ -79,11 +79,6 @@ __global__ void k_vd_rowexp(int nw, int n_up, int n_dn, size_t msz, const double
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) rexp[row] = exp_bound(m);
-}
-
-__device__ __forceinline__ double pow2d(int e)   // 2^e, |e| <= 1000
-{
-    return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
 // Two CTAs per SM (256 threads, N = 64 AOs per tile, one operand stage of
@@ -181,7 +176,9 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
     const float2 r2[3] = {ff::from_double(rw[0]), ff::from_double(rw[1]), ff::from_double(rw[2])};
     const uint32_t *my_mask = a.masks + ((size_t)(evalid ? ew : 0) * N + e) * mw;
     const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
-    double b0 = 0.0, b1 = 0.0, b2 = 0.0, lap = 0.0;
+    // drift and Laplacian accumulated as float pairs on the FP32 pipes (GB300's FP64 rate is 1/64
+    // of FP32: FP64 sums here kept the FP64 pipe 30% busy)
+    float2 b0 = make_float2(0.f, 0.f), b1 = b0, b2 = b0, lap = b0;
 
     int ncommit = 0;
     bool ok = true;
@@ -239,7 +236,7 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
         // epilogue: v for 32 AOs of this walker row, then the AO derivatives at r_e
         FfRadial rd;
         int last_sh = -1;
-        double *vbuf = reinterpret_cast<double *>(base);   // [16][256]: the stage buffer is idle here
+        float2 *vbuf = reinterpret_cast<float2 *>(base);   // [16][256]: the stage buffer is idle here
         for (int h = 0; h < 2; ++h) {
             const int c0 = cg * 32 + h * 16;
             {
@@ -248,10 +245,16 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
                 tmem_ld16(tmem + tlane + (uint32_t)(1 * kVdN + c0), v1);
                 tmem_ld16(tmem + tlane + (uint32_t)(2 * kVdN + c0), v2);
                 tmem_ld16(tmem + tlane + (uint32_t)(3 * kVdN + c0), v3);
+                // the four order sums (integers in their units) added as a float pair
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    vbuf[q * kVdThreads + t] = (((double)__uint_as_float(v0[q]) + (double)__uint_as_float(v1[q])) +
-                                                (double)__uint_as_float(v2[q])) + (double)__uint_as_float(v3[q]);
+                for (int q = 0; q < 16; ++q) {
+                    float s, e, s2, e2;
+                    ff::two_sum(__uint_as_float(v0[q]), __uint_as_float(v1[q]), s, e);
+                    ff::two_sum(s, __uint_as_float(v2[q]), s2, e2);
+                    e = __fadd_rn(e, e2);
+                    ff::two_sum(s2, __uint_as_float(v3[q]), s, e2);
+                    vbuf[q * kVdThreads + t] = ff::renorm(s, __fadd_rn(e, e2));
+                }
             }
             if (!evalid) continue;
 #pragma unroll 1
@@ -260,7 +263,9 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
                 if (mu < 0) break;
                 const int sh = s.ao_shell[mu];
                 if (!((my_mask[sh >> 5] >> (sh & 31)) & 1u)) continue;
-                const double vmu = vbuf[q * kVdThreads + t] * pow2d(Ee + a.gexp[spin][mu]);
+                const int ex = Ee + a.gexp[spin][mu];
+                const float2 vr = vbuf[q * kVdThreads + t];
+                const float2 vmu = make_float2(scale_pow2(vr.x, ex), scale_pow2(vr.y, ex));   // exact scaling
                 if (sh != last_sh) {
                     last_sh = sh;
                     ff_radial(s, a.fb, sh, r2, rd);
@@ -284,10 +289,10 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
                 const float g1 = c * ((nx ? nx * ip(dx, nx - 1) : 0.f) * py * pz * g + m2gd * dx * P);
                 const float g2 = c * (px * (ny ? ny * ip(dy, ny - 1) : 0.f) * pz * g + m2gd * dy * P);
                 const float g3 = c * (px * py * (nz ? nz * ip(dz, nz - 1) : 0.f) * g + m2gd * dz * P);
-                b0 += vmu * (double)g1;
-                b1 += vmu * (double)g2;
-                b2 += vmu * (double)g3;
-                lap += vmu * ((double)lp.x + (double)lp.y);
+                b0 = ff::fma2(b0, vmu, make_float2(g1, 0.f));
+                b1 = ff::fma2(b1, vmu, make_float2(g2, 0.f));
+                b2 = ff::fma2(b2, vmu, make_float2(g3, 0.f));
+                lap = ff::fma2(lap, vmu, lp);
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -303,10 +308,10 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
     // the two column groups' partial sums of each row, added in a fixed order
     double *red = reinterpret_cast<double *>(base);        // [2 groups][128 rows][4]; operands no longer read
-    red[((size_t)cg * TC_M + erow) * 4 + 0] = b0;
-    red[((size_t)cg * TC_M + erow) * 4 + 1] = b1;
-    red[((size_t)cg * TC_M + erow) * 4 + 2] = b2;
-    red[((size_t)cg * TC_M + erow) * 4 + 3] = lap;
+    red[((size_t)cg * TC_M + erow) * 4 + 0] = ff::val(b0);
+    red[((size_t)cg * TC_M + erow) * 4 + 1] = ff::val(b1);
+    red[((size_t)cg * TC_M + erow) * 4 + 2] = ff::val(b2);
+    red[((size_t)cg * TC_M + erow) * 4 + 3] = ff::val(lap);
     __syncthreads();
     for (int q = t; q < TC_M * 4; q += kVdThreads) {
         const int r = q >> 2, c = q & 3;
