@@ -11,6 +11,7 @@ contraction); this module compiles it with gcc and marshals numpy arrays.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -308,3 +309,40 @@ def dmc_step(oracle, state, tau, e_trial, seed, step, nthreads=0):
     new = {k: v[idx].copy() for k, v in sel.items()}
     return new, {"weight": wt, "accept": acc, "idx": idx, "sum_w": sw, "sum_w_eloc": swe, "alive": alive,
                  "R_proposed": R_new}
+
+
+# --- multi-determinant expansion (Sec. II.C, Eq. psit) -----------------------
+def multidet_eval(oracles, coef, R, nthreads=0):
+    """Psi = sum_K c_K Psi_K with Psi_K = e^J Det_K,up Det_K,dn, from one oracle per
+    determinant (same nuclei, basis and Jastrow; its own MO coefficients).
+    By the definitions: log|Psi| = log|sum_K c_K s_K e^{L_K}|; drift = grad Psi / Psi =
+    sum_K c_K Psi_K b_K / Psi; lap Psi / Psi = sum_K c_K Psi_K (lap Psi_K / Psi_K) / Psi, so
+    T and E_L are the same weighted sums (V does not depend on K).  Determinants that are
+    exactly singular contribute nothing."""
+    evs = [o.eval(R, nthreads=nthreads) for o in oracles]
+    W = R.shape[0]
+    L = np.stack([e["logpsi"] for e in evs])                      # [K, W]
+    S = np.stack([e["sign"] for e in evs])
+    live = (S != 0) & np.isfinite(L)
+    Lmax = np.max(np.where(live, L, -np.inf), axis=0)
+    out = {k: np.zeros_like(v) for k, v in evs[0].items()}
+    c = np.asarray(coef, dtype=np.float64)
+    for w in range(W):
+        terms = [c[k] * S[k, w] * math.exp(L[k, w] - Lmax[w]) if live[k, w] else 0.0 for k in range(len(evs))]
+        tot = math.fsum(terms)
+        out["status"][w] = 0
+        if not np.isfinite(Lmax[w]) or tot == 0.0:
+            out["logpsi"][w], out["sign"][w] = -np.inf, 0.0
+            out["status"][w] = ST_SINGULAR_UP | ST_SINGULAR_DN
+            out["drift"][w], out["e_loc"][w] = np.nan, np.nan
+            out["e_parts"][w] = np.nan
+            continue
+        om = [t / tot for t in terms]
+        out["logpsi"][w] = Lmax[w] + math.log(abs(tot))
+        out["sign"][w] = 1.0 if tot > 0 else -1.0
+        out["drift"][w] = sum(om[k] * evs[k]["drift"][w] for k in range(len(evs)) if live[k, w])
+        out["e_loc"][w] = math.fsum(om[k] * evs[k]["e_loc"][w] for k in range(len(evs)) if live[k, w])
+        out["e_parts"][w, 0] = math.fsum(om[k] * evs[k]["e_parts"][w, 0] for k in range(len(evs)) if live[k, w])
+        out["e_parts"][w, 1:] = evs[0]["e_parts"][w, 1:]
+        out["logabs"][w] = np.nan
+    return out

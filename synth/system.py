@@ -312,3 +312,35 @@ def tiny_system(kind: str = "h2o_like", seed=7):
     if kind == "mini_chain":
         return make_system(3, 1, 1, 6, seed=seed, name="mini")
     raise ValueError(kind)
+
+
+def excited_determinants(system: System, n_det: int, *, seed=7):
+    """Determinants of a multi-determinant expansion built on `system`: the
+    reference (its own MO columns) and single excitations of both spins --
+    determinant k >= 1 replaces occupied MO column (n_s - k) of each spin with
+    virtual orbital k - 1 of an orthonormal extension of the MO set (random
+    vectors orthogonalised against the occupied columns, seeded).  Returns a
+    list of Systems that differ only in A_up / A_dn."""
+    import dataclasses
+    rng = np.random.default_rng([int(system.seed), int(seed), 77])
+    out = [system]
+
+    def extend(A, m):
+        A64 = np.asarray(A, dtype=np.float64)
+        V = rng.normal(size=(A64.shape[0], m))
+        V -= A64 @ (A64.T @ V)
+        V, _ = np.linalg.qr(V)
+        return V
+
+    Vu = extend(system.A_up, n_det)
+    Vd = extend(system.A_dn, n_det) if system.n_dn else np.zeros((system.n_ao, n_det))
+    for k in range(1, n_det):
+        Au = np.array(system.A_up, dtype=np.float64, copy=True)
+        Au[:, system.n_up - k] = Vu[:, k - 1]
+        Ad = np.array(system.A_dn, dtype=np.float64, copy=True)
+        if system.n_dn:
+            Ad[:, system.n_dn - k] = Vd[:, k - 1]
+        dt = np.asarray(system.A_up).dtype
+        out.append(dataclasses.replace(system, A_up=np.ascontiguousarray(Au, dtype=dt),
+                                       A_dn=np.ascontiguousarray(Ad, dtype=dt), name=f"{system.name}_det{k}"))
+    return out
