@@ -498,6 +498,31 @@ int qmc_det_inverse(int batch, int n, double *X, double *Dinv, double *logabs, d
                     uint32_t *singular, qmc_stream_t stream);
 
 /*
+ * qmc_multidet_eval -- a1..a6 for a multi-determinant trial function (Sec. II.C,
+ * Eq. psit): Psi = e^J sum_K c_K Det_K,up Det_K,dn, K = 0..n_det-1 (1..64).
+ * Determinant K is a loaded system with the MO coefficients of its
+ * configuration (e.g. an excitation of the reference); all share the device,
+ * the electron counts, nuclei, basis and Jastrow factor (QMC_ERR_INVALID
+ * otherwise).  Each determinant is evaluated with qmc_walkers_eval's kernels,
+ * then combined per walker: with L_K = log|Psi_K|, s_K its sign, L = max L_K
+ * over the determinants that are not singular, S = sum_K c_K s_K e^{L_K - L}
+ * and w_K = c_K s_K e^{L_K - L} / S:
+ *   log|Psi| = L + log|S|, sign = sign(S), drift = sum_K w_K b_K,
+ *   T = sum_K w_K T_K, E_L = sum_K w_K E_L,K (the potential is the same).
+ * S == 0 (a node of the expansion) or every determinant singular: status
+ * SINGULAR_UP | SINGULAR_DN, log|Psi| = -inf.  out->logabs (optional) is NaN
+ * (no per-spin determinant exists); out->dinv must be NULL.
+ *   coef host [n_det]; R device [W][N][3]; ws of qmc_multidet_workspace_size
+ *   bytes (per-determinant results and one evaluation's workspace; a smaller
+ *   evaluation part processes the walkers in chunks).  Cost: n_det evaluations
+ *   (an excitation-based update of D^-1 per determinant is not used).
+ */
+int qmc_multidet_workspace_size(const qmc_system *const *dets, int n_det, int n_walk, int precision,
+                                size_t *bytes);
+int qmc_multidet_eval(const qmc_system *const *dets, const double *coef, int n_det, int n_walk, const double *R,
+                      int precision, const qmc_eval_out *out, void *ws, size_t ws_bytes, qmc_stream_t stream);
+
+/*
  * ---------------------------------------------------------------------------
  * The Monte Carlo step around the evaluation (Sec. II.A and II.B): fixed-node
  * diffusion Monte Carlo with a constant number of walkers.

@@ -111,6 +111,8 @@ def lib():
             L.qmc_slater_matrices.argtypes = [_vp, _i, _vp, _i, _vp, _vp, C.c_size_t, _vp]
             L.qmc_det_inverse.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             u64 = C.c_uint64
+            L.qmc_multidet_workspace_size.argtypes = [_vp, _i, _i, _i, C.POINTER(C.c_size_t)]
+            L.qmc_multidet_eval.argtypes = [_vp, _vp, _i, _i, _vp, _i, C.POINTER(EvalOut), _vp, C.c_size_t, _vp]
             L.qmc_dmc_move.argtypes = [_i, _i, _vp, _vp, C.c_double, u64, u64, _vp, _vp, _vp]
             L.qmc_dmc_weight.argtypes = [_i, _vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp,
                                          _vp]
@@ -127,7 +129,7 @@ def lib():
                          "qmc_logpsi_backward", "qmc_backward_workspace_size", "qmc_logpsi_backward_ex",
                          "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices", "qmc_det_inverse",
                          "qmc_dmc_move", "qmc_dmc_weight", "qmc_srmc_reconfigure", "qmc_dmc_workspace_size",
-                         "qmc_dmc_step"):
+                         "qmc_dmc_step", "qmc_multidet_workspace_size", "qmc_multidet_eval"):
                 getattr(L, name).restype = _i
             _lib = L
     return _lib
@@ -148,4 +150,4 @@ EXPORTED = ("qmc_system_load", "qmc_system_free", "qmc_system_shell_r2", "qmc_sy
             "qmc_walkers_eval", "qmc_walkers_eval_timed", "qmc_walkers_eval_static", "qmc_logpsi_backward",
             "qmc_backward_workspace_size", "qmc_logpsi_backward_ex", "qmc_screen_ao", "qmc_shell_masks", "qmc_slater_matrices",
             "qmc_det_inverse", "qmc_dmc_move", "qmc_dmc_weight", "qmc_srmc_reconfigure", "qmc_dmc_workspace_size",
-            "qmc_dmc_step", "qmc_last_error", "qmc_version")
+            "qmc_dmc_step", "qmc_multidet_workspace_size", "qmc_multidet_eval", "qmc_last_error", "qmc_version")

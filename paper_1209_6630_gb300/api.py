@@ -15,7 +15,7 @@ from ._lib import (PREC, DTYPE_F32, DTYPE_F64, DmcParams, EvalOut, Jastrow, QmcE
                    WalkerState, check, lib)
 
 __all__ = ["QmcSystem", "QmcBatch", "det_inverse", "LogPsi", "QmcError", "dmc_move", "dmc_weight",
-           "srmc_reconfigure"]
+           "srmc_reconfigure", "multidet_eval"]
 
 
 def _stream(device):
@@ -377,6 +377,28 @@ class QmcBatch:
                 lib().qmc_graph_free(self._g)
         except Exception:
             pass
+
+
+def multidet_eval(systems, coef, R, precision: str = "f64"):
+    """Psi = e^J sum_K c_K Det_K (qmc_multidet_eval): systems = QmcSystem per determinant
+    (same device, basis, nuclei, electrons, Jastrow), coef = host sequence of n_det
+    coefficients, R cuda f64 [W, N, 3].  Returns the outputs of QmcSystem.eval
+    (logabs NaN, no dinv)."""
+    q0 = systems[0]
+    W = int(R.shape[0])
+    _req_cuda(R, torch.float64, "R", (W, q0.N, 3))
+    K = len(systems)
+    hs = (C.c_void_p * K)(*[q.handle.value for q in systems])
+    cf = np.ascontiguousarray(coef, dtype=np.float64)
+    assert cf.shape == (K,)
+    b = C.c_size_t()
+    check(lib().qmc_multidet_workspace_size(hs, K, W, PREC[precision], C.byref(b)))
+    ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=q0.device)
+    o = q0.alloc_out(W)
+    eo = _eval_out_struct(o)
+    check(lib().qmc_multidet_eval(hs, C.c_void_p(cf.ctypes.data), K, W, _ptr(R), PREC[precision], C.byref(eo),
+                                  _ptr(ws), ws.numel(), _stream(q0.device)))
+    return o
 
 
 def _state_struct(st):

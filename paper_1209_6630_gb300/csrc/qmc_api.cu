@@ -1265,6 +1265,100 @@ extern "C" int qmc_walkers_eval_static(const qmc_system *sys, int n_walk, const 
 }
 
 // ---------------------------------------------------------------------------
+// Multi-determinant expansion (Sec. II.C, Eq. psit): the determinants one after the
+// other with the same evaluation, then their combination.
+namespace {
+
+struct MdCarve {
+    double *lp, *sg, *el, *ep, *dr;
+    uint32_t *st;
+    char *eval_ws;
+    size_t eval_bytes;
+};
+
+size_t md_own_bytes(int K, int W, int N)
+{
+    return 3 * al((size_t)K * W * 8) + al((size_t)K * W * 32) + al((size_t)K * W * N * 24) + al((size_t)K * W * 4);
+}
+
+int md_check(const qmc_system *const *dets, int n_det, int precision, const char *who)
+{
+    if (!dets || n_det < 1 || n_det > kMaxDets) return invalid(std::string(who) + ": need 1..64 determinants");
+    if (precision < QMC_PREC_F64 || precision > QMC_PREC_F64_TCA4) return invalid(std::string(who) + ": precision");
+    for (int k = 0; k < n_det; ++k) {
+        const qmc_system *a = dets[k], *b = dets[0];
+        if (!a) return invalid(std::string(who) + ": null determinant");
+        if (a->device != b->device || a->d.n_up != b->d.n_up || a->d.n_dn != b->d.n_dn || a->d.n_atom != b->d.n_atom ||
+            a->d.n_ao != b->d.n_ao)
+            return invalid(std::string(who) + ": determinants must share the device, electrons, atoms and basis");
+        if (a->d.jas != b->d.jas || (a->d.jas && (a->d.ja_par != b->d.ja_par || a->d.ja_anti != b->d.ja_anti ||
+                                                  a->d.jb_ee != b->d.jb_ee)))
+            return invalid(std::string(who) + ": determinants must carry the same Jastrow factor");
+    }
+    return QMC_OK;
+}
+
+}  // namespace
+
+extern "C" int qmc_multidet_workspace_size(const qmc_system *const *dets, int n_det, int n_walk, int precision,
+                                           size_t *bytes)
+{
+    int rc = md_check(dets, n_det, precision, "qmc_multidet_workspace_size");
+    if (rc) return rc;
+    if (!bytes || n_walk < 0) return invalid("qmc_multidet_workspace_size: bad argument");
+    size_t ev = 0;
+    for (int k = 0; k < n_det; ++k) ev = std::max(ev, bytes_for(make_plan(dets[k], precision, true), std::min(n_walk, 65535)));
+    *bytes = md_own_bytes(n_det, n_walk, dets[0]->d.n_elec) + ev;
+    return QMC_OK;
+}
+
+extern "C" int qmc_multidet_eval(const qmc_system *const *dets, const double *coef, int n_det, int n_walk,
+                                 const double *R, int precision, const qmc_eval_out *out, void *ws, size_t ws_bytes,
+                                 qmc_stream_t stream)
+{
+    int rc = md_check(dets, n_det, precision, "qmc_multidet_eval");
+    if (rc) return rc;
+    if (!coef || !out || n_walk < 0) return invalid("qmc_multidet_eval: bad argument");
+    if (n_walk == 0) return QMC_OK;
+    if (!R || !out->logpsi || !out->sign || !out->drift || !out->e_loc || !out->status || !ws)
+        return invalid("qmc_multidet_eval: null required pointer");
+    if (out->dinv) return invalid("qmc_multidet_eval: no single D^-1 exists for an expansion (pass dinv = NULL)");
+    const int N = dets[0]->d.n_elec, W = n_walk, K = n_det;
+    char *b = static_cast<char *>(ws);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { char *r = b + o; o = al(o + bytes); return r; };
+    MdCarve c;
+    c.lp = reinterpret_cast<double *>(take((size_t)K * W * 8));
+    c.sg = reinterpret_cast<double *>(take((size_t)K * W * 8));
+    c.el = reinterpret_cast<double *>(take((size_t)K * W * 8));
+    c.ep = reinterpret_cast<double *>(take((size_t)K * W * 32));
+    c.dr = reinterpret_cast<double *>(take((size_t)K * W * N * 24));
+    c.st = reinterpret_cast<uint32_t *>(take((size_t)K * W * 4));
+    if (o > ws_bytes) {
+        set_error("qmc_multidet_eval: workspace below qmc_multidet_workspace_size");
+        return QMC_ERR_CAPACITY;
+    }
+    c.eval_ws = b + o;
+    c.eval_bytes = ws_bytes - o;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int k = 0; k < K; ++k) {
+        qmc_eval_out eo;
+        memset(&eo, 0, sizeof eo);
+        eo.logpsi = c.lp + (size_t)k * W;
+        eo.sign = c.sg + (size_t)k * W;
+        eo.e_loc = c.el + (size_t)k * W;
+        eo.e_parts = c.ep + (size_t)k * W * 4;
+        eo.drift = c.dr + (size_t)k * W * N * 3;
+        eo.status = c.st + (size_t)k * W;
+        rc = eval_impl(dets[k], W, R, precision, &eo, c.eval_ws, c.eval_bytes, st, nullptr);
+        if (rc) return rc;
+    }
+    cudaError_t e = launch_multidet_combine(W, N, K, coef, c.lp, c.sg, c.dr, c.el, c.ep, c.st, *out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qmc_multidet_eval: combine launch");
+    return QMC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // The Monte Carlo step (Sec. II.A, II.B).
 namespace {
 

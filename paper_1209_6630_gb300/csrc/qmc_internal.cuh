@@ -195,6 +195,12 @@ cudaError_t launch_backward_f64(const SysDev &s, int nw, const double *R, const 
                                 const double *g, double *dA_up, double *dA_dn, cudaStream_t st,
                                 int max_ao_per_atom);
 
+// Multi-determinant expansion (k_multidet.cu)
+constexpr int kMaxDets = 64;
+cudaError_t launch_multidet_combine(int nw, int N, int K, const double *coef, const double *lp, const double *sg,
+                                    const double *dr, const double *el, const double *ep, const uint32_t *st,
+                                    const qmc_eval_out &o, cudaStream_t stream);
+
 // Monte Carlo step (k_dmc.cu)
 cudaError_t launch_dmc_move(int nw, int n_elec, const double *R, const double *drift, double tau, uint64_t seed,
                             uint64_t step, const uint64_t *step_ptr, double *Rn, cudaStream_t st);
