@@ -20,7 +20,8 @@
 //   k_gt_update  X[i][j] <- [i is not a pivot row of the panel] X[i][j]
 //                           + sum_c P[i][c] U[c][j]
 //                for every column j outside the panel; one CTA per 128 rows
-//                loops over the 64-column tiles and issues, per tile, 2 K16
+//                (two CTAs per SM) loops over the 32-column tiles and issues,
+//                per tile, 2 K16
 //                steps x 28 slice-pair MMAs into seven TMEM
 //                accumulators, one per order d = i + j <= 6 of the pair: each
 //                sums at most 7 x 32 products of at most 128 x 128 units of
@@ -52,19 +53,31 @@ constexpr int kGtThreads = 256;                      // init and final kernels
 constexpr int kGtWarps = kGtThreads / 32;
 constexpr int kGpThreads = 512;                      // panel kernel: one warp per row, 16 rows at a time
 constexpr int kGpWarps = kGpThreads / 32;
-constexpr int kGtUpThreads = 512;                    // update kernel: 4 lane quadrants x 4 column groups
-constexpr int kGtN = 64;                             // columns per update tile
+constexpr int kGtUpThreads = 256;                    // update kernel: 4 lane quadrants x 2 column groups
+constexpr int kGtN = 32;                             // columns per update tile (two CTAs per SM: 7 x 32 TMEM columns each)
 constexpr int kGtSl = 7;                             // slices per operand
 constexpr int kGtAcc = kGtSl;                        // one TMEM accumulator per order 0..6
 constexpr uint32_t kGtAPlane = 128 * kGtB * 2;       // [128 rows][32 K] BF16, K-major, 64-byte swizzle: 8 KB
-constexpr uint32_t kGtBPlane = kGtB * kGtN * 2;      // [32 K][64 columns] BF16, MN-major, 128-byte swizzle: 4 KB
-constexpr uint32_t kGtBSbo = 1024;                   // next group of 8 K rows (one 64-column atom each)
+constexpr uint32_t kGtBPlane = kGtB * kGtN * 2;      // [32 K][32 columns] BF16, MN-major, 64-byte swizzle: 2 KB
+constexpr uint32_t kGtBSbo = 512;                    // next group of 8 K rows (one 32-column atom each)
 
-// MN-major, 128-byte swizzle, one 64-column atom per group of 8 K rows: byte
+// MN-major, 64-byte swizzle, one 32-column atom per group of 8 K rows: byte
 // offset of the 16-byte chunk holding columns n0..n0+7 of K row r
-__device__ __forceinline__ uint32_t b_off64c(int r, int n0)
+__device__ __forceinline__ uint32_t b_off32c(int r, int n0)
 {
-    return (uint32_t)((r >> 3) * kGtBSbo + (r & 7) * 128 + ((((n0 & 63) >> 3) ^ (r & 7)) << 4));
+    return (uint32_t)((r >> 3) * kGtBSbo + (r & 7) * 64 + ((((n0 & 31) >> 3) ^ ((r & 7) >> 1)) << 4));
+}
+
+// tcgen05 shared-memory descriptor, 64-byte swizzle, both strides given (MN-major operand)
+__device__ __forceinline__ uint64_t umma_desc_sw64_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;    // SWIZZLE_64B
+    return d;
 }
 
 struct GtState {                                     // per matrix, kept across the panel launches
@@ -332,7 +345,7 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
         for (int c = 0; c < kGtB; ++c) {
             float s7[kGtSl];
             slice_n<kGtSl>(u[c], F, s7);
-            unsigned char *b = base + b_off64c(c, cl & ~7);
+            unsigned char *b = base + b_off32c(c, cl & ~7);
 #pragma unroll
             for (int j = 0; j < kGtSl; ++j)
                 *reinterpret_cast<__nv_bfloat16 *>(b + (size_t)j * kGtBPlane) = __float2bfloat16_rn(s7[j]);
@@ -345,9 +358,11 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
 // column tile: MMAs into the seven accumulators; once they complete, the
 // accumulators are read into registers (summed as float pairs), TMEM is
 // released to the next tile's MMAs, and the float-pair read-modify-write of
-// the tile's rows runs while those MMAs execute.  512 threads: TMEM lane
-// quadrant x four groups of 16 columns.
-__global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0)
+// the tile's rows runs while those MMAs execute.  256 threads: TMEM lane
+// quadrant x two groups of 16 columns; 224 of the 256 TMEM columns and ~90 KB
+// of shared memory, so that two CTAs share an SM and one's read-modify-write
+// overlaps the other's.
+__global__ void __launch_bounds__(kGtUpThreads, 2) k_gt_update(GtJobs js, int z0)
 {
     extern __shared__ __align__(1024) unsigned char gt_smem[];
     unsigned char *base = gt_smem + ((1024 - (smem_u32(gt_smem) & 1023)) & 1023);
@@ -374,7 +389,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
     unsigned char *As = base;                                    // 7 x 8 KB
-    unsigned char *Bs0 = base + kGtSl * kGtAPlane;               // 2 x 7 x 4 KB
+    unsigned char *Bs0 = base + kGtSl * kGtAPlane;               // 2 x 7 x 2 KB
     int *Fs = reinterpret_cast<int *>(Bs0 + 2 * kGtSl * kGtBPlane);   // [n]
     const unsigned char *Ag = sc + L.a + (size_t)rt * kGtSl * kGtAPlane;
     auto load_b = [&](int ct) {
@@ -390,7 +405,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
     if (nc > 1) load_b(1);                                       // group 1: B(1)
     for (int c = t; c < n; c += kGtUpThreads) Fs[c] = Fcol[c];
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
                      :: "r"(smem_u32(&tmem_slot)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -429,7 +444,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
         if (ct < nc && t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t dA = umma_desc_sw64(smem_u32(As), 512);
-            const uint64_t dB = umma_desc(smem_u32(Bs0 + (size_t)(ct & 1) * kGtSl * kGtBPlane), kGtBSbo, kGtBSbo);
+            const uint64_t dB = umma_desc_sw64_mn(smem_u32(Bs0 + (size_t)(ct & 1) * kGtSl * kGtBPlane), kGtBSbo, kGtBSbo);
 #pragma unroll
             for (int kk = 0; kk < kGtB / 16; ++kk)
 #pragma unroll
@@ -530,7 +545,7 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(GtJobs js, int z0
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
 }
 
 __global__ void __launch_bounds__(kGtThreads) k_gt_final(GtJobs js, double kappa_max)
@@ -639,8 +654,8 @@ cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStrea
     const size_t sm_panel = sizeof(float2) * (size_t)nmax * kGtB + sizeof(short) * (size_t)nmax;
     // 112 KB of operands and the column exponents; at least 120 KB so that one CTA
     // holds an SM (it allocates all 512 TMEM columns)
-    const size_t sm_up = std::max<size_t>(1024 + kGtSl * (size_t)(kGtAPlane + 2 * kGtBPlane) + 4 * (size_t)nmax,
-                                          120 * 1024);
+    // 57 KB of panel slices, 28 KB of pivot-row slices, the column exponents: two CTAs per SM
+    const size_t sm_up = 1024 + kGtSl * (size_t)(kGtAPlane + 2 * kGtBPlane) + 4 * (size_t)nmax;
     const size_t sm_fin = sizeof(float2) * 32 * 33 + sizeof(short) * 2 * (size_t)nmax;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_gt_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_panel)) !=
