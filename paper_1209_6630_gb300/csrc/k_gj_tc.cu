@@ -7,7 +7,7 @@
 // on a float-pair work matrix (~48-bit significand), in panels of kGtB = 32
 // columns, as launches over all matrices of a walker chunk:
 //
-//   k_gt_init    float-pair copy of X and ||X||_inf
+//   k_gt_init    float-pair copy of X (rows padded to an even length) and ||X||_inf
 //   per panel jb:
 //   k_gt_panel   one CTA per matrix eliminates the n x 32 panel in shared
 //                memory (pivot = the first row with the largest |entry| among
@@ -19,9 +19,10 @@
 //                each (the scheme of the C1/C5 products, one slice more)
 //   k_gt_update  X[i][j] <- [i is not a pivot row of the panel] X[i][j]
 //                           + sum_c P[i][c] U[c][j]
-//                for every column j outside the panel; one CTA per 128 rows
-//                (two CTAs per SM) loops over the 32-column tiles and issues,
-//                per tile, 2 K16
+//                for every column j outside the panel; one CTA per 128 rows,
+//                warp-specialised (a copy warp moving operands and old values
+//                with bulk copies, an MMA warp, 16 epilogue warps), loops over
+//                the 32-column tiles and issues, per tile, 2 K16
 //                steps x 28 slice-pair MMAs into seven TMEM
 //                accumulators, one per order d = i + j <= 6 of the pair: each
 //                sums at most 7 x 32 products of at most 128 x 128 units of
@@ -38,8 +39,13 @@
 // (C1 from the positions and the FP64 elimination) replaces them, exactly as
 // for k_gj_ff.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "ff_math.cuh"
 #include "qmc_internal.cuh"
@@ -53,31 +59,24 @@ constexpr int kGtThreads = 256;                      // init and final kernels
 constexpr int kGtWarps = kGtThreads / 32;
 constexpr int kGpThreads = 512;                      // panel kernel: one warp per row, 16 rows at a time
 constexpr int kGpWarps = kGpThreads / 32;
-constexpr int kGtUpThreads = 256;                    // update kernel: 4 lane quadrants x 2 column groups
-constexpr int kGtN = 32;                             // columns per update tile (two CTAs per SM: 7 x 32 TMEM columns each)
+constexpr int kGtEpWarps = 16;                       // update kernel: 4 lane quadrants x 4 groups of 8 columns,
+constexpr int kGtUpThreads = 32 * (kGtEpWarps + 3);  // plus the X, B and MMA warps
+constexpr int kGtN = 32;                             // columns per update tile (= the panel width)
 constexpr int kGtSl = 7;                             // slices per operand
-constexpr int kGtAcc = kGtSl;                        // one TMEM accumulator per order 0..6
 constexpr uint32_t kGtAPlane = 128 * kGtB * 2;       // [128 rows][32 K] BF16, K-major, 64-byte swizzle: 8 KB
 constexpr uint32_t kGtBPlane = kGtB * kGtN * 2;      // [32 K][32 columns] BF16, MN-major, 64-byte swizzle: 2 KB
 constexpr uint32_t kGtBSbo = 512;                    // next group of 8 K rows (one 32-column atom each)
+constexpr int kGtBs = 3;                             // stages of pivot-row slices
+constexpr int kGtXs = 3;                             // stages of old values
+constexpr uint32_t kGtXStage = 128 * kGtN * 8;       // [2 halves][128 rows][16 float pairs], 128-byte swizzle
+constexpr uint32_t kGtATmem = 256;                   // TMEM: 7 accumulators of 32 columns at 0, the panel
+                                                     // slices (7 x 16 columns) from 256
 
 // MN-major, 64-byte swizzle, one 32-column atom per group of 8 K rows: byte
 // offset of the 16-byte chunk holding columns n0..n0+7 of K row r
 __device__ __forceinline__ uint32_t b_off32c(int r, int n0)
 {
     return (uint32_t)((r >> 3) * kGtBSbo + (r & 7) * 64 + ((((n0 & 31) >> 3) ^ ((r & 7) >> 1)) << 4));
-}
-
-// tcgen05 shared-memory descriptor, 64-byte swizzle, both strides given (MN-major operand)
-__device__ __forceinline__ uint64_t umma_desc_sw64_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;    // SWIZZLE_64B
-    return d;
 }
 
 struct GtState {                                     // per matrix, kept across the panel launches
@@ -88,16 +87,21 @@ struct GtState {                                     // per matrix, kept across 
 };
 
 struct GtLayout {                                    // scratch of one matrix
-    size_t a, b, e, f, pp, used, piv, state, per;
+    size_t w, a, b, e, f, pp, used, piv, state, per;
 };
 
 __host__ __device__ inline size_t gt_al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// row stride of the float-pair work matrix: n rounded up to even, so that every row and
+// every 32-column segment of it starts on a 16-byte boundary (the bulk copies' rule)
+__host__ __device__ inline int gt_ld(int n) { return (n + 1) & ~1; }
 
 __host__ __device__ inline GtLayout gt_layout(int n)
 {
     const size_t nt = (size_t)(n + 127) / 128, nc = (size_t)(n + kGtN - 1) / kGtN;
     GtLayout L;
     size_t o = 0;
+    L.w = o; o += gt_al(8 * (size_t)n * gt_ld(n));     // the float-pair work matrix [n][gt_ld(n)]
     L.a = o; o += nt * kGtSl * kGtAPlane;             // [row tile][slice] planes of P
     L.b = o; o += nc * kGtSl * kGtBPlane;             // [column tile][slice] planes of U
     L.e = o; o += gt_al(4 * nt * 128);                // E_i
@@ -117,6 +121,7 @@ struct GtJobs {
     int jb;                                          // current panel
     unsigned long long wait_ns;                      // limit of each wait (WaitCfg)
     int expire_m;                                    // test hook: matrix whose first update wait runs out
+    CUtensorMap tmw[2];                              // the work matrices of job q as [matrix][row][column]
 };
 
 __device__ __forceinline__ void gt_argmax_merge(float &v, int &i, float v2, int i2)
@@ -144,7 +149,8 @@ __global__ void __launch_bounds__(kGtThreads) k_gt_init(GtJobs js)
     const GtLayout L = gt_layout(n);
     unsigned char *sc = js.scr[blockIdx.y] + (size_t)m * L.per;
     const double *__restrict__ X = J.X + (size_t)m * J.x_stride;
-    float2 *__restrict__ Wk = J.work + (size_t)m * J.x_stride;
+    float2 *__restrict__ Wk = reinterpret_cast<float2 *>(sc + L.w);
+    const int ld = gt_ld(n);
     short *used = reinterpret_cast<short *>(sc + L.used);
     unsigned char *piv = sc + L.piv;
     GtState *st = reinterpret_cast<GtState *>(sc + L.state);
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(kGtThreads) k_gt_init(GtJobs js)
         for (int c = lane; c < n; c += 32) {
             const double x = X[(size_t)i * n + c];
             const float h = (float)x;
-            Wk[(size_t)i * n + c] = make_float2(h, (float)(x - (double)h));
+            Wk[(size_t)i * ld + c] = make_float2(h, (float)(x - (double)h));
             rs += fabsf(h);
         }
 #pragma unroll
@@ -189,7 +195,8 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
     unsigned char *sc = js.scr[blockIdx.y] + (size_t)m * L.per;
     GtState *st = reinterpret_cast<GtState *>(sc + L.state);
     if (st->sing) return;
-    float2 *__restrict__ Wk = J.work + (size_t)m * J.x_stride;
+    float2 *__restrict__ Wk = reinterpret_cast<float2 *>(sc + L.w);
+    const int ld = gt_ld(n);
     short *pp_g = reinterpret_cast<short *>(sc + L.pp);
     short *used_g = reinterpret_cast<short *>(sc + L.used);
     unsigned char *piv_g = sc + L.piv;
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = i0 + u * kGpWarps;
-            v[u] = (i < n && lane < w) ? Wk[(size_t)i * n + jb + lane] : make_float2(0.f, 0.f);
+            v[u] = (i < n && lane < w) ? Wk[(size_t)i * ld + jb + lane] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
     }
     // the eliminated panel is part of the result; bookkeeping of the pivots
     for (int i = wid; i < n; i += kGpWarps)
-        if (lane < w) Wk[(size_t)i * n + jb + lane] = P[i * kGtB + lane];
+        if (lane < w) Wk[(size_t)i * ld + jb + lane] = P[i * kGtB + lane];
     if (t < w) {
         const int p = ppS[t];
         pp_g[jb + t] = (short)p;
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
         float mx = 0.f;
 #pragma unroll
         for (int c = 0; c < kGtB; ++c) {
-            u[c] = (vcol && c < w) ? Wk[(size_t)ppS[c] * n + col] : make_float2(0.f, 0.f);
+            u[c] = (vcol && c < w) ? Wk[(size_t)ppS[c] * ld + col] : make_float2(0.f, 0.f);
             mx = fmaxf(mx, fabsf(u[c].x));
         }
         const int F = exp_bound(mx);
@@ -353,20 +360,67 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
     }
 }
 
-// One CTA per (matrix, tile of 128 rows): the row tile's 7 A planes stay in
-// shared memory; the column tiles' B planes stream through two buffers.  Per
-// column tile: MMAs into the seven accumulators; once they complete, the
-// accumulators are read into registers (summed as float pairs), TMEM is
-// released to the next tile's MMAs, and the float-pair read-modify-write of
-// the tile's rows runs while those MMAs execute.  256 threads: TMEM lane
-// quadrant x two groups of 16 columns; 224 of the 256 TMEM columns and ~90 KB
-// of shared memory, so that two CTAs share an SM and one's read-modify-write
-// overlaps the other's.
-__global__ void __launch_bounds__(kGtUpThreads, 2) k_gt_update(GtJobs js, int z0)
+static_assert(kGtN == kGtB, "a column tile of the update is exactly one panel");
+
+// Bounded wait of one thread with the CTA's abort flag: false on timeout (which sets the
+// flag) or as soon as another role has set it.
+__device__ __forceinline__ bool gt_wait1(uint32_t mbar, uint32_t parity, uint64_t limit_ns, volatile int *abort)
+{
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (*abort) return false;
+        if (globaltimer() - t0 > limit_ns) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// The same for a whole warp, which stays converged: every lane polls (the phase, once
+// complete, stays complete until this warp has arrived for it), the decisions are taken
+// together.  A warp left diverged here (one lane polling, the others parked) made each
+// following elect.sync -- the MMA warp issues every MMA through one -- cost ~300 cycles.
+__device__ __forceinline__ bool gt_wait_warp(uint32_t mbar, uint32_t parity, uint64_t limit_ns, volatile int *abort,
+                                             int lane)
+{
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        const bool done = mbar_try_wait(mbar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        if (__any_sync(0xffffffffu, *abort != 0)) return false;
+        int late = lane == 0 && globaltimer() - t0 > limit_ns;
+        late = __shfl_sync(0xffffffffu, late, 0);
+        if (late) {
+            if (lane == 0) *abort = 1;
+            return false;
+        }
+    }
+}
+
+// One CTA per (matrix, tile of 128 rows), one CTA per SM, four roles:
+//   X warp          the tile's old float pairs in and the updated ones out by tensor TMA
+//                   (two 16-column boxes of 128 rows each way, 128-byte swizzle; rows and
+//                   columns outside the matrix are zero-filled on load, clipped on store),
+//                   three stages
+//   B warp          bulk copies of each column tile's 7 pivot-row slice planes, three stages
+//   MMA warp        the row tile's 7 panel planes (one bulk copy), then per column tile the
+//                   2 K16 x 28 slice-pair MMAs into the seven accumulators (7 x 32 TMEM
+//                   columns) once the epilogue has read the previous tile's
+//   16 epilogue     TMEM lane quadrant x 8 columns: the seven order sums, the old values
+//   warps           read from and the results written back to the stage in shared memory;
+//                   first, warps 0..3 move the panel planes into TMEM, where the MMAs read
+//                   them (A from TMEM: per MMA only the 1 KB B slice is read from shared
+//                   memory, instead of 4 KB of A + 1 KB of B, which bounded the MMAs)
+// The panel's own column tile is final and skipped.  Every wait is bounded; one that runs
+// out sets the CTA's abort flag and every role leaves at its next wait; the matrix goes to
+// the FP64 recomputation, and the copies and MMAs in flight drain before TMEM is freed.
+__global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(const __grid_constant__ GtJobs js, int z0)
 {
     extern __shared__ __align__(1024) unsigned char gt_smem[];
     unsigned char *base = gt_smem + ((1024 - (smem_u32(gt_smem) & 1023)) & 1023);
-    __shared__ __align__(8) uint64_t mbar;
+    constexpr int kBars = 2 + 2 * kGtBs + 2 * kGtXs + 2;
+    __shared__ __align__(8) uint64_t bar[kBars];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort, s_never;
 
@@ -376,41 +430,47 @@ __global__ void __launch_bounds__(kGtUpThreads, 2) k_gt_update(GtJobs js, int z0
     const int n = J.n, jb = js.jb;
     const int rt = blockIdx.x;
     if (m >= J.count || jb >= n || rt * 128 >= n) return;
+    const int nc = (n + kGtN - 1) / kGtN;
+    const int jp = jb / kGtN;                                    // the panel's own column tile
+    const int ntl = nc - 1;                                      // column tiles updated
+    if (ntl == 0) return;
     const GtLayout L = gt_layout(n);
     unsigned char *sc = js.scr[q] + (size_t)m * L.per;
     const GtState *st = reinterpret_cast<const GtState *>(sc + L.state);
     if (st->sing) return;
-    float2 *__restrict__ Wk = J.work + (size_t)m * J.x_stride;
-    const int *Erow = reinterpret_cast<const int *>(sc + L.e);
-    const int *Fcol = reinterpret_cast<const int *>(sc + L.f);
-    const unsigned char *piv = sc + L.piv;
-    const int w = min(kGtB, n - jb);
-    const int nc = (n + kGtN - 1) / kGtN;
+    const int r0 = rt * 128, nr = min(128, n - r0);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint64_t tmap = reinterpret_cast<uint64_t>(&js.tmw[q]);
 
     unsigned char *As = base;                                    // 7 x 8 KB
-    unsigned char *Bs0 = base + kGtSl * kGtAPlane;               // 2 x 7 x 2 KB
-    int *Fs = reinterpret_cast<int *>(Bs0 + 2 * kGtSl * kGtBPlane);   // [n]
-    const unsigned char *Ag = sc + L.a + (size_t)rt * kGtSl * kGtAPlane;
-    auto load_b = [&](int ct) {
-        const unsigned char *Bg = sc + L.b + (size_t)ct * kGtSl * kGtBPlane;
-        unsigned char *Bs = Bs0 + (size_t)(ct & 1) * kGtSl * kGtBPlane;
-        for (int q16 = t; q16 < (int)(kGtSl * kGtBPlane / 16); q16 += kGtUpThreads)
-            cp_async16(smem_u32(Bs + 16 * q16), Bg + 16 * (size_t)q16, true);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    for (int q16 = t; q16 < (int)(kGtSl * kGtAPlane / 16); q16 += kGtUpThreads)
-        cp_async16(smem_u32(As + 16 * q16), Ag + 16 * (size_t)q16, true);
-    load_b(0);                                                   // group 0: A and B(0)
-    if (nc > 1) load_b(1);                                       // group 1: B(1)
+    unsigned char *Bs = As + kGtSl * kGtAPlane;                  // 3 x 7 x 2 KB
+    unsigned char *Xs = Bs + kGtBs * kGtSl * kGtBPlane;          // 3 x 2 x 16 KB
+    int *Fs = reinterpret_cast<int *>(Xs + kGtXs * kGtXStage);   // [n]
+    const uint32_t b0 = smem_u32(&bar[0]);
+    const uint32_t bA = b0;
+    auto BF = [&](int sb) { return b0 + 8u * (uint32_t)(1 + sb); };
+    auto BE = [&](int sb) { return b0 + 8u * (uint32_t)(1 + kGtBs + sb); };
+    auto XF = [&](int sx) { return b0 + 8u * (uint32_t)(1 + 2 * kGtBs + sx); };
+    auto XW = [&](int sx) { return b0 + 8u * (uint32_t)(1 + 2 * kGtBs + kGtXs + sx); };
+    const uint32_t bTF = b0 + 8u * (uint32_t)(1 + 2 * kGtBs + 2 * kGtXs);   // accumulators complete
+    const uint32_t bTE = bTF + 8u;                                         // ... and read
+    const uint32_t bAT = bTF + 16u;                                        // panel slices in TMEM
+    auto col_tile = [&](int i) { return i < jp ? i : i + 1; };
+
+    const int *Fcol = reinterpret_cast<const int *>(sc + L.f);
     for (int c = t; c < n; c += kGtUpThreads) Fs[c] = Fcol[c];
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
                      :: "r"(smem_u32(&tmem_slot)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
+    if (t == 32) {
+        mbar_init(bA, 1);
+        for (int sb = 0; sb < kGtBs; ++sb) { mbar_init(BF(sb), 1); mbar_init(BE(sb), 1); }
+        for (int sx = 0; sx < kGtXs; ++sx) { mbar_init(XF(sx), 1); mbar_init(XW(sx), kGtEpWarps); }
+        mbar_init(bTF, 1);
+        mbar_init(bTE, kGtEpWarps);
+        mbar_init(bAT, 4);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
         s_never = 0;
@@ -419,133 +479,194 @@ __global__ void __launch_bounds__(kGtUpThreads, 2) k_gt_update(GtJobs js, int z0
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t mb = smem_u32(&mbar);
-    const uint32_t idesc = umma_idesc_f16(128, kGtN, 1);
-    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
+    int nld = 0, nst = 0, nb = 0, nmma = 0;                      // tiles loaded / stored / copied / multiplied
 
-    const int i = rt * 128 + (warp & 3) * 32 + lane;             // this thread's row (TMEM lane)
-    const int cb = (warp >> 2) * 16;                             // its 16 columns of a tile
-    const bool row_ok = i < n;
-    const int E = row_ok ? Erow[i] : 0;
-    const bool is_piv = row_ok && piv[i] != 0;
-    float2 *row = Wk + (size_t)(row_ok ? i : 0) * n;
-    float hs[16], ls[16];
-    int ncommit = 0;
-
-    for (int ct = 0; ct <= nc; ++ct) {
-        if (ct < nc) {
-            // B(ct) (and A) have landed: groups complete in order, one may stay in flight
-            if (ct + 1 < nc) asm volatile("cp.async.wait_group 1;" ::: "memory");
-            else asm volatile("cp.async.wait_group 0;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
-        __syncthreads();                                         // also: TMEM of tile ct-1 has been read
-        if (s_abort) break;
-        if (ct < nc && t == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t dA = umma_desc_sw64(smem_u32(As), 512);
-            const uint64_t dB = umma_desc_sw64_mn(smem_u32(Bs0 + (size_t)(ct & 1) * kGtSl * kGtBPlane), kGtBSbo, kGtBSbo);
-#pragma unroll
-            for (int kk = 0; kk < kGtB / 16; ++kk)
-#pragma unroll
-                for (int d = 0; d < kGtSl; ++d)
-#pragma unroll
-                    for (int ii = 0; ii <= d; ++ii) {
-                        const int j = d - ii;
-                        const uint64_t ad = dA + ((ii * kGtAPlane + 32 * kk) >> 4);
-                        const uint64_t bd = dB + ((j * kGtBPlane + 2 * kk * kGtBSbo) >> 4);
-                        umma_bf16(tmem + d * kGtN, ad, bd, idesc, (kk == 0 && ii == 0) ? 0u : 1u);
-                    }
-            umma_commit(mb);
-        }
-        // read-modify-write of tile ct-1 (its update is in hs/ls), overlapping the MMAs of tile ct:
-        // the 16 old values are loaded first (16-byte loads where aligned), then updated and stored
-        if (ct > 0 && row_ok) {
-            const int c0 = (ct - 1) * kGtN + cb;
-            float2 x[16];
-            const bool vec = ((reinterpret_cast<uintptr_t>(row + c0) & 15) == 0) && c0 + 16 <= n;
-            if (vec) {
-                const float4 *r4 = reinterpret_cast<const float4 *>(row + c0);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const float4 v4 = is_piv ? make_float4(0.f, 0.f, 0.f, 0.f) : r4[k];
-                    x[2 * k] = make_float2(v4.x, v4.y);
-                    x[2 * k + 1] = make_float2(v4.z, v4.w);
+    if (warp == kGtEpWarps) {
+        // ---- X warp: stage sx holds tile i; before tile i + 3 is loaded into it, tile i is
+        // stored and the store has finished reading the stage
+        if (lane == 0) {
+            auto store = [&](int i) {
+                const int sx = i % kGtXs, c0 = col_tile(i) * kGtN;
+                const uint32_t xs = smem_u32(Xs + sx * kGtXStage);
+                tma_store_3d(tmap, xs, c0, r0, m);
+                tma_store_3d(tmap, xs + kGtXStage / 2, c0 + 16, r0, m);
+                bulk_commit();
+                nst = i + 1;
+            };
+            for (int i = 0; i < ntl; ++i) {
+                const int sx = i % kGtXs;
+                if (i >= kGtXs) {
+                    if (!gt_wait1(XW(sx), ((i / kGtXs) - 1) & 1, js.wait_ns, &s_abort)) break;
+                    store(i - kGtXs);
+                    bulk_wait_read0();
                 }
+                const int c0 = col_tile(i) * kGtN;
+                const uint32_t xs = smem_u32(Xs + sx * kGtXStage);
+                mbar_expect_tx(XF(sx), kGtXStage);
+                tma_load_3d(tmap, xs, c0, r0, m, XF(sx));
+                tma_load_3d(tmap, xs + kGtXStage / 2, c0 + 16, r0, m, XF(sx));
+                nld = i + 1;
+            }
+            if (nld == ntl)
+                for (int i = max(0, ntl - kGtXs); i < ntl; ++i) {
+                    if (!gt_wait1(XW(i % kGtXs), (i / kGtXs) & 1, js.wait_ns, &s_abort)) break;
+                    store(i);
+                }
+            bulk_wait_all0();                                    // every store complete
+        }
+    } else if (warp == kGtEpWarps + 1) {
+        // ---- B warp
+        if (lane == 0)
+            for (int i = 0; i < ntl; ++i) {
+                const int sb = i % kGtBs;
+                if (i >= kGtBs && !gt_wait1(BE(sb), ((i / kGtBs) - 1) & 1, js.wait_ns, &s_abort)) break;
+                mbar_expect_tx(BF(sb), kGtSl * kGtBPlane);
+                bulk_g2s(smem_u32(Bs + sb * kGtSl * kGtBPlane), sc + L.b + (size_t)col_tile(i) * kGtSl * kGtBPlane,
+                         kGtSl * kGtBPlane, BF(sb));
+                nb = i + 1;
+            }
+    } else if (warp == kGtEpWarps + 2) {
+        // ---- MMA warp: warp-uniform control flow, one elected lane issues each MMA and commit
+        if (lane == 0) {
+            mbar_expect_tx(bA, kGtSl * kGtAPlane);
+            bulk_g2s(smem_u32(As), sc + L.a + (size_t)rt * kGtSl * kGtAPlane, kGtSl * kGtAPlane, bA);
+        }
+        __syncwarp();
+        if (gt_wait_warp(bAT, 0, js.wait_ns, &s_abort, lane)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = umma_idesc_f16(128, kGtN, 1);
+            for (int i = 0; i < ntl; ++i) {
+                const int sb = i % kGtBs;
+                if (!gt_wait_warp(BF(sb), (i / kGtBs) & 1, js.wait_ns, &s_abort, lane)) break;
+                if (i >= 1 && !gt_wait_warp(bTE, (i - 1) & 1, js.wait_ns, &s_abort, lane)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t dB = umma_desc_sw64_mn(smem_u32(Bs + sb * kGtSl * kGtBPlane), kGtBSbo, kGtBSbo);
+#pragma unroll
+                for (int kk = 0; kk < kGtB / 16; ++kk)
+#pragma unroll
+                    for (int d = 0; d < kGtSl; ++d)
+#pragma unroll
+                        for (int ii = 0; ii <= d; ++ii) {
+                            const int j = d - ii;
+                            const uint32_t at = tmem + kGtATmem + (uint32_t)((ii * 2 + kk) * 8);
+                            const uint64_t bd = dB + ((j * kGtBPlane + 2 * kk * kGtBSbo) >> 4);
+                            if (kk == 0 && ii == 0) umma_bf16_ts_warp<0>(tmem + d * kGtN, at, bd, idesc);
+                            else umma_bf16_ts_warp<1>(tmem + d * kGtN, at, bd, idesc);
+                        }
+                umma_commit_warp(BE(sb));                        // the B stage may be refilled
+                umma_commit_warp(bTF);                           // the accumulators may be read
+                nmma = i + 1;
+            }
+        }
+    } else {
+        // ---- epilogue warps: row r of the tile (TMEM lane), columns cg * 8 .. + 7 of each column tile
+        const int quad = warp & 3, cg = warp >> 2;
+        const int r = quad * 32 + lane;
+        const bool row_ok = r < nr;
+        const int i_row = r0 + (row_ok ? r : 0);
+        const int E = row_ok ? reinterpret_cast<const int *>(sc + L.e)[i_row] : 0;
+        const bool is_piv = row_ok && (sc + L.piv)[i_row] != 0;
+        const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+        const uint32_t tl = tmem + tlane + (uint32_t)(cg * 8);
+        if (warp < 4) {
+            // the panel planes into TMEM columns 256 + 16 ii .. + 15: this thread's row, its 32
+            // K values packed in pairs (the 64-byte swizzle of the shared-memory planes undone)
+            if (gt_wait_warp(bA, 0, js.wait_ns, &s_abort, lane)) {
+#pragma unroll 1
+                for (int ii = 0; ii < kGtSl; ++ii) {
+                    uint32_t w[16];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(As + ii * kGtAPlane + a_off64(r, c));
+                        w[4 * c] = u.x; w[4 * c + 1] = u.y; w[4 * c + 2] = u.z; w[4 * c + 3] = u.w;
+                    }
+                    tmem_st16(tmem + tlane + kGtATmem + (uint32_t)(16 * ii), w);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bAT);
+            }
+        }
+        // this thread's four 16-byte chunks of a stage (128-byte swizzle: chunk ^ (row & 7))
+        const uint32_t xoff = (uint32_t)((cg >> 1) * (kGtXStage / 2) + r * 128);
+        const int ck0 = (cg & 1) * 4;
+        // test hook: the first panel's first wait of the chosen matrix runs out
+        const bool expire = m == js.expire_m && jb == 0 && rt == 0;
+        for (int i = 0; i < ntl; ++i) {
+            const int sx = i % kGtXs;
+            bool ok;
+            if (expire && i == 0) {
+                int f = 0;
+                if (lane == 0) {
+                    f = flag_wait(&s_never, js.wait_ns);
+                    if (!f) s_abort = 1;
+                }
+                ok = __shfl_sync(0xffffffffu, f, 0) != 0;
             } else {
-#pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    x[k] = (!is_piv && c0 + k < n) ? row[c0 + k] : make_float2(0.f, 0.f);
+                ok = gt_wait_warp(bTF, i & 1, js.wait_ns, &s_abort, lane);
             }
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[kGtSl][8];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int ex = E + Fs[c0 + k < n ? c0 + k : 0];
-                const float2 corr = make_float2(scale_pow2(hs[k], ex), scale_pow2(ls[k], ex));
-                x[k] = ff::add(x[k], corr);
+            for (int d = 0; d < kGtSl; ++d) tmem_ld8_async(tl + (uint32_t)(d * kGtN), v[d]);
+            tmem_wait_ld(v);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bTE);
+            // the seven order sums, exact integers in their units: orders 0..3 added as float
+            // pairs, orders 4..6 (below 2^-21 of the update) first in FP32 (rounding ~2^-46)
+            float hs[8], ls[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                ff::two_sum(__uint_as_float(v[0][k]), __uint_as_float(v[1][k]), hs[k], ls[k]);
+                float sh, se;
+                ff::two_sum(hs[k], __uint_as_float(v[2][k]), sh, se);
+                ls[k] = __fadd_rn(ls[k], se);
+                ff::two_sum(sh, __uint_as_float(v[3][k]), hs[k], se);
+                ls[k] = __fadd_rn(ls[k], se);
+                const float t456 = __fadd_rn(__uint_as_float(v[4][k]),
+                                             __fadd_rn(__uint_as_float(v[5][k]), __uint_as_float(v[6][k])));
+                ls[k] = __fadd_rn(ls[k], t456);
             }
-            const bool in_panel = c0 < jb + w && c0 + 16 > jb;   // the panel's columns are final
-            if (vec && !in_panel) {
-                float4 *r4 = reinterpret_cast<float4 *>(row + c0);
+            if (!gt_wait_warp(XF(sx), (i / kGtXs) & 1, js.wait_ns, &s_abort, lane)) break;
+            unsigned char *xs = Xs + sx * kGtXStage + xoff;
+            const int c0 = col_tile(i) * kGtN + cg * 8;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) r4[k] = make_float4(x[2 * k].x, x[2 * k].y, x[2 * k + 1].x, x[2 * k + 1].y);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    if (c0 + k < n && !(c0 + k >= jb && c0 + k < jb + w)) row[c0 + k] = x[k];
+            for (int k = 0; k < 4; ++k) {
+                float4 *p4 = reinterpret_cast<float4 *>(xs + (((ck0 + k) ^ (r & 7)) << 4));
+                const float4 o = *p4;
+                float2 x0 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.x, o.y);
+                float2 x1 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.z, o.w);
+                const int ex0 = E + Fs[min(c0 + 2 * k, n - 1)], ex1 = E + Fs[min(c0 + 2 * k + 1, n - 1)];
+                x0 = ff::add(x0, make_float2(scale_pow2(hs[2 * k], ex0), scale_pow2(ls[2 * k], ex0)));
+                x1 = ff::add(x1, make_float2(scale_pow2(hs[2 * k + 1], ex1), scale_pow2(ls[2 * k + 1], ex1)));
+                *p4 = make_float4(x0.x, x0.y, x1.x, x1.y);
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // for the TMA store
+            __syncwarp();
+            if (lane == 0) mbar_arrive(XW(sx));
         }
-        if (ct == nc) break;
-        ++ncommit;
-        // all leave at the next barrier; the test hook replaces the first panel's first wait of
-        // the chosen matrix by one that runs out
-        const bool expire = m == js.expire_m && jb == 0 && rt == 0 && ct == 0;
-        if (expire ? !flag_wait(&s_never, js.wait_ns) : !mbar_wait(mb, (ncommit - 1) & 1, js.wait_ns)) s_abort = 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ct + 2 < nc) load_b(ct + 2);                         // B buffer ct & 1 is free again
-        // the seven order sums, exact integers in their units: orders 0..3 added as float
-        // pairs, orders 4..6 (below 2^-21 of the update) first in FP32 (rounding ~2^-46)
-        uint32_t v0[16], v1[16];
-        tmem_ld16(tmem + tlane + (uint32_t)cb, v0);
-        tmem_ld16(tmem + tlane + (uint32_t)(kGtN + cb), v1);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) ff::two_sum(__uint_as_float(v0[k]), __uint_as_float(v1[k]), hs[k], ls[k]);
-        tmem_ld16(tmem + tlane + (uint32_t)(2 * kGtN + cb), v0);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            float sh, se;
-            ff::two_sum(hs[k], __uint_as_float(v0[k]), sh, se);
-            hs[k] = sh;
-            ls[k] = __fadd_rn(ls[k], se);
-        }
-        tmem_ld16(tmem + tlane + (uint32_t)(3 * kGtN + cb), v0);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            float sh, se;
-            ff::two_sum(hs[k], __uint_as_float(v0[k]), sh, se);
-            hs[k] = sh;
-            ls[k] = __fadd_rn(ls[k], se);
-        }
-        tmem_ld16(tmem + tlane + (uint32_t)(4 * kGtN + cb), v0);
-        tmem_ld16(tmem + tlane + (uint32_t)(5 * kGtN + cb), v1);
-        uint32_t v2[16];
-        tmem_ld16(tmem + tlane + (uint32_t)(6 * kGtN + cb), v2);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float t456 = __fadd_rn(__uint_as_float(v0[k]),
-                                         __fadd_rn(__uint_as_float(v1[k]), __uint_as_float(v2[k])));
-            ls[k] = __fadd_rn(ls[k], t456);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     __syncthreads();
-    if (s_abort) {                                               // recomputed in FP64
-        if (t == 0 && J.redo) J.redo[m * J.redo_stride] = 1;
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        if (ncommit > 0) mbar_wait(mb, (ncommit - 1) & 1, kDrainNs);   // let MMAs in flight drain
+    if (s_abort && t == 0 && J.redo) J.redo[m * J.redo_stride] = 1;   // recomputed in FP64
+    // nothing may land in this CTA's shared memory or TMEM after it exits: the copying
+    // threads wait for their last copies, the MMA thread for its last commits (in a normal
+    // run all of these have completed or complete at once)
+    if (s_abort && warp == kGtEpWarps && lane == 0)
+        for (int i = max(0, nld - kGtXs); i < nld; ++i) mbar_wait(XF(i % kGtXs), (i / kGtXs) & 1, kDrainNs);
+    if (s_abort && warp == kGtEpWarps + 1 && lane == 0)
+        for (int i = max(0, nb - kGtBs); i < nb; ++i) mbar_wait(BF(i % kGtBs), (i / kGtBs) & 1, kDrainNs);
+    if (warp == kGtEpWarps + 2 && lane == 0) {
+        if (s_abort) mbar_wait(bA, 0, kDrainNs);
+        for (int i = max(0, nmma - kGtBs); i < nmma; ++i) mbar_wait(BE(i % kGtBs), (i / kGtBs) & 1, kDrainNs);
+        if (nmma > 0) mbar_wait(bTF, (nmma - 1) & 1, kDrainNs);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
+    (void)nst;
 }
 
 __global__ void __launch_bounds__(kGtThreads) k_gt_final(GtJobs js, double kappa_max)
@@ -561,7 +682,8 @@ __global__ void __launch_bounds__(kGtThreads) k_gt_final(GtJobs js, double kappa
         if (threadIdx.x == 0 && J.redo) J.redo[m * J.redo_stride] = 1;
         return;
     }
-    const float2 *__restrict__ Wk = J.work + (size_t)m * J.x_stride;
+    const float2 *__restrict__ Wk = reinterpret_cast<const float2 *>(sc + L.w);
+    const int ld = gt_ld(n);
     double *__restrict__ Dout = J.Dinv + (size_t)m * J.d_stride;
     const short *pp_g = reinterpret_cast<const short *>(sc + L.pp);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -578,7 +700,7 @@ __global__ void __launch_bounds__(kGtThreads) k_gt_final(GtJobs js, double kappa
     float imax = 0.f;
     for (int i = wid; i < n; i += kGtWarps) {
         float rs = 0.f;
-        for (int c = lane; c < n; c += 32) rs += fabsf(Wk[(size_t)i * n + c].x);
+        for (int c = lane; c < n; c += 32) rs += fabsf(Wk[(size_t)i * ld + c].x);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
         imax = fmaxf(imax, rs);
@@ -589,7 +711,7 @@ __global__ void __launch_bounds__(kGtThreads) k_gt_final(GtJobs js, double kappa
         for (int cb = 0; cb < n; cb += 32) {
             for (int r = wid; r < 32; r += kGtWarps) {
                 const int k = kb + r, c = cb + lane;
-                tile[r * 33 + lane] = (k < n && c < n) ? Wk[(size_t)pp[k] * n + c] : make_float2(0.f, 0.f);
+                tile[r * 33 + lane] = (k < n && c < n) ? Wk[(size_t)pp[k] * ld + c] : make_float2(0.f, 0.f);
             }
             __syncthreads();
             for (int r = wid; r < 32; r += kGtWarps) {
@@ -631,6 +753,38 @@ size_t gjtc_bytes(int n_up, int n_dn, int nw)
     return b + 256;
 }
 
+// The update kernel's tensor maps: job q's work matrices as a 3-D tensor of 8-byte float
+// pairs [count][n][n] (row stride gt_ld(n), matrix stride the scratch per matrix), boxes of
+// 16 columns x 128 rows with 128-byte swizzle.
+static cudaError_t gt_tensor_maps(GtJobs &js)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    static cudaError_t init_err = cudaSuccess;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        init_err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr);
+        if (init_err == cudaSuccess && (qr != cudaDriverEntryPointSuccess || !f)) init_err = cudaErrorSymbolNotFound;
+        if (init_err == cudaSuccess) encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    if (init_err != cudaSuccess) return init_err;
+    for (int q = 0; q < 2; ++q) {
+        memset(&js.tmw[q], 0, sizeof(CUtensorMap));
+        if (q >= js.nj || js.j[q].count == 0) continue;
+        const int n = js.j[q].n;
+        const GtLayout L = gt_layout(n);
+        const cuuint64_t dim[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)js.j[q].count};
+        const cuuint64_t stride[2] = {(cuuint64_t)gt_ld(n) * 8, (cuuint64_t)L.per};
+        const cuuint32_t box[3] = {16, 128, 1}, estride[3] = {1, 1, 1};
+        const CUresult r = encode(&js.tmw[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, js.scr[q] + L.w, dim, stride, box,
+                                  estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, double kappa_max,
                          const WaitCfg &wc)
 {
@@ -652,12 +806,13 @@ cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStrea
     if (cmax == 0 || n_jobs == 0) return cudaSuccess;
     if (!gjtc_fits(nmax)) return cudaErrorInvalidConfiguration;
     const size_t sm_panel = sizeof(float2) * (size_t)nmax * kGtB + sizeof(short) * (size_t)nmax;
-    // 112 KB of operands and the column exponents; at least 120 KB so that one CTA
-    // holds an SM (it allocates all 512 TMEM columns)
-    // 57 KB of panel slices, 28 KB of pivot-row slices, the column exponents: two CTAs per SM
-    const size_t sm_up = 1024 + kGtSl * (size_t)(kGtAPlane + 2 * kGtBPlane) + 4 * (size_t)nmax;
+    // 56 KB of panel slices, 3 x 14 KB of pivot-row slices, 3 x 32 KB of old values, the
+    // column exponents: one CTA per SM
+    const size_t sm_up = 1024 + kGtSl * (size_t)(kGtAPlane + kGtBs * kGtBPlane) + kGtXs * (size_t)kGtXStage +
+                         4 * (size_t)nmax;
     const size_t sm_fin = sizeof(float2) * 32 * 33 + sizeof(short) * 2 * (size_t)nmax;
     cudaError_t e;
+    if ((e = gt_tensor_maps(js)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_gt_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_panel)) !=
         cudaSuccess)
         return e;

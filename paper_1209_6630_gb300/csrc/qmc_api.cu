@@ -749,7 +749,8 @@ bool carve(const Plan &p, int nw, void *ws, size_t ws_bytes, Carve &c)
     c.sg = reinterpret_cast<double *>(take(16 * (size_t)nw));
     c.st = reinterpret_cast<uint32_t *>(take(4 * (size_t)nw));
     c.masks = p.mask_bytes ? reinterpret_cast<uint32_t *>(take(p.mask_bytes * nw)) : nullptr;
-    c.work = p.ffgj ? reinterpret_cast<float2 *>(take(p.msz * 8 * nw)) : nullptr;
+    // (the tensor-core a4 keeps its work matrices in its own scratch, rows 16-byte aligned)
+    c.work = (p.ffgj && !p.tcgj) ? reinterpret_cast<float2 *>(take(p.msz * 8 * nw)) : nullptr;
     c.redo = p.ffgj ? reinterpret_cast<uint8_t *>(take(2 * (size_t)nw)) : nullptr;
     c.redo_scratch = p.ffgj ? take(p.redo_bytes) : nullptr;
     c.c15tc = p.c15tc ? take(c15tc_bytes(*p.sd, nw)) : nullptr;
@@ -765,7 +766,8 @@ size_t bytes_for(const Plan &p, int nw)
     o += p.dinv ? al(p.msz * 8 * nw) : 0;
     o += al(16 * (size_t)nw) * 2 + al(4 * (size_t)nw);
     o += p.mask_bytes ? al(p.mask_bytes * nw) : 0;
-    o += p.ffgj ? al(p.msz * 8 * nw) + al(2 * (size_t)nw) + al(p.redo_bytes) : 0;
+    o += (p.ffgj && !p.tcgj) ? al(p.msz * 8 * nw) : 0;
+    o += p.ffgj ? al(2 * (size_t)nw) + al(p.redo_bytes) : 0;
     o += p.c15tc ? al(c15tc_bytes(*p.sd, nw)) : 0;
     o += p.tcgj ? al(gjtc_bytes(p.sd->n_up, p.sd->n_dn, nw)) : 0;
     return o;
@@ -943,7 +945,7 @@ int eval_impl(const qmc_system *sys, int n_walk, const double *R, int precision,
             j.sign = c.sg + spin;
             j.flag = c.st; j.flag_bit = spin ? QMC_STATUS_SINGULAR_DN : QMC_STATUS_SINGULAR_UP;
             j.n = ns; j.count = nw;
-            if (p.ffgj) { j.work = c.work + off; j.redo = c.redo + spin; j.redo_stride = 2; }
+            if (p.ffgj) { j.work = c.work ? c.work + off : nullptr; j.redo = c.redo + spin; j.redo_stride = 2; }
         }
         if (p.ffgj) {
             // float-pair elimination for every matrix, FP64 for those it flags

@@ -74,17 +74,48 @@ __device__ __forceinline__ uint64_t globaltimer()
     return t;
 }
 
+// One test of the mbarrier phase with the given parity (true: that phase has completed).
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
 // Bounded wait for the mbarrier phase with the given parity; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64_t limit_ns)
 {
     const uint64_t t0 = globaltimer();
     while (true) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
+        if (mbar_try_wait(mbar, parity)) return true;
         if (globaltimer() - t0 > limit_ns) return false;
     }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+
+// Arrive and add `bytes` to the phase's expected transaction count (the bulk copies that
+// complete on this barrier count their bytes down).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> this CTA's shared memory (the TMA's untiled form): both addresses
+// 16-byte aligned, bytes a multiple of 16; completion counted in bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
 
 // Bounded wait on a flag that nothing in the kernel sets (the test hook that
@@ -132,6 +163,82 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// MMA with the A operand in TMEM (K-major, two 16-bit elements per 32-bit column, the lower
+// K index in the low half) and B in shared memory, executed by a whole warp with
+// warp-uniform operands: one lane, chosen by elect.sync, issues the MMA.  Issued this way (operands in uniform registers) an MMA of
+// M = 128, N = 32, K = 16 costs ~17 cycles; from one thread of a divergent branch ~60.
+template <int ACC>
+__device__ __forceinline__ void umma_bf16_ts_warp(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc)
+{
+    asm volatile("{\n\t.reg .pred e, p;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+                 :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(idesc), "n"(ACC));
+}
+
+// tcgen05.commit from a whole warp (one elected lane)
+__device__ __forceinline__ void umma_commit_warp(uint32_t mbar)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n"
+                 :: "r"(mbar) : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes from registers; then
+// tcgen05.wait::st before the data is used
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                    "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+                    "r"(v[15])
+                 : "memory");
+}
+
+// Tensor TMA through a tensor map (param, const or global space): a 3-D box into this
+// CTA's shared memory (completion counted in bytes on the mbarrier), and from shared memory
+// back to global memory (a bulk async-group of the issuing thread).  The innermost
+// coordinate times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(uint64_t tmap, uint32_t dst, int x, int y, int z, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(uint64_t tmap, uint32_t src, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 :: "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(src) : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// this thread's bulk stores have finished reading shared memory / have completed
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes, without the wait: several
+// loads are issued, then tmem_wait_ld() makes all of them usable
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
+// Wait for this thread's TMEM loads; the registers pass through the statement so that no
+// use of them is scheduled before it.
+template <int R, int C>
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[R][C])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) asm volatile("" : "+r"(v[r][c]));
+}
+
 // hi/lo split of two values into packed 16-bit pairs: hi = rn(x), lo = rn(x - hi)
 __device__ __forceinline__ void split2(float a, float b, int f16, uint32_t &hi, uint32_t &lo)
 {
@@ -157,6 +264,19 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr, uint32_t sbo)
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;    // leading byte offset: unused for swizzled K-major
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;    // SWIZZLE_64B
+    return d;
+}
+
+// ... with both strides given (an MN-major operand: LBO between 32-element MN atoms, SBO
+// between groups of 8 K rows)
+__device__ __forceinline__ uint64_t umma_desc_sw64_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)4 << 61;    // SWIZZLE_64B
