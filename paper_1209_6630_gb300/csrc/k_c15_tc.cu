@@ -46,7 +46,9 @@
 namespace qmc {
 
 constexpr int kPrepThreads = 256;                              // two threads per walker row
-constexpr int kMmaThreads = 512;
+constexpr int kMmaEpWarps = 8;                                 // MMA kernel: epilogue warps,
+constexpr int kMmaCpWarps = 4;                                 // copy warps
+constexpr int kMmaThreads = 32 * (kMmaEpWarps + kMmaCpWarps + 1);   // and an MMA warp
 constexpr int kGradPlane0 = 2 * kC15Slices;                    // first C2..C4 plane of a stage
 constexpr int kPlanesPerStep = 2 * kC15Slices + 6;             // [C1 slice][C5 slice][gradient l][hi, lo]
 // A K step of 64 AOs is staged as two stages of 32 (the MMA kernel double-buffers
@@ -316,6 +318,35 @@ __global__ void __launch_bounds__(kPrepThreads, 3) k_c15_prep(C15TcArgs a)
         }
 }
 
+// Bounded wait of a whole warp, which stays converged (every lane polls; the phase, once
+// complete, stays complete until this warp has moved on), with the CTA's abort flag.
+__device__ __forceinline__ bool c15_wait_warp(uint32_t mbar, uint32_t parity, uint64_t limit_ns,
+                                              volatile int *abort, int lane)
+{
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        const bool done = mbar_try_wait(mbar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        if (__any_sync(0xffffffffu, *abort != 0)) return false;
+        int late = lane == 0 && globaltimer() - t0 > limit_ns;
+        late = __shfl_sync(0xffffffffu, late, 0);
+        if (late) {
+            if (lane == 0) *abort = 1;
+            return false;
+        }
+    }
+}
+
+// Warp-specialised: 8 epilogue warps (TMEM lane quadrant x two groups of 64 columns), 4
+// copy warps and an MMA warp.  Per stage of 32 AOs the copy warps move the 6 staged operand
+// planes with one bulk copy (TMA) and gather the MO-coefficient slice rows of the stage's
+// AOs with 16-byte cp.async into the MN-major, 128-byte-swizzled layout the MMA reads (AO
+// padding rows and columns past the padded MO count as zeros), into one of two stage
+// buffers; the MMA warp issues the stage's slice-pair MMAs (each through elect.sync) and
+// releases the buffer with a commit; at the end of each chunk of 1024 AOs the epilogue adds
+// the accumulators to the output.  (Gathering the rows with tensor TMA instead --
+// tile::gather4, 96 copies of 4 rows x 128 bytes per stage -- was slower: the TMA unit's
+// cost per copy, not the bytes, set the pace.)
 __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -323,7 +354,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     // two stage buffers, each [A: 6 planes x 8 KB][B: 6 planes x 8 KB]
     constexpr uint32_t kBufBytes = kC15Slices * (kSPlaneBytes + kSBPlaneBytes);
     int *ao_s = reinterpret_cast<int *>(base + 2 * kBufBytes);     // [kmax_steps * 64]
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t bar[6];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort, s_never;
 
@@ -344,87 +375,84 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
     const int nks = a.nks[slot];
     const int *lst = a.ao_list + slot * (size_t)a.kmax_steps * TC_K;
     for (int q = t; q < nks * TC_K; q += kMmaThreads) ao_s[q] = lst[q];
-    if (t == 0) { s_abort = 0; s_never = 0; }
-
+    const uint32_t b0 = smem_u32(&bar[0]);
+    auto FULL = [&](int buf) { return b0 + 8u * (uint32_t)buf; };            // stage copied
+    auto EMPTY = [&](int buf) { return b0 + 8u * (uint32_t)(2 + buf); };     // stage's MMAs complete
+    const uint32_t bCD = b0 + 32u;                                            // chunk accumulated
+    const uint32_t bED = b0 + 40u;                                            // accumulators read
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
                      :: "r"(smem_u32(&tmem_slot)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
+    if (t == 32) {
+        for (int b = 0; b < 2; ++b) { mbar_init(FULL(b), 1 + 32 * kMmaCpWarps); mbar_init(EMPTY(b), 1); }
+        mbar_init(bCD, 1);
+        mbar_init(bED, kMmaEpWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+        s_never = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t mbs[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
     const bool grad = o == 2;
-    const uint32_t idesc = umma_idesc_f16(TC_M, ncols, grad ? (a.tt.f16 ? 0 : 1) : 1);
     const uint64_t kWait = a.wait_ns;
-    // test hook: the C1 CTA of electron 0, MO tile 0 of the chosen walker tile
-    const bool expire = tile == a.expire_tile && e == 0 && mt == 0 && o == 0;
-    const uint16_t *__restrict__ Bsl = a.slice[spin];
-    const unsigned char *Ag = a.planes + slot * (size_t)a.kmax_steps * kStepBytes +
-                              (size_t)o * kC15Slices * kSPlaneBytes;     // o = 2: the gradient planes
-    const size_t slice_stride = (size_t)s.n_ao * nspad;
-    const int nbplanes = grad ? 2 : kC15Slices;
-    int ncb[2] = {0, 0};                                 // commits per stage buffer
-    bool ok = true;
-
-    const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
-    double *outp = o ? a.L5 : a.X;
-    const int row = (warp & 3) * 32 + lane;            // TMEM lane = walker row of this thread
-    const int w = tile * TC_M + row;
-
-    // copies of stage sg (AO positions 32 sg .. 32 sg + 31) into stage buffer buf
-    auto issue_loads = [&](int sg, int buf) {
-        unsigned char *Ab = base + buf * kBufBytes, *Bb = Ab + kC15Slices * kSPlaneBytes;
-        const unsigned char *ag = Ag + (size_t)sg * kStageBytes;
-        for (int q = t; q < kC15Slices * (int)kSPlaneBytes / 16; q += kMmaThreads)
-            cp_async16(smem_u32(Ab + 16 * q), ag + 16 * (size_t)q, true);
-        for (int q = t; q < nbplanes * SK * (TC_N / 8); q += kMmaThreads) {
-            const int j = q / (SK * (TC_N / 8));
-            const int rem = q - j * (SK * (TC_N / 8));
-            const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
-            const int mu = ao_s[sg * SK + r];
-            const bool v = mu >= 0 && 8 * c < ncols;
-            const uint16_t *bsrc = grad ? (j ? a.tt.lo[spin] : a.tt.hi[spin]) : Bsl + j * slice_stride;
-            const uint16_t *src = bsrc + (size_t)(v ? mu : 0) * nspad + k0 + (v ? 8 * c : 0);
-            cp_async16(smem_u32(Bb + j * kSBPlaneBytes + b_off(r, 8 * c)), src, v);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-
     const int nst = 2 * nks;                             // stages of 32 AOs
-    for (int s0 = 0; s0 < max(nst, 1); s0 += 2 * kChunkSteps) {
-        const int s1 = min(nst, s0 + 2 * kChunkSteps);
-        const int c0 = s0;                               // 0 for the first chunk
-        if (s0 < s1) issue_loads(s0, s0 & 1);
-        for (int sg = s0; sg < s1; ++sg) {
+    const int nchunk = max(1, (nst + 2 * kChunkSteps - 1) / (2 * kChunkSteps));
+    int nissued = 0, nmma = 0;                           // stages copied / multiplied (drain)
+
+    if (warp >= kMmaEpWarps && warp < kMmaEpWarps + kMmaCpWarps) {
+        // ---- copy warps: the stage's 6 operand planes by one bulk copy (TMA), the gathered
+        // MO-coefficient rows by 16-byte cp.async; each lane waits for its own copies, makes
+        // them visible to the tensor cores' proxy and arrives
+        const int cl = t - 32 * kMmaEpWarps;                 // 0 .. 32 * kMmaCpWarps - 1
+        const unsigned char *Ag = a.planes + slot * (size_t)a.kmax_steps * kStepBytes +
+                                  (size_t)o * kC15Slices * kSPlaneBytes;     // o = 2: the gradient planes
+        const int nbplanes = grad ? 2 : kC15Slices;
+        const uint16_t *__restrict__ Bsl = a.slice[spin];
+        const size_t slice_stride = (size_t)s.n_ao * nspad;
+        for (int sg = 0; sg < nst; ++sg) {
             const int buf = sg & 1;
-            if (sg + 1 < s1) {
-                const int nb = buf ^ 1;
-                // the MMAs of stage sg - 1 read buffer nb: wait before overwriting it
-                if (ncb[nb] > 0 && !mbar_wait(mbs[nb], (ncb[nb] - 1) & 1, kWait)) s_abort = 1;
-                issue_loads(sg + 1, nb);
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-            } else {
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (sg >= 2 && !c15_wait_warp(EMPTY(buf), ((sg >> 1) - 1) & 1, kWait, &s_abort, lane)) break;
+            unsigned char *Ab = base + buf * kBufBytes, *Bb = Ab + kC15Slices * kSPlaneBytes;
+            if (cl == 0) {
+                mbar_expect_tx(FULL(buf), kC15Slices * kSPlaneBytes);
+                bulk_g2s(smem_u32(Ab), Ag + (size_t)sg * kStageBytes, kC15Slices * kSPlaneBytes, FULL(buf));
             }
+            for (int q = cl; q < nbplanes * SK * (TC_N / 8); q += 32 * kMmaCpWarps) {
+                const int j = q / (SK * (TC_N / 8));
+                const int rem = q - j * (SK * (TC_N / 8));
+                const int r = rem / (TC_N / 8), c = rem - r * (TC_N / 8);
+                const int mu = ao_s[sg * SK + r];
+                const bool v = mu >= 0 && 8 * c < ncols;
+                const uint16_t *bsrc = grad ? (j ? a.tt.lo[spin] : a.tt.hi[spin]) : Bsl + j * slice_stride;
+                const uint16_t *src = bsrc + (size_t)(v ? mu : 0) * nspad + k0 + (v ? 8 * c : 0);
+                cp_async16(smem_u32(Bb + j * kSBPlaneBytes + b_off(r, 8 * c)), src, v);
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (s_abort) break;
-            if (t == 0) {
+            mbar_arrive(FULL(buf));
+            nissued = sg + 1;
+        }
+    } else if (warp == kMmaEpWarps + kMmaCpWarps) {
+        // ---- MMA warp: converged, one elected lane issues each MMA and commit
+        const uint32_t idesc = umma_idesc_f16(TC_M, ncols, grad ? (a.tt.f16 ? 0 : 1) : 1);
+        for (int c = 0; c < nchunk; ++c) {
+            const int s0 = c * 2 * kChunkSteps, s1 = min(nst, s0 + 2 * kChunkSteps);
+            if (c > 0 && !c15_wait_warp(bED, (c - 1) & 1, kWait, &s_abort, lane)) break;
+            bool ok = true;
+            for (int sg = s0; sg < s1; ++sg) {
+                const int buf = sg & 1;
+                if (!c15_wait_warp(FULL(buf), (sg >> 1) & 1, kWait, &s_abort, lane)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 // descriptors of the buffer's first A and B planes; the others differ only in
                 // the start-address field (address / 16 in the low bits), by constants
                 const uint32_t a0 = smem_u32(base + buf * kBufBytes);
                 const uint64_t dA = umma_desc_sw64(a0, 512);
                 const uint64_t dB = umma_desc(a0 + kC15Slices * kSPlaneBytes, kBLbo, kBSbo);
-                const bool fresh = sg == s0;                  // first stage of a chunk
+                const uint32_t fresh = sg == s0 ? 1u : 0u;     // first stage of a chunk
                 if (grad) {
 #pragma unroll
                     for (int kk = 0; kk < SK / 16; ++kk) {
@@ -435,9 +463,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
                             const uint64_t ah = dA + (((2 * l) * kSPlaneBytes + 32 * kk) >> 4);
                             const uint64_t al = dA + (((2 * l + 1) * kSPlaneBytes + 32 * kk) >> 4);
                             const uint32_t dd = tmem + l * TC_N;
-                            umma_bf16(dd, ah, bh, idesc, (!fresh || kk > 0) ? 1u : 0u);
-                            umma_bf16(dd, ah, bl, idesc, 1u);
-                            umma_bf16(dd, al, bh, idesc, 1u);
+                            umma_bf16_warp(dd, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
+                            umma_bf16_warp(dd, ah, bl, idesc, 1u);
+                            umma_bf16_warp(dd, al, bh, idesc, 1u);
                         }
                     }
                 } else {
@@ -451,117 +479,130 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_c15_mma(C15TcArgs a)
                                 const int j = d - i;
                                 const uint64_t ad = dA + ((i * kSPlaneBytes + 32 * kk) >> 4);
                                 const uint64_t bd = dB + ((j * kSBPlaneBytes + 2 * kk * kBSbo) >> 4);
-                                const bool first = fresh && kk == 0 && i == 0 && d <= kAcc - 1;
-                                umma_bf16(tmem + acc * TC_N, ad, bd, idesc, first ? 0u : 1u);
+                                const bool first = kk == 0 && i == 0 && d <= kAcc - 1;
+                                umma_bf16_warp(tmem + acc * TC_N, ad, bd, idesc, (fresh && first) ? 0u : 1u);
                             }
                         }
                     }
                 }
-                umma_commit(mbs[buf]);
+                umma_commit_warp(EMPTY(buf));                 // the stage buffer may be refilled
+                nmma = sg + 1;
             }
-            ++ncb[buf];
+            if (!ok) break;
+            umma_commit_warp(bCD);                            // the chunk's sums are complete
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        if (expire && !flag_wait(&s_never, kWait)) s_abort = 1;
-        for (int bq = 0; bq < 2; ++bq)
-            if (!s_abort && ncb[bq] > 0 && !mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kWait)) s_abort = 1;
-        __syncthreads();
-        ok = !s_abort;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (grad) {
-            // epilogue C2..C4: FP32 accumulators times the power-of-two output scale
-            const size_t nss = (size_t)ns * ns;
-            float *crow = a.Cg + (size_t)(w < a.nw ? w : 0) * 3 * msz +
-                          (spin ? 3 * (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
-            for (int l = 0; l < 3; ++l) {
-                const float osc = a.tt.out_scale[spin][l];
-                for (int cb = (warp >> 2) * 32; cb < ncols; cb += 32 * (kMmaThreads / 128)) {
-                    uint32_t v[32];
-                    const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(l * TC_N + cb);
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                                   "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-                                   "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-                                   "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-                                   "=r"(v[31])
-                                 : "r"(ta));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (w < a.nw) {
-                        float *dst = crow + (size_t)l * nss;
+    } else {
+        // ---- epilogue warps: row = TMEM lane, columns cgrp * 32 + 64 m
+        const size_t msz = (size_t)s.n_up * s.n_up + (size_t)s.n_dn * s.n_dn;
+        double *outp = o ? a.L5 : a.X;
+        const int row = (warp & 3) * 32 + lane;        // TMEM lane = walker row of this thread
+        const int w = tile * TC_M + row;
+        const int cgrp = warp >> 2;
+        // test hook: the C1 CTA of electron 0, MO tile 0 of the chosen walker tile
+        const bool expire = tile == a.expire_tile && e == 0 && mt == 0 && o == 0;
+        for (int c = 0; c < nchunk; ++c) {
+            bool ok;
+            if (expire && c == 0) {
+                int f = 0;
+                if (lane == 0) {
+                    f = flag_wait(&s_never, kWait);
+                    if (!f) s_abort = 1;
+                }
+                ok = __shfl_sync(0xffffffffu, f, 0) != 0;
+            } else {
+                ok = c15_wait_warp(bCD, c & 1, kWait, &s_abort, lane);
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int c0 = c * 2 * kChunkSteps;          // 0 for the first chunk
+            if (grad) {
+                // epilogue C2..C4: FP32 accumulators times the power-of-two output scale
+                const size_t nss = (size_t)ns * ns;
+                float *crow = a.Cg + (size_t)(w < a.nw ? w : 0) * 3 * msz +
+                              (spin ? 3 * (size_t)s.n_up * s.n_up : 0) + (size_t)ei * ns;
+                for (int l = 0; l < 3; ++l) {
+                    const float osc = a.tt.out_scale[spin][l];
+                    for (int cb = cgrp * 32; cb < ncols; cb += 32 * (kMmaEpWarps / 4)) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(l * TC_N + cb), v);
+                        if (w < a.nw) {
+                            float *dst = crow + (size_t)l * nss;
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) {
+                                const int k = k0 + cb + q;
+                                if (k >= ns) break;
+                                const float val = nks > 0 ? __uint_as_float(v[q]) * osc : 0.f;
+                                if (c0 == 0) dst[k] = val;
+                                else dst[k] += val;
+                            }
+                        }
+                    }
+                }
+            } else {
+                // epilogue C1 / C5: the four accumulators (orders 0, 1, 2 exact; 3..5 rounded at
+                // 2^-45) summed as float pairs on the FP32 pipes (each addition exact but the last
+                // two lo additions, 2^-47 of the sum), scaled by 2^(E_w + F_k) and converted once:
+                // two conversions and one FP64 addition per element instead of nine FP64 operations
+                const int E = (w < a.nw) ? a.rexp[(slot * TC_M + row) * 2 + o] : 0;
+                double *dst = outp + (size_t)(w < a.nw ? w : 0) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
+                              (size_t)ei * ns;
+                for (int cb = cgrp * 32; cb < ncols; cb += 32 * (kMmaEpWarps / 4)) {
+                    float hs[32], ls[32];
+                    {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            hs[q] = __uint_as_float(v[q]);
+                            ls[q] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int acc = 1; acc < kAcc; ++acc) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * TC_N + cb), v);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            float sh, se;
+                            ff::two_sum(hs[q], __uint_as_float(v[q]), sh, se);
+                            hs[q] = sh;
+                            ls[q] = __fadd_rn(ls[q], se);
+                        }
+                    }
+                    if (w < a.nw && nks > 0) {
 #pragma unroll
                         for (int q = 0; q < 32; ++q) {
                             const int k = k0 + cb + q;
                             if (k >= ns) break;
-                            const float val = nks > 0 ? __uint_as_float(v[q]) * osc : 0.f;
+                            float h2, l2;
+                            ff::fast_two_sum(hs[q], ls[q], h2, l2);
+                            const int ex = E + a.fexp[spin][k];   // exact power-of-two scaling in FP32
+                            const double val = (double)scale_pow2(h2, ex) + (double)scale_pow2(l2, ex);
                             if (c0 == 0) dst[k] = val;
                             else dst[k] += val;
                         }
+                    } else if (w < a.nw) {
+                        for (int q = 0; q < 32 && k0 + cb + q < ns; ++q) dst[k0 + cb + q] = 0.0;
                     }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            continue;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bED);
         }
-        // epilogue C1 / C5: the four accumulators (orders 0, 1, 2 exact; 3..5 rounded at
-        // 2^-45) summed as float pairs on the FP32 pipes (each addition exact but the last
-        // two lo additions, 2^-47 of the sum), scaled by 2^(E_w + F_k) and converted once:
-        // two conversions and one FP64 addition per element instead of nine FP64 operations
-        const int E = (w < a.nw) ? a.rexp[(slot * TC_M + row) * 2 + o] : 0;
-        double *dst = outp + (size_t)(w < a.nw ? w : 0) * msz + (spin ? (size_t)s.n_up * s.n_up : 0) +
-                      (size_t)ei * ns;
-        for (int cb = (warp >> 2) * 32; cb < ncols; cb += 32 * (kMmaThreads / 128)) {
-            float hs[32], ls[32];
-            {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    hs[q] = __uint_as_float(v[q]);
-                    ls[q] = 0.f;
-                }
-            }
-#pragma unroll
-            for (int acc = 1; acc < kAcc; ++acc) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * TC_N + cb), v);
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    float sh, se;
-                    ff::two_sum(hs[q], __uint_as_float(v[q]), sh, se);
-                    hs[q] = sh;
-                    ls[q] = __fadd_rn(ls[q], se);
-                }
-            }
-            if (w < a.nw && nks > 0) {
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int k = k0 + cb + q;
-                    if (k >= ns) break;
-                    float h2, l2;
-                    ff::fast_two_sum(hs[q], ls[q], h2, l2);
-                    const int ex = E + a.fexp[spin][k];   // exact power-of-two scaling in FP32
-                    const double val = (double)scale_pow2(h2, ex) + (double)scale_pow2(l2, ex);
-                    if (c0 == 0) dst[k] = val;
-                    else dst[k] += val;
-                }
-            } else if (w < a.nw) {
-                for (int q = 0; q < 32 && k0 + cb + q < ns; ++q) dst[k0 + cb + q] = 0.0;
-            }
+    }
+    __syncthreads();
+    if (s_abort) {
+        if (warp < kMmaEpWarps && (warp >> 2) == 0) {
+            const int w = tile * TC_M + (warp & 3) * 32 + lane;
+            if (w < a.nw) atomicOr(a.wstatus + w, (uint32_t)QMC_STATUS_TIMEOUT);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        // nothing may land in shared memory or TMEM after the CTA exits
+        if (warp == kMmaEpWarps && lane == 0)              // the bulk copies (cp.async: waited above)
+            for (int sg = max(0, nissued - 2); sg < nissued; ++sg) mbar_wait(FULL(sg & 1), (sg >> 1) & 1, kDrainNs);
     }
-    if (!ok) {
-        if (w < a.nw && (warp >> 2) == 0) atomicOr(a.wstatus + w, (uint32_t)QMC_STATUS_TIMEOUT);
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        for (int bq = 0; bq < 2; ++bq)                  // let MMAs in flight drain
-            if (ncb[bq] > 0) mbar_wait(mbs[bq], (ncb[bq] - 1) & 1, kDrainNs);
-    }
+    if (warp == kMmaEpWarps + kMmaCpWarps && lane == 0)
+        for (int sg = max(0, nmma - 2); sg < nmma; ++sg) mbar_wait(EMPTY(sg & 1), (sg >> 1) & 1, kDrainNs);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");

@@ -42,10 +42,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
-
-#include <cuda.h>
-#include <cudaTypedefs.h>
 
 #include "ff_math.cuh"
 #include "qmc_internal.cuh"
@@ -758,29 +754,17 @@ size_t gjtc_bytes(int n_up, int n_dn, int nw)
 // 16 columns x 128 rows with 128-byte swizzle.
 static cudaError_t gt_tensor_maps(GtJobs &js)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    static std::once_flag once;
-    static cudaError_t init_err = cudaSuccess;
-    std::call_once(once, [] {
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult qr;
-        init_err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr);
-        if (init_err == cudaSuccess && (qr != cudaDriverEntryPointSuccess || !f)) init_err = cudaErrorSymbolNotFound;
-        if (init_err == cudaSuccess) encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    });
-    if (init_err != cudaSuccess) return init_err;
     for (int q = 0; q < 2; ++q) {
         memset(&js.tmw[q], 0, sizeof(CUtensorMap));
         if (q >= js.nj || js.j[q].count == 0) continue;
         const int n = js.j[q].n;
         const GtLayout L = gt_layout(n);
-        const cuuint64_t dim[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)js.j[q].count};
-        const cuuint64_t stride[2] = {(cuuint64_t)gt_ld(n) * 8, (cuuint64_t)L.per};
-        const cuuint32_t box[3] = {16, 128, 1}, estride[3] = {1, 1, 1};
-        const CUresult r = encode(&js.tmw[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, js.scr[q] + L.w, dim, stride, box,
-                                  estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        const uint64_t dim[3] = {(uint64_t)n, (uint64_t)n, (uint64_t)js.j[q].count};
+        const uint64_t stride[2] = {(uint64_t)gt_ld(n) * 8, (uint64_t)L.per};
+        const uint32_t box[3] = {16, 128, 1};
+        const cudaError_t e = tmap_encode(&js.tmw[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, js.scr[q] + L.w, dim,
+                                          stride, box, CU_TENSOR_MAP_SWIZZLE_128B);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

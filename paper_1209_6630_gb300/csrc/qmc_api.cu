@@ -673,6 +673,37 @@ extern "C" int qmc_system_shell_r2(const qmc_system *sys, double *R2_host)
 // ---------------------------------------------------------------------------
 // Workspace plan per walker: X (C1 in FP64, LU input), Cd (C2..C5), Dinv,
 // per-spin log|det| and sign, status bits.
+cudaError_t qmc::tmap_encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *addr,
+                             const uint64_t *dims, const uint64_t *strides, const uint32_t *box,
+                             CUtensorMapSwizzle swz)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    static cudaError_t init_err = cudaSuccess;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        init_err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr);
+        if (init_err == cudaSuccess && (qr != cudaDriverEntryPointSuccess || !f)) init_err = cudaErrorSymbolNotFound;
+        if (init_err == cudaSuccess) encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    if (init_err != cudaSuccess) return init_err;
+    if (rank < 1 || rank > 5) return cudaErrorInvalidValue;
+    cuuint64_t d[5], st[4];
+    cuuint32_t b[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        es[i] = 1;
+        if (i > 0) st[i - 1] = strides[i - 1];
+    }
+    memset(m, 0, sizeof(CUtensorMap));
+    const CUresult r = encode(m, dt, (cuuint32_t)rank, const_cast<void *>(addr), d, st, b, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 namespace {
 
 struct Plan {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libqmcgb translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -187,6 +188,13 @@ cudaError_t launch_backward_tc(const SysDev &s, const MixedTables &mt, const BwB
                                const double *dinv, const double *g, double *dA_up, double *dA_dn, void *ws,
                                size_t ws_bytes, cudaStream_t st, const WaitCfg &wc);
 // a4 of the mixed path with the panel updates on the tensor cores
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the
+// driver library): a rank-d map of 8- or 16-bit elements, row-major, boxes `box`,
+// the given swizzle, zero fill outside the tensor.  strides[] are the byte strides of
+// dimensions 1..rank-1 (multiples of 16).
+cudaError_t tmap_encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *addr, const uint64_t *dims,
+                        const uint64_t *strides, const uint32_t *box, CUtensorMapSwizzle swz);
+
 bool gjtc_fits(int nmax);
 size_t gjtc_bytes(int n_up, int n_dn, int nw);
 cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStream_t st, double kappa_max,

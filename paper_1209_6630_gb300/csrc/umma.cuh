@@ -163,6 +163,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// MMA with both operands in shared memory, executed by a whole converged warp with
+// warp-uniform operands: one lane, chosen by elect.sync, issues it (acc: accumulate or
+// overwrite, warp-uniform).
+__device__ __forceinline__ void umma_bf16_warp(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred e, p;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 // MMA with the A operand in TMEM (K-major, two 16-bit elements per 32-bit column, the lower
 // K index in the low half) and B in shared memory, executed by a whole warp with
 // warp-uniform operands: one lane, chosen by elect.sync, issues the MMA.  Issued this way (operands in uniform registers) an MMA of
