@@ -10,15 +10,16 @@
 //
 // k_vd_rowexp: the exponent bound E of every D^-1 row (|D^-1[e,k]| < 2^E).
 // k_vd_mma (one CTA per walker tile of 128 and electron e): the union of the
-// tile's active AOs for e (from the shell masks), then per AO tile of 128: v
+// tile's active AOs for e (from the shell masks), then per AO tile of 64: v
 // on the tcgen05 tensor cores as M = 128 walkers x N = 128 AOs x K = N_s MOs
 // from exact BF16 slices, the split of the C1 products (k_c15_tc.cu) with
 // the roles of the indices exchanged: D^-1 rows scaled by 2^-E_{w,e} (sliced
 // in the kernel from the FP64 inverse), A rows scaled by 2^-G_mu (sliced at
 // load), six slices each, the 21 slice pairs of order <= 5 into four FP32
 // accumulators (orders 0, 1, 2 exact; 3..5 together); K stages of 32 MOs
-// through two buffers (B rows by cp.async, A slices stored by all threads),
-// one thread issuing the MMAs, mbarrier commits, bounded waits.  Epilogue:
+// through one stage buffer per CTA, two CTAs per SM (the staged D^-1 slices
+// by one bulk copy, the B rows by cp.async), a converged warp issuing the MMAs
+// through elect.sync, mbarrier commits, bounded waits.  Epilogue:
 // v = 2^(E + G_mu) (acc0 + acc1 + acc2 + acc3) as a float pair (the order sums
 // are exact integers in their units; the power of two is applied exactly),
 // and for every active AO of the walker the gradient (FP32) and Laplacian
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
     int *ao_s = reinterpret_cast<int *>(base + kVdBuf);       // [n_ao + kVdN]
     __shared__ uint32_t un_s[256];
     __shared__ int warp_s[kVdThreads / 32];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar, cbar;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
 
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
     }
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
+        mbar_init(smem_u32(&cbar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -165,7 +167,10 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
                                bf16_pair(sl[4][j], sl[5][j]), bf16_pair(sl[6][j], sl[7][j]));
         }
     }
-    __syncthreads();                                       // the block's global writes, before its cp.async reads
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // the staging is read back by bulk copies
+    __syncthreads();                                       // the block's global writes, before the copies read them
+    const uint32_t cb = smem_u32(&cbar);
+    int ncopy = 0;
 
     // epilogue role: walker row erow (TMEM lane), columns cg * 32 .. + 32 of an AO tile of 64
     const int erow = (warp & 3) * 32 + lane, cg = warp >> 2;
@@ -189,8 +194,10 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
             // the stage buffer: A (the staged D^-1 slices) and B (the rows of A of this AO tile)
             const int k0 = sg * kVdK;
             const unsigned char *As = ast + (size_t)sg * kC15Slices * kVdPlane;
-            for (int q = t; q < (int)(kC15Slices * kVdPlane / 16); q += kVdThreads)
-                cp_async16(smem_u32(Ab + 16 * q), As + 16 * (size_t)q, true);
+            if (t == 0) {                                  // the staged D^-1 slices: one bulk copy
+                mbar_expect_tx(cb, kC15Slices * kVdPlane);
+                bulk_g2s(smem_u32(Ab), As, kC15Slices * kVdPlane, cb);
+            }
             for (int q = t; q < kC15Slices * kVdN * 4; q += kVdThreads) {
                 const int j = q / (kVdN * 4), rem = q - j * (kVdN * 4);
                 const int r = rem >> 2, c = rem & 3;
@@ -202,8 +209,10 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
             asm volatile("cp.async.commit_group;" ::: "memory");
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            ++ncopy;
+            if (!mbar_wait(cb, (ncopy - 1) & 1, kWait)) s_abort = 1;
             __syncthreads();
-            if (t == 0) {
+            if (warp == 0) {                                   // converged: elect.sync per MMA
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint64_t dA = umma_desc_sw64(smem_u32(Ab), 512);
                 const uint64_t dB = umma_desc_sw64(smem_u32(Bb), 512);
@@ -218,10 +227,10 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
                             const uint64_t ad = dA + ((i * kVdPlane + 32 * kk) >> 4);
                             const uint64_t bd = dB + ((j * kVdBPlane + 32 * kk) >> 4);
                             const bool first = sg == 0 && kk == 0 && i == 0 && d <= kVdAcc - 1;
-                            umma_bf16(tmem + acc * kVdN, ad, bd, idesc, first ? 0u : 1u);
+                            umma_bf16_warp(tmem + acc * kVdN, ad, bd, idesc, first ? 0u : 1u);
                         }
                     }
-                umma_commit(mb);
+                umma_commit_warp(mb);
             }
             ++ncommit;
             // the buffer is rewritten by the next stage: wait for these MMAs (the other CTA
@@ -301,6 +310,7 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
     if (!ok) {
         if (t < TC_M && tile * TC_M + t < a.nw) atomicOr(a.wstatus + tile * TC_M + t, (uint32_t)QMC_STATUS_TIMEOUT);
         asm volatile("cp.async.wait_all;" ::: "memory");
+        if (ncopy > 0) mbar_wait(cb, (ncopy - 1) & 1, kDrainNs);        // the last bulk copy
         if (ncommit > 0) mbar_wait(mb, (ncommit - 1) & 1, kDrainNs);   // let MMAs in flight drain
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
