@@ -362,11 +362,13 @@ def cfree_bench(q, R, prec, flush, e0, e1, mode):
     return res, out
 
 
-def dmc_bench(q, R, prec, flush, e0, e1, t_eval_ms):
+def dmc_bench(q, R, prec, flush, e0, e1):
     """One fixed-node DMC step with constant population (qmc_dmc_step: move
     Eq. 1, evaluation, weight Eq. 3, reconfiguration Sec. II.B, copy of the
     drawn walkers) on the same batch, timed like the evaluation; the MC
-    kernels' share is the difference to the evaluation alone."""
+    kernels (move, weight, reconfiguration) are also timed on their own
+    through their entry points.  (The step evaluates the moved walkers, so
+    its time minus the evaluation of the unmoved batch is not the MC share.)"""
     import torch
     W = int(R.shape[0])
     a0 = q.init_state(R, precision=prec)
@@ -395,8 +397,23 @@ def dmc_bench(q, R, prec, flush, e0, e1, t_eval_ms):
         ts.append(e0.elapsed_time(e1))
     t = sum(ts) / len(ts)
     sv = stats.cpu().numpy()
+    from paper_1209_6630_gb300 import dmc_move, dmc_weight, srmc_reconfigure
+    st0 = a0
+
+    def one(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+    mc = {"move": one(lambda: dmc_move(st0["R"], st0["drift"], tau, 17, 9)),
+          "weight": one(lambda: dmc_weight(st0["e_loc"], st0["sign"], st0["status"], st0["e_loc"], st0["sign"],
+                                           st0["status"], tau, e_t)),
+          "reconfiguration": one(lambda: srmc_reconfigure(st0["e_loc"].abs(), 17, 9))}
     res = {"walker_steps_per_s": W / (t / 1e3), "ms_per_step": t, "tau": tau,
-           "mc_kernels_ms": t - t_eval_ms, "accepted": int(sv[3]), "walkers_alive": int(sv[1]),
+           "mc_kernels_ms": mc, "accepted": int(sv[3]), "walkers_alive": int(sv[1]),
            "what": "move (Eq. 1) + evaluation + fixed-node weight (Eq. 3) + SRMC draw (Sec. II.B) + copy"}
     del a, a0, b, ws
     torch.cuda.empty_cache()
@@ -722,7 +739,7 @@ def main():
                    "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host_out.values()))}
 
     if not a.no_dmc:
-        line["dmc_step"] = dmc_bench(q, R, prec, flush, e0, e1, t_step)
+        line["dmc_step"] = dmc_bench(q, R, prec, flush, e0, e1)
     cf_out = None
     if prec != "f64" and not a.no_cfree and q.tiles()["c15_mode"] in ("tensor", "cfree"):
         alt = "tensor" if q.tiles()["c15_mode"] == "cfree" else "cfree"

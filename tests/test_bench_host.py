@@ -65,6 +65,10 @@ def test_bench_calls_only_defined_or_imported_names():
     for n in ast.walk(tree):
         if isinstance(n, (ast.Import, ast.ImportFrom)):
             known |= {(a.asname or a.name).split(".")[0] for a in n.names}
+        if isinstance(n, ast.arg):                  # parameters (a callable passed in)
+            known.add(n.arg)
+        if isinstance(n, ast.Assign):               # local callables (lambdas, aliases)
+            known |= {t.id for t in n.targets if isinstance(t, ast.Name)}
     calls = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
     missing = sorted(c for c in calls if c not in known and not hasattr(builtins, c))
     assert not missing, missing
