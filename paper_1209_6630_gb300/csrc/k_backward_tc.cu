@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_bw_mma(BwTcArgs a)
                     const int j = ord - i;
                     const uint64_t ad = dA + ((i * kBtAPlane + 2 * kk * kBSbo) >> 4);
                     const uint64_t xd = dX + ((j * xplane + 32 * kk) >> 4);
-                    umma_bf16(d, ad, xd, idesc, (first && kk == 0 && ord == 0) ? 0u : 1u);
+                    umma_bf16_warp(d, ad, xd, idesc, (first && kk == 0 && ord == 0) ? 0u : 1u);
                 }
     };
 
@@ -382,10 +382,10 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_bw_mma(BwTcArgs a)
                 ok = false;
                 break;
             }
-            if (t == 0) {
+            if (warp == 0) {                              // converged: elect.sync per MMA
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 mma(stage & 1, tile, j % kBtABufs, stage == 0);
-                umma_commit(mbs[j % kBtABufs]);
+                umma_commit_warp(mbs[j % kBtABufs]);
             }
             ncommit = j + 1;
             if (!has_next) break;
