@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (t == 0) {
+        if ((t >> 5) == 0) {                          // converged warp: elect.sync per MMA
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll
@@ -750,12 +750,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(TcArgs p)
                     const uint64_t ah = umma_desc(a0 + (2 * l) * kAPlaneBytes + 32 * kk, 16, 1024);
                     const uint64_t al = umma_desc(a0 + (2 * l + 1) * kAPlaneBytes + 32 * kk, 16, 1024);
                     const uint32_t d = tmem + l * TC_N;
-                    umma_bf16(d, ah, bh, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
-                    umma_bf16(d, ah, bl, idesc, 1u);
-                    umma_bf16(d, al, bh, idesc, 1u);
+                    umma_bf16_warp(d, ah, bh, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16_warp(d, ah, bl, idesc, 1u);
+                    umma_bf16_warp(d, al, bh, idesc, 1u);
                 }
             }
-            umma_commit(mbar_a);
+            umma_commit_warp(mbar_a);
         }
     }
 

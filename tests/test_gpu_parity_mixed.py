@@ -91,3 +91,33 @@ def test_mixed_matches_f64_path_on_gpu(sys158):
     b = q.eval(R, precision="f64")
     assert (a["logpsi"] - b["logpsi"]).abs().max().item() < 1e-6
     assert ((a["e_loc"] - b["e_loc"]).abs() / b["e_loc"].abs()).max().item() < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol_d", [("mixed", 1e-5), ("mixed_bf16", 5e-5)])
+def test_float_float_c15_mode_vs_oracle(prec, tol_d):
+    """The alternative C1/C5 arithmetic (c15_mode = float_float: float-float products for
+    C1 and C5, C2..C4 by the separate tensor-core contraction), Slater entries and the
+    evaluation against the oracle at the same bars."""
+    s = config_system("158e")
+    o, q = Oracle(s), _q(s)
+    q.set_tiles(c15_mode="float_float")
+    W = 130
+    R = make_walkers(s, W, first=500)
+    Rd = torch.from_numpy(R).to(dev)
+    up, dn = q.slater(Rd, precision=prec)
+    up, dn = up.cpu().numpy(), dn.cpu().numpy()
+    worst_ff, worst_d = 0.0, 0.0
+    for w in (0, 63, 127, 128, 129):
+        d = o.eval_debug(R[w])
+        for got, ref in ((up[w], d["C_up"]), (dn[w], d["C_dn"])):
+            worst_ff = max(worst_ff, _rowwise_rel(got[0], ref[0]), _rowwise_rel(got[4], ref[4]))
+            worst_d = max(worst_d, max(_rowwise_rel(got[l], ref[l]) for l in range(1, 4)))
+    assert worst_ff < 1e-9, worst_ff
+    assert worst_d < tol_d, worst_d
+    out = q.eval(Rd, precision=prec)
+    ref = o.eval(R)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    np.testing.assert_array_equal(g["status"], ref["status"])
+    np.testing.assert_array_equal(g["sign"], ref["sign"])
+    assert np.abs(g["logpsi"] - ref["logpsi"]).max() < 1e-6
+    assert (np.abs(g["e_loc"] - ref["e_loc"]) / np.abs(ref["e_loc"])).max() < 1e-5
