@@ -181,6 +181,40 @@ __global__ void __launch_bounds__(kGtThreads) k_gt_init(GtJobs js)
     }
 }
 
+// Operand B of the update: the pivot rows before the update (zero in the panel's columns
+// and for c >= w), scaled per column; one thread per column, its 32 values loaded at once.
+__device__ __forceinline__ void gt_operand_b(unsigned char *sc, const GtLayout &L, int n, int jb, int w,
+                                             const short *ppS)
+{
+    const float2 *__restrict__ Wk = reinterpret_cast<const float2 *>(sc + L.w);
+    const int ld = gt_ld(n);
+    int *Fcol = reinterpret_cast<int *>(sc + L.f);
+    unsigned char *Bpl = sc + L.b;
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        const bool vcol = !(col >= jb && col < jb + w);
+        float2 u[kGtB];
+        float mx = 0.f;
+#pragma unroll
+        for (int c = 0; c < kGtB; ++c) {
+            u[c] = (vcol && c < w) ? Wk[(size_t)ppS[c] * ld + col] : make_float2(0.f, 0.f);
+            mx = fmaxf(mx, fabsf(u[c].x));
+        }
+        const int F = exp_bound(mx);
+        Fcol[col] = F;
+        const int cl = col % kGtN;
+        unsigned char *base = Bpl + (size_t)(col / kGtN) * kGtSl * kGtBPlane + (cl & 7) * 2;
+#pragma unroll
+        for (int c = 0; c < kGtB; ++c) {
+            float s7[kGtSl];
+            slice_n<kGtSl>(u[c], F, s7);
+            unsigned char *b = base + b_off32c(c, cl & ~7);
+#pragma unroll
+            for (int j = 0; j < kGtSl; ++j)
+                *reinterpret_cast<__nv_bfloat16 *>(b + (size_t)j * kGtBPlane) = __float2bfloat16_rn(s7[j]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
 {
     const GjJob &J = js.j[blockIdx.y];
@@ -197,8 +231,7 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
     short *used_g = reinterpret_cast<short *>(sc + L.used);
     unsigned char *piv_g = sc + L.piv;
     int *Erow = reinterpret_cast<int *>(sc + L.e);
-    int *Fcol = reinterpret_cast<int *>(sc + L.f);
-    unsigned char *Apl = sc + L.a, *Bpl = sc + L.b;
+    unsigned char *Apl = sc + L.a;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *P = reinterpret_cast<float2 *>(smem_raw);           // [n][32]
@@ -329,31 +362,194 @@ __global__ void __launch_bounds__(kGpThreads, 1) k_gt_panel(GtJobs js)
             *reinterpret_cast<__nv_bfloat16 *>(base + (size_t)j * kGtAPlane) = __float2bfloat16_rn(s7[j]);
         if (lane == 0) Erow[i] = E;
     }
-    // operand B: the pivot rows before the update (zero in the panel's columns and
-    // for c >= w), scaled per column; one thread per column, its 32 values loaded at once
-    for (int col = t; col < n; col += kGpThreads) {
-        const bool vcol = !(col >= jb && col < jb + w);
-        float2 u[kGtB];
-        float mx = 0.f;
+    gt_operand_b(sc, L, n, jb, w, ppS);
+}
+
+// The panel kernel with one thread per row (n <= kGpRowMax): thread i owns row i of the
+// n x 32 panel (shared memory, rows padded to 33 float pairs: conflict-free).  The 32 columns
+// are eliminated in four sub-panels of 8, whose columns sit in the thread's registers: each
+// pivot step updates only those 8 columns (the pivot column becomes the column of the step's
+// Gauss-Jordan transformation, as in k_gt_panel); after the sub-panel its composed
+// transformation T = I + W S (W: the 8 transformation columns, S: the 8 pivot rows) is
+// applied to the other 24 panel columns as one rank-8 float-float update,
+//   X[i][j] <- [i not a pivot of the sub-panel] X[i][j] + sum_k W[i][k] X[p_k][j],
+// with the pivot rows' values from before the sub-panel.  The pivot rule (largest |entry|
+// among the rows not used yet, the first on ties) and the arithmetic per multiply-add are
+// those of the column-by-column elimination; the sums over a sub-panel's pivots are taken in
+// pivot order.  ~3x fewer instructions than k_gt_panel.
+constexpr int kGpRowMax = 544;
+constexpr int kGpSub = 8;
+constexpr int kGpRowLd = kGtB + 1;                       // float pairs per shared-memory row
+
+__global__ void __launch_bounds__(kGpRowMax, 1) k_gt_panel_t(GtJobs js)
+{
+    const GjJob &J = js.j[blockIdx.y];
+    const int m = blockIdx.x;
+    const int n = J.n, jb = js.jb;
+    if (m >= J.count || jb >= n) return;
+    const GtLayout L = gt_layout(n);
+    unsigned char *sc = js.scr[blockIdx.y] + (size_t)m * L.per;
+    GtState *st = reinterpret_cast<GtState *>(sc + L.state);
+    if (st->sing) return;
+    float2 *__restrict__ Wk = reinterpret_cast<float2 *>(sc + L.w);
+    const int ld = gt_ld(n);
+    short *pp_g = reinterpret_cast<short *>(sc + L.pp);
+    short *used_g = reinterpret_cast<short *>(sc + L.used);
+    unsigned char *piv_g = sc + L.piv;
+    int *Erow = reinterpret_cast<int *>(sc + L.e);
+    unsigned char *Apl = sc + L.a;
+
+    extern __shared__ __align__(16) unsigned char gp_smem[];
+    float2 *P = reinterpret_cast<float2 *>(gp_smem);     // [blockDim.x][kGpRowLd]
+    __shared__ float2 U_s[kGpSub][kGtB];                  // the sub-panel's pivot rows, before it
+    __shared__ float2 prow_s[kGpSub + 1];                 // the step's pivot row on the sub-panel, scaled; 1 / pivot
+    __shared__ short ppS[kGtB];
+    __shared__ int red_i[kGpRowMax / 32];
+    __shared__ float red_f[kGpRowMax / 32];
+
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nwarps = blockDim.x >> 5;
+    const int w = min(kGtB, n - jb);
+    const int i = t;                                      // this thread's row
+    const bool row_ok = i < n;
+    float2 *row = P + (size_t)t * kGpRowLd;
+    // the previous panel's pivots stop being pivots of the current panel
+    if (jb > 0 && t < kGtB) piv_g[pp_g[jb - kGtB + t]] = 0;
+    if (row_ok && w == kGtB) {
+        const float4 *src = reinterpret_cast<const float4 *>(Wk + (size_t)i * ld + jb);
 #pragma unroll
-        for (int c = 0; c < kGtB; ++c) {
-            u[c] = (vcol && c < w) ? Wk[(size_t)ppS[c] * ld + col] : make_float2(0.f, 0.f);
-            mx = fmaxf(mx, fabsf(u[c].x));
+        for (int q = 0; q < kGtB / 2; ++q) {
+            const float4 v = src[q];
+            row[2 * q] = make_float2(v.x, v.y);
+            row[2 * q + 1] = make_float2(v.z, v.w);
         }
-        const int F = exp_bound(mx);
-        Fcol[col] = F;
-        const int cl = col % kGtN;
-        unsigned char *base = Bpl + (size_t)(col / kGtN) * kGtSl * kGtBPlane + (cl & 7) * 2;
+    } else {
+        for (int j = 0; j < kGtB; ++j) row[j] = (row_ok && j < w) ? Wk[(size_t)i * ld + jb + j] : make_float2(0.f, 0.f);
+    }
+    bool used = !row_ok || used_g[i] != 0;
+    GtState S = *st;
+    bool sing = false;
+
+    for (int sb = 0; sb < kGtB / kGpSub && sb * kGpSub < w; ++sb) {
+        const int c0 = sb * kGpSub;
+        float2 xs[kGpSub];                                // the sub-panel's columns of this row
 #pragma unroll
-        for (int c = 0; c < kGtB; ++c) {
-            float s7[kGtSl];
-            slice_n<kGtSl>(u[c], F, s7);
-            unsigned char *b = base + b_off32c(c, cl & ~7);
+        for (int q = 0; q < kGpSub; ++q) xs[q] = row[c0 + q];
+        int nk = 0;                                       // pivots of this sub-panel
+        bool sub_piv = false;                             // this row is one of them
 #pragma unroll
-            for (int j = 0; j < kGtSl; ++j)
-                *reinterpret_cast<__nv_bfloat16 *>(b + (size_t)j * kGtBPlane) = __float2bfloat16_rn(s7[j]);
+        for (int cc = 0; cc < kGpSub; ++cc) {
+            if (c0 + cc >= w) break;
+            // block-wide argmax of |x[c]| over the rows not used yet
+            float bv = used ? -1.f : fabsf(xs[cc].x);
+            int bi = used ? n : i;
+            gt_block_argmax(bv, bi, red_f, red_i, lane, wid);
+            __syncthreads();
+            // every warp merges the warps' candidates by shuffles (the same merge rule, any order)
+            float v = lane < nwarps ? red_f[lane] : -1.f;
+            int p = lane < nwarps ? red_i[lane] : n;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+                gt_argmax_merge(v, p, v2, p2);
+            }
+            if (!(v > 0.f)) {                             // every thread sees the same candidates
+                sing = true;
+                break;
+            }
+            if (i == p) {                                 // publish the pivot row (all 32 columns) and,
+                for (int j = 0; j < kGtB; ++j) U_s[cc][j] = row[j];   // scaled by 1 / pivot, its
+#pragma unroll                                            // sub-panel part
+                for (int q = 0; q < kGpSub; ++q) U_s[cc][c0 + q] = xs[q];
+                const float2 pinv_o = ff::inv(xs[cc]);
+#pragma unroll
+                for (int q = 0; q < kGpSub; ++q) prow_s[q] = (q == cc) ? pinv_o : ff::mul(xs[q], pinv_o);
+                prow_s[kGpSub] = pinv_o;
+                used = true;
+                sub_piv = true;
+            }
+            __syncthreads();
+            const float2 pv = U_s[cc][c0 + cc];
+            if (t == 0) {
+                const float2 a = pv.x < 0.f ? ff::neg(pv) : pv;
+                const float2 mg = ff::mul(make_float2(S.mag_h, S.mag_l), a);
+                int ex;
+                frexpf(mg.x, &ex);
+                S.mag_h = ldexpf(mg.x, -ex);
+                S.mag_l = ldexpf(mg.y, -ex);
+                S.mag_e += ex;
+                S.neg ^= pv.x < 0.f;
+                ppS[c0 + cc] = (short)p;
+            }
+            // the step on the sub-panel's 8 columns (the same expressions as k_gt_panel)
+            const float2 mf = ff::neg(xs[cc]);
+#pragma unroll
+            for (int q = 0; q < kGpSub; ++q) {
+                const float2 prow = prow_s[q];
+                if (i == p) xs[q] = prow;
+                else xs[q] = ff::fma2(q == cc ? make_float2(0.f, 0.f) : xs[q], mf, prow);
+            }
+            ++nk;
+        }
+        if (sing) break;
+#pragma unroll
+        for (int q = 0; q < kGpSub; ++q) row[c0 + q] = xs[q];
+        // the sub-panel's transformation on the other 24 columns, pivot rows from before it
+        for (int j = 0; j < kGtB; ++j) {
+            if (j >= c0 && j < c0 + kGpSub) continue;
+            float2 acc = sub_piv ? make_float2(0.f, 0.f) : row[j];
+#pragma unroll
+            for (int k = 0; k < kGpSub; ++k)
+                if (k < nk) acc = ff::fma2(acc, xs[k], U_s[k][j]);
+            row[j] = acc;
+        }
+        __syncthreads();                                  // U_s is rewritten by the next sub-panel
+    }
+    if (sing) {
+        if (t == 0) st->sing = 1;
+        return;
+    }
+    // the eliminated panel is part of the result; bookkeeping of the pivots
+    if (row_ok) {
+        if (w == kGtB) {
+            float4 *dst = reinterpret_cast<float4 *>(Wk + (size_t)i * ld + jb);
+#pragma unroll
+            for (int q = 0; q < kGtB / 2; ++q)
+                dst[q] = make_float4(row[2 * q].x, row[2 * q].y, row[2 * q + 1].x, row[2 * q + 1].y);
+        } else {
+            for (int j = 0; j < w; ++j) Wk[(size_t)i * ld + jb + j] = row[j];
         }
     }
+    if (t < w) {
+        const int p = ppS[t];
+        pp_g[jb + t] = (short)p;
+        used_g[p] = 1;
+        piv_g[p] = 1;
+    }
+    if (t == 0) {
+        GtState o = *st;
+        o.mag_h = S.mag_h; o.mag_l = S.mag_l; o.mag_e = S.mag_e; o.neg = S.neg;
+        *st = o;
+    }
+    __syncthreads();
+    // operand A: the panel's rows, scaled per row, seven slices, [row tile][slice] planes
+    // (a warp per row, lane = column)
+    for (int r = wid; r < n; r += nwarps) {
+        const float2 xr = P[(size_t)r * kGpRowLd + lane];
+        float mx = fabsf(xr.x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int E = exp_bound(mx);
+        float s7[kGtSl];
+        slice_n<kGtSl>(xr, E, s7);
+        unsigned char *base = Apl + (size_t)(r >> 7) * kGtSl * kGtAPlane + a_off64(r & 127, lane >> 3) +
+                              (lane & 7) * 2;
+#pragma unroll
+        for (int j = 0; j < kGtSl; ++j)
+            *reinterpret_cast<__nv_bfloat16 *>(base + (size_t)j * kGtAPlane) = __float2bfloat16_rn(s7[j]);
+        if (lane == 0) Erow[r] = E;
+    }
+    gt_operand_b(sc, L, n, jb, w, ppS);
 }
 
 static_assert(kGtN == kGtB, "a column tile of the update is exactly one panel");
@@ -800,6 +996,11 @@ cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStrea
     if ((e = cudaFuncSetAttribute(k_gt_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_panel)) !=
         cudaSuccess)
         return e;
+    const int nthr_t = (nmax + 31) / 32 * 32;
+    const size_t sm_t = sizeof(float2) * (size_t)nthr_t * kGpRowLd;
+    if (nmax <= kGpRowMax &&
+        (e = cudaFuncSetAttribute(k_gt_panel_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_t)) != cudaSuccess)
+        return e;
     if ((e = cudaFuncSetAttribute(k_gt_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_up)) !=
         cudaSuccess)
         return e;
@@ -812,7 +1013,9 @@ cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStrea
     const int nz = cmax * n_jobs;
     for (int jb = 0; jb < nmax; jb += kGtB) {
         js.jb = jb;
-        k_gt_panel<<<g1, kGpThreads, sm_panel, st>>>(js);
+        // one thread per row where the rows fit one CTA, else the panel in shared memory
+        if (nmax <= kGpRowMax) k_gt_panel_t<<<g1, nthr_t, sm_t, st>>>(js);
+        else k_gt_panel<<<g1, kGpThreads, sm_panel, st>>>(js);
         for (int z0 = 0; z0 < nz; z0 += 65535) {
             const int zn = nz - z0 < 65535 ? nz - z0 : 65535;
             k_gt_update<<<dim3(nt, 1, zn), kGtUpThreads, sm_up, st>>>(js, z0);
