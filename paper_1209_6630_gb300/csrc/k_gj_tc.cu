@@ -637,7 +637,8 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(const __grid_cons
     unsigned char *As = base;                                    // 7 x 8 KB
     unsigned char *Bs = As + kGtSl * kGtAPlane;                  // 3 x 7 x 2 KB
     unsigned char *Xs = Bs + kGtBs * kGtSl * kGtBPlane;          // 3 x 2 x 16 KB
-    int *Fs = reinterpret_cast<int *>(Xs + kGtXs * kGtXStage);   // [n]
+    int *Fs = reinterpret_cast<int *>(Xs + kGtXs * kGtXStage);   // [nc * 32] column exponents F_j
+    float *Fsc = reinterpret_cast<float *>(Fs + nc * kGtN);      // [nc * 32] 2^F_j where |F_j| <= 60, else 0
     const uint32_t b0 = smem_u32(&bar[0]);
     const uint32_t bA = b0;
     auto BF = [&](int sb) { return b0 + 8u * (uint32_t)(1 + sb); };
@@ -650,7 +651,17 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(const __grid_cons
     auto col_tile = [&](int i) { return i < jp ? i : i + 1; };
 
     const int *Fcol = reinterpret_cast<const int *>(sc + L.f);
-    for (int c = t; c < n; c += kGtUpThreads) Fs[c] = Fcol[c];
+    // a tile whose column exponents all lie in [-60, 60] takes the fast scaling in the epilogue
+    __shared__ int tile_ok[1024 / kGtN];
+    if (t < 1024 / kGtN) tile_ok[t] = 1;
+    __syncthreads();
+    for (int c = t; c < nc * kGtN; c += kGtUpThreads) {
+        const int F = c < n ? Fcol[c] : 0;
+        const bool in = F >= -60 && F <= 60;
+        Fs[c] = F;
+        Fsc[c] = in ? __int_as_float((127 + F) << 23) : 0.f;
+        if (!in) tile_ok[c / kGtN] = 0;
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
                      :: "r"(smem_u32(&tmem_slot)) : "memory");
@@ -758,6 +769,11 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(const __grid_cons
         const int i_row = r0 + (row_ok ? r : 0);
         const int E = row_ok ? reinterpret_cast<const int *>(sc + L.e)[i_row] : 0;
         const bool is_piv = row_ok && (sc + L.piv)[i_row] != 0;
+        // 2^(E + F) as two exact multiplications by 2^E and 2^F when both lie in [-60, 60]: the
+        // order sums are 0 or at least 2^-56 in magnitude (multiples of the smallest unit), so
+        // the product with 2^E is a normal float, and the final rounding equals scale_pow2's
+        const bool E_ok = E >= -60 && E <= 60;
+        const float sE = __int_as_float((127 + (E_ok ? E : 0)) << 23);
         const uint32_t tlane = (uint32_t)(quad * 32) << 16;
         const uint32_t tl = tmem + tlane + (uint32_t)(cg * 8);
         if (warp < 4) {
@@ -824,17 +840,34 @@ __global__ void __launch_bounds__(kGtUpThreads, 1) k_gt_update(const __grid_cons
             }
             if (!gt_wait_warp(XF(sx), (i / kGtXs) & 1, js.wait_ns, &s_abort, lane)) break;
             unsigned char *xs = Xs + sx * kGtXStage + xoff;
-            const int c0 = col_tile(i) * kGtN + cg * 8;
+            const int ct = col_tile(i);
+            const int c0 = ct * kGtN + cg * 8;
+            if (E_ok && tile_ok[ct]) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float4 *p4 = reinterpret_cast<float4 *>(xs + (((ck0 + k) ^ (r & 7)) << 4));
-                const float4 o = *p4;
-                float2 x0 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.x, o.y);
-                float2 x1 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.z, o.w);
-                const int ex0 = E + Fs[min(c0 + 2 * k, n - 1)], ex1 = E + Fs[min(c0 + 2 * k + 1, n - 1)];
-                x0 = ff::add(x0, make_float2(scale_pow2(hs[2 * k], ex0), scale_pow2(ls[2 * k], ex0)));
-                x1 = ff::add(x1, make_float2(scale_pow2(hs[2 * k + 1], ex1), scale_pow2(ls[2 * k + 1], ex1)));
-                *p4 = make_float4(x0.x, x0.y, x1.x, x1.y);
+                for (int k = 0; k < 4; ++k) {
+                    float4 *p4 = reinterpret_cast<float4 *>(xs + (((ck0 + k) ^ (r & 7)) << 4));
+                    const float4 o = *p4;
+                    float2 x0 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.x, o.y);
+                    float2 x1 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.z, o.w);
+                    const float f0 = Fsc[c0 + 2 * k], f1 = Fsc[c0 + 2 * k + 1];
+                    x0 = ff::add(x0, make_float2(__fmul_rn(__fmul_rn(hs[2 * k], sE), f0),
+                                                 __fmul_rn(__fmul_rn(ls[2 * k], sE), f0)));
+                    x1 = ff::add(x1, make_float2(__fmul_rn(__fmul_rn(hs[2 * k + 1], sE), f1),
+                                                 __fmul_rn(__fmul_rn(ls[2 * k + 1], sE), f1)));
+                    *p4 = make_float4(x0.x, x0.y, x1.x, x1.y);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float4 *p4 = reinterpret_cast<float4 *>(xs + (((ck0 + k) ^ (r & 7)) << 4));
+                    const float4 o = *p4;
+                    float2 x0 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.x, o.y);
+                    float2 x1 = is_piv ? make_float2(0.f, 0.f) : make_float2(o.z, o.w);
+                    const int ex0 = E + Fs[c0 + 2 * k], ex1 = E + Fs[c0 + 2 * k + 1];
+                    x0 = ff::add(x0, make_float2(scale_pow2(hs[2 * k], ex0), scale_pow2(ls[2 * k], ex0)));
+                    x1 = ff::add(x1, make_float2(scale_pow2(hs[2 * k + 1], ex1), scale_pow2(ls[2 * k + 1], ex1)));
+                    *p4 = make_float4(x0.x, x0.y, x1.x, x1.y);
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // for the TMA store
             __syncwarp();
@@ -989,7 +1022,7 @@ cudaError_t launch_gj_tc(const GjJob *jobs, int n_jobs, void *scratch, cudaStrea
     // 56 KB of panel slices, 3 x 14 KB of pivot-row slices, 3 x 32 KB of old values, the
     // column exponents: one CTA per SM
     const size_t sm_up = 1024 + kGtSl * (size_t)(kGtAPlane + kGtBs * kGtBPlane) + kGtXs * (size_t)kGtXStage +
-                         4 * (size_t)nmax;
+                         8 * (size_t)((nmax + kGtN - 1) / kGtN * kGtN);
     const size_t sm_fin = sizeof(float2) * 32 * 33 + sizeof(short) * 2 * (size_t)nmax;
     cudaError_t e;
     if ((e = gt_tensor_maps(js)) != cudaSuccess) return e;

@@ -77,3 +77,24 @@ def test_tensor_singular_decided_in_fp64():
     assert st[2] == 1 and st[4] == 2 and (st[[0, 1, 3, 5]] == 0).all()
     lp = o["logpsi"].cpu().numpy()
     assert lp[2] == -np.inf and lp[4] == -np.inf
+
+
+@pytest.mark.parametrize("kind", ["mini_chain", "small_chain"])
+def test_tensor_small_matrices_vs_oracle(kind):
+    """Matrices of one column tile (20 and 19 rows: no update tile besides the panel's own) and
+    of two (49 rows: one update tile, ragged), 130 walkers."""
+    from paper_1209_6630_gb300 import QmcSystem
+    from synth import tiny_system
+    from synth.system import make_system
+    s = tiny_system("mini_chain") if kind == "mini_chain" else make_system(8, 2, 2, 20, seed=3)
+    q = QmcSystem(s, 0)
+    W = 130
+    R = make_walkers(s, W, first=40)
+    ref = Oracle(s).eval(R)
+    q.set_tiles(a4_mode="tensor")
+    g = q.eval(torch.from_numpy(R).to(dev), precision="mixed")
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    np.testing.assert_array_equal(g["status"], ref["status"])
+    np.testing.assert_array_equal(g["sign"], ref["sign"])
+    assert np.abs(g["logpsi"] - ref["logpsi"]).max() < 1e-6
+    assert (np.abs(g["e_loc"] - ref["e_loc"]) / np.abs(ref["e_loc"])).max() < 1e-5
