@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kGpRowMax, 1) k_gt_panel_t(GtJobs js)
 
     extern __shared__ __align__(16) unsigned char gp_smem[];
     float2 *P = reinterpret_cast<float2 *>(gp_smem);     // [blockDim.x][kGpRowLd]
-    __shared__ float2 U_s[kGpSub][kGtB];                  // the sub-panel's pivot rows, before it
+    __shared__ __align__(16) float2 U_s[kGpSub][kGtB];    // the sub-panel's pivot rows, before it
     __shared__ float2 prow_s[kGpSub + 1];                 // the step's pivot row on the sub-panel, scaled; 1 / pivot
     __shared__ short ppS[kGtB];
     __shared__ int red_i[kGpRowMax / 32];
@@ -495,13 +495,20 @@ __global__ void __launch_bounds__(kGpRowMax, 1) k_gt_panel_t(GtJobs js)
 #pragma unroll
         for (int q = 0; q < kGpSub; ++q) row[c0 + q] = xs[q];
         // the sub-panel's transformation on the other 24 columns, pivot rows from before it
-        for (int j = 0; j < kGtB; ++j) {
+        // (two columns per pass: two independent chains, U_s read 16 bytes at a time)
+        for (int j = 0; j < kGtB; j += 2) {
             if (j >= c0 && j < c0 + kGpSub) continue;
-            float2 acc = sub_piv ? make_float2(0.f, 0.f) : row[j];
+            float2 a0 = sub_piv ? make_float2(0.f, 0.f) : row[j];
+            float2 a1 = sub_piv ? make_float2(0.f, 0.f) : row[j + 1];
 #pragma unroll
             for (int k = 0; k < kGpSub; ++k)
-                if (k < nk) acc = ff::fma2(acc, xs[k], U_s[k][j]);
-            row[j] = acc;
+                if (k < nk) {
+                    const float4 u = *reinterpret_cast<const float4 *>(&U_s[k][j]);
+                    a0 = ff::fma2(a0, xs[k], make_float2(u.x, u.y));
+                    a1 = ff::fma2(a1, xs[k], make_float2(u.z, u.w));
+                }
+            row[j] = a0;
+            row[j + 1] = a1;
         }
         __syncthreads();                                  // U_s is rewritten by the next sub-panel
     }
