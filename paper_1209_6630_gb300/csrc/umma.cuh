@@ -54,19 +54,6 @@ __host__ __device__ constexpr uint32_t umma_idesc_f16_major(int M, int N, int bf
 }
 static_assert(umma_idesc_f16_major(128, 96, 1, 0, 1) == umma_idesc_f16(128, 96, 1), "descriptor fields");
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
-                 : "memory");
-}
-
 __device__ __forceinline__ uint64_t globaltimer()
 {
     uint64_t t;
