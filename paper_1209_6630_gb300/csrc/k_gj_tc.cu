@@ -9,10 +9,12 @@
 //
 //   k_gt_init    float-pair copy of X (rows padded to an even length) and ||X||_inf
 //   per panel jb:
-//   k_gt_panel   one CTA per matrix eliminates the n x 32 panel in shared
-//                memory (pivot = the first row with the largest |entry| among
+//   k_gt_panel_t one CTA per matrix eliminates the n x 32 panel in shared
+//   (k_gt_panel) memory (pivot = the first row with the largest |entry| among
 //                the rows not used yet: the pivots of LU with partial
-//                pivoting) and writes the operands of the panel's update in
+//                pivoting) -- one thread per row, in sub-panels of 8 with
+//                rank-8 updates between them, up to 544 rows, else one warp
+//                per row -- and writes the operands of the panel's update in
 //                exact BF16 slices: the panel P [n][32] (row i scaled by
 //                2^-E_i) and the pivot rows U [32][n] as they were before the
 //                update (column j scaled by 2^-F_j), seven slices of 7 bits
@@ -20,8 +22,9 @@
 //   k_gt_update  X[i][j] <- [i is not a pivot row of the panel] X[i][j]
 //                           + sum_c P[i][c] U[c][j]
 //                for every column j outside the panel; one CTA per 128 rows,
-//                warp-specialised (a copy warp moving operands and old values
-//                with bulk copies, an MMA warp, 16 epilogue warps), loops over
+//                warp-specialised (warps moving the old values by tensor TMA
+//                and the operands by bulk copies, an MMA warp, 16 epilogue
+//                warps), loops over
 //                the 32-column tiles and issues, per tile, 2 K16
 //                steps x 28 slice-pair MMAs into seven TMEM
 //                accumulators, one per order d = i + j <= 6 of the pair: each
