@@ -210,7 +210,9 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             ++ncopy;
-            if (!mbar_wait(cb, (ncopy - 1) & 1, kWait)) s_abort = 1;
+            // one warp observes the bulk copy (only the MMA issue reads it); the others wait at
+            // the barrier without spending issue slots the other CTA's epilogue needs
+            if (warp == 0 && !mbar_wait(cb, (ncopy - 1) & 1, kWait)) s_abort = 1;
             __syncthreads();
             if (warp == 0) {                                   // converged: elect.sync per MMA
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kVdThreads, 2) k_vd_mma(VdArgs a)
             ++ncommit;
             // the buffer is rewritten by the next stage: wait for these MMAs (the other CTA
             // on the SM keeps the tensor pipe busy meanwhile)
-            if (!mbar_wait(mb, (ncommit - 1) & 1, kWait)) s_abort = 1;
+            if (warp == 0 && !mbar_wait(mb, (ncommit - 1) & 1, kWait)) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
         }
