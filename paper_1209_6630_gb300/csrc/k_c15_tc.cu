@@ -32,11 +32,12 @@
 //
 // k_c15_mma (one CTA per MO tile of 128, walker tile, electron and output
 // class: C1, C5, or C2..C4 together):
-// per K step, the 6 slice planes of its output (copied with cp.async) and the
-// 6 slice planes of the MO coefficient rows gathered by AO index (MN-major);
-// one thread issues the 21 slice-pair MMAs of each K16 sub-step into the four
-// TMEM accumulators and commits to an mbarrier; waits are bounded by
-// %globaltimer (QMC_STATUS_TIMEOUT on expiry).  Unions longer than 1024 AOs
+// per stage of 32 AOs, the 6 slice planes of its output (one bulk copy) and
+// the 6 slice planes of the MO coefficient rows gathered by AO index
+// (MN-major, cp.async) from copy warps; a converged MMA warp issues the 21
+// slice-pair MMAs of each K16 sub-step into the four TMEM accumulators and
+// commits to mbarriers; waits are bounded by %globaltimer
+// (QMC_STATUS_TIMEOUT on expiry).  Unions longer than 1024 AOs
 // are accumulated in chunks of 1024, each added to the output in FP64.
 #include "ao_ff.cuh"
 #include "qmc_internal.cuh"
