@@ -326,6 +326,88 @@ def config4_forward(a, flush, e0, e1):
                                       "status_mismatch": int((om["status"] != of["status"]).sum().item())}}
 
 
+def config2_precision_report(a, flush, e0, e1):
+    """The 434-electron chain (two 217 x 217 Slater matrices) with 4096 walkers:
+    the contraction's precision modes with the LU / inverse in FP64 (a4_mode
+    fp64), each result's error against the plain FP64 GPU path over every walker
+    (that path meets the oracle at 1e-10), the Slater entries against the FP64
+    oracle on sampled walkers, and the time per step.  Modes: C1/C5 from exact
+    BF16 slices on the tensor cores with C2..C4 split FP16x3 (mixed) or BF16x3
+    (mixed_bf16); C1/C5 in float-float on the FP32 pipes with C2..C4 FP16x3;
+    and the default mixed step (C-free variant, its a4)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1209_6630_gb300 import QmcSystem
+    from synth import config_system, make_walkers
+    s = config_system("434e")
+    q = QmcSystem(s, 0)
+    W = 4096
+    Rn = make_walkers(s, W, first=21000)
+    R = torch.from_numpy(Rn).cuda()
+    defaults = q.tiles()
+
+    def timed(prec, reps):
+        ws = q.workspace(W, prec)
+        out = q.alloc_out(W)
+        q.eval(R, precision=prec, out=out, ws=ws)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0.record()
+            q.eval(R, precision=prec, out=out, ws=ws)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts), out
+
+    t_f, of = timed("f64", 1)
+    sample = [0, 1, 2047, 4095]
+    dbg = [oracle.Oracle(s).eval_debug(Rn[w]) for w in sample]
+
+    def rowwise(a_, b_):
+        den = np.abs(b_).max(axis=-1, keepdims=True)
+        return float((np.abs(a_ - b_) / np.where(den == 0, 1.0, den)).max())
+
+    modes = {}
+    for label, prec, tiles in (("c1c5_exact_slices_c2c4_fp16x3", "mixed", dict(c15_mode="tensor", a4_mode="fp64")),
+                               ("c1c5_exact_slices_c2c4_bf16x3", "mixed_bf16", dict(c15_mode="tensor", a4_mode="fp64")),
+                               ("c1c5_float_float_c2c4_fp16x3", "mixed", dict(c15_mode="float_float", a4_mode="fp64")),
+                               ("default_mixed_step", "mixed", {})):
+        q.set_tiles(**{**{k: defaults[k] for k in ("c15_mode", "a4_mode")}, **tiles})
+        t_m, om = timed(prec, 2)
+        ok = (om["status"] == 0) & (of["status"] == 0)
+        dlp = (om["logpsi"] - of["logpsi"]).abs()[ok]
+        del_ = ((om["e_loc"] - of["e_loc"]).abs() / of["e_loc"].abs())[ok]
+        ddr = ((om["drift"] - of["drift"]).abs().amax(dim=(1, 2)) / of["drift"].abs().amax(dim=(1, 2)))[ok]
+        rec = {"precision": prec, "tiles": tiles or "library defaults",
+               "walker_steps_per_s": W / (t_m / 1e3), "ms_per_step": t_m,
+               "vs_fp64_path": {"walkers": int(ok.sum().item()), "max_abs_logpsi_err": float(dlp.max().item()),
+                                "p99_abs_logpsi_err": float(torch.quantile(dlp, 0.99).item()),
+                                "max_rel_eloc_err": float(del_.max().item()),
+                                "max_drift_normwise_err": float(ddr.max().item()),
+                                "status_mismatch": int((om["status"] != of["status"]).sum().item())}}
+        if tiles:
+            up, dn = q.slater(R[sample], precision=prec)
+            up, dn = up.cpu().numpy(), dn.cpu().numpy()
+            err = {"C1": 0.0, "C2..C4": 0.0, "C5": 0.0}
+            for k, d in enumerate(dbg):
+                for got, ref in ((up[k], d["C_up"]), (dn[k], d["C_dn"])):
+                    err["C1"] = max(err["C1"], rowwise(got[0], ref[0]))
+                    err["C5"] = max(err["C5"], rowwise(got[4], ref[4]))
+                    err["C2..C4"] = max(err["C2..C4"], max(rowwise(got[l], ref[l]) for l in range(1, 4)))
+            rec["slater_vs_oracle_rowwise"] = {"walkers": len(sample), **err}
+        modes[label] = rec
+    q.set_tiles(c15_mode=defaults["c15_mode"], a4_mode=defaults["a4_mode"])
+    q.close()
+    return {"workload": "434e synthetic chain (217+217 e, 1260 AOs), 4096 walkers; LU/inverse in FP64 (a4_mode fp64) "
+                        "for the contraction modes",
+            "fp64_path": {"walker_steps_per_s": W / (t_f / 1e3), "ms_per_step": t_f},
+            "modes": modes,
+            "not_built": "TF32x1 / TF32x3 contraction modes (the exact BF16 slices reach FP64-class entries instead)"}
+
+
 def cfree_bench(q, R, prec, flush, e0, e1, mode):
     """The other C1..C5 arithmetic on the same batch (c15_mode tensor: C1..C5 on
     the tensor cores; cfree: C1 alone, then the drift and Laplacian from
@@ -839,6 +921,8 @@ def main():
         del wsbuf, out
         torch.cuda.empty_cache()
         line["config4_forward"] = config4_forward(a, flush, e0, e1)
+        torch.cuda.empty_cache()
+        line["config2_precision_report"] = config2_precision_report(a, flush, e0, e1)
         torch.cuda.empty_cache()
         r5 = mixed_batch_run(1024, local, rank, prec, False, 3, 3, not a.no_cpu)
         line["config5_mixed_batch"] = {
