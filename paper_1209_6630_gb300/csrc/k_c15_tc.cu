@@ -619,11 +619,14 @@ bool c15tc_fits(const SysDev &s, int mw)
 }
 
 // Electrons per producer / MMA launch pair: enough CTAs per launch for large
-// batches of walkers, a small staging buffer for small ones.
+// batches of walkers (fewer launches, so fewer partly filled last waves), a
+// small staging buffer for small ones; spread evenly over the launches.
 size_t c15tc_batch(int n_elec, int n_tiles)
 {
-    const int b = n_tiles >= 8 ? 64 : (n_tiles >= 2 ? 32 : 16);
-    return (size_t)(n_elec < b ? (n_elec > 0 ? n_elec : 1) : b);
+    const int b = n_tiles >= 8 ? 128 : (n_tiles >= 2 ? 32 : 16);
+    if (n_elec <= b) return (size_t)(n_elec > 0 ? n_elec : 1);
+    const int nl = (n_elec + b - 1) / b;                   // launches, then the electrons spread evenly
+    return (size_t)((n_elec + nl - 1) / nl);
 }
 
 size_t c15tc_bytes(const SysDev &s, int nw)

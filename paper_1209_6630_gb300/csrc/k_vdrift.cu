@@ -343,8 +343,15 @@ bool vdrift_fits(const SysDev &s)
     return sm <= 227 * 1024;
 }
 
-// electrons per launch (the A staging holds one image per CTA of a batch)
-int vdrift_batch(const SysDev &s) { return s.n_elec < 64 ? s.n_elec : 64; }
+// electrons per launch (the A staging holds one image per CTA of a batch): up to 264, spread
+// evenly over the launches (fewer launches, so fewer partly filled last waves)
+int vdrift_batch(const SysDev &s)
+{
+    constexpr int kMax = 264;
+    if (s.n_elec <= kMax) return s.n_elec;
+    const int nl = (s.n_elec + kMax - 1) / kMax;
+    return (s.n_elec + nl - 1) / nl;
+}
 
 size_t vdrift_stage_per(const SysDev &s)
 {

@@ -30,16 +30,24 @@ def _tiles(**kw):
 
 
 def test_launches_tensor_a4_1056e():
-    # masks 1, C1..C5 17 x (producer + MMA), a4 init 1 + 17 x (panel + update) + final 1,
-    # FP64 recomputation: list 1, C1 rows 1, 33 x (panel + update), final 1, FP64 pass 1; energy 1
+    # masks 1, C1..C5 9 x (producer + MMA) (batches of 118 electrons), a4 init 1 + 17 x (panel +
+    # update) + final 1, FP64 recomputation: list 1, C1 rows 1, 33 x (panel + update), final 1,
+    # FP64 pass 1; energy 1
     q = _Sys(528, 528, _tiles())
-    assert bench.launches_per_step(q, "mixed", 2048) == 1 + 34 + 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
+    assert bench.launches_per_step(q, "mixed", 2048) == 1 + 18 + 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
+
+
+def test_launches_cfree_1056e():
+    # the C-free default: C1 alone in 9 x (producer + MMA), then the D^-1 row exponents 1 and
+    # v / drift / Laplacian in 4 launches of 264 electrons; a4 and the rest as above
+    q = _Sys(528, 528, _tiles(c15_mode="cfree"))
+    assert bench.launches_per_step(q, "mixed", 2048) == 1 + 18 + 1 + 4 + 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
 
 
 def test_launches_float_float_a4_1056e():
     # as above with one float-float Gauss-Jordan launch in place of the 36 tensor-core a4 launches
     q = _Sys(528, 528, _tiles(a4_mode="float_float"))
-    assert bench.launches_per_step(q, "mixed", 2048) == 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
+    assert bench.launches_per_step(q, "mixed", 2048) == 1 + 18 + 1 + 1 + 1 + 66 + 1 + 1 + 1
 
 
 def test_launches_fp64_path():
