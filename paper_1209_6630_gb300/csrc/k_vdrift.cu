@@ -343,11 +343,13 @@ bool vdrift_fits(const SysDev &s)
     return sm <= 227 * 1024;
 }
 
-// electrons per launch (the A staging holds one image per CTA of a batch): up to 264, spread
-// evenly over the launches (fewer launches, so fewer partly filled last waves)
-int vdrift_batch(const SysDev &s)
+// electrons per launch (the A staging holds one image per CTA of a batch): up to 264 from 8
+// walker tiles on (fewer launches, so fewer partly filled last waves), else up to 64 (a small
+// staging buffer for small batches of walkers); spread evenly over the launches.  Never
+// smaller for more tiles, so the staging carved for a walker chunk holds a shorter one's.
+int vdrift_batch(const SysDev &s, int tiles)
 {
-    constexpr int kMax = 264;
+    const int kMax = tiles >= 8 ? 264 : 64;
     if (s.n_elec <= kMax) return s.n_elec;
     const int nl = (s.n_elec + kMax - 1) / kMax;
     return (s.n_elec + nl - 1) / nl;
@@ -364,7 +366,7 @@ size_t vdrift_bytes(const SysDev &s, int nw)
 {
     const size_t tiles = (size_t)(nw + TC_M - 1) / TC_M;
     return ((sizeof(int) * (size_t)nw * s.n_elec + 255) / 256) * 256 +
-           tiles * (size_t)vdrift_batch(s) * vdrift_stage_per(s);
+           tiles * (size_t)vdrift_batch(s, (int)tiles) * vdrift_stage_per(s);
 }
 
 cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables &mt, int nw, const double *R,
@@ -395,7 +397,7 @@ cudaError_t launch_vdrift(const SysDev &s, const FfBasis &fb, const MixedTables 
     cudaError_t e = cudaFuncSetAttribute(k_vd_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int tiles = (nw + TC_M - 1) / TC_M;
-    const int nb = vdrift_batch(s);
+    const int nb = vdrift_batch(s, tiles);
     for (int e0 = 0; e0 < s.n_elec; e0 += nb) {
         a.e0 = e0;
         const int ne = s.n_elec - e0 < nb ? s.n_elec - e0 : nb;
