@@ -42,9 +42,9 @@ def launches_per_step(q, prec, n_walk):
         b = 128 if n_walk > 7 * 128 else (32 if n_walk > 128 else 16)
         n += 2 * -(-q.N // b)          # slice producer + MMA kernel per batch of electrons (C1..C5, or C1)
         if t["c15_mode"] == "cfree":
-            bv = 264 if n_walk > 7 * 128 else 64
+            bv = 264 if n_walk > 128 else 64
             n += 1 + -(-q.N // bv)    # row exponents of D^-1; v = D^-1 A^T with the drift / Laplacian per
-                                      # batch of up to 264 electrons (up to 64 below 8 walker tiles)
+                                      # batch of up to 264 electrons (up to 64 for one walker tile)
     else:
         n += 2                        # float-float C1/C5, tensor-core C2..C4
     nmax = max(q.n_up, q.n_dn)

@@ -343,13 +343,13 @@ bool vdrift_fits(const SysDev &s)
     return sm <= 227 * 1024;
 }
 
-// electrons per launch (the A staging holds one image per CTA of a batch): up to 264 from 8
-// walker tiles on (fewer launches, so fewer partly filled last waves), else up to 64 (a small
-// staging buffer for small batches of walkers); spread evenly over the launches.  Never
-// smaller for more tiles, so the staging carved for a walker chunk holds a shorter one's.
+// electrons per launch (the A staging holds one image per CTA of a batch): up to 264 from 2
+// walker tiles on (fewer launches, so fewer partly filled last waves), else up to 64 (one
+// walker's scratch stays small); spread evenly over the launches.  Never smaller for more
+// tiles, so the staging carved for a walker chunk holds a shorter one's.
 int vdrift_batch(const SysDev &s, int tiles)
 {
-    const int kMax = tiles >= 8 ? 264 : 64;
+    const int kMax = tiles >= 2 ? 264 : 64;
     if (s.n_elec <= kMax) return s.n_elec;
     const int nl = (s.n_elec + kMax - 1) / kMax;
     return (s.n_elec + nl - 1) / nl;

@@ -44,10 +44,12 @@ def test_launches_cfree_1056e():
     assert bench.launches_per_step(q, "mixed", 2048) == 1 + 18 + 1 + 4 + 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
 
 
-def test_launches_cfree_1056e_below_8_tiles():
-    # 512 walkers (4 tiles): C1 in 33 batches of 32 electrons, v in 17 batches of up to 64
+def test_launches_cfree_1056e_fewer_tiles():
+    # 512 walkers (4 tiles): C1 in 33 batches of 32 electrons, v in 4 batches of up to 264;
+    # 128 walkers (one tile): C1 in 66 batches of 16, v in 17 batches of up to 64
     q = _Sys(528, 528, _tiles(c15_mode="cfree"))
-    assert bench.launches_per_step(q, "mixed", 512) == 1 + 66 + 1 + 17 + 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
+    assert bench.launches_per_step(q, "mixed", 512) == 1 + 66 + 1 + 4 + 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
+    assert bench.launches_per_step(q, "mixed", 128) == 1 + 132 + 1 + 17 + 1 + 34 + 1 + 1 + 1 + 66 + 1 + 1 + 1
 
 
 def test_launches_float_float_a4_1056e():
