@@ -11,11 +11,12 @@
 // k_vd_rowexp: the exponent bound E of every D^-1 row (|D^-1[e,k]| < 2^E).
 // k_vd_mma (one CTA per walker tile of 128 and electron e): the union of the
 // tile's active AOs for e (from the shell masks), then per AO tile of 64: v
-// on the tcgen05 tensor cores as M = 128 walkers x N = 128 AOs x K = N_s MOs
+// on the tcgen05 tensor cores as M = 128 walkers x N = 64 AOs x K = N_s MOs
 // from exact BF16 slices, the split of the C1 products (k_c15_tc.cu) with
 // the roles of the indices exchanged: D^-1 rows scaled by 2^-E_{w,e} (sliced
-// in the kernel from the FP64 inverse), A rows scaled by 2^-G_mu (sliced at
-// load), six slices each, the 21 slice pairs of order <= 5 into four FP32
+// from the FP64 inverse once per CTA into a staging image in global memory
+// that every AO tile copies), A rows scaled by 2^-G_mu (sliced at load), six
+// slices each, the 21 slice pairs of order <= 5 into four FP32
 // accumulators (orders 0, 1, 2 exact; 3..5 together); K stages of 32 MOs
 // through one stage buffer per CTA, two CTAs per SM (the staged D^-1 slices
 // by one bulk copy, the B rows by cp.async), a converged warp issuing the MMAs
